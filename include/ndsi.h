@@ -1,0 +1,183 @@
+/*
+ * ndsi.h - nested-dissection selected inversion for contour-integrated density matrices.
+ *
+ * C ABI of the GB300 (sm_103a) library libndsi.so.  Problem statement (Sec. II.A-II.B of
+ * Ozaki, "Numerically exact O(N^{7/3}) method for large-scale electronic structure
+ * calculations"): given real symmetric H and S on one sparse pattern (Eq. 2 and the remark
+ * that both share the same sparse structure), a chemical potential mu and temperature kT,
+ * return the density matrix rho on that pattern (Eq. 8) and the electron count Tr(rho S)
+ * (Eq. 40), through the Green function G(Z) = (Z S - H)^{-1} (Eq. 6) evaluated at the poles
+ * alpha_p = mu + i z_p / beta of the continued fraction of the Fermi function (Eq. 7).
+ *
+ * Conventions
+ *  - Every function returns an int status (NDSI_OK = 0); the message of the last failure on
+ *    the calling thread is available from ndsi_last_error().  No C++ exception crosses the ABI.
+ *  - Complex numbers are passed as interleaved (re, im) pairs of double.
+ *  - Arrays "on the pattern" are indexed like the CSR arrays of ndsi_pattern (original basis
+ *    order, row-major CSR order).
+ *  - Pointers documented as "device or host" are classified with cudaPointerGetAttributes:
+ *    host memory is staged through the library's device buffers on the given stream.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).  Calls are
+ *    stream-ordered; results written to device memory are valid after the stream reaches them.
+ *  - The caller owns every input and output buffer.  The library owns plan and factor
+ *    handles (and the device workspace behind them) and frees them in *_destroy.
+ *  - All work runs on the current CUDA device.  A plan may be used by one stream at a time.
+ */
+#ifndef NDSI_H
+#define NDSI_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Status codes. */
+#define NDSI_OK               0
+#define NDSI_ERR_INVALID      1   /* bad pattern, sizes, options or pointer */
+#define NDSI_ERR_SINGULAR     2   /* a diagonal pivot block was singular or non-finite */
+#define NDSI_ERR_OOM          3   /* device or host allocation failed, or over the workspace cap */
+#define NDSI_ERR_CUDA         4   /* a CUDA runtime call failed */
+#define NDSI_ERR_TIMEOUT      5   /* a bounded device wait gave up */
+#define NDSI_ERR_UNSUPPORTED  6   /* feature not available on this device or build */
+
+/* Arithmetic of the dense contractions (separator Schur updates and selected-inverse
+ * products).  Diagonal pivot blocks, their inverses and the residue sum are FP64 in both. */
+#define NDSI_PREC_FP64   0   /* FP64 operands and accumulation on the CUDA cores */
+#define NDSI_PREC_SPLIT  1   /* FP64 emulated by BF16 slices on the tcgen05 tensor cores */
+
+typedef struct ndsi_plan ndsi_plan;
+typedef struct ndsi_factors ndsi_factors;
+
+/* Symmetric sparsity pattern of H and S (CSR, original basis order).  Every row must hold its
+ * diagonal, column indices must be strictly increasing within a row, and (i,j) present implies
+ * (j,i) present.  Host pointers; read only during ndsi_analyze. */
+typedef struct {
+    int64_t n;              /* number of basis functions */
+    const int64_t* rowptr;  /* [n+1], rowptr[0] = 0, rowptr[n] = nnz */
+    const int32_t* col;     /* [nnz] */
+} ndsi_pattern;
+
+typedef struct {
+    int32_t leaf_atoms;          /* innermost-domain threshold of the dissection (default 20) */
+    int32_t precision;           /* NDSI_PREC_FP64 or NDSI_PREC_SPLIT (default FP64) */
+    int32_t split_slices;        /* BF16 slices per operand in split mode (default 6) */
+    int32_t block;               /* FP64 pivot block size, 16/32/64 (0 = default 32) */
+    double m0_radius;            /* R of the zeroth-moment point Z = iR (default 1e7) */
+    int64_t max_workspace_bytes; /* device workspace cap; poles are chunked to fit (0 = auto) */
+} ndsi_options;
+
+/* Summary of a plan, filled by ndsi_plan_info. */
+typedef struct {
+    int64_t n;                 /* basis functions */
+    int64_t nnz;               /* pattern entries */
+    int32_t n_atoms;
+    int32_t n_nodes;           /* supernodes of the dissection tree (innermost domains + separators) */
+    int32_t n_levels;          /* tree levels (0 = innermost domains) */
+    int32_t max_front;         /* largest dense front |J| + |struct(J)| */
+    int64_t front_elems;       /* sum of front sizes squared (complex elements per pole) */
+    double flops_per_pole;     /* algorithmic real FP64 flops of factor + selected inversion */
+    double bytes_per_pole;     /* algorithmic front bytes written + read per pole */
+} ndsi_plan_summary;
+
+/* Items for ndsi_plan_export. */
+#define NDSI_EXPORT_PERM_ATOMS   1  /* int32[n_atoms]: structured position -> atom id */
+#define NDSI_EXPORT_PERM_BASIS   2  /* int32[n]: structured position -> basis index */
+#define NDSI_EXPORT_NODE_ATOMS   3  /* int32[n_nodes+1]: first structured atom position per node */
+#define NDSI_EXPORT_PARENT       4  /* int32[n_nodes]: parent node (-1 = root), nodes in postorder */
+#define NDSI_EXPORT_STRUCT_PTR   5  /* int64[n_nodes+1]: offsets into NDSI_EXPORT_STRUCT_ATOMS */
+#define NDSI_EXPORT_STRUCT_ATOMS 6  /* int32[...]: struct(J) as atom ids, by structured position */
+#define NDSI_EXPORT_LEVEL        7  /* int32[n_nodes]: tree level of each node */
+
+/* Fill *opt with the defaults listed above. */
+void ndsi_default_options(ndsi_options* opt);
+
+/* Poles z_p (ascending, z_1 ~ pi) and residues R_p (< 0) of the Fermi continued fraction of
+ * Eq. 7 truncated after the denominator 4M-1, so that
+ *   1/(1+e^x) ~= 1/2 + sum_{p=1..M} R_p/(x - i z_p) + R_p/(x + i z_p).
+ * Host arrays z_out[M], R_out[M].  Pure host computation (symmetric tridiagonal eigenproblem
+ * of order 2M).  Errors: NDSI_ERR_INVALID if M < 1 or a pointer is NULL. */
+int ndsi_poles(int32_t M, double* z_out, double* R_out);
+
+/* Structure analysis (Sec. II.C.1, once per geometry): geometric nested dissection of the
+ * atoms along the three axes (steps i-v), the binary separator tree, the supernodal
+ * structure struct(J) of every node, and every index table the numeric phase needs
+ * (the "table function" of Sec. II.C.2).  Integer only; runs on the host.
+ *   pat            - pattern of H and S (host).
+ *   n_atoms        - number of atoms.
+ *   centers        - host double[n_atoms*3], Cartesian centre of each atom.
+ *   atom_of_basis  - host int32[n], atom owning each basis function.
+ *   opt            - options (NULL = defaults).
+ *   plan_out       - receives the plan; free with ndsi_plan_destroy.
+ * Errors: NDSI_ERR_INVALID for a malformed pattern, NDSI_ERR_OOM. */
+int ndsi_analyze(const ndsi_pattern* pat, int32_t n_atoms, const double* centers,
+                 const int32_t* atom_of_basis, const ndsi_options* opt, ndsi_plan** plan_out);
+
+int ndsi_plan_info(const ndsi_plan* plan, ndsi_plan_summary* out);
+
+/* Copy one structure table of the plan (see NDSI_EXPORT_*) into host memory `out`, which must
+ * hold the documented number of elements.  Errors: NDSI_ERR_INVALID for an unknown item. */
+int ndsi_plan_export(const ndsi_plan* plan, int32_t what, void* out);
+
+/* Factor X_p = z_p S - H for every p in nested-dissection order as a supernodal block LDL^T
+ * (Eqs. 18-21 applied recursively; the Schur complements of Eq. 32 and the recurrence of
+ * Eqs. 28-31 appear as dense front updates), no pivoting across supernodes.
+ *   H, S     - values on the pattern, double[nnz], device or host.
+ *   z        - n_poles complex points, interleaved double[2*n_poles], host.
+ *   n_poles  - >= 1.  Im z_p != 0 keeps every leading block nonsingular for S SPD.
+ *   f_out    - receives the factors (device fronts of all poles); free with ndsi_factors_destroy.
+ * The factors hold all poles at once; NDSI_ERR_OOM if they do not fit.  Singular pivot blocks
+ * are reported by ndsi_selinv (the check needs a stream synchronisation). */
+int ndsi_factor_poles(ndsi_plan* plan, const double* H, const double* S, const double* z,
+                      int32_t n_poles, ndsi_factors** f_out, void* stream);
+
+/* Selected inversion (Eqs. 38-39, Takahashi/Erisman-Tinney form) of factors from
+ * ndsi_factor_poles: G_ij(z_p) for every (i,j) of the pattern.
+ *   G_out - device or host, interleaved complex double[2 * n_poles * nnz], pole-major
+ *           (G_out[2*(p*nnz + k)] is Re G(z_p) at pattern entry k); NULL skips the gather.
+ * Synchronises `stream`.  Errors: NDSI_ERR_SINGULAR (pivot check), NDSI_ERR_CUDA. */
+int ndsi_selinv(ndsi_factors* f, double* G_out, void* stream);
+
+/* Density matrix by the contour sum of Eq. 8 with M = n_poles pole pairs:
+ *   rho = M0 + sum_p w_p Re G(alpha_p),  alpha_p = mu + i z_p/beta,  w_p = -4 R_p/beta,
+ * with M0 = Re(iR G(iR)) (the zeroth moment, R = opt.m0_radius), and
+ *   n_elec = Tr(rho S) = sum_k rho_k S_k.
+ *   H, S       - values on the pattern, double[nnz], device or host.
+ *   rho_out    - double[nnz], device or host.
+ *   n_elec_out - one double, device or host (may be NULL).
+ * Runs factor, selected inversion and the residue sum for all poles (chunked to the
+ * workspace cap) and synchronises `stream`.  Errors: NDSI_ERR_INVALID (kT <= 0, n_poles < 1),
+ * NDSI_ERR_SINGULAR, NDSI_ERR_OOM, NDSI_ERR_CUDA. */
+int ndsi_density(ndsi_plan* plan, const double* H, const double* S, double mu, double kT,
+                 int32_t n_poles, double* rho_out, double* n_elec_out, void* stream);
+
+/* Per-kernel timing.  While enabled, every launch made for this plan by ndsi_factor_poles,
+ * ndsi_selinv and ndsi_density is bracketed by CUDA events on its stream; durations, launch
+ * counts and the algorithmic flops and bytes of the launches accumulate per kernel family.
+ * ndsi_profile_enable(plan, 1) also clears the counters; 0 stops recording. */
+typedef struct {
+    char name[32];      /* kernel family: gemm_f64, diaginv, assemble, scatter, copy, gather,
+                           accumulate, reduce */
+    int64_t launches;   /* launches recorded */
+    double ms;          /* summed event-timed durations of those launches */
+    double flops;       /* summed algorithmic real flops (complex MAC = 8 flops) */
+    double bytes;       /* summed algorithmic global-memory bytes (reads + writes) */
+} ndsi_profile_entry;
+
+int ndsi_profile_enable(ndsi_plan* plan, int32_t enable);
+
+/* Copy up to max_entries families into `out` (host) and their number into *n_out.
+ * Errors: NDSI_ERR_INVALID for NULL arguments. */
+int ndsi_profile_read(const ndsi_plan* plan, ndsi_profile_entry* out, int32_t max_entries,
+                      int32_t* n_out);
+
+void ndsi_plan_destroy(ndsi_plan* plan);
+void ndsi_factors_destroy(ndsi_factors* f);
+
+/* Message of the last failing call on this thread ("" if none).  Valid until the next call. */
+const char* ndsi_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* NDSI_H */

@@ -1,0 +1,10 @@
+"""Nested-dissection selected inversion of contour-integrated density matrices on GB300.
+
+The compute path lives in libndsi.so (C ABI, include/ndsi.h); this package holds its build script
+(`build`) and the ctypes binding (`ndsi`).
+"""
+from .ndsi import (  # noqa: F401
+    NdsiError, load, ndsi_default_options, ndsi_poles, ndsi_analyze, ndsi_plan_info,
+    ndsi_plan_export, ndsi_factor_poles, ndsi_selinv, ndsi_density, analyze_system,
+    NDSI_PREC_FP64, NDSI_PREC_SPLIT, EXPORTED_SYMBOLS, ndsi_profile_enable, ndsi_profile_read,
+)

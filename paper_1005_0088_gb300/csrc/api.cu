@@ -1,0 +1,578 @@
+// C-ABI entry points: plan life cycle, pole-batched factor / selected inversion / density.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <memory>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "kernels.cuh"
+#include "ndsi.h"
+#include "plan.hpp"
+
+namespace ndsi {
+// Event-timed launch records, resolved after the stream synchronises.
+constexpr int kFamilies = 8;
+static const char* const kFamilyName[kFamilies] = {"gemm_f64", "diaginv", "assemble", "scatter",
+                                                   "copy", "gather", "accumulate", "reduce"};
+struct ProfRec {
+    int family;
+    double flops, bytes;
+    cudaEvent_t e0, e1;
+};
+struct Profiler {
+    bool on = false;
+    std::vector<cudaEvent_t> pool;
+    size_t used = 0;
+    std::vector<ProfRec> pending;
+    double ms[kFamilies] = {}, flops[kFamilies] = {}, bytes[kFamilies] = {};
+    int64_t launches[kFamilies] = {};
+};
+}  // namespace ndsi
+
+struct ndsi_plan {
+    ndsi::Plan P;
+    ndsi::Profiler prof;
+    ndsi::DevTables T;
+    int device = -1;
+    // density workspace (reused across calls)
+    ndsi::Workspace W;
+    double2* cw = nullptr;       // per-chunk points and weights
+    double2* zw = nullptr;
+    int32_t cw_cap = 0;
+    double* partials = nullptr;  // trace reduction scratch
+    double* stage = nullptr;     // staging for host H, S, rho, n_elec
+    int64_t stage_cap = 0;
+    std::vector<double> pole_z, pole_R;  // cached continued-fraction poles
+    int32_t pole_M = 0;
+};
+
+struct ndsi_factors {
+    ndsi_plan* plan = nullptr;
+    ndsi::Workspace W;
+    double2* zd = nullptr;
+    int32_t np = 0;
+};
+
+namespace ndsi {
+
+namespace {
+thread_local std::string g_last_error;
+}
+
+void set_last_error(const std::string& msg) { g_last_error = msg; }
+
+namespace {
+
+int fail(int code, const std::string& msg) {
+    set_last_error(msg);
+    return code;
+}
+
+#define NDSI_CK(call)                                                                          \
+    do {                                                                                       \
+        cudaError_t e_ = (call);                                                               \
+        if (e_ != cudaSuccess) {                                                               \
+            return fail(e_ == cudaErrorMemoryAllocation ? NDSI_ERR_OOM : NDSI_ERR_CUDA,        \
+                        std::string(#call) + ": " + cudaGetErrorString(e_));                   \
+        }                                                                                      \
+    } while (0)
+
+template <class T>
+size_t bytes_of(const std::vector<T>& v) {
+    return v.size() * sizeof(T);
+}
+
+size_t align256(size_t x) { return (x + 255) & ~static_cast<size_t>(255); }
+
+// Upload every index table of the plan into one device allocation (first use only).
+int upload_tables(ndsi_plan* h) {
+    if (h->T.blob) return NDSI_OK;
+    Plan& P = h->P;
+    NDSI_CK(cudaGetDevice(&h->device));
+    struct Part {
+        const void* src;
+        size_t bytes;
+        void** dst;
+    };
+    DevTables& T = h->T;
+    std::vector<Part> parts = {
+        {P.nodes.data(), bytes_of(P.nodes), reinterpret_cast<void**>(&T.nodes)},
+        {P.asm_map.data(), bytes_of(P.asm_map), reinterpret_cast<void**>(&T.asm_map)},
+        {P.out_map.data(), bytes_of(P.out_map), reinterpret_cast<void**>(&T.out_map)},
+        {P.inv_map.data(), bytes_of(P.inv_map), reinterpret_cast<void**>(&T.inv_map)},
+        {P.rel_map.data(), bytes_of(P.rel_map), reinterpret_cast<void**>(&T.rel_map)},
+        {P.scatter_idx.data(), bytes_of(P.scatter_idx), reinterpret_cast<void**>(&T.scatter_idx)},
+        {P.gemm_items.data(), bytes_of(P.gemm_items), reinterpret_cast<void**>(&T.gemm_items)},
+        {P.gemm_tiles.data(), bytes_of(P.gemm_tiles), reinterpret_cast<void**>(&T.gemm_tiles)},
+        {P.copy_items.data(), bytes_of(P.copy_items), reinterpret_cast<void**>(&T.copy_items)},
+        {P.diag_items.data(), bytes_of(P.diag_items), reinterpret_cast<void**>(&T.diag_items)},
+        {P.node_tiles.data(), bytes_of(P.node_tiles), reinterpret_cast<void**>(&T.node_tiles)},
+        {nullptr, sizeof(int) * 4, reinterpret_cast<void**>(&T.status)},
+    };
+    size_t total = 0;
+    for (const Part& p : parts) total += align256(std::max<size_t>(p.bytes, 16));
+    void* blob = nullptr;
+    NDSI_CK(cudaMalloc(&blob, total));
+    T.blob = blob;
+    size_t off = 0;
+    for (const Part& p : parts) {
+        char* dst = static_cast<char*>(blob) + off;
+        *p.dst = dst;
+        if (p.src && p.bytes) NDSI_CK(cudaMemcpy(dst, p.src, p.bytes, cudaMemcpyHostToDevice));
+        off += align256(std::max<size_t>(p.bytes, 16));
+    }
+    NDSI_CK(cudaMemset(T.status, 0, sizeof(int) * 4));
+    NDSI_CK(kernels_init());
+    return NDSI_OK;
+}
+
+bool is_device_ptr(const void* p) {
+    if (!p) return false;
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+int alloc_workspace(Workspace& W, const Plan& P, int32_t np) {
+    if (W.np_cap >= np && W.fronts) return NDSI_OK;
+    if (W.fronts) cudaFree(W.fronts);
+    if (W.scr) cudaFree(W.scr);
+    W = Workspace{};
+    W.front_stride = P.front_total;
+    W.scr_stride = P.scr_total;
+    NDSI_CK(cudaMalloc(&W.fronts, sizeof(double2) * static_cast<size_t>(W.front_stride) * np));
+    NDSI_CK(cudaMalloc(&W.scr, sizeof(double2) * static_cast<size_t>(W.scr_stride) * np));
+    W.np_cap = np;
+    return NDSI_OK;
+}
+
+void free_workspace(Workspace& W) {
+    if (W.fronts) cudaFree(W.fronts);
+    if (W.scr) cudaFree(W.scr);
+    W = Workspace{};
+}
+
+int family_of(int kind) {
+    switch (kind) {
+        case L_GEMM: return 0;
+        case L_DIAGINV: return 1;
+        case L_ASSEMBLE: return 2;
+        case L_SCATTER: return 3;
+        case L_COPY: return 4;
+        case L_GATHER: return 5;
+        default: return 4;
+    }
+}
+
+cudaEvent_t prof_event(Profiler& pf) {
+    if (pf.used == pf.pool.size()) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        pf.pool.push_back(e);
+    }
+    return pf.pool[pf.used++];
+}
+
+// Bracket a launch with events when profiling; `fn` performs the launch.
+template <class Fn>
+cudaError_t timed(Profiler& pf, int family, double flops, double bytes, cudaStream_t st, Fn fn) {
+    if (!pf.on) return fn();
+    cudaEvent_t e0 = prof_event(pf), e1 = prof_event(pf);
+    if (e0) cudaEventRecord(e0, st);
+    cudaError_t e = fn();
+    if (e1) cudaEventRecord(e1, st);
+    if (e0 && e1) pf.pending.push_back(ProfRec{family, flops, bytes, e0, e1});
+    return e;
+}
+
+// Fold finished records into the per-family totals (the stream has been synchronised).
+void prof_resolve(Profiler& pf) {
+    for (const ProfRec& r : pf.pending) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, r.e0, r.e1) == cudaSuccess) {
+            pf.ms[r.family] += ms;
+            pf.flops[r.family] += r.flops;
+            pf.bytes[r.family] += r.bytes;
+            pf.launches[r.family] += 1;
+        } else {
+            cudaGetLastError();
+        }
+    }
+    pf.pending.clear();
+    pf.used = 0;
+}
+
+int run_phase(ndsi_plan* h, const Workspace& W, int phase, const double* H, const double* S,
+              const double2* z, int np, cudaStream_t st) {
+    const Plan& P = h->P;
+    for (const Launch& l : P.launches) {
+        if (l.phase != phase) continue;
+        cudaError_t e = timed(h->prof, family_of(l.kind), l.flops * np, l.bytes * np, st,
+                              [&]() { return launch_step(P, h->T, l, W, H, S, z, np, st); });
+        if (e != cudaSuccess)
+            return fail(NDSI_ERR_CUDA, std::string("kernel launch (step ") + std::to_string(l.tag) +
+                                           "): " + cudaGetErrorString(e));
+    }
+    return NDSI_OK;
+}
+
+int check_status(ndsi_plan* h, cudaStream_t st) {
+    int hs[4] = {0, 0, 0, 0};
+    NDSI_CK(cudaMemcpyAsync(hs, h->T.status, sizeof(hs), cudaMemcpyDeviceToHost, st));
+    NDSI_CK(cudaStreamSynchronize(st));
+    prof_resolve(h->prof);
+    if (hs[0] != 0) {
+        NDSI_CK(cudaMemsetAsync(h->T.status, 0, sizeof(int) * 4, st));
+        NDSI_CK(cudaStreamSynchronize(st));
+        if (hs[0] & kStatusSingular) return fail(NDSI_ERR_SINGULAR, "singular or non-finite pivot block");
+        return fail(NDSI_ERR_TIMEOUT, "bounded device wait gave up");
+    }
+    return NDSI_OK;
+}
+
+int ensure_stage(ndsi_plan* h, int64_t doubles) {
+    if (h->stage_cap >= doubles) return NDSI_OK;
+    if (h->stage) cudaFree(h->stage);
+    h->stage = nullptr;
+    h->stage_cap = 0;
+    NDSI_CK(cudaMalloc(&h->stage, sizeof(double) * static_cast<size_t>(doubles)));
+    h->stage_cap = doubles;
+    return NDSI_OK;
+}
+
+// Device copies of H and S (staged when the caller passed host memory).
+int device_inputs(ndsi_plan* h, const double* H, const double* S, const double** Hd,
+                  const double** Sd, cudaStream_t st) {
+    const int64_t nnz = h->P.nnz;
+    const bool hd = is_device_ptr(H), sd = is_device_ptr(S);
+    if (!hd || !sd) {
+        int rc = ensure_stage(h, 3 * nnz + 8);
+        if (rc) return rc;
+    }
+    *Hd = H;
+    *Sd = S;
+    if (!hd) {
+        NDSI_CK(cudaMemcpyAsync(h->stage, H, sizeof(double) * nnz, cudaMemcpyHostToDevice, st));
+        *Hd = h->stage;
+    }
+    if (!sd) {
+        NDSI_CK(cudaMemcpyAsync(h->stage + nnz, S, sizeof(double) * nnz, cudaMemcpyHostToDevice, st));
+        *Sd = h->stage + nnz;
+    }
+    return NDSI_OK;
+}
+
+int64_t workspace_cap(const ndsi_plan* h) {
+    if (h->P.opt.max_workspace_bytes > 0) return h->P.opt.max_workspace_bytes;
+    size_t freeb = 0, totalb = 0;
+    if (cudaMemGetInfo(&freeb, &totalb) != cudaSuccess) {
+        cudaGetLastError();
+        return int64_t(8) << 30;
+    }
+    int64_t have = static_cast<int64_t>(freeb) +
+                   static_cast<int64_t>(h->W.np_cap) * 16 * (h->W.front_stride + h->W.scr_stride);
+    return static_cast<int64_t>(0.85 * static_cast<double>(have));
+}
+
+}  // namespace
+}  // namespace ndsi
+
+using namespace ndsi;
+
+extern "C" {
+
+void ndsi_default_options(ndsi_options* opt) {
+    if (!opt) return;
+    opt->leaf_atoms = 20;
+    opt->precision = NDSI_PREC_FP64;
+    opt->split_slices = 6;
+    opt->block = 32;
+    opt->m0_radius = 1e7;
+    opt->max_workspace_bytes = 0;
+}
+
+int ndsi_poles(int32_t M, double* z_out, double* R_out) {
+    std::string err;
+    int rc = cf_poles(M, z_out, R_out, err);
+    if (rc) set_last_error(err);
+    return rc;
+}
+
+int ndsi_analyze(const ndsi_pattern* pat, int32_t n_atoms, const double* centers,
+                 const int32_t* atom_of_basis, const ndsi_options* opt, ndsi_plan** plan_out) {
+    if (!plan_out) return fail(NDSI_ERR_INVALID, "ndsi_analyze: plan_out is NULL");
+    *plan_out = nullptr;
+    ndsi_options o;
+    ndsi_default_options(&o);
+    if (opt) o = *opt;
+    if (o.m0_radius <= 0) o.m0_radius = 1e7;
+    if (o.precision != NDSI_PREC_FP64 && o.precision != NDSI_PREC_SPLIT)
+        return fail(NDSI_ERR_INVALID, "ndsi_analyze: unknown precision");
+    ndsi_plan* h = new (std::nothrow) ndsi_plan();
+    if (!h) return fail(NDSI_ERR_OOM, "ndsi_analyze: out of host memory");
+    std::string err;
+    int rc;
+    try {
+        rc = analyze(pat, n_atoms, centers, atom_of_basis, o, h->P, err);
+    } catch (const std::bad_alloc&) {
+        rc = NDSI_ERR_OOM;
+        err = "ndsi_analyze: out of host memory";
+    } catch (...) {
+        rc = NDSI_ERR_INVALID;
+        err = "ndsi_analyze: internal error";
+    }
+    if (rc) {
+        delete h;
+        return fail(rc, err);
+    }
+    *plan_out = h;
+    return NDSI_OK;
+}
+
+int ndsi_plan_info(const ndsi_plan* h, ndsi_plan_summary* out) {
+    if (!h || !out) return fail(NDSI_ERR_INVALID, "ndsi_plan_info: NULL argument");
+    const Plan& P = h->P;
+    out->n = P.n;
+    out->nnz = P.nnz;
+    out->n_atoms = P.n_atoms;
+    out->n_nodes = P.n_nodes;
+    out->n_levels = P.n_levels;
+    out->max_front = P.max_front;
+    out->front_elems = P.front_total;
+    out->flops_per_pole = P.flops_per_pole;
+    out->bytes_per_pole = P.bytes_per_pole;
+    return NDSI_OK;
+}
+
+int ndsi_plan_export(const ndsi_plan* h, int32_t what, void* out) {
+    if (!h || !out) return fail(NDSI_ERR_INVALID, "ndsi_plan_export: NULL argument");
+    const Plan& P = h->P;
+    switch (what) {
+        case NDSI_EXPORT_PERM_ATOMS: std::memcpy(out, P.perm_atoms.data(), bytes_of(P.perm_atoms)); break;
+        case NDSI_EXPORT_PERM_BASIS: std::memcpy(out, P.perm_basis.data(), bytes_of(P.perm_basis)); break;
+        case NDSI_EXPORT_NODE_ATOMS: std::memcpy(out, P.node_atom_first.data(), bytes_of(P.node_atom_first)); break;
+        case NDSI_EXPORT_PARENT: std::memcpy(out, P.parent.data(), bytes_of(P.parent)); break;
+        case NDSI_EXPORT_STRUCT_PTR: std::memcpy(out, P.struct_ptr.data(), bytes_of(P.struct_ptr)); break;
+        case NDSI_EXPORT_STRUCT_ATOMS:
+            if (!P.struct_atoms.empty()) std::memcpy(out, P.struct_atoms.data(), bytes_of(P.struct_atoms));
+            break;
+        case NDSI_EXPORT_LEVEL: std::memcpy(out, P.level.data(), bytes_of(P.level)); break;
+        default: return fail(NDSI_ERR_INVALID, "ndsi_plan_export: unknown item");
+    }
+    return NDSI_OK;
+}
+
+int ndsi_factor_poles(ndsi_plan* h, const double* H, const double* S, const double* z, int32_t n_poles,
+                      ndsi_factors** f_out, void* stream) {
+    if (!h || !H || !S || !z || !f_out || n_poles < 1)
+        return fail(NDSI_ERR_INVALID, "ndsi_factor_poles: invalid argument");
+    *f_out = nullptr;
+    if (h->P.opt.precision != NDSI_PREC_FP64)
+        return fail(NDSI_ERR_UNSUPPORTED, "ndsi_factor_poles: split precision not built in this library");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    int rc = upload_tables(h);
+    if (rc) return rc;
+    const int64_t need = int64_t(16) * n_poles * (h->P.front_total + h->P.scr_total);
+    if (h->P.opt.max_workspace_bytes > 0 && need > h->P.opt.max_workspace_bytes)
+        return fail(NDSI_ERR_OOM, "ndsi_factor_poles: factors exceed max_workspace_bytes");
+    std::unique_ptr<ndsi_factors> f(new (std::nothrow) ndsi_factors());
+    if (!f) return fail(NDSI_ERR_OOM, "ndsi_factor_poles: out of host memory");
+    f->plan = h;
+    f->np = n_poles;
+    rc = alloc_workspace(f->W, h->P, n_poles);
+    if (rc) {
+        free_workspace(f->W);
+        return rc;
+    }
+    if (cudaMalloc(&f->zd, sizeof(double2) * n_poles) != cudaSuccess) {
+        cudaGetLastError();
+        free_workspace(f->W);
+        return fail(NDSI_ERR_OOM, "ndsi_factor_poles: cudaMalloc of pole array failed");
+    }
+    auto cleanup = [&]() {
+        free_workspace(f->W);
+        cudaFree(f->zd);
+    };
+    if (cudaMemcpyAsync(f->zd, z, sizeof(double2) * n_poles, cudaMemcpyHostToDevice, st) != cudaSuccess) {
+        cleanup();
+        return fail(NDSI_ERR_CUDA, "ndsi_factor_poles: pole upload failed");
+    }
+    const double *Hd, *Sd;
+    rc = device_inputs(h, H, S, &Hd, &Sd, st);
+    if (!rc) rc = run_phase(h, f->W, 0, Hd, Sd, f->zd, n_poles, st);
+    if (rc) {
+        cleanup();
+        return rc;
+    }
+    *f_out = f.release();
+    return NDSI_OK;
+}
+
+int ndsi_selinv(ndsi_factors* f, double* G_out, void* stream) {
+    if (!f || !f->plan) return fail(NDSI_ERR_INVALID, "ndsi_selinv: NULL factors");
+    ndsi_plan* h = f->plan;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    int rc = run_phase(h, f->W, 1, nullptr, nullptr, f->zd, f->np, st);
+    if (rc) return rc;
+    if (G_out) {
+        const bool dev = is_device_ptr(G_out);
+        double2* dst = reinterpret_cast<double2*>(G_out);
+        double2* tmp = nullptr;
+        const size_t bytes = sizeof(double2) * static_cast<size_t>(f->np) * h->P.nnz;
+        if (!dev) NDSI_CK(cudaMalloc(&tmp, bytes));
+        NDSI_CK(launch_gather_pattern(h->P, h->T, f->W, f->np, dev ? dst : tmp, 0, st));
+        if (!dev) {
+            cudaError_t e = cudaMemcpyAsync(G_out, tmp, bytes, cudaMemcpyDeviceToHost, st);
+            cudaError_t e2 = cudaStreamSynchronize(st);
+            cudaFree(tmp);
+            NDSI_CK(e);
+            NDSI_CK(e2);
+        }
+    }
+    return check_status(h, st);
+}
+
+int ndsi_density(ndsi_plan* h, const double* H, const double* S, double mu, double kT, int32_t n_poles,
+                 double* rho_out, double* n_elec_out, void* stream) {
+    if (!h || !H || !S || !rho_out || n_poles < 1 || !(kT > 0) || !std::isfinite(mu))
+        return fail(NDSI_ERR_INVALID, "ndsi_density: invalid argument");
+    if (h->P.opt.precision != NDSI_PREC_FP64)
+        return fail(NDSI_ERR_UNSUPPORTED, "ndsi_density: split precision not built in this library");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    int rc = upload_tables(h);
+    if (rc) return rc;
+    // poles of Eq. 7 (cached per M) -> points alpha_p and weights w_p of Eq. 8, plus iR for M0
+    if (h->pole_M != n_poles) {
+        h->pole_z.assign(n_poles, 0.0);
+        h->pole_R.assign(n_poles, 0.0);
+        std::string err;
+        rc = cf_poles(n_poles, h->pole_z.data(), h->pole_R.data(), err);
+        if (rc) return fail(rc, err);
+        h->pole_M = n_poles;
+    }
+    const int32_t nq = n_poles + 1;
+    std::vector<double2> zq(nq), cq(nq);
+    for (int32_t p = 0; p < n_poles; ++p) {
+        zq[p] = make_double2(mu, h->pole_z[p] * kT);
+        cq[p] = make_double2(-4.0 * h->pole_R[p] * kT, 0.0);
+    }
+    const double R = h->P.opt.m0_radius;
+    zq[n_poles] = make_double2(0.0, R);
+    cq[n_poles] = make_double2(0.0, R);
+    // chunk the points to the workspace cap
+    const int64_t per_pole = int64_t(16) * (h->P.front_total + h->P.scr_total);
+    int64_t cap = workspace_cap(h);
+    int32_t chunk = static_cast<int32_t>(std::min<int64_t>(nq, std::max<int64_t>(1, cap / per_pole)));
+    if (cap < per_pole) return fail(NDSI_ERR_OOM, "ndsi_density: one pole does not fit the workspace cap");
+    rc = alloc_workspace(h->W, h->P, chunk);
+    if (rc) return rc;
+    if (h->cw_cap < nq) {
+        if (h->cw) cudaFree(h->cw);
+        if (h->zw) cudaFree(h->zw);
+        h->cw = h->zw = nullptr;
+        h->cw_cap = 0;
+        NDSI_CK(cudaMalloc(&h->cw, sizeof(double2) * nq));
+        NDSI_CK(cudaMalloc(&h->zw, sizeof(double2) * nq));
+        h->cw_cap = nq;
+    }
+    if (!h->partials) NDSI_CK(cudaMalloc(&h->partials, sizeof(double) * (accumulate_blocks(h->P.nnz) + 1)));
+    NDSI_CK(cudaMemcpyAsync(h->zw, zq.data(), sizeof(double2) * nq, cudaMemcpyHostToDevice, st));
+    NDSI_CK(cudaMemcpyAsync(h->cw, cq.data(), sizeof(double2) * nq, cudaMemcpyHostToDevice, st));
+    const double *Hd, *Sd;
+    rc = device_inputs(h, H, S, &Hd, &Sd, st);
+    if (rc) return rc;
+    const bool rho_dev = is_device_ptr(rho_out);
+    const bool ne_dev = n_elec_out && is_device_ptr(n_elec_out);
+    if (!rho_dev || (n_elec_out && !ne_dev)) {
+        rc = ensure_stage(h, 3 * h->P.nnz + 8);
+        if (rc) return rc;
+    }
+    double* rho_d = rho_dev ? rho_out : h->stage + 2 * h->P.nnz;
+    double* ne_d = ne_dev ? n_elec_out : h->stage + 3 * h->P.nnz;
+    for (int32_t q0 = 0; q0 < nq; q0 += chunk) {
+        const int32_t np = std::min(chunk, nq - q0);
+        rc = run_phase(h, h->W, 0, Hd, Sd, h->zw + q0, np, st);
+        if (!rc) rc = run_phase(h, h->W, 1, Hd, Sd, h->zw + q0, np, st);
+        if (rc) return rc;
+        const int last = q0 + np >= nq;
+        const double acc_bytes = static_cast<double>(h->P.nnz) * (8.0 + 16.0 * np + 8.0 + 8.0 +
+                                                                  (q0 > 0 ? 8.0 : 0.0));
+        NDSI_CK(timed(h->prof, 6, 2.0 * np * h->P.nnz, acc_bytes, st, [&]() {
+            return launch_accumulate(h->P, h->T, h->W, np, h->cw + q0, Sd, rho_d, q0 > 0 ? 1 : 0,
+                                     last, h->partials, st);
+        }));
+    }
+    const int nblk = accumulate_blocks(h->P.nnz);
+    NDSI_CK(timed(h->prof, 7, static_cast<double>(nblk), 8.0 * nblk, st,
+                  [&]() { return launch_reduce(h->partials, nblk, ne_d, st); }));
+    if (!rho_dev) NDSI_CK(cudaMemcpyAsync(rho_out, rho_d, sizeof(double) * h->P.nnz, cudaMemcpyDeviceToHost, st));
+    if (n_elec_out && !ne_dev) NDSI_CK(cudaMemcpyAsync(n_elec_out, ne_d, sizeof(double), cudaMemcpyDeviceToHost, st));
+    return check_status(h, st);
+}
+
+int ndsi_profile_enable(ndsi_plan* h, int32_t enable) {
+    if (!h) return fail(NDSI_ERR_INVALID, "ndsi_profile_enable: NULL plan");
+    Profiler& pf = h->prof;
+    pf.on = enable != 0;
+    if (pf.on) {
+        std::fill(pf.ms, pf.ms + kFamilies, 0.0);
+        std::fill(pf.flops, pf.flops + kFamilies, 0.0);
+        std::fill(pf.bytes, pf.bytes + kFamilies, 0.0);
+        std::fill(pf.launches, pf.launches + kFamilies, int64_t(0));
+        pf.pending.clear();
+        pf.used = 0;
+    }
+    return NDSI_OK;
+}
+
+int ndsi_profile_read(const ndsi_plan* h, ndsi_profile_entry* out, int32_t max_entries, int32_t* n_out) {
+    if (!h || !out || !n_out || max_entries < 0)
+        return fail(NDSI_ERR_INVALID, "ndsi_profile_read: invalid argument");
+    const Profiler& pf = h->prof;
+    int32_t n = 0;
+    for (int f = 0; f < kFamilies && n < max_entries; ++f) {
+        if (pf.launches[f] == 0) continue;
+        ndsi_profile_entry& e = out[n++];
+        std::memset(&e, 0, sizeof(e));
+        std::strncpy(e.name, kFamilyName[f], sizeof(e.name) - 1);
+        e.launches = pf.launches[f];
+        e.ms = pf.ms[f];
+        e.flops = pf.flops[f];
+        e.bytes = pf.bytes[f];
+    }
+    *n_out = n;
+    return NDSI_OK;
+}
+
+void ndsi_factors_destroy(ndsi_factors* f) {
+    if (!f) return;
+    free_workspace(f->W);
+    if (f->zd) cudaFree(f->zd);
+    delete f;
+}
+
+void ndsi_plan_destroy(ndsi_plan* h) {
+    if (!h) return;
+    free_workspace(h->W);
+    for (cudaEvent_t e : h->prof.pool) cudaEventDestroy(e);
+    if (h->T.blob) cudaFree(h->T.blob);
+    if (h->cw) cudaFree(h->cw);
+    if (h->zw) cudaFree(h->zw);
+    if (h->partials) cudaFree(h->partials);
+    if (h->stage) cudaFree(h->stage);
+    delete h;
+}
+
+const char* ndsi_last_error(void) { return g_last_error.c_str(); }
+
+}  // extern "C"

@@ -1,0 +1,436 @@
+// FP64 kernels of the per-pole factor / selected-inversion path.
+//
+// Front layout: every supernode J owns a dense f x f complex front (f = |J| + |struct(J)|),
+// column-major, J's columns first; only the lower triangle is kept valid.  All poles of a chunk
+// are batched in one launch (grid.y = pole), each pole owning one slab of fronts and one slab
+// of scratch.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "kernels.cuh"
+
+namespace ndsi {
+
+namespace {
+
+__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+    return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+
+// ---------------------------------------------------------------------------------------------
+// Front assembly: F_J = sum over children c of U_c (extend-add through the inverse relative
+// index maps), written for the lower triangle of every front of a level.  Zero where no child
+// contributes; the original entries are added afterwards by k_scatter.
+__global__ void __launch_bounds__(256) k_assemble(const NodeDev* __restrict__ nodes,
+                                                  const NodeTile* __restrict__ tiles, int64_t first,
+                                                  const int32_t* __restrict__ inv_map,
+                                                  double2* __restrict__ F, int64_t stride) {
+    const NodeTile t = tiles[first + blockIdx.x];
+    const NodeDev nd = nodes[t.node];
+    double2* Fp = F + static_cast<int64_t>(blockIdx.y) * stride;
+    __shared__ NodeDev ch[2];
+    if (threadIdx.x < nd.nchild && threadIdx.y == 0) ch[threadIdx.x] = nodes[nd.child[threadIdx.x]];
+    __syncthreads();
+    const int a = t.i0 + threadIdx.x;
+    if (a >= nd.f) return;
+    int ia[2];
+    for (int c = 0; c < nd.nchild; ++c) ia[c] = inv_map[nd.inv_off[c] + a];
+    for (int q = threadIdx.y; q < kNodeTile; q += blockDim.y) {
+        const int b = t.j0 + q;
+        if (b > a || b >= nd.f) continue;
+        double2 v = make_double2(0.0, 0.0);
+        for (int c = 0; c < nd.nchild; ++c) {
+            const int ib = inv_map[nd.inv_off[c] + b];
+            if (ia[c] >= 0 && ib >= 0) {
+                const NodeDev& cd = ch[c];
+                v = cadd(v, Fp[cd.front_off + (cd.s + ia[c]) + static_cast<int64_t>(cd.s + ib) * cd.f]);
+            }
+        }
+        Fp[nd.front_off + a + static_cast<int64_t>(b) * nd.f] = v;
+    }
+}
+
+// X = z S - H on the level's entries (each front element receives at most one entry).
+__global__ void __launch_bounds__(256) k_scatter(const int64_t* __restrict__ idx, int64_t first,
+                                                 int64_t count, const int64_t* __restrict__ asm_map,
+                                                 const double* __restrict__ H,
+                                                 const double* __restrict__ S,
+                                                 const double2* __restrict__ z,
+                                                 double2* __restrict__ F, int64_t stride) {
+    const double2 zq = z[blockIdx.y];
+    double2* Fp = F + static_cast<int64_t>(blockIdx.y) * stride;
+    for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < count;
+         e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const int64_t k = idx[first + e];
+        const int64_t off = asm_map[k];
+        const double h = H[k], s = S[k];
+        double2 v = Fp[off];
+        v.x += zq.x * s - h;
+        v.y += zq.y * s;
+        Fp[off] = v;
+    }
+}
+
+// FP64 inverse of a complex-symmetric pivot block (Gauss-Jordan sweeps without pivoting).
+// No pivoting is needed: for Im z != 0 and S SPD, Im(X) = Im(z) S is definite, so every leading
+// block and every Schur complement of X is nonsingular.  A zero or non-finite pivot sets the
+// singular bit of the status word.
+template <int NB>
+__global__ void __launch_bounds__(256) k_diaginv(const DiagItem* __restrict__ items, int64_t first,
+                                                 double2* __restrict__ F, int64_t stride,
+                                                 int* __restrict__ status) {
+    extern __shared__ double2 smem_dinv[];
+    double2 (*a)[NB + 1] = reinterpret_cast<double2 (*)[NB + 1]>(smem_dinv);
+    const DiagItem d = items[first + blockIdx.x];
+    double2* A = F + static_cast<int64_t>(blockIdx.y) * stride + d.off;
+    const int nb = d.nb, ld = d.ld;
+    const int tid = threadIdx.x;
+    for (int e = tid; e < nb * nb; e += blockDim.x) {
+        const int i = e % nb, j = e / nb;
+        a[i][j] = i >= j ? A[i + static_cast<int64_t>(j) * ld] : A[j + static_cast<int64_t>(i) * ld];
+    }
+    __syncthreads();
+    constexpr int kPer = (NB * NB + 255) / 256;
+    for (int t = 0; t < nb; ++t) {
+        const double2 p = a[t][t];
+        const double den = p.x * p.x + p.y * p.y;
+        if (tid == 0 && !(den > 0.0 && isfinite(den))) atomicOr(status, kStatusSingular);
+        const double2 ip = make_double2(p.x / den, -p.y / den);
+        double2 nv[kPer];
+        #pragma unroll
+        for (int u = 0; u < kPer; ++u) {
+            const int e = tid + u * 256;
+            if (e < nb * nb) {
+                const int i = e % nb, j = e / nb;
+                if (i == t && j == t) {
+                    nv[u] = ip;
+                } else if (i == t) {
+                    nv[u] = cmul(a[t][j], ip);
+                } else if (j == t) {
+                    const double2 v = cmul(a[i][t], ip);
+                    nv[u] = make_double2(-v.x, -v.y);
+                } else {
+                    const double2 v = cmul(cmul(a[i][t], ip), a[t][j]);
+                    nv[u] = make_double2(a[i][j].x - v.x, a[i][j].y - v.y);
+                }
+            }
+        }
+        __syncthreads();
+        #pragma unroll
+        for (int u = 0; u < kPer; ++u) {
+            const int e = tid + u * 256;
+            if (e < nb * nb) a[e % nb][e / nb] = nv[u];
+        }
+        __syncthreads();
+    }
+    for (int e = tid; e < nb * nb; e += blockDim.x) {
+        const int i = e % nb, j = e / nb;
+        if (i >= j) A[i + static_cast<int64_t>(j) * ld] = a[i][j];
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Batched complex FP64 GEMM on the CUDA cores: C = alpha op(A) op(B) + beta C for every tile of
+// a schedule step.  64 x 64 output tile, K step 16, 256 threads with 4 x 4 outputs each.
+constexpr int BM = kGemmTile, BN = kGemmTile, BK = 16;
+
+template <int OP>
+__device__ __forceinline__ double2 load_op(const double2* __restrict__ X, int ld, int r, int c) {
+    if (OP == OP_N) return X[r + static_cast<int64_t>(c) * ld];
+    if (OP == OP_T) return X[c + static_cast<int64_t>(r) * ld];
+    const int hi = r > c ? r : c, lo = r > c ? c : r;
+    return X[hi + static_cast<int64_t>(lo) * ld];
+}
+
+template <int OPA, int OPB>
+__global__ void __launch_bounds__(256) k_gemm_f64(const GemmItem* __restrict__ items,
+                                                  const GemmTile* __restrict__ tiles, int64_t tfirst,
+                                                  int64_t ifirst, const double2* __restrict__ Abuf,
+                                                  int64_t sA, const double2* __restrict__ Bbuf,
+                                                  int64_t sB, double2* __restrict__ Cbuf, int64_t sC,
+                                                  double alpha, double beta, int lower) {
+    __shared__ double2 As[BK][BM + 1];
+    __shared__ double2 Bs[BK][BN + 1];
+    const GemmTile t = tiles[tfirst + blockIdx.x];
+    const GemmItem it = items[ifirst + t.item];
+    const int64_t pole = blockIdx.y;
+    const double2* A = Abuf + pole * sA + it.a_off;
+    const double2* B = Bbuf + pole * sB + it.b_off;
+    double2* C = Cbuf + pole * sC + it.c_off;
+    const int tid = threadIdx.x;
+    const int tx = tid % 16, ty = tid / 16;
+    double2 acc[4][4];
+    #pragma unroll
+    for (int i = 0; i < 4; ++i)
+        #pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = make_double2(0.0, 0.0);
+    for (int k0 = 0; k0 < it.K; k0 += BK) {
+        // A tile (BM x BK): coalesced along the contiguous index of the stored operand
+        #pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            int lm, lk;
+            if (OPA == OP_T) {
+                lk = tid % BK;
+                lm = tid / BK + 16 * u;
+            } else {
+                lm = tid % BM;
+                lk = tid / BM + 4 * u;
+            }
+            const int m = t.m0 + lm, k = k0 + lk;
+            As[lk][lm] = (m < it.M && k < it.K) ? load_op<OPA>(A, it.lda, m, k) : make_double2(0.0, 0.0);
+        }
+        #pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            int ln, lk;
+            if (OPB == OP_T) {
+                ln = tid % BN;
+                lk = tid / BN + 4 * u;
+            } else {
+                lk = tid % BK;
+                ln = tid / BK + 16 * u;
+            }
+            const int n = t.n0 + ln, k = k0 + lk;
+            Bs[lk][ln] = (n < it.N && k < it.K) ? load_op<OPB>(B, it.ldb, k, n) : make_double2(0.0, 0.0);
+        }
+        __syncthreads();
+        #pragma unroll 4
+        for (int kk = 0; kk < BK; ++kk) {
+            double2 av[4], bv[4];
+            #pragma unroll
+            for (int i = 0; i < 4; ++i) av[i] = As[kk][tx + 16 * i];
+            #pragma unroll
+            for (int j = 0; j < 4; ++j) bv[j] = Bs[kk][ty + 16 * j];
+            #pragma unroll
+            for (int i = 0; i < 4; ++i)
+                #pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    acc[i][j].x = fma(av[i].x, bv[j].x, acc[i][j].x);
+                    acc[i][j].x = fma(-av[i].y, bv[j].y, acc[i][j].x);
+                    acc[i][j].y = fma(av[i].x, bv[j].y, acc[i][j].y);
+                    acc[i][j].y = fma(av[i].y, bv[j].x, acc[i][j].y);
+                }
+        }
+        __syncthreads();
+    }
+    #pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const int n = t.n0 + ty + 16 * j;
+        #pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int m = t.m0 + tx + 16 * i;
+            if (m < it.M && n < it.N && (!lower || m >= n)) {
+                double2* c = C + m + static_cast<int64_t>(n) * it.ldc;
+                double2 v = make_double2(alpha * acc[i][j].x, alpha * acc[i][j].y);
+                if (beta != 0.0) {
+                    const double2 old = *c;
+                    v.x += beta * old.x;
+                    v.y += beta * old.y;
+                }
+                *c = v;
+            }
+        }
+    }
+}
+
+// dst = scale * src for the blocks of a step (SCR -> FRONT).
+__global__ void __launch_bounds__(256) k_copy(const CopyItem* __restrict__ items, int64_t first,
+                                              const double2* __restrict__ src, int64_t s_src,
+                                              double2* __restrict__ dst, int64_t s_dst, double scale) {
+    const CopyItem c = items[first + blockIdx.x];
+    const double2* S = src + static_cast<int64_t>(blockIdx.y) * s_src + c.src_off;
+    double2* D = dst + static_cast<int64_t>(blockIdx.y) * s_dst + c.dst_off;
+    for (int j = blockIdx.z; j < c.cols; j += gridDim.z) {
+        for (int i = threadIdx.x; i < c.rows; i += blockDim.x) {
+            const double2 v = S[i + static_cast<int64_t>(j) * c.lds];
+            D[i + static_cast<int64_t>(j) * c.ldd] = make_double2(scale * v.x, scale * v.y);
+        }
+    }
+}
+
+// G_RR of a node from the full (lower-valid) G front of its parent (Eq. 38's reuse of
+// ancestor blocks), through the node's relative index map.
+__global__ void __launch_bounds__(256) k_gather(const NodeDev* __restrict__ nodes,
+                                                const NodeTile* __restrict__ tiles, int64_t first,
+                                                const int32_t* __restrict__ rel_map,
+                                                double2* __restrict__ F, int64_t stride) {
+    const NodeTile t = tiles[first + blockIdx.x];
+    const NodeDev nd = nodes[t.node];
+    const NodeDev pd = nodes[nd.parent];
+    double2* Fp = F + static_cast<int64_t>(blockIdx.y) * stride;
+    const int i = t.i0 + threadIdx.x;
+    if (i >= nd.r) return;
+    const int ra = rel_map[nd.rel_off + i];
+    for (int q = threadIdx.y; q < kNodeTile; q += blockDim.y) {
+        const int j = t.j0 + q;
+        if (j > i) continue;
+        const int rb = rel_map[nd.rel_off + j];
+        Fp[nd.front_off + (nd.s + i) + static_cast<int64_t>(nd.s + j) * nd.f] =
+            Fp[pd.front_off + ra + static_cast<int64_t>(rb) * pd.f];
+    }
+}
+
+// Residue sum of Eq. 8 on the pattern: rho_k (+)= sum_q Re(c_q G_q(k)); per-block partial sums
+// of rho_k S_k for Tr(rho S) (Eq. 40), reduced in a fixed order by k_reduce.
+constexpr int kAccThreads = 256;
+
+__global__ void __launch_bounds__(kAccThreads) k_accumulate(const int64_t* __restrict__ out_map,
+                                                            int64_t nnz,
+                                                            const double2* __restrict__ F,
+                                                            int64_t stride, int np,
+                                                            const double2* __restrict__ c,
+                                                            const double* __restrict__ S,
+                                                            double* __restrict__ rho, int accumulate,
+                                                            int want_trace,
+                                                            double* __restrict__ partials) {
+    __shared__ double red[kAccThreads / 32];
+    const int64_t k = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+    double tr = 0.0;
+    if (k < nnz) {
+        const int64_t off = out_map[k];
+        double sum = accumulate ? rho[k] : 0.0;
+        for (int q = 0; q < np; ++q) {
+            const double2 g = F[static_cast<int64_t>(q) * stride + off];
+            const double2 w = c[q];
+            sum += w.x * g.x - w.y * g.y;
+        }
+        rho[k] = sum;
+        tr = sum * S[k];
+    }
+    if (!want_trace) return;
+    #pragma unroll
+    for (int o = 16; o > 0; o >>= 1) tr += __shfl_down_sync(0xffffffffu, tr, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = tr;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double v = threadIdx.x < kAccThreads / 32 ? red[threadIdx.x] : 0.0;
+        #pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if (threadIdx.x == 0) partials[blockIdx.x] = v;
+    }
+}
+
+__global__ void __launch_bounds__(1024) k_reduce(const double* __restrict__ partials, int n,
+                                                 double* __restrict__ out) {
+    __shared__ double red[32];
+    double v = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) v += partials[i];
+    #pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double w = threadIdx.x < (blockDim.x + 31) / 32 ? red[threadIdx.x] : 0.0;
+        #pragma unroll
+        for (int o = 16; o > 0; o >>= 1) w += __shfl_down_sync(0xffffffffu, w, o);
+        if (threadIdx.x == 0) *out = w;
+    }
+}
+
+__global__ void __launch_bounds__(256) k_gather_pattern(const int64_t* __restrict__ out_map,
+                                                        int64_t nnz,
+                                                        const double2* __restrict__ F,
+                                                        int64_t stride, double2* __restrict__ G,
+                                                        int64_t q0) {
+    const int64_t q = blockIdx.y;
+    for (int64_t k = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; k < nnz;
+         k += static_cast<int64_t>(gridDim.x) * blockDim.x)
+        G[(q0 + q) * nnz + k] = F[q * stride + out_map[k]];
+}
+
+template <int OPA, int OPB>
+cudaError_t gemm_launch(const Plan& P, const DevTables& T, const Launch& l, const Workspace& W,
+                        int np, cudaStream_t st) {
+    const double2* bufs[2] = {W.fronts, W.scr};
+    const int64_t strides[2] = {W.front_stride, W.scr_stride};
+    dim3 grid(static_cast<unsigned>(l.tcount), static_cast<unsigned>(np));
+    k_gemm_f64<OPA, OPB><<<grid, 256, 0, st>>>(T.gemm_items, T.gemm_tiles, l.tfirst, l.first,
+                                               bufs[l.bufA], strides[l.bufA], bufs[l.bufB],
+                                               strides[l.bufB], const_cast<double2*>(bufs[l.bufC]),
+                                               strides[l.bufC], l.alpha, l.beta, l.lower);
+    (void)P;
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_step(const Plan& P, const DevTables& T, const Launch& l, const Workspace& W,
+                        const double* H, const double* S, const double2* z, int np, cudaStream_t st) {
+    switch (l.kind) {
+        case L_ASSEMBLE: {
+            dim3 grid(static_cast<unsigned>(l.count), static_cast<unsigned>(np));
+            k_assemble<<<grid, dim3(32, 8), 0, st>>>(T.nodes, T.node_tiles, l.first, T.inv_map, W.fronts,
+                                                    W.front_stride);
+            return cudaGetLastError();
+        }
+        case L_SCATTER: {
+            const int64_t blocks = (l.count + 255) / 256;
+            dim3 grid(static_cast<unsigned>(blocks < 4096 ? blocks : 4096), static_cast<unsigned>(np));
+            k_scatter<<<grid, 256, 0, st>>>(T.scatter_idx, l.first, l.count, T.asm_map, H, S, z, W.fronts,
+                                            W.front_stride);
+            return cudaGetLastError();
+        }
+        case L_DIAGINV: {
+            dim3 grid(static_cast<unsigned>(l.count), static_cast<unsigned>(np));
+            const int b = P.block;
+            const size_t sm = static_cast<size_t>(b) * (b + 1) * sizeof(double2);
+            if (b <= 16) k_diaginv<16><<<grid, 256, sm, st>>>(T.diag_items, l.first, W.fronts, W.front_stride, T.status);
+            else if (b <= 32) k_diaginv<32><<<grid, 256, sm, st>>>(T.diag_items, l.first, W.fronts, W.front_stride, T.status);
+            else k_diaginv<64><<<grid, 256, sm, st>>>(T.diag_items, l.first, W.fronts, W.front_stride, T.status);
+            return cudaGetLastError();
+        }
+        case L_GEMM: {
+            if (l.opA == OP_N && l.opB == OP_S) return gemm_launch<OP_N, OP_S>(P, T, l, W, np, st);
+            if (l.opA == OP_N && l.opB == OP_T) return gemm_launch<OP_N, OP_T>(P, T, l, W, np, st);
+            if (l.opA == OP_S && l.opB == OP_N) return gemm_launch<OP_S, OP_N>(P, T, l, W, np, st);
+            if (l.opA == OP_T && l.opB == OP_N) return gemm_launch<OP_T, OP_N>(P, T, l, W, np, st);
+            return cudaErrorInvalidValue;
+        }
+        case L_COPY: {
+            dim3 grid(static_cast<unsigned>(l.count), static_cast<unsigned>(np), 8);
+            k_copy<<<grid, 256, 0, st>>>(T.copy_items, l.first, W.scr, W.scr_stride, W.fronts, W.front_stride,
+                                         l.alpha);
+            return cudaGetLastError();
+        }
+        case L_GATHER: {
+            dim3 grid(static_cast<unsigned>(l.count), static_cast<unsigned>(np));
+            k_gather<<<grid, dim3(32, 8), 0, st>>>(T.nodes, T.node_tiles, l.first, T.rel_map, W.fronts,
+                                                  W.front_stride);
+            return cudaGetLastError();
+        }
+        default:
+            return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t kernels_init() {
+    const int sm64 = 64 * 65 * static_cast<int>(sizeof(double2));
+    return cudaFuncSetAttribute(k_diaginv<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm64);
+}
+
+int accumulate_blocks(int64_t nnz) { return static_cast<int>((nnz + kAccThreads - 1) / kAccThreads); }
+
+cudaError_t launch_accumulate(const Plan& P, const DevTables& T, const Workspace& W, int np,
+                              const double2* c, const double* S, double* rho, int accumulate,
+                              int want_trace, double* partials, cudaStream_t st) {
+    const int blocks = accumulate_blocks(P.nnz);
+    k_accumulate<<<blocks, kAccThreads, 0, st>>>(T.out_map, P.nnz, W.fronts, W.front_stride, np, c, S, rho,
+                                                 accumulate, want_trace, partials);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reduce(const double* partials, int nblocks, double* out, cudaStream_t st) {
+    k_reduce<<<1, 1024, 0, st>>>(partials, nblocks, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gather_pattern(const Plan& P, const DevTables& T, const Workspace& W, int np,
+                                  double2* G_out, int64_t q0, cudaStream_t st) {
+    const int64_t blocks = (P.nnz + 255) / 256;
+    dim3 grid(static_cast<unsigned>(blocks < 2048 ? blocks : 2048), static_cast<unsigned>(np));
+    k_gather_pattern<<<grid, 256, 0, st>>>(T.out_map, P.nnz, W.fronts, W.front_stride, G_out, q0);
+    return cudaGetLastError();
+}
+
+}  // namespace ndsi

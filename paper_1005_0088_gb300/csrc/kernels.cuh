@@ -1,0 +1,58 @@
+// Device kernels of the FP64 numeric phase (shared declarations).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "plan.hpp"
+
+namespace ndsi {
+
+// Error bits latched in the device status word.
+constexpr int kStatusSingular = 1;
+constexpr int kStatusTimeout = 2;
+
+struct DevTables {
+    NodeDev* nodes = nullptr;
+    int64_t* asm_map = nullptr;
+    int64_t* out_map = nullptr;
+    int32_t* inv_map = nullptr;
+    int32_t* rel_map = nullptr;
+    int64_t* scatter_idx = nullptr;
+    GemmItem* gemm_items = nullptr;
+    GemmTile* gemm_tiles = nullptr;
+    CopyItem* copy_items = nullptr;
+    DiagItem* diag_items = nullptr;
+    NodeTile* node_tiles = nullptr;
+    int* status = nullptr;
+    void* blob = nullptr;  // single allocation holding all of the above
+};
+
+// Pole-batched workspace: `np` slabs of fronts and of scratch.
+struct Workspace {
+    double2* fronts = nullptr;
+    double2* scr = nullptr;
+    int64_t front_stride = 0;   // complex elements per pole slab
+    int64_t scr_stride = 0;
+    int32_t np_cap = 0;         // poles the buffers hold
+};
+
+// One-time kernel attributes (large dynamic shared memory).
+cudaError_t kernels_init();
+
+// Launch one schedule step over `np` poles whose slabs start at the workspace base.
+cudaError_t launch_step(const Plan& P, const DevTables& T, const Launch& l, const Workspace& W,
+                        const double* H, const double* S, const double2* z, int np, cudaStream_t st);
+
+// rho(k) (+)= sum_q Re(c_q G_q(k)) over the pattern; `partials` receives per-block sums of
+// rho(k) S(k) when `want_trace` is set (nblocks = accumulate_blocks(nnz)).
+cudaError_t launch_accumulate(const Plan& P, const DevTables& T, const Workspace& W, int np,
+                              const double2* c, const double* S, double* rho, int accumulate,
+                              int want_trace, double* partials, cudaStream_t st);
+int accumulate_blocks(int64_t nnz);
+cudaError_t launch_reduce(const double* partials, int nblocks, double* out, cudaStream_t st);
+
+// G_out[q*nnz + k] = G_q(k) for the np poles of the workspace.
+cudaError_t launch_gather_pattern(const Plan& P, const DevTables& T, const Workspace& W, int np,
+                                  double2* G_out, int64_t q0, cudaStream_t st);
+
+}  // namespace ndsi

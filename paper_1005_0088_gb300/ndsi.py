@@ -1,0 +1,254 @@
+"""ctypes binding of libndsi.so: the C-ABI entry points under the same names.
+
+Argument marshalling only: every step of the path runs inside the library.  Array arguments may
+be torch tensors (CUDA or CPU) or numpy arrays; they are passed as raw pointers.  The library
+raises NdsiError when it is missing or a call fails; there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libndsi.so")
+
+NDSI_OK = 0
+NDSI_ERR_INVALID = 1
+NDSI_ERR_SINGULAR = 2
+NDSI_ERR_OOM = 3
+NDSI_ERR_CUDA = 4
+NDSI_ERR_TIMEOUT = 5
+NDSI_ERR_UNSUPPORTED = 6
+NDSI_PREC_FP64 = 0
+NDSI_PREC_SPLIT = 1
+EXPORT = dict(perm_atoms=1, perm_basis=2, node_atoms=3, parent=4, struct_ptr=5, struct_atoms=6,
+              level=7)
+
+# Every function declared in include/ndsi.h.
+EXPORTED_SYMBOLS = (
+    "ndsi_default_options", "ndsi_poles", "ndsi_analyze", "ndsi_plan_info", "ndsi_plan_export",
+    "ndsi_factor_poles", "ndsi_selinv", "ndsi_density", "ndsi_plan_destroy",
+    "ndsi_factors_destroy", "ndsi_last_error", "ndsi_profile_enable", "ndsi_profile_read",
+)
+
+
+class NdsiError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"ndsi error {code}: {msg}")
+        self.code = code
+
+
+class ndsi_pattern(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("rowptr", ctypes.c_void_p), ("col", ctypes.c_void_p)]
+
+
+class ndsi_options(ctypes.Structure):
+    _fields_ = [("leaf_atoms", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("split_slices", ctypes.c_int32), ("block", ctypes.c_int32),
+                ("m0_radius", ctypes.c_double), ("max_workspace_bytes", ctypes.c_int64)]
+
+
+class ndsi_plan_summary(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("nnz", ctypes.c_int64), ("n_atoms", ctypes.c_int32),
+                ("n_nodes", ctypes.c_int32), ("n_levels", ctypes.c_int32),
+                ("max_front", ctypes.c_int32), ("front_elems", ctypes.c_int64),
+                ("flops_per_pole", ctypes.c_double), ("bytes_per_pole", ctypes.c_double)]
+
+
+class ndsi_profile_entry(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_int64), ("ms", ctypes.c_double),
+                ("flops", ctypes.c_double), ("bytes", ctypes.c_double)]
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libndsi.so (build it first with paper_1005_0088_gb300.build.build())."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise NdsiError(-1, f"{path} is missing: run paper_1005_0088_gb300.build.build() "
+                            "(the CUDA library is required; there is no fallback)")
+    lib = ctypes.CDLL(path)
+    vp, i32, i64, dbl = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+    lib.ndsi_default_options.argtypes = [ctypes.POINTER(ndsi_options)]
+    lib.ndsi_default_options.restype = None
+    lib.ndsi_poles.argtypes = [i32, vp, vp]
+    lib.ndsi_analyze.argtypes = [ctypes.POINTER(ndsi_pattern), i32, vp, vp,
+                                 ctypes.POINTER(ndsi_options), ctypes.POINTER(vp)]
+    lib.ndsi_plan_info.argtypes = [vp, ctypes.POINTER(ndsi_plan_summary)]
+    lib.ndsi_plan_export.argtypes = [vp, i32, vp]
+    lib.ndsi_factor_poles.argtypes = [vp, vp, vp, vp, i32, ctypes.POINTER(vp), vp]
+    lib.ndsi_selinv.argtypes = [vp, vp, vp]
+    lib.ndsi_density.argtypes = [vp, vp, vp, dbl, dbl, i32, vp, vp, vp]
+    lib.ndsi_plan_destroy.argtypes = [vp]
+    lib.ndsi_plan_destroy.restype = None
+    lib.ndsi_factors_destroy.argtypes = [vp]
+    lib.ndsi_factors_destroy.restype = None
+    lib.ndsi_profile_enable.argtypes = [vp, i32]
+    lib.ndsi_profile_read.argtypes = [vp, ctypes.POINTER(ndsi_profile_entry), i32,
+                                      ctypes.POINTER(i32)]
+    lib.ndsi_last_error.argtypes = []
+    lib.ndsi_last_error.restype = ctypes.c_char_p
+    for name in ("ndsi_poles", "ndsi_analyze", "ndsi_plan_info", "ndsi_plan_export",
+                 "ndsi_factor_poles", "ndsi_selinv", "ndsi_density", "ndsi_profile_enable",
+                 "ndsi_profile_read"):
+        getattr(lib, name).restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def _check(rc):
+    if rc != NDSI_OK:
+        raise NdsiError(rc, load().ndsi_last_error().decode())
+
+
+def _ptr(x):
+    """Raw address of a torch tensor / numpy array (None -> NULL)."""
+    if x is None:
+        return None
+    if hasattr(x, "data_ptr"):
+        if not x.is_contiguous():
+            raise ValueError("contiguous tensor required")
+        return ctypes.c_void_p(x.data_ptr())
+    if isinstance(x, np.ndarray):
+        if not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("contiguous array required")
+        return ctypes.c_void_p(x.ctypes.data)
+    raise TypeError(type(x))
+
+
+def _stream(stream):
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+        except ImportError:
+            pass
+        return None
+    if hasattr(stream, "cuda_stream"):
+        return ctypes.c_void_p(stream.cuda_stream)
+    return ctypes.c_void_p(int(stream))
+
+
+def ndsi_default_options():
+    o = ndsi_options()
+    load().ndsi_default_options(ctypes.byref(o))
+    return o
+
+
+def ndsi_poles(M: int):
+    """(z, R): poles and residues of the Eq. 7 fraction with M pole pairs (host)."""
+    z = np.zeros(M)
+    R = np.zeros(M)
+    _check(load().ndsi_poles(int(M), _ptr(z), _ptr(R)))
+    return z, R
+
+
+class Plan:
+    """Owner of an ndsi_plan handle."""
+
+    def __init__(self, handle):
+        self.handle = handle
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.ndsi_plan_destroy(self.handle)
+            self.handle = None
+
+
+class Factors:
+    """Owner of an ndsi_factors handle (keeps its plan alive)."""
+
+    def __init__(self, handle, plan, n_poles):
+        self.handle = handle
+        self.plan = plan
+        self.n_poles = n_poles
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.ndsi_factors_destroy(self.handle)
+            self.handle = None
+
+
+def ndsi_analyze(n, rowptr, col, n_atoms, centers, atom_of_basis, options=None) -> Plan:
+    rowptr = np.ascontiguousarray(rowptr, dtype=np.int64)
+    col = np.ascontiguousarray(col, dtype=np.int32)
+    centers = np.ascontiguousarray(centers, dtype=np.float64)
+    aob = np.ascontiguousarray(atom_of_basis, dtype=np.int32)
+    pat = ndsi_pattern(int(n), rowptr.ctypes.data, col.ctypes.data)
+    opt = options if options is not None else ndsi_default_options()
+    h = ctypes.c_void_p()
+    _check(load().ndsi_analyze(ctypes.byref(pat), int(n_atoms), _ptr(centers), _ptr(aob),
+                               ctypes.byref(opt), ctypes.byref(h)))
+    return Plan(h)
+
+
+def ndsi_plan_info(plan: Plan) -> dict:
+    s = ndsi_plan_summary()
+    _check(load().ndsi_plan_info(plan.handle, ctypes.byref(s)))
+    return {name: getattr(s, name) for name, _ in ndsi_plan_summary._fields_}
+
+
+def ndsi_plan_export(plan: Plan, what: str) -> np.ndarray:
+    info = ndsi_plan_info(plan)
+    nn = info["n_nodes"]
+    if what == "struct_atoms":
+        ptr = ndsi_plan_export(plan, "struct_ptr")
+        out = np.zeros(max(int(ptr[-1]), 1), dtype=np.int32)
+        _check(load().ndsi_plan_export(plan.handle, EXPORT[what], _ptr(out)))
+        return out[:int(ptr[-1])]
+    sizes = dict(perm_atoms=(info["n_atoms"], np.int32), perm_basis=(info["n"], np.int32),
+                 node_atoms=(nn + 1, np.int32), parent=(nn, np.int32),
+                 struct_ptr=(nn + 1, np.int64), level=(nn, np.int32))
+    cnt, dt = sizes[what]
+    out = np.zeros(cnt, dtype=dt)
+    _check(load().ndsi_plan_export(plan.handle, EXPORT[what], _ptr(out)))
+    return out
+
+
+def ndsi_factor_poles(plan: Plan, H, S, z, stream=None) -> Factors:
+    z = np.ascontiguousarray(np.asarray(z, dtype=np.complex128))
+    zz = np.ascontiguousarray(z.view(np.float64))
+    h = ctypes.c_void_p()
+    _check(load().ndsi_factor_poles(plan.handle, _ptr(H), _ptr(S), _ptr(zz), int(z.shape[0]),
+                                    ctypes.byref(h), _stream(stream)))
+    return Factors(h, plan, int(z.shape[0]))
+
+
+def ndsi_selinv(factors: Factors, G_out=None, stream=None):
+    _check(load().ndsi_selinv(factors.handle, _ptr(G_out), _stream(stream)))
+    return G_out
+
+
+def ndsi_density(plan: Plan, H, S, mu, kT, n_poles, rho_out, n_elec_out=None, stream=None):
+    _check(load().ndsi_density(plan.handle, _ptr(H), _ptr(S), float(mu), float(kT), int(n_poles),
+                               _ptr(rho_out), _ptr(n_elec_out), _stream(stream)))
+    return rho_out
+
+
+def analyze_system(system, **options) -> Plan:
+    """ndsi_analyze on a synth.System-like object (fields n, rowptr, col, centers, atom_of_basis)."""
+    opt = ndsi_default_options()
+    for k, v in options.items():
+        setattr(opt, k, v)
+    return ndsi_analyze(system.n, system.rowptr, system.col, system.centers.shape[0],
+                        system.centers, system.atom_of_basis, opt)
+
+
+def ndsi_profile_enable(plan: Plan, enable: bool = True):
+    _check(load().ndsi_profile_enable(plan.handle, 1 if enable else 0))
+
+
+def ndsi_profile_read(plan: Plan) -> dict:
+    """{family: dict(launches, ms, flops, bytes)} accumulated since ndsi_profile_enable."""
+    buf = (ndsi_profile_entry * 16)()
+    n = ctypes.c_int32()
+    _check(load().ndsi_profile_read(plan.handle, buf, 16, ctypes.byref(n)))
+    return {buf[i].name.decode(): dict(launches=buf[i].launches, ms=buf[i].ms, flops=buf[i].flops,
+                                       bytes=buf[i].bytes) for i in range(n.value)}
