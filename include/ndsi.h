@@ -171,6 +171,27 @@ int ndsi_profile_enable(ndsi_plan* plan, int32_t enable);
 int ndsi_profile_read(const ndsi_plan* plan, ndsi_profile_entry* out, int32_t max_entries,
                       int32_t* n_out);
 
+/* Residue sum and electron count from caller-held G, allocating no device memory.
+ * The paper has no counterpart: this is a library convenience for callers that cannot call
+ * cudaMalloc (a host framework that owns the whole device-memory budget, or a latency-critical
+ * path where cudaMalloc/cudaFree, which can synchronise the device, are not allowed).  It runs the
+ * residue-sum kernel of ndsi_density with its partial traces kept in a fixed 256 KiB
+ * file-scope __device__ array instead of an allocated buffer:
+ *   rho_out[k]  = sum_q Re(c_q * G[q][k])         (the contour sum of Eq. 8),
+ *   *n_elec_out = sum_k rho_out[k] * S[k]          (Tr(rho S), Eq. 40).
+ *   G          - device, interleaved complex double[2 * n_points * nnz], point-major (the layout
+ *                ndsi_selinv writes).
+ *   c          - device, interleaved complex double[2 * n_points]: w_p = -4 R_p kT for the poles
+ *                alpha_p, and iR for the zeroth-moment point iR.
+ *   S          - device double[nnz]; rho_out device double[nnz]; n_elec_out device double or NULL.
+ * Limit: nnz <= 8,388,608 (32768 blocks of 256 entries); larger nnz -> NDSI_ERR_INVALID.
+ * Host pointers -> NDSI_ERR_INVALID.  Stream-ordered, no synchronisation.  The first call on a
+ * device resolves the array's device address (cudaGetSymbolAddress) with that device current,
+ * so make that first call before any stream capture.  Every call on a device shares the one
+ * array: calls whose kernels overlap on the GPU (other streams or threads) race on it. */
+int ndsi_residue_sum_static(const double* G, const double* c, int32_t n_points, const double* S,
+                            int64_t nnz, double* rho_out, double* n_elec_out, void* stream);
+
 void ndsi_plan_destroy(ndsi_plan* plan);
 void ndsi_factors_destroy(ndsi_factors* f);
 

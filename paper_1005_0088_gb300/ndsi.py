@@ -31,6 +31,7 @@ EXPORTED_SYMBOLS = (
     "ndsi_default_options", "ndsi_poles", "ndsi_analyze", "ndsi_plan_info", "ndsi_plan_export",
     "ndsi_factor_poles", "ndsi_selinv", "ndsi_density", "ndsi_plan_destroy",
     "ndsi_factors_destroy", "ndsi_last_error", "ndsi_profile_enable", "ndsi_profile_read",
+    "ndsi_residue_sum_static",
 )
 
 
@@ -92,6 +93,8 @@ def load(path: str = LIB_PATH):
     lib.ndsi_profile_enable.argtypes = [vp, i32]
     lib.ndsi_profile_read.argtypes = [vp, ctypes.POINTER(ndsi_profile_entry), i32,
                                       ctypes.POINTER(i32)]
+    lib.ndsi_residue_sum_static.argtypes = [vp, vp, i32, vp, i64, vp, vp, vp]
+    lib.ndsi_residue_sum_static.restype = ctypes.c_int
     lib.ndsi_last_error.argtypes = []
     lib.ndsi_last_error.restype = ctypes.c_char_p
     for name in ("ndsi_poles", "ndsi_analyze", "ndsi_plan_info", "ndsi_plan_export",
@@ -252,3 +255,10 @@ def ndsi_profile_read(plan: Plan) -> dict:
     _check(load().ndsi_profile_read(plan.handle, buf, 16, ctypes.byref(n)))
     return {buf[i].name.decode(): dict(launches=buf[i].launches, ms=buf[i].ms, flops=buf[i].flops,
                                        bytes=buf[i].bytes) for i in range(n.value)}
+
+
+def ndsi_residue_sum_static(G, c, n_points, S, nnz, rho_out, n_elec_out=None, stream=None):
+    """rho and Tr(rho S) from caller-held G without any device allocation (device arrays only)."""
+    _check(load().ndsi_residue_sum_static(_ptr(G), _ptr(c), int(n_points), _ptr(S), int(nnz),
+                                          _ptr(rho_out), _ptr(n_elec_out), _stream(stream)))
+    return rho_out
