@@ -12,12 +12,15 @@
 #include "kernels.cuh"
 #include "ndsi.h"
 #include "plan.hpp"
+#include "split_gemm.cuh"
 
 namespace ndsi {
 // Event-timed launch records, resolved after the stream synchronises.
-constexpr int kFamilies = 8;
-static const char* const kFamilyName[kFamilies] = {"gemm_f64", "diaginv", "assemble", "scatter",
-                                                   "copy", "gather", "accumulate", "reduce"};
+constexpr int kFamSplit = 8;
+constexpr int kFamiliesAll = 9;
+static const char* const kFamilyName[kFamiliesAll] = {"gemm_f64", "diaginv", "assemble", "scatter",
+                                                      "copy", "gather", "accumulate", "reduce",
+                                                      "gemm_split"};
 struct ProfRec {
     int family;
     double flops, bytes;
@@ -28,14 +31,29 @@ struct Profiler {
     std::vector<cudaEvent_t> pool;
     size_t used = 0;
     std::vector<ProfRec> pending;
-    double ms[kFamilies] = {}, flops[kFamilies] = {}, bytes[kFamilies] = {};
-    int64_t launches[kFamilies] = {};
+    double ms[kFamiliesAll] = {}, flops[kFamiliesAll] = {}, bytes[kFamiliesAll] = {};
+    int64_t launches[kFamiliesAll] = {};
+};
+
+// Split-precision metadata of a plan (built when opt.precision == NDSI_PREC_SPLIT).
+struct SplitPlan {
+    std::vector<SplitItem> items;
+    std::vector<SplitStep> steps;
+    std::vector<GemmTile> tiles;
+    std::vector<SliceBlock> blocks;
+    std::vector<int32_t> step_of_launch;
+    SplitItem* d_items = nullptr;
+    GemmTile* d_tiles = nullptr;
+    SliceBlock* d_blocks = nullptr;
+    void* blob = nullptr;
 };
 }  // namespace ndsi
 
 struct ndsi_plan {
     ndsi::Plan P;
     ndsi::Profiler prof;
+    ndsi::SplitPlan SP;
+    ndsi::SplitBuffers SB;       // slice buffers of the density workspace
     ndsi::DevTables T;
     int device = -1;
     // density workspace (reused across calls)
@@ -53,6 +71,7 @@ struct ndsi_plan {
 struct ndsi_factors {
     ndsi_plan* plan = nullptr;
     ndsi::Workspace W;
+    ndsi::SplitBuffers SB;
     double2* zd = nullptr;
     int32_t np = 0;
 };
@@ -127,6 +146,20 @@ int upload_tables(ndsi_plan* h) {
     }
     NDSI_CK(cudaMemset(T.status, 0, sizeof(int) * 4));
     NDSI_CK(kernels_init());
+    if (P.opt.precision == NDSI_PREC_SPLIT) {
+        SplitPlan& S = h->SP;
+        const size_t bi = align256(std::max<size_t>(bytes_of(S.items), 16));
+        const size_t bt = align256(std::max<size_t>(bytes_of(S.tiles), 16));
+        const size_t bb = align256(std::max<size_t>(bytes_of(S.blocks), 16));
+        NDSI_CK(cudaMalloc(&S.blob, bi + bt + bb));
+        S.d_items = reinterpret_cast<SplitItem*>(S.blob);
+        S.d_tiles = reinterpret_cast<GemmTile*>(static_cast<char*>(S.blob) + bi);
+        S.d_blocks = reinterpret_cast<SliceBlock*>(static_cast<char*>(S.blob) + bi + bt);
+        if (!S.items.empty()) NDSI_CK(cudaMemcpy(S.d_items, S.items.data(), bytes_of(S.items), cudaMemcpyHostToDevice));
+        if (!S.tiles.empty()) NDSI_CK(cudaMemcpy(S.d_tiles, S.tiles.data(), bytes_of(S.tiles), cudaMemcpyHostToDevice));
+        if (!S.blocks.empty()) NDSI_CK(cudaMemcpy(S.d_blocks, S.blocks.data(), bytes_of(S.blocks), cudaMemcpyHostToDevice));
+        NDSI_CK(split_init());
+    }
     return NDSI_OK;
 }
 
@@ -212,13 +245,28 @@ void prof_resolve(Profiler& pf) {
     pf.used = 0;
 }
 
-int run_phase(ndsi_plan* h, const Workspace& W, int phase, const double* H, const double* S,
-              const double2* z, int np, cudaStream_t st) {
+int run_phase(ndsi_plan* h, const Workspace& W, const SplitBuffers& SB, int phase, const double* H,
+              const double* S, const double2* z, int np, cudaStream_t st) {
     const Plan& P = h->P;
-    for (const Launch& l : P.launches) {
+    const bool split = P.opt.precision == NDSI_PREC_SPLIT;
+    for (size_t li = 0; li < P.launches.size(); ++li) {
+        const Launch& l = P.launches[li];
         if (l.phase != phase) continue;
-        cudaError_t e = timed(h->prof, family_of(l.kind), l.flops * np, l.bytes * np, st,
-                              [&]() { return launch_step(P, h->T, l, W, H, S, z, np, st); });
+        cudaError_t e;
+        if (split && l.kind == L_GEMM) {
+            const int si = h->SP.step_of_launch[li];
+            const double2* bufs[2] = {W.fronts, W.scr};
+            const int64_t strides[2] = {W.front_stride, W.scr_stride};
+            e = timed(h->prof, kFamSplit, l.flops * np, l.bytes * np, st, [&]() {
+                return split_gemm_step(l, si, h->T.gemm_items, h->SP.d_items, h->SP.d_tiles, h->SP.d_blocks,
+                                       h->SP.steps[si], SB, P.opt.split_slices, bufs[l.bufA], strides[l.bufA],
+                                       bufs[l.bufB], strides[l.bufB], const_cast<double2*>(bufs[l.bufC]),
+                                       strides[l.bufC], np, h->T.status, st);
+            });
+        } else {
+            e = timed(h->prof, family_of(l.kind), l.flops * np, l.bytes * np, st,
+                      [&]() { return launch_step(P, h->T, l, W, H, S, z, np, st); });
+        }
         if (e != cudaSuccess)
             return fail(NDSI_ERR_CUDA, std::string("kernel launch (step ") + std::to_string(l.tag) +
                                            "): " + cudaGetErrorString(e));
@@ -272,6 +320,22 @@ int device_inputs(ndsi_plan* h, const double* H, const double* S, const double**
     return NDSI_OK;
 }
 
+// Device bytes one pole needs: fronts, scratch and (split mode) the largest step's slices.
+int64_t bytes_per_pole(const ndsi_plan* h) {
+    int64_t b = int64_t(16) * (h->P.front_total + h->P.scr_total);
+    if (h->P.opt.precision == NDSI_PREC_SPLIT) {
+        int64_t a = 0, bb = 0, ea = 0, eb = 0;
+        for (const SplitStep& st : h->SP.steps) {
+            a = std::max<int64_t>(a, st.rowsA * st.Kcols);
+            bb = std::max<int64_t>(bb, st.rowsB * st.Kcols);
+            ea = std::max<int64_t>(ea, st.erowsA);
+            eb = std::max<int64_t>(eb, st.erowsB);
+        }
+        b += 2 * (a + bb) + 4 * (ea + eb);
+    }
+    return b;
+}
+
 int64_t workspace_cap(const ndsi_plan* h) {
     if (h->P.opt.max_workspace_bytes > 0) return h->P.opt.max_workspace_bytes;
     size_t freeb = 0, totalb = 0;
@@ -279,8 +343,7 @@ int64_t workspace_cap(const ndsi_plan* h) {
         cudaGetLastError();
         return int64_t(8) << 30;
     }
-    int64_t have = static_cast<int64_t>(freeb) +
-                   static_cast<int64_t>(h->W.np_cap) * 16 * (h->W.front_stride + h->W.scr_stride);
+    int64_t have = static_cast<int64_t>(freeb) + static_cast<int64_t>(h->W.np_cap) * bytes_per_pole(h);
     return static_cast<int64_t>(0.85 * static_cast<double>(have));
 }
 
@@ -335,6 +398,18 @@ int ndsi_analyze(const ndsi_pattern* pat, int32_t n_atoms, const double* centers
         delete h;
         return fail(rc, err);
     }
+    if (o.precision == NDSI_PREC_SPLIT) {
+        if (o.split_slices < 4 || o.split_slices > kSplitMaxSlices) {
+            delete h;
+            return fail(NDSI_ERR_INVALID, "ndsi_analyze: split_slices must be in [4, 7]");
+        }
+        SplitPlan& S = h->SP;
+        build_split_schedule(h->P, o.split_slices, S.items, S.steps, S.tiles, S.blocks);
+        S.step_of_launch.assign(h->P.launches.size(), -1);
+        int k = 0;
+        for (size_t li = 0; li < h->P.launches.size(); ++li)
+            if (h->P.launches[li].kind == L_GEMM) S.step_of_launch[li] = k++;
+    }
     *plan_out = h;
     return NDSI_OK;
 }
@@ -377,12 +452,10 @@ int ndsi_factor_poles(ndsi_plan* h, const double* H, const double* S, const doub
     if (!h || !H || !S || !z || !f_out || n_poles < 1)
         return fail(NDSI_ERR_INVALID, "ndsi_factor_poles: invalid argument");
     *f_out = nullptr;
-    if (h->P.opt.precision != NDSI_PREC_FP64)
-        return fail(NDSI_ERR_UNSUPPORTED, "ndsi_factor_poles: split precision not built in this library");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     int rc = upload_tables(h);
     if (rc) return rc;
-    const int64_t need = int64_t(16) * n_poles * (h->P.front_total + h->P.scr_total);
+    const int64_t need = int64_t(n_poles) * bytes_per_pole(h);
     if (h->P.opt.max_workspace_bytes > 0 && need > h->P.opt.max_workspace_bytes)
         return fail(NDSI_ERR_OOM, "ndsi_factor_poles: factors exceed max_workspace_bytes");
     std::unique_ptr<ndsi_factors> f(new (std::nothrow) ndsi_factors());
@@ -401,15 +474,25 @@ int ndsi_factor_poles(ndsi_plan* h, const double* H, const double* S, const doub
     }
     auto cleanup = [&]() {
         free_workspace(f->W);
+        split_free(f->SB);
         cudaFree(f->zd);
     };
+    if (h->P.opt.precision == NDSI_PREC_SPLIT) {
+        cudaError_t e = split_alloc(f->SB, h->SP.steps, h->P.opt.split_slices, n_poles);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            cleanup();
+            return fail(e == cudaErrorMemoryAllocation ? NDSI_ERR_OOM : NDSI_ERR_CUDA,
+                        std::string("ndsi_factor_poles: split buffers: ") + cudaGetErrorString(e));
+        }
+    }
     if (cudaMemcpyAsync(f->zd, z, sizeof(double2) * n_poles, cudaMemcpyHostToDevice, st) != cudaSuccess) {
         cleanup();
         return fail(NDSI_ERR_CUDA, "ndsi_factor_poles: pole upload failed");
     }
     const double *Hd, *Sd;
     rc = device_inputs(h, H, S, &Hd, &Sd, st);
-    if (!rc) rc = run_phase(h, f->W, 0, Hd, Sd, f->zd, n_poles, st);
+    if (!rc) rc = run_phase(h, f->W, f->SB, 0, Hd, Sd, f->zd, n_poles, st);
     if (rc) {
         cleanup();
         return rc;
@@ -422,7 +505,7 @@ int ndsi_selinv(ndsi_factors* f, double* G_out, void* stream) {
     if (!f || !f->plan) return fail(NDSI_ERR_INVALID, "ndsi_selinv: NULL factors");
     ndsi_plan* h = f->plan;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    int rc = run_phase(h, f->W, 1, nullptr, nullptr, f->zd, f->np, st);
+    int rc = run_phase(h, f->W, f->SB, 1, nullptr, nullptr, f->zd, f->np, st);
     if (rc) return rc;
     if (G_out) {
         const bool dev = is_device_ptr(G_out);
@@ -446,8 +529,6 @@ int ndsi_density(ndsi_plan* h, const double* H, const double* S, double mu, doub
                  double* rho_out, double* n_elec_out, void* stream) {
     if (!h || !H || !S || !rho_out || n_poles < 1 || !(kT > 0) || !std::isfinite(mu))
         return fail(NDSI_ERR_INVALID, "ndsi_density: invalid argument");
-    if (h->P.opt.precision != NDSI_PREC_FP64)
-        return fail(NDSI_ERR_UNSUPPORTED, "ndsi_density: split precision not built in this library");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     int rc = upload_tables(h);
     if (rc) return rc;
@@ -470,12 +551,13 @@ int ndsi_density(ndsi_plan* h, const double* H, const double* S, double mu, doub
     zq[n_poles] = make_double2(0.0, R);
     cq[n_poles] = make_double2(0.0, R);
     // chunk the points to the workspace cap
-    const int64_t per_pole = int64_t(16) * (h->P.front_total + h->P.scr_total);
+    const int64_t per_pole = bytes_per_pole(h);
     int64_t cap = workspace_cap(h);
     int32_t chunk = static_cast<int32_t>(std::min<int64_t>(nq, std::max<int64_t>(1, cap / per_pole)));
     if (cap < per_pole) return fail(NDSI_ERR_OOM, "ndsi_density: one pole does not fit the workspace cap");
     rc = alloc_workspace(h->W, h->P, chunk);
     if (rc) return rc;
+    if (h->P.opt.precision == NDSI_PREC_SPLIT) NDSI_CK(split_alloc(h->SB, h->SP.steps, h->P.opt.split_slices, chunk));
     if (h->cw_cap < nq) {
         if (h->cw) cudaFree(h->cw);
         if (h->zw) cudaFree(h->zw);
@@ -501,8 +583,8 @@ int ndsi_density(ndsi_plan* h, const double* H, const double* S, double mu, doub
     double* ne_d = ne_dev ? n_elec_out : h->stage + 3 * h->P.nnz;
     for (int32_t q0 = 0; q0 < nq; q0 += chunk) {
         const int32_t np = std::min(chunk, nq - q0);
-        rc = run_phase(h, h->W, 0, Hd, Sd, h->zw + q0, np, st);
-        if (!rc) rc = run_phase(h, h->W, 1, Hd, Sd, h->zw + q0, np, st);
+        rc = run_phase(h, h->W, h->SB, 0, Hd, Sd, h->zw + q0, np, st);
+        if (!rc) rc = run_phase(h, h->W, h->SB, 1, Hd, Sd, h->zw + q0, np, st);
         if (rc) return rc;
         const int last = q0 + np >= nq;
         const double acc_bytes = static_cast<double>(h->P.nnz) * (8.0 + 16.0 * np + 8.0 + 8.0 +
@@ -525,10 +607,10 @@ int ndsi_profile_enable(ndsi_plan* h, int32_t enable) {
     Profiler& pf = h->prof;
     pf.on = enable != 0;
     if (pf.on) {
-        std::fill(pf.ms, pf.ms + kFamilies, 0.0);
-        std::fill(pf.flops, pf.flops + kFamilies, 0.0);
-        std::fill(pf.bytes, pf.bytes + kFamilies, 0.0);
-        std::fill(pf.launches, pf.launches + kFamilies, int64_t(0));
+        std::fill(pf.ms, pf.ms + kFamiliesAll, 0.0);
+        std::fill(pf.flops, pf.flops + kFamiliesAll, 0.0);
+        std::fill(pf.bytes, pf.bytes + kFamiliesAll, 0.0);
+        std::fill(pf.launches, pf.launches + kFamiliesAll, int64_t(0));
         pf.pending.clear();
         pf.used = 0;
     }
@@ -540,7 +622,7 @@ int ndsi_profile_read(const ndsi_plan* h, ndsi_profile_entry* out, int32_t max_e
         return fail(NDSI_ERR_INVALID, "ndsi_profile_read: invalid argument");
     const Profiler& pf = h->prof;
     int32_t n = 0;
-    for (int f = 0; f < kFamilies && n < max_entries; ++f) {
+    for (int f = 0; f < kFamiliesAll && n < max_entries; ++f) {
         if (pf.launches[f] == 0) continue;
         ndsi_profile_entry& e = out[n++];
         std::memset(&e, 0, sizeof(e));
@@ -557,6 +639,7 @@ int ndsi_profile_read(const ndsi_plan* h, ndsi_profile_entry* out, int32_t max_e
 void ndsi_factors_destroy(ndsi_factors* f) {
     if (!f) return;
     free_workspace(f->W);
+    split_free(f->SB);
     if (f->zd) cudaFree(f->zd);
     delete f;
 }
@@ -564,6 +647,8 @@ void ndsi_factors_destroy(ndsi_factors* f) {
 void ndsi_plan_destroy(ndsi_plan* h) {
     if (!h) return;
     free_workspace(h->W);
+    split_free(h->SB);
+    if (h->SP.blob) cudaFree(h->SP.blob);
     for (cudaEvent_t e : h->prof.pool) cudaEventDestroy(e);
     if (h->T.blob) cudaFree(h->T.blob);
     if (h->cw) cudaFree(h->cw);

@@ -1,0 +1,718 @@
+// Emulated-FP64 complex GEMM on the tcgen05 tensor cores (the separator Schur updates and the
+// selected-inverse products of the factor and selinv schedules).
+//
+// Method (an error-free splitting in the spirit of Ozaki, Ogita, Oishi and Rump's scheme, with
+// BF16 digits and FP32 tensor-core accumulation):
+//  * complex operands are stacked as real matrices: A'' = [Re A | Im A] (M x 2K) and, per
+//    64-column tile of B, 64 rows [Re B | -Im B] followed by 64 rows [Im B | Re B], so that one
+//    real product gives Re C in the first 64 accumulator columns and Im C in the next 64;
+//  * every row of A'' (column of B) is scaled by a power of two 2^E with |x| < 2^E and written as
+//    S balanced base-256 digits, x = 2^(E-7) sum_t d_t 2^(-8(t-1)), d_1 in [-128,128],
+//    d_t in [-128,127]; digit t is stored pre-scaled, d_t 2^(-8(t-1)), exactly as BF16.  The
+//    digits come from the FP64 bit pattern with integer operations only;
+//  * the slice products A_t B_u^T with t+u <= S+1 are accumulated in TMEM in four bands:
+//    t+u = 2, 3, 4 each in its own accumulator, where every partial sum over a 256-element K
+//    chunk is an integer below 2^24 times a power of two and so exact in FP32; those three are
+//    read out after every chunk into a per-element float-float (hi, lo) sum.  t+u >= 5 share one
+//    accumulator, also read out per chunk: the tensor core truncates products that are not
+//    multiples of the accumulator's ulp, so mixed-scale sums must stay short;
+//  * the epilogue scales by 2^(E_m + F_n - 14) and forms C = alpha*(hi+lo)*scale + beta*C in FP64.
+// Pipeline: warp 0 issues TMA loads (2 stages of S+S 128x32 BF16 tiles, 64-byte swizzle), warp 1
+// issues the MMAs (M=128, N=128, K=16), warps 2-17 read TMEM (4 per lane quarter, 32 columns each).  Every mbarrier wait is bounded: on
+// time-out the kernel flags NDSI timeout status, drains what it issued and frees its TMEM.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdint>
+
+#include "kernels.cuh"
+#include "split_gemm.cuh"
+
+namespace ndsi {
+
+void build_split_schedule(const Plan& P, int slices, std::vector<SplitItem>& items,
+                          std::vector<SplitStep>& steps, std::vector<GemmTile>& tiles,
+                          std::vector<SliceBlock>& blocks) {
+    items.assign(P.gemm_items.size(), SplitItem{});
+    steps.clear();
+    tiles.clear();
+    blocks.clear();
+    for (const Launch& l : P.launches) {
+        if (l.kind != L_GEMM) continue;
+        SplitStep st{};
+        int32_t kmax = 0;
+        st.tfirst = static_cast<int64_t>(tiles.size());
+        st.sa_first = static_cast<int64_t>(blocks.size());
+        for (int64_t i = 0; i < l.count; ++i) {
+            const GemmItem& g = P.gemm_items[l.first + i];
+            SplitItem& s = items[l.first + i];
+            s.Mpad = (g.M + kSplitBM - 1) / kSplitBM * kSplitBM;
+            s.Npad = (g.N + kSplitBNc - 1) / kSplitBNc * kSplitBNc;
+            s.Kpad = (g.K + kSplitKB - 1) / kSplitKB * kSplitKB;
+            s.rowA = st.rowsA;
+            s.rowB = st.rowsB;
+            s.erowA = st.erowsA;
+            s.erowB = st.erowsB;
+            st.rowsA += static_cast<int64_t>(slices) * s.Mpad;
+            st.rowsB += static_cast<int64_t>(slices) * 2 * s.Npad;
+            st.erowsA += s.Mpad;
+            st.erowsB += s.Npad;
+            kmax = std::max(kmax, s.Kpad);
+            for (int32_t m0 = 0; m0 < g.M; m0 += kSplitBM)
+                for (int32_t n0 = 0; n0 < g.N; n0 += kSplitBNc) {
+                    if (l.lower && n0 > m0 + kSplitBM - 1) continue;
+                    tiles.push_back(GemmTile{static_cast<int32_t>(i), m0, n0, 0});
+                }
+        }
+        st.tcount = static_cast<int64_t>(tiles.size()) - st.tfirst;
+        for (int64_t i = 0; i < l.count; ++i) {
+            const GemmItem& g = P.gemm_items[l.first + i];
+            for (int32_t r0 = 0; r0 < g.M; r0 += 64) blocks.push_back(SliceBlock{static_cast<int32_t>(i), r0});
+        }
+        st.sa_count = static_cast<int64_t>(blocks.size()) - st.sa_first;
+        st.sb_first = static_cast<int64_t>(blocks.size());
+        for (int64_t i = 0; i < l.count; ++i) {
+            const GemmItem& g = P.gemm_items[l.first + i];
+            for (int32_t n0 = 0; n0 < g.N; n0 += 64) blocks.push_back(SliceBlock{static_cast<int32_t>(i), n0});
+        }
+        st.sb_count = static_cast<int64_t>(blocks.size()) - st.sb_first;
+        st.Kcols = std::max(64, 2 * kmax);
+        st.Kcols = (st.Kcols + 63) / 64 * 64;
+        steps.push_back(st);
+    }
+}
+
+namespace {
+
+// ------------------------------------------------------------------------------------ PTX ---
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(done)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+constexpr uint64_t kWaitLimitNs = 2000000000ull;  // 2 s
+
+// Wait for the given phase parity; gives up (raising *abort) after kWaitLimitNs or when another
+// role already aborted.
+__device__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = global_ns();
+    while (true) {
+        if (*abort) return false;
+        if (mbar_try_wait(bar, parity)) return true;
+        if (global_ns() - t0 > kWaitLimitNs) {
+            *abort = 1;
+            return false;
+        }
+    }
+}
+// Bounded wait used while draining after an abort (ignores the abort flag).
+__device__ bool mbar_wait_drain(uint64_t* bar, uint32_t parity) {
+    const uint64_t t0 = global_ns();
+    while (!mbar_try_wait(bar, parity)) {
+        if (global_ns() - t0 > kWaitLimitNs) return false;
+    }
+    return true;
+}
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+            smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+        : "memory");
+}
+__device__ __forceinline__ void tmem_alloc(uint32_t* holder, uint32_t ncols) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(holder)),
+                 "r"(ncols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void umma_bf16(uint32_t d, uint64_t da, uint64_t db, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(d),
+        "l"(da), "l"(db), "r"(idesc), "r"(acc)
+        : "memory");
+}
+__device__ __forceinline__ void umma_commit(uint64_t* bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                     smem_u32(bar))
+                 : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float* v) {
+    uint32_t r[8];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Shared-memory matrix descriptor: K-major tile of 8-row x 64-byte swizzle atoms stacked along M
+// (stride 512 bytes), descriptor version 1, 64-byte swizzle.
+__device__ __forceinline__ uint64_t sdesc_sw64(uint32_t saddr) {
+    uint64_t d = static_cast<uint64_t>((saddr >> 4) & 0x3FFFu);
+    d |= static_cast<uint64_t>(1) << 16;
+    d |= static_cast<uint64_t>(512 >> 4) << 32;
+    d |= static_cast<uint64_t>(1) << 46;
+    d |= static_cast<uint64_t>(4) << 61;
+    return d;
+}
+// Instruction descriptor: D = F32, A = B = BF16, both K-major, N = 128, M = 128.
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((128u >> 3) << 17) | ((128u >> 4) << 24);
+
+// float-float accumulation hi + lo += v (Knuth's two-sum).
+__device__ __forceinline__ void ff_add(float& hi, float& lo, float v) {
+    const float s = hi + v;
+    const float bb = s - hi;
+    const float e = (hi - (s - bb)) + (v - bb);
+    hi = s;
+    lo += e;
+}
+
+// ----------------------------------------------------------------------------- slicing -----
+// Biased FP64 exponent of x with zero mapped to -1 (and subnormals to 1).
+__device__ __forceinline__ int fp64_expo(double x) {
+    const int64_t b = __double_as_longlong(x);
+    const int ex = static_cast<int>((b >> 52) & 0x7FF);
+    if ((b & 0x7FFFFFFFFFFFFFFFLL) == 0) return -1;
+    return ex == 0 ? 1 : ex;
+}
+
+// Balanced base-256 digits of x / 2^(E+1) * 2^(8S): d[0] in [-128,128], d[1..S-1] in [-128,127].
+template <int S>
+__device__ __forceinline__ void fp64_digits(double x, int E, int* d) {
+    const int64_t b = __double_as_longlong(x);
+    int ex = static_cast<int>((b >> 52) & 0x7FF);
+    int64_t mant = b & 0xFFFFFFFFFFFFFLL;
+    if (ex) mant |= 0x10000000000000LL; else ex = 1;
+    const int shift = ex - 1076 - E + 8 * S;
+    int64_t F;
+    if (shift >= 0) {
+        F = mant << shift;
+    } else {
+        const int rsh = -shift;
+        F = rsh >= 62 ? 0 : (((mant >> (rsh - 1)) + 1) >> 1);
+    }
+    if (b < 0) F = -F;
+#pragma unroll
+    for (int t = S - 1; t >= 1; --t) {
+        int low = static_cast<int>(F & 0xFF);
+        if (low >= 128) low -= 256;
+        d[t] = low;
+        F = (F - low) >> 8;
+    }
+    d[0] = static_cast<int>(F);
+}
+
+// BF16 bit pattern of d * 2^(-8t), |d| <= 128 (exact).
+__device__ __forceinline__ uint16_t bf16_digit(int d, int t) {
+    if (d == 0) return 0;
+    const uint32_t sgn = d < 0 ? 0x8000u : 0u;
+    const uint32_t a = static_cast<uint32_t>(d < 0 ? -d : d);
+    const int e = 31 - __clz(a);
+    const uint32_t mant = (a << (7 - e)) & 0x7Fu;
+    const uint32_t bexp = static_cast<uint32_t>(127 + e - 8 * t);
+    return static_cast<uint16_t>(sgn | (bexp << 7) | mant);
+}
+
+struct SliceArgs {
+    const GemmItem* items;
+    const SplitItem* sitems;
+    const SliceBlock* blocks;
+    int64_t bfirst, ifirst;
+    const double2* X;
+    int64_t sX;
+    int op;       // OP_N / OP_T / OP_S of the GEMM operand
+    int isB;
+    uint16_t* out;
+    int64_t rows_pole;
+    int32_t Kcols;
+    int32_t* expo;
+    int64_t erows_pole;
+};
+
+// Slices of one 64-row block of the stacked operand (A: rows m of op(A); B: columns n of op(B)).
+template <int S>
+__global__ void __launch_bounds__(256) k_slice(const SliceArgs p) {
+    __shared__ double2 tile[64][33];
+    __shared__ int rowmax[64];
+    const SliceBlock blk = p.blocks[p.bfirst + blockIdx.x];
+    const GemmItem it = p.items[p.ifirst + blk.item];
+    const SplitItem si = p.sitems[p.ifirst + blk.item];
+    const int64_t pole = blockIdx.y;
+    const int nrows = p.isB ? it.N : it.M;
+    const int K = it.K;
+    const double2* base = p.X + pole * p.sX + (p.isB ? it.b_off : it.a_off);
+    const int ld = p.isB ? it.ldb : it.lda;
+    const bool sym = p.op == OP_S;
+    const bool rows_contig = !sym && (p.isB ? p.op == OP_T : p.op == OP_N);
+    const int tid = threadIdx.x;
+    const int r0 = blk.r0;
+    if (tid < 64) rowmax[tid] = -1;
+    auto elem = [&](int row, int k) -> double2 {
+        if (sym) {
+            const int hi = row > k ? row : k, lo = row > k ? k : row;
+            return base[hi + static_cast<int64_t>(lo) * ld];
+        }
+        return rows_contig ? base[row + static_cast<int64_t>(k) * ld] : base[k + static_cast<int64_t>(row) * ld];
+    };
+    auto load_tile = [&](int k0) {
+        // 64 rows x 32 k, coalesced along the stored contiguous index
+        for (int e = tid; e < 64 * 32; e += 256) {
+            int r, kk;
+            if (rows_contig) {
+                r = e % 64;
+                kk = e / 64;
+            } else {
+                kk = e % 32;
+                r = e / 32;
+            }
+            const int row = r0 + r, k = k0 + kk;
+            tile[r][kk] = (row < nrows && k < K) ? elem(row, k) : make_double2(0.0, 0.0);
+        }
+    };
+    // phase 1: row exponents
+    __syncthreads();
+    int lmax = -1;
+    const int my_r = tid % 64, my_k = (tid / 64) * 8;
+    for (int k0 = 0; k0 < K; k0 += 32) {
+        load_tile(k0);
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const double2 v = tile[my_r][my_k + j];
+            lmax = max(lmax, max(fp64_expo(v.x), fp64_expo(v.y)));
+        }
+        __syncthreads();
+    }
+    atomicMax(&rowmax[my_r], lmax);
+    __syncthreads();
+    // phase 2: digits
+    const int kk = tid % 32;
+    for (int k0 = 0; k0 < si.Kpad; k0 += 32) {
+        load_tile(k0);
+        __syncthreads();
+        for (int r = tid / 32; r < 64; r += 8) {
+            const int row = r0 + r;
+            if (row >= nrows) continue;
+            const int E = rowmax[r] < 0 ? -1021 : rowmax[r] - 1022;
+            const double2 v = tile[r][kk];
+            int dr[S], di[S];
+            fp64_digits<S>(v.x, E, dr);
+            fp64_digits<S>(v.y, E, di);
+            const int64_t col = k0 + kk;
+#pragma unroll
+            for (int t = 0; t < S; ++t) {
+                if (!p.isB) {
+                    const int64_t orow = pole * p.rows_pole + si.rowA + static_cast<int64_t>(t) * si.Mpad + row;
+                    uint16_t* o = p.out + orow * p.Kcols;
+                    o[col] = bf16_digit(dr[t], t);
+                    o[si.Kpad + col] = bf16_digit(di[t], t);
+                } else {
+                    const int64_t orow = pole * p.rows_pole + si.rowB + static_cast<int64_t>(t) * 2 * si.Npad +
+                                         (row / 64) * 128 + (row % 64);
+                    uint16_t* o1 = p.out + orow * p.Kcols;
+                    uint16_t* o2 = p.out + (orow + 64) * p.Kcols;
+                    o1[col] = bf16_digit(dr[t], t);
+                    o1[si.Kpad + col] = bf16_digit(-di[t], t);
+                    o2[col] = bf16_digit(di[t], t);
+                    o2[si.Kpad + col] = bf16_digit(dr[t], t);
+                }
+            }
+        }
+        __syncthreads();
+    }
+    if (tid < 64 && r0 + tid < nrows) {
+        const int E = rowmax[tid] < 0 ? -1021 : rowmax[tid] - 1022;
+        p.expo[pole * p.erows_pole + (p.isB ? si.erowB : si.erowA) + r0 + tid] = E;
+    }
+}
+
+// ---------------------------------------------------------------------------- the GEMM -----
+struct GemmArgs {
+    const GemmItem* items;
+    const SplitItem* sitems;
+    const GemmTile* tiles;
+    int64_t tfirst, ifirst;
+    int64_t rowsA, rowsB, erowsA, erowsB;
+    const int32_t* expA;
+    const int32_t* expB;
+    double2* C;
+    int64_t sC;
+    double alpha, beta;
+    int lower;
+    int* status;
+};
+
+constexpr int kTileBytes = kSplitBM * kSplitKB * 2;  // 128 rows x 64 bytes
+constexpr int kThreads = 576;
+constexpr int kEpiWarps = 16;
+
+template <int S>
+constexpr int split_smem_bytes() {
+    return 2 * 2 * S * kTileBytes + 128 + 1024;
+}
+
+template <int S>
+__global__ void __launch_bounds__(kThreads, 1)
+    k_gemm_split(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const GemmArgs p) {
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + 2 * 2 * S * kTileBytes);
+    uint64_t* full = bars;            // [2]
+    uint64_t* empty = bars + 2;       // [2]
+    uint64_t* chunk_full = bars + 4;
+    uint64_t* tmem_free = bars + 5;
+    uint64_t* mma_done = bars + 6;
+    uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(bars + 8);
+    volatile int* abort = reinterpret_cast<volatile int*>(bars + 9);
+
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    const int64_t pole = blockIdx.y;
+    const int tile_item = p.tiles[p.tfirst + blockIdx.x].item;
+    const int nkb = 2 * p.sitems[p.ifirst + tile_item].Kpad / kSplitKB;
+    const int nchunks = (nkb + kSplitChunkKB - 1) / kSplitChunkKB;
+
+    if (threadIdx.x == 0) {
+        mbar_init(&full[0], 1);
+        mbar_init(&full[1], 1);
+        mbar_init(&empty[0], 1);
+        mbar_init(&empty[1], 1);
+        mbar_init(chunk_full, 1);
+        mbar_init(tmem_free, kEpiWarps);
+        mbar_init(mma_done, 1);
+        *abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) tmem_alloc(tmem_holder, 512);
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_holder;
+    auto a_tile = [&](int stage, int t) { return smem + (stage * 2 * S + t) * kTileBytes; };
+    auto b_tile = [&](int stage, int u) { return smem + (stage * 2 * S + S + u) * kTileBytes; };
+
+    if (warp == 0) {
+        if (lane == 0) {
+            const GemmTile tile = p.tiles[p.tfirst + blockIdx.x];
+            const SplitItem si = p.sitems[p.ifirst + tile.item];
+            const int yA0 = static_cast<int>(pole * p.rowsA + si.rowA + tile.m0);
+            const int yB0 = static_cast<int>(pole * p.rowsB + si.rowB + (tile.n0 / kSplitBNc) * 128);
+            int armed = 0;  // k-blocks whose loads were issued
+            for (int kb = 0; kb < nkb; ++kb) {
+                const int stage = kb & 1;
+                if (kb >= 2 && !mbar_wait(&empty[stage], ((kb >> 1) - 1) & 1, abort)) break;
+                mbar_expect_tx(&full[stage], 2 * S * kTileBytes);
+#pragma unroll
+                for (int t = 0; t < S; ++t) tma_load_2d(a_tile(stage, t), &tmA, kb * kSplitKB, yA0 + t * si.Mpad, &full[stage]);
+#pragma unroll
+                for (int u = 0; u < S; ++u)
+                    tma_load_2d(b_tile(stage, u), &tmB, kb * kSplitKB, yB0 + u * 2 * si.Npad, &full[stage]);
+                armed = kb + 1;
+            }
+            if (*abort) {
+                // drain: wait for the last (up to two) armed stages' copies to land
+                for (int kb = armed > 2 ? armed - 2 : 0; kb < armed; ++kb)
+                    mbar_wait_drain(&full[kb & 1], (kb >> 1) & 1);
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            bool tail_started = false;
+            int issued = 0;
+            for (int kb = 0; kb < nkb; ++kb) {
+                const int stage = kb & 1;
+                if (!mbar_wait(&full[stage], (kb >> 1) & 1, abort)) break;
+                tc_fence_after();
+                const int chunk = kb / kSplitChunkKB;
+                const bool first_in_chunk = (kb % kSplitChunkKB) == 0;
+                if (first_in_chunk) {
+                    tail_started = false;
+                    if (chunk > 0) {
+                        if (!mbar_wait(tmem_free, (chunk - 1) & 1, abort)) break;
+                        tc_fence_after();
+                    }
+                }
+                // band 3: slice pairs with t+u >= 5 (1-based), read out per chunk like the others
+#pragma unroll 1
+                for (int t = 0; t < S; ++t)
+#pragma unroll 1
+                    for (int u = 0; u < S; ++u) {
+                        if (t + u > S - 1 || t + u < 3) continue;
+#pragma unroll
+                        for (int ks = 0; ks < 2; ++ks) {
+                            const uint64_t da = sdesc_sw64(smem_u32(a_tile(stage, t)) + ks * 32);
+                            const uint64_t db = sdesc_sw64(smem_u32(b_tile(stage, u)) + ks * 32);
+                            umma_bf16(tmem + 3 * 128, da, db, kIdesc, tail_started ? 1u : 0u);
+                            tail_started = true;
+                        }
+                    }
+                // bands 0..2: t+u = 2, 3, 4 (1-based), exact within a chunk
+#pragma unroll 1
+                for (int band = 0; band < 3; ++band) {
+                    bool first = first_in_chunk;
+#pragma unroll 1
+                    for (int t = 0; t < S; ++t) {
+                        const int u = band - t;
+                        if (u < 0 || u >= S) continue;
+#pragma unroll
+                        for (int ks = 0; ks < 2; ++ks) {
+                            const uint64_t da = sdesc_sw64(smem_u32(a_tile(stage, t)) + ks * 32);
+                            const uint64_t db = sdesc_sw64(smem_u32(b_tile(stage, u)) + ks * 32);
+                            umma_bf16(tmem + band * 128, da, db, kIdesc, first ? 0u : 1u);
+                            first = false;
+                        }
+                    }
+                }
+                umma_commit(&empty[stage]);
+                if ((kb % kSplitChunkKB) == kSplitChunkKB - 1 || kb == nkb - 1) umma_commit(chunk_full);
+                issued = kb + 1;
+            }
+            umma_commit(mma_done);
+            (void)issued;
+        }
+    } else {
+        // epilogue: warp quarter q reads TMEM lanes 32q..32q+31; column group cg the accumulator
+        // columns 32cg..32cg+31 (cg 0,1: Re C; cg 2,3: Im C of the same 64 complex columns)
+        const int q = warp & 3;
+        const int cg = (warp - 2) >> 2;
+        float hi[32], lo[32];
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+            hi[j] = 0.f;
+            lo[j] = 0.f;
+        }
+        bool ok = true;
+        for (int c = 0; c < nchunks; ++c) {
+            if (!mbar_wait(chunk_full, c & 1, abort)) {
+                ok = false;
+                break;
+            }
+            tc_fence_after();
+            const int nb = 4;
+#pragma unroll
+            for (int band = 0; band < 4; ++band) {
+                if (band < nb) {
+#pragma unroll
+                    for (int j2 = 0; j2 < 4; ++j2) {
+                        float v[8];
+                        tmem_ld8(tmem + (static_cast<uint32_t>(32 * q) << 16) + band * 128 + cg * 32 + j2 * 8, v);
+#pragma unroll
+                        for (int i = 0; i < 8; ++i) ff_add(hi[j2 * 8 + i], lo[j2 * 8 + i], v[i]);
+                    }
+                }
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(tmem_free);
+        }
+        // stage (hi, lo) in the pipeline shared memory (idle once the last chunk completed), then
+        // all epilogue warps form C = alpha*scale*(hi+lo) + beta*C with coalesced complex stores
+        float* sm_hi = reinterpret_cast<float*>(smem);          // [128 columns][128 rows]
+        float* sm_lo = sm_hi + 128 * 128;
+        if (ok && !*abort) {
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+                const int col = cg * 32 + j;
+                sm_hi[col * 128 + 32 * q + lane] = hi[j];
+                sm_lo[col * 128 + 32 * q + lane] = lo[j];
+            }
+        }
+        asm volatile("bar.sync 1, %0;" ::"n"(kEpiWarps * 32) : "memory");
+        if (ok && !*abort) {
+            const GemmTile tile = p.tiles[p.tfirst + blockIdx.x];
+            const GemmItem it = p.items[p.ifirst + tile.item];
+            const SplitItem si = p.sitems[p.ifirst + tile.item];
+            const int et = threadIdx.x - 64;
+            double2* Cp = p.C + pole * p.sC + it.c_off;
+            for (int idx = et; idx < 128 * 64; idx += kEpiWarps * 32) {
+                const int r = idx % 128, j = idx / 128;
+                const int m = tile.m0 + r, n = tile.n0 + j;
+                if (m >= it.M || n >= it.N || (p.lower && n > m)) continue;
+                const int e0 = p.expA[pole * p.erowsA + si.erowA + m] + p.expB[pole * p.erowsB + si.erowB + n] - 14;
+                const int e = e0 < -1022 ? -1022 : (e0 > 1023 ? 1023 : e0);
+                const double scale = __longlong_as_double(static_cast<int64_t>(e + 1023) << 52) * p.alpha;
+                const double re = (static_cast<double>(sm_hi[j * 128 + r]) + static_cast<double>(sm_lo[j * 128 + r])) * scale;
+                const double im = (static_cast<double>(sm_hi[(64 + j) * 128 + r]) +
+                                   static_cast<double>(sm_lo[(64 + j) * 128 + r])) * scale;
+                double2* dst = Cp + m + static_cast<int64_t>(n) * it.ldc;
+                double2 v = make_double2(re, im);
+                if (p.beta != 0.0) {
+                    const double2 old = *dst;
+                    v.x += p.beta * old.x;
+                    v.y += p.beta * old.y;
+                }
+                *dst = v;
+            }
+        }
+    }
+    __syncthreads();
+    if (warp == 1) {
+        if (*abort) {
+            if (lane == 0) mbar_wait_drain(mma_done, 0);
+            __syncwarp();
+        }
+        tc_fence_after();
+        tmem_dealloc(tmem, 512);
+    }
+    if (threadIdx.x == 0 && *abort) atomicOr(p.status, kStatusTimeout);
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+
+template <int S>
+cudaError_t set_attrs() {
+    return cudaFuncSetAttribute(k_gemm_split<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, split_smem_bytes<S>());
+}
+
+}  // namespace
+
+cudaError_t split_init() {
+    if (!g_encode) {
+        cudaDriverEntryPointQueryResult q;
+        void* fn = nullptr;
+        cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+        if (e != cudaSuccess) return e;
+        if (q != cudaDriverEntryPointSuccess || !fn) return cudaErrorNotSupported;
+        g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    }
+    cudaError_t e;
+    if ((e = set_attrs<4>()) != cudaSuccess) return e;
+    if ((e = set_attrs<5>()) != cudaSuccess) return e;
+    if ((e = set_attrs<6>()) != cudaSuccess) return e;
+    if ((e = set_attrs<7>()) != cudaSuccess) return e;
+    return cudaSuccess;
+}
+
+void split_free(SplitBuffers& B) {
+    if (B.sliceA) cudaFree(B.sliceA);
+    if (B.sliceB) cudaFree(B.sliceB);
+    if (B.expA) cudaFree(B.expA);
+    if (B.expB) cudaFree(B.expB);
+    B = SplitBuffers{};
+}
+
+static cudaError_t encode(CUtensorMap* map, void* base, int64_t cols, int64_t rows) {
+    cuuint64_t dims[2] = {static_cast<cuuint64_t>(cols), static_cast<cuuint64_t>(rows)};
+    cuuint64_t strides[1] = {static_cast<cuuint64_t>(cols * 2)};
+    cuuint32_t box[2] = {static_cast<cuuint32_t>(kSplitKB), static_cast<cuuint32_t>(kSplitBM)};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = g_encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, base, dims, strides, box, estr,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
+                          CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+cudaError_t split_alloc(SplitBuffers& B, const std::vector<SplitStep>& steps, int slices, int np) {
+    (void)slices;
+    size_t ca = 0, cb = 0, cea = 0, ceb = 0;
+    for (const SplitStep& s : steps) {
+        ca = std::max(ca, static_cast<size_t>(s.rowsA) * s.Kcols * np);
+        cb = std::max(cb, static_cast<size_t>(s.rowsB) * s.Kcols * np);
+        cea = std::max(cea, static_cast<size_t>(s.erowsA) * np);
+        ceb = std::max(ceb, static_cast<size_t>(s.erowsB) * np);
+    }
+    if (B.np >= np && B.capA >= ca && B.capB >= cb && !B.tmA.empty()) return cudaSuccess;
+    split_free(B);
+    cudaError_t e;
+    if ((e = cudaMalloc(&B.sliceA, std::max<size_t>(ca, 64) * 2)) != cudaSuccess) return e;
+    if ((e = cudaMalloc(&B.sliceB, std::max<size_t>(cb, 64) * 2)) != cudaSuccess) return e;
+    if ((e = cudaMalloc(&B.expA, std::max<size_t>(cea, 1) * 4)) != cudaSuccess) return e;
+    if ((e = cudaMalloc(&B.expB, std::max<size_t>(ceb, 1) * 4)) != cudaSuccess) return e;
+    B.capA = ca;
+    B.capB = cb;
+    B.capEA = cea;
+    B.capEB = ceb;
+    B.np = np;
+    B.tmA.assign(steps.size(), CUtensorMap{});
+    B.tmB.assign(steps.size(), CUtensorMap{});
+    for (size_t i = 0; i < steps.size(); ++i) {
+        const SplitStep& s = steps[i];
+        if ((e = encode(&B.tmA[i], B.sliceA, s.Kcols, std::max<int64_t>(s.rowsA * np, 128))) != cudaSuccess) return e;
+        if ((e = encode(&B.tmB[i], B.sliceB, s.Kcols, std::max<int64_t>(s.rowsB * np, 128))) != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+template <int S>
+static cudaError_t run_step(const Launch& l, int step_index, const GemmItem* items_dev,
+                            const SplitItem* sitems_dev, const GemmTile* stiles_dev,
+                            const SliceBlock* blocks_dev, const SplitStep& step, const SplitBuffers& B,
+                            const double2* Abuf, int64_t sA, const double2* Bbuf, int64_t sB, double2* Cbuf,
+                            int64_t sC, int np, int* status, cudaStream_t st) {
+    SliceArgs sa{items_dev, sitems_dev, blocks_dev, step.sa_first, l.first, Abuf, sA, l.opA, 0,
+                 B.sliceA, step.rowsA, step.Kcols, B.expA, step.erowsA};
+    k_slice<S><<<dim3(static_cast<unsigned>(step.sa_count), np), 256, 0, st>>>(sa);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    SliceArgs sb{items_dev, sitems_dev, blocks_dev, step.sb_first, l.first, Bbuf, sB, l.opB, 1,
+                 B.sliceB, step.rowsB, step.Kcols, B.expB, step.erowsB};
+    k_slice<S><<<dim3(static_cast<unsigned>(step.sb_count), np), 256, 0, st>>>(sb);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    GemmArgs ga{items_dev, sitems_dev, stiles_dev, step.tfirst, l.first, step.rowsA, step.rowsB,
+                step.erowsA, step.erowsB, B.expA, B.expB, Cbuf, sC, l.alpha, l.beta, l.lower, status};
+    k_gemm_split<S><<<dim3(static_cast<unsigned>(step.tcount), np), kThreads, split_smem_bytes<S>(), st>>>(
+        B.tmA[step_index], B.tmB[step_index], ga);
+    return cudaGetLastError();
+}
+
+cudaError_t split_gemm_step(const Launch& l, int step_index, const GemmItem* items_dev,
+                            const SplitItem* sitems_dev, const GemmTile* stiles_dev,
+                            const SliceBlock* blocks_dev, const SplitStep& step,
+                            const SplitBuffers& B, int slices, const double2* Abuf, int64_t sA,
+                            const double2* Bbuf, int64_t sB, double2* Cbuf, int64_t sC, int np,
+                            int* status, cudaStream_t st) {
+    switch (slices) {
+        case 4: return run_step<4>(l, step_index, items_dev, sitems_dev, stiles_dev, blocks_dev, step, B, Abuf, sA, Bbuf, sB, Cbuf, sC, np, status, st);
+        case 5: return run_step<5>(l, step_index, items_dev, sitems_dev, stiles_dev, blocks_dev, step, B, Abuf, sA, Bbuf, sB, Cbuf, sC, np, status, st);
+        case 6: return run_step<6>(l, step_index, items_dev, sitems_dev, stiles_dev, blocks_dev, step, B, Abuf, sA, Bbuf, sB, Cbuf, sC, np, status, st);
+        case 7: return run_step<7>(l, step_index, items_dev, sitems_dev, stiles_dev, blocks_dev, step, B, Abuf, sA, Bbuf, sB, Cbuf, sC, np, status, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace ndsi

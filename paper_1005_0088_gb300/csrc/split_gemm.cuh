@@ -1,0 +1,74 @@
+// Split-precision (emulated FP64) complex GEMM on the tcgen05 tensor cores.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include <vector>
+
+#include "plan.hpp"
+
+namespace ndsi {
+
+// Tile of the split GEMM: 128 output rows x 64 complex output columns.
+constexpr int kSplitBM = 128;
+constexpr int kSplitBNc = 64;      // complex columns per tile (128 rows of the stacked B operand)
+constexpr int kSplitKB = 32;       // K per pipeline stage (64-byte rows, 64B swizzle)
+#ifdef NDSI_SPLIT_CHUNK_KB
+constexpr int kSplitChunkKB = NDSI_SPLIT_CHUNK_KB;
+#else
+constexpr int kSplitChunkKB = 8;   // stages per exact chunk (256 stacked-K elements)
+#endif
+constexpr int kSplitMaxSlices = 7;
+
+// Where an item's slices and exponents live inside one pole's block of the step buffers.
+struct SplitItem {
+    int64_t rowA, rowB;     // first slice row of the item (A: S*Mpad rows, B: S*2*Npad rows)
+    int64_t erowA, erowB;   // first exponent of the item
+    int32_t Mpad, Npad;     // Mpad multiple of 128 rows, Npad multiple of 64 complex columns
+    int32_t Kpad, pad;      // multiple of 32 (complex K); stacked K is 2*Kpad
+};
+
+// Per GEMM launch: sizes of one pole's block in the step buffers, and the split tile range.
+struct SplitStep {
+    int64_t rowsA, rowsB, erowsA, erowsB;  // per pole
+    int32_t Kcols, pad;                    // row length of the slice buffers (2*max Kpad)
+    int64_t tfirst, tcount;                // tiles in the split tile list
+    int64_t sa_first, sa_count;            // 64-row slicing blocks of A in the block list
+    int64_t sb_first, sb_count;            // 64-column slicing blocks of B
+};
+
+// A slicing block: item (relative to the launch) and its first row (A) or complex column (B).
+struct SliceBlock {
+    int32_t item, r0;
+};
+
+// Build the split metadata of every GEMM launch (called by the analysis in split mode).
+void build_split_schedule(const Plan& P, int slices, std::vector<SplitItem>& items,
+                          std::vector<SplitStep>& steps, std::vector<GemmTile>& tiles,
+                          std::vector<SliceBlock>& blocks);
+
+struct SplitBuffers {
+    uint16_t* sliceA = nullptr;   // bf16 bit patterns
+    uint16_t* sliceB = nullptr;
+    int32_t* expA = nullptr;
+    int32_t* expB = nullptr;
+    size_t capA = 0, capB = 0, capEA = 0, capEB = 0;  // elements
+    std::vector<CUtensorMap> tmA, tmB;                // one per split step (for np_cap poles)
+    int32_t np = 0;
+};
+
+cudaError_t split_init();
+// Allocate the slice buffers for np poles and encode the tensor maps of every step.
+cudaError_t split_alloc(SplitBuffers& B, const std::vector<SplitStep>& steps, int slices, int np);
+void split_free(SplitBuffers& B);
+
+// Run one GEMM launch of the schedule in split precision: slice A, slice B, tensor-core GEMM.
+cudaError_t split_gemm_step(const Launch& l, int step_index, const GemmItem* items_dev,
+                            const SplitItem* sitems_dev, const GemmTile* stiles_dev,
+                            const SliceBlock* blocks_dev, const SplitStep& step,
+                            const SplitBuffers& B, int slices, const double2* Abuf, int64_t sA,
+                            const double2* Bbuf, int64_t sB, double2* Cbuf, int64_t sC, int np,
+                            int* status, cudaStream_t st);
+
+}  // namespace ndsi

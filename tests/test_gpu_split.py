@@ -1,0 +1,81 @@
+"""GPU parity of the split-precision (emulated FP64 on BF16 tensor cores) path.
+
+Tolerance: 1e-9 max-abs on rho for the split form (the FP64 form keeps 1e-10).  G is compared
+to the dense inverse relative to max|G|.
+"""
+import numpy as np
+import pytest
+
+from synth import config_system, lattice_system
+from oracle.dense import (generalized_eig, density_eig, find_mu_eig, on_pattern,
+                          electron_count_pattern, green_dense)
+from tests.libtools import lib
+from tests.test_gpu_parity import _selinv, _density
+
+pytestmark = pytest.mark.gpu
+
+RHO_TOL_SPLIT = 1e-9
+
+
+@pytest.mark.parametrize("shape,o,nb,leaf", [
+    ((40, 1, 1), 3, "1d", 6), ((9, 7, 1), 2, "2d", 5), ((5, 4, 4), 2, "3d", 6),
+    ((11, 10, 1), 4, "2d", 20), ((6, 6, 5), 3, "3d", 20)])
+def test_split_selected_inverse_matches_dense(shape, o, nb, leaf):
+    sysm = lattice_system(shape, o, nb, 77)
+    Hd, Sd = sysm.dense()
+    Z = [0.1 + 0.0314j, -0.7 + 2.5j, 1e7j]
+    g = _selinv(sysm, Z, leaf_atoms=leaf, precision=lib().NDSI_PREC_SPLIT)
+    for q, z in enumerate(Z):
+        ref = on_pattern(green_dense(Hd, Sd, z), sysm)
+        rel = np.max(np.abs(g[q] - ref)) / np.max(np.abs(ref))
+        print(f"split G rel err {shape} z={z}: {rel:.2e}")
+        assert rel < 1e-9
+
+
+def _rho_split(sysm, kT, M, leaf=20, slices=6):
+    Hd, Sd = sysm.dense()
+    eps, C = generalized_eig(Hd, Sd)
+    mu = find_mu_eig(eps, kT, sysm.n_electrons, M)
+    ref = on_pattern(density_eig(eps, C, mu, kT, M), sysm)
+    rho, ne = _density(sysm, mu, kT, M, leaf_atoms=leaf, precision=lib().NDSI_PREC_SPLIT,
+                       split_slices=slices)
+    return rho, ne, ref
+
+
+def test_split_density_C1():
+    sysm = config_system("C1")
+    rho, ne, ref = _rho_split(sysm, sysm.meta["kT"], sysm.meta["poles"])
+    err = np.max(np.abs(rho - ref))
+    print(f"split C1 rho err {err:.2e}")
+    assert err < RHO_TOL_SPLIT
+    assert abs(ne - sysm.n_electrons) < 1e-7
+
+
+@pytest.mark.parametrize("shape,o,nb,leaf,M", [
+    ((12, 12, 1), 2, "2d", 20, 40), ((6, 6, 6), 2, "3d", 20, 40), ((7, 5, 3), 3, "3d", 8, 60)])
+def test_split_density_lattices(shape, o, nb, leaf, M):
+    rho, ne, ref = _rho_split(lattice_system(shape, o, nb, 123), 0.01, M, leaf)
+    err = np.max(np.abs(rho - ref))
+    print(f"split rho err {shape}: {err:.2e}")
+    assert err < RHO_TOL_SPLIT
+
+
+def test_split_error_falls_with_slices():
+    sysm = lattice_system((10, 10, 1), 3, "2d", 99)
+    errs = {}
+    for S in (4, 5, 6):
+        rho, ne, ref = _rho_split(sysm, 0.01, 30, slices=S)
+        errs[S] = np.max(np.abs(rho - ref))
+    print("split rho err by slices", errs)
+    assert errs[4] > errs[6]
+    assert errs[6] < RHO_TOL_SPLIT
+
+
+def test_split_matches_fp64_path_C2():
+    sysm = config_system("C2")
+    kT, M, mu = sysm.meta["kT"], sysm.meta["poles"], -0.12
+    r64, n64 = _density(sysm, mu, kT, M)
+    rs, ns = _density(sysm, mu, kT, M, precision=lib().NDSI_PREC_SPLIT)
+    err = np.max(np.abs(rs - r64))
+    print(f"split vs fp64 C2: rho {err:.2e}, N_e {abs(ns - n64):.2e}")
+    assert err < RHO_TOL_SPLIT
