@@ -158,6 +158,68 @@ def run_reference(args):
     return 0
 
 
+def _kernel_totals(prof):
+    """Aggregate per-step profiler entries ("gemm_split:schur") into kernels ("gemm_split")."""
+    out = {}
+    for name, v in prof.items():
+        k = name.split(":")[0]
+        o = out.setdefault(k, dict(launches=0, ms=0.0, flops=0.0, bytes=0.0, tensor_flops=0.0))
+        for f in o:
+            o[f] += v[f]
+    return out
+
+
+def _roofline(prof, steps, peaks):
+    kern = _kernel_totals(prof)
+    dname, d = max(kern.items(), key=lambda kv: kv[1]["ms"])
+    total = sum(v["ms"] for v in kern.values())
+    if dname == "gemm_split":
+        peak = peaks.get("bf16_tflops_sustained", 1738.1)
+        achieved = d["tensor_flops"] / (d["ms"] * 1e-3) / 1e12
+        r = {"bound": "tensor", "unit": "TFLOP/s", "peak": peak,
+             "peak_source": "of measured (MEASURED_PEAKS.json bf16_tflops_sustained; the kernel runs "
+                            "inside a long step)",
+             "fp64_equivalent_tflops": d["flops"] / (d["ms"] * 1e-3) / 1e12}
+    elif dname in ("gemm_f64", "diaginv"):
+        peak = FP64_PEAK_TFLOPS
+        achieved = d["flops"] / (d["ms"] * 1e-3) / 1e12
+        r = {"bound": "alu", "unit": "TFLOP/s", "peak": peak,
+             "peak_source": "nominal GB300 FP64 DFMA rate from the hardware table (1.25 TFLOP/s); "
+                            "a DFMA loop measured 1.01 TFLOP/s"}
+    else:
+        peak = peaks.get("hbm_gbs", 6800.0)
+        achieved = d["bytes"] / (d["ms"] * 1e-3) / 1e9
+        r = {"bound": "hbm", "unit": "GB/s", "peak": peak,
+             "peak_source": "of measured (MEASURED_PEAKS.json hbm_gbs)"}
+    r.update({"kernel": dname, "achieved": achieved, "frac": achieved / peak, "traffic": None,
+              "launches": d["launches"], "kernel_ms_per_step": d["ms"] / steps,
+              "share": d["ms"] / total})
+    return r, kern
+
+
+def _measure(nd, torch, plan, H, S, rho, ne, kT, M, steps, warmup, stream, flush, clocks=None):
+    def step():
+        nd.ndsi_density(plan, H, S, MU, kT, M, rho, ne, stream=stream)
+    for _ in range(max(warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    nd.ndsi_profile_enable(plan, True)
+    times = []
+    torch.cuda.synchronize()
+    for _ in range(steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    prof = nd.ndsi_profile_read(plan)
+    nd.ndsi_profile_enable(plan, False)
+    return times, prof
+
+
 def run_ndsi(args):
     import numpy as np
     import torch
@@ -177,8 +239,8 @@ def run_ndsi(args):
 
     system = config_system(args.config)
     kT, M = system.meta["kT"], system.meta["poles"]
-    prec = {"fp64": nd.NDSI_PREC_FP64, "split": nd.NDSI_PREC_SPLIT}[args.precision]
-    plan = nd.analyze_system(system, precision=prec)
+    prec_code = {"fp64": nd.NDSI_PREC_FP64, "split": nd.NDSI_PREC_SPLIT}
+    plan = nd.analyze_system(system, precision=prec_code[args.precision])
     info = nd.ndsi_plan_info(plan)
     dev = torch.device("cuda", local)
     H = torch.as_tensor(system.H, device=dev)
@@ -188,32 +250,13 @@ def run_ndsi(args):
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > L2
     stream = torch.cuda.current_stream()
 
-    def step():
-        nd.ndsi_density(plan, H, S, MU, kT, M, rho, ne, stream=stream)
-
-    for _ in range(max(args.warmup, 3)):
-        step()
-    torch.cuda.synchronize()
-    nd.ndsi_profile_enable(plan, True)
-    times = []
     if world > 1:
         dist.barrier()
-    torch.cuda.synchronize()
     with ClockSampler(local) as clk:
-        for _ in range(args.steps):
-            flush.zero_()
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            step()
-            e1.record(stream)
-            torch.cuda.synchronize()
-            times.append(e0.elapsed_time(e1))
-    torch.cuda.synchronize()
+        times, prof = _measure(nd, torch, plan, H, S, rho, ne, kT, M, args.steps, args.warmup, stream,
+                               flush)
     if world > 1:
         dist.barrier()
-    prof = nd.ndsi_profile_read(plan)
-    nd.ndsi_profile_enable(plan, False)
     total_ms = sum(times)
     if world > 1:
         t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
@@ -221,6 +264,7 @@ def run_ndsi(args):
         total_ms = float(t.item())
     ms_step = total_ms / args.steps
     value = world * M * system.n / (ms_step * 1e-3)
+    rho_main = rho.cpu().numpy()
     # end to end through the public API with pinned host buffers (copies inside the call)
     Hh = torch.as_tensor(system.H).pin_memory()
     Sh = torch.as_tensor(system.S).pin_memory()
@@ -239,32 +283,35 @@ def run_ndsi(args):
         t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e_s = float(t.item())
+    # the other precision on the same workload: split-vs-FP64 speedup and rho difference
+    other = None
+    if not args.no_other and rank == 0:
+        oprec = "split" if args.precision == "fp64" else "fp64"
+        plan2 = nd.analyze_system(system, precision=prec_code[oprec])
+        rho2 = torch.zeros_like(rho)
+        ne2 = torch.zeros_like(ne)
+        t2, prof2 = _measure(nd, torch, plan2, H, S, rho2, ne2, kT, M, args.steps, args.warmup, stream,
+                             flush)
+        ms2 = sum(t2) / len(t2)
+        ms_split, ms_fp64 = (ms2, ms_step) if oprec == "split" else (ms_step, ms2)
+        rl2, k2 = _roofline(prof2, args.steps, _peaks())
+        other = {"precision": oprec, "ms_per_step": ms2, "value": M * system.n / (ms2 * 1e-3),
+                 "split_speedup_vs_fp64": ms_fp64 / ms_split,
+                 "max_abs_rho_diff_vs_headline": float(np.max(np.abs(rho2.cpu().numpy() - rho_main))),
+                 "roofline": rl2,
+                 "kernels": {k: {"launches": v["launches"] // args.steps, "ms_per_step": v["ms"] / args.steps}
+                             for k, v in k2.items()}}
+        del plan2
     if rank != 0:
-        dist.destroy_process_group() if world > 1 else None
+        if world > 1:
+            dist.destroy_process_group()
         return 0
-    # roofline of the dominant kernel family
-    dom = max(prof.items(), key=lambda kv: kv[1]["ms"])
-    dname, d = dom
-    peaks = _peaks()
-    if dname.startswith("gemm_f64") or dname == "diaginv":
-        bound, unit, peak = "alu", "TFLOP/s", FP64_PEAK_TFLOPS
-        achieved = d["flops"] / (d["ms"] * 1e-3) / 1e12
-        peak_note = "nominal GB300 FP64 DFMA rate (hardware table); measured DFMA loop: 1.01 TFLOP/s"
-    else:
-        bound, unit = "hbm", "GB/s"
-        peak = peaks.get("hbm_gbs", 6800.0)
-        achieved = d["bytes"] / (d["ms"] * 1e-3) / 1e9
-        peak_note = "of measured (MEASURED_PEAKS.json hbm_gbs)"
-    roofline = {"kernel": dname, "bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
-                "frac": achieved / peak, "traffic": None, "peak_source": peak_note,
-                "launches": d["launches"], "kernel_ms_per_step": d["ms"] / args.steps,
-                "share": d["ms"] / sum(v["ms"] for v in prof.values())}
-    launches = sum(v["launches"] for v in prof.values()) // args.steps
+    roofline, kern = _roofline(prof, args.steps, _peaks())
+    launches = sum(v["launches"] for v in kern.values())
     # parity spot check outside the timed region: sampled columns from the oracle
     parity = None
     if not args.no_parity:
         from oracle.dense import density_columns
-        rho_np = rho.cpu().numpy()
         rng = np.random.default_rng(11)
         cols = sorted(rng.choice(system.n, 3, replace=False).tolist())
         ref = density_columns(system, MU, kT, M, cols)
@@ -272,8 +319,9 @@ def run_ndsi(args):
         err = 0.0
         for t_, j in enumerate(cols):
             sel = np.nonzero(system.col == j)[0]
-            err = max(err, float(np.max(np.abs(rho_np[sel] - ref[rows[sel], t_]))))
-        parity = {"max_abs_err_rho": err, "columns": cols, "tolerance": 1e-10}
+            err = max(err, float(np.max(np.abs(rho_main[sel] - ref[rows[sel], t_]))))
+        parity = {"max_abs_err_rho": err, "columns": cols,
+                  "tolerance": 1e-10 if args.precision == "fp64" else 1e-9}
     cpu = None
     if world == 1 and not args.no_cpu:
         v, reps, t_rep = cpu_oracle_rate(system, MU, kT, M)
@@ -283,20 +331,23 @@ def run_ndsi(args):
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": ms_step,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f64" if args.precision == "fp64" else "bf16x{}->f64".format(6),
+            "dtype": "f64" if args.precision == "fp64" else "bf16x6->f64",
             "data": "synthetic",
             "config": {"workload": system.meta["label"] + f", {M} poles, {args.precision} path",
                        "n": system.n, "poles": M, "kT": kT, "mu": MU, "nnz": system.nnz,
-                       "precision": args.precision, "l2": "flushed (256 MB write) before every timed step",
+                       "precision": args.precision,
+                       "l2": "flushed (256 MB write) before every timed step",
                        "flops_per_pole": info["flops_per_pole"], "parallelism": f"replicas x{world}"},
             "e2e": {"value": world * M * system.n / e2e_s, "unit": UNIT,
                     "h2d_bytes_per_step": 2 * 8 * system.nnz,
                     "d2h_bytes_per_step": 8 * system.nnz + 8},
-            "gpu_launches": launches * args.steps,
+            "gpu_launches": launches,
             "roofline": roofline, "clocks": clk.summary(), "cpu_baseline": cpu,
-            "parity": parity,
-            "kernels": {k: {"launches": v["launches"], "ms_per_step": v["ms"] / args.steps}
-                        for k, v in prof.items()}}
+            "parity": parity, "other_precision": other,
+            "kernels": {k: {"launches": v["launches"] // args.steps, "ms_per_step": v["ms"] / args.steps}
+                        for k, v in kern.items()},
+            "steps_detail": {k: {"launches": v["launches"] // args.steps, "ms_per_step": v["ms"] / args.steps}
+                             for k, v in prof.items()}}
     print(json.dumps(line))
     if world > 1:
         dist.destroy_process_group()
@@ -313,6 +364,8 @@ def main():
     ap.add_argument("--precision", default="fp64", choices=["fp64", "split"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-parity", action="store_true", help="skip the sampled-column check")
+    ap.add_argument("--no-other", action="store_true",
+                    help="skip the run of the other precision (split-vs-FP64 speedup)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

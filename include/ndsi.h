@@ -156,12 +156,14 @@ int ndsi_density(ndsi_plan* plan, const double* H, const double* S, double mu, d
  * counts and the algorithmic flops and bytes of the launches accumulate per kernel family.
  * ndsi_profile_enable(plan, 1) also clears the counters; 0 stops recording. */
 typedef struct {
-    char name[32];      /* kernel family: gemm_f64, diaginv, assemble, scatter, copy, gather,
-                           accumulate, reduce */
-    int64_t launches;   /* launches recorded */
-    double ms;          /* summed event-timed durations of those launches */
-    double flops;       /* summed algorithmic real flops (complex MAC = 8 flops) */
-    double bytes;       /* summed algorithmic global-memory bytes (reads + writes) */
+    char name[32];        /* kernel family and schedule step: "gemm_f64:<step>", "slice:<step>",
+                             "gemm_split:<step>", diaginv, assemble, scatter, copy, gather,
+                             accumulate, reduce */
+    int64_t launches;     /* launches recorded */
+    double ms;            /* summed event-timed durations of those launches */
+    double flops;         /* summed algorithmic real flops (complex MAC = 8 flops) */
+    double bytes;         /* summed algorithmic global-memory bytes (reads + writes) */
+    double tensor_flops;  /* summed tensor-core flops issued (split GEMM only) */
 } ndsi_profile_entry;
 
 int ndsi_profile_enable(ndsi_plan* plan, int32_t enable);

@@ -15,15 +15,15 @@
 #include "split_gemm.cuh"
 
 namespace ndsi {
-// Event-timed launch records, resolved after the stream synchronises.
-constexpr int kFamSplit = 8;
-constexpr int kFamiliesAll = 9;
-static const char* const kFamilyName[kFamiliesAll] = {"gemm_f64", "diaginv", "assemble", "scatter",
-                                                      "copy", "gather", "accumulate", "reduce",
-                                                      "gemm_split"};
+// Event-timed launch records, resolved after the stream synchronises, keyed by kernel family
+// and schedule step ("gemm_split:schur", "diaginv", ...).
+struct ProfStat {
+    int64_t launches = 0;
+    double ms = 0, flops = 0, bytes = 0, tensor_flops = 0;
+};
 struct ProfRec {
-    int family;
-    double flops, bytes;
+    int key;
+    double flops, bytes, tensor_flops;
     cudaEvent_t e0, e1;
 };
 struct Profiler {
@@ -31,8 +31,15 @@ struct Profiler {
     std::vector<cudaEvent_t> pool;
     size_t used = 0;
     std::vector<ProfRec> pending;
-    double ms[kFamiliesAll] = {}, flops[kFamiliesAll] = {}, bytes[kFamiliesAll] = {};
-    int64_t launches[kFamiliesAll] = {};
+    std::vector<std::string> names;
+    std::vector<ProfStat> stats;
+    int key(const std::string& name) {
+        for (size_t i = 0; i < names.size(); ++i)
+            if (names[i] == name) return static_cast<int>(i);
+        names.push_back(name);
+        stats.emplace_back();
+        return static_cast<int>(names.size()) - 1;
+    }
 };
 
 // Split-precision metadata of a plan (built when opt.precision == NDSI_PREC_SPLIT).
@@ -42,6 +49,8 @@ struct SplitPlan {
     std::vector<GemmTile> tiles;
     std::vector<SliceBlock> blocks;
     std::vector<int32_t> step_of_launch;
+    std::vector<double> tensor_flops;   // per step, one pole
+    std::vector<double> slice_bytes;    // per step, one pole: FP64 operand reads + BF16 slice writes
     SplitItem* d_items = nullptr;
     GemmTile* d_tiles = nullptr;
     SliceBlock* d_blocks = nullptr;
@@ -192,15 +201,22 @@ void free_workspace(Workspace& W) {
     W = Workspace{};
 }
 
-int family_of(int kind) {
-    switch (kind) {
-        case L_GEMM: return 0;
-        case L_DIAGINV: return 1;
-        case L_ASSEMBLE: return 2;
-        case L_SCATTER: return 3;
-        case L_COPY: return 4;
-        case L_GATHER: return 5;
-        default: return 4;
+const char* tag_name(int tag) {
+    static const char* const names[] = {"assemble", "scatter", "dinv", "panel", "update", "pcopy", "ainv_t",
+                                        "ainv_d", "ainv_copy", "lrj", "schur", "lcopy", "gather", "sel_t",
+                                        "sel_d", "sel_copy"};
+    return (tag >= 0 && tag < 16) ? names[tag] : "other";
+}
+
+std::string family_of(const Launch& l) {
+    switch (l.kind) {
+        case L_GEMM: return std::string("gemm_f64:") + tag_name(l.tag);
+        case L_DIAGINV: return "diaginv";
+        case L_ASSEMBLE: return "assemble";
+        case L_SCATTER: return "scatter";
+        case L_COPY: return "copy";
+        case L_GATHER: return "gather";
+        default: return "other";
     }
 }
 
@@ -218,13 +234,14 @@ cudaEvent_t prof_event(Profiler& pf) {
 
 // Bracket a launch with events when profiling; `fn` performs the launch.
 template <class Fn>
-cudaError_t timed(Profiler& pf, int family, double flops, double bytes, cudaStream_t st, Fn fn) {
+cudaError_t timed(Profiler& pf, const std::string& family, double flops, double bytes, cudaStream_t st, Fn fn,
+                  double tensor_flops = 0) {
     if (!pf.on) return fn();
     cudaEvent_t e0 = prof_event(pf), e1 = prof_event(pf);
     if (e0) cudaEventRecord(e0, st);
     cudaError_t e = fn();
     if (e1) cudaEventRecord(e1, st);
-    if (e0 && e1) pf.pending.push_back(ProfRec{family, flops, bytes, e0, e1});
+    if (e0 && e1) pf.pending.push_back(ProfRec{pf.key(family), flops, bytes, tensor_flops, e0, e1});
     return e;
 }
 
@@ -233,10 +250,12 @@ void prof_resolve(Profiler& pf) {
     for (const ProfRec& r : pf.pending) {
         float ms = 0.f;
         if (cudaEventElapsedTime(&ms, r.e0, r.e1) == cudaSuccess) {
-            pf.ms[r.family] += ms;
-            pf.flops[r.family] += r.flops;
-            pf.bytes[r.family] += r.bytes;
-            pf.launches[r.family] += 1;
+            ProfStat& st = pf.stats[r.key];
+            st.ms += ms;
+            st.flops += r.flops;
+            st.bytes += r.bytes;
+            st.tensor_flops += r.tensor_flops;
+            st.launches += 1;
         } else {
             cudaGetLastError();
         }
@@ -254,17 +273,27 @@ int run_phase(ndsi_plan* h, const Workspace& W, const SplitBuffers& SB, int phas
         if (l.phase != phase) continue;
         cudaError_t e;
         if (split && l.kind == L_GEMM) {
-            const int si = h->SP.step_of_launch[li];
+            const int si = h->SP.steps.empty() ? 0 : h->SP.step_of_launch[li];
+            const SplitStep& step = h->SP.steps[si];
             const double2* bufs[2] = {W.fronts, W.scr};
             const int64_t strides[2] = {W.front_stride, W.scr_stride};
-            e = timed(h->prof, kFamSplit, l.flops * np, l.bytes * np, st, [&]() {
-                return split_gemm_step(l, si, h->T.gemm_items, h->SP.d_items, h->SP.d_tiles, h->SP.d_blocks,
-                                       h->SP.steps[si], SB, P.opt.split_slices, bufs[l.bufA], strides[l.bufA],
-                                       bufs[l.bufB], strides[l.bufB], const_cast<double2*>(bufs[l.bufC]),
-                                       strides[l.bufC], np, h->T.status, st);
+            const std::string tg = tag_name(l.tag);
+            e = timed(h->prof, "slice:" + tg, 0.0, h->SP.slice_bytes[si] * np, st, [&]() {
+                return split_slice_step(l, h->T.gemm_items, h->SP.d_items, h->SP.d_blocks, step, SB,
+                                        P.opt.split_slices, bufs[l.bufA], strides[l.bufA], bufs[l.bufB],
+                                        strides[l.bufB], np, st);
             });
+            if (e == cudaSuccess)
+                e = timed(
+                    h->prof, "gemm_split:" + tg, l.flops * np, l.bytes * np, st,
+                    [&]() {
+                        return split_mma_step(l, si, h->T.gemm_items, h->SP.d_items, h->SP.d_tiles, step, SB,
+                                              P.opt.split_slices, const_cast<double2*>(bufs[l.bufC]),
+                                              strides[l.bufC], np, h->T.status, st);
+                    },
+                    h->SP.tensor_flops[si] * np);
         } else {
-            e = timed(h->prof, family_of(l.kind), l.flops * np, l.bytes * np, st,
+            e = timed(h->prof, family_of(l), l.flops * np, l.bytes * np, st,
                       [&]() { return launch_step(P, h->T, l, W, H, S, z, np, st); });
         }
         if (e != cudaSuccess)
@@ -407,8 +436,20 @@ int ndsi_analyze(const ndsi_pattern* pat, int32_t n_atoms, const double* centers
         build_split_schedule(h->P, o.split_slices, S.items, S.steps, S.tiles, S.blocks);
         S.step_of_launch.assign(h->P.launches.size(), -1);
         int k = 0;
-        for (size_t li = 0; li < h->P.launches.size(); ++li)
-            if (h->P.launches[li].kind == L_GEMM) S.step_of_launch[li] = k++;
+        for (size_t li = 0; li < h->P.launches.size(); ++li) {
+            const Launch& l = h->P.launches[li];
+            if (l.kind != L_GEMM) continue;
+            const SplitStep& st = S.steps[k];
+            S.tensor_flops.push_back(split_executed_flops(h->P, st, S.items, S.tiles, l, o.split_slices));
+            double sb = 0;
+            for (int64_t i = 0; i < l.count; ++i) {
+                const GemmItem& g = h->P.gemm_items[l.first + i];
+                sb += 2.0 * 16.0 * (static_cast<double>(g.M) * g.K + static_cast<double>(g.N) * g.K);
+            }
+            sb += 2.0 * (static_cast<double>(st.rowsA) + st.rowsB) * st.Kcols;
+            S.slice_bytes.push_back(sb);
+            S.step_of_launch[li] = k++;
+        }
     }
     *plan_out = h;
     return NDSI_OK;
@@ -589,13 +630,13 @@ int ndsi_density(ndsi_plan* h, const double* H, const double* S, double mu, doub
         const int last = q0 + np >= nq;
         const double acc_bytes = static_cast<double>(h->P.nnz) * (8.0 + 16.0 * np + 8.0 + 8.0 +
                                                                   (q0 > 0 ? 8.0 : 0.0));
-        NDSI_CK(timed(h->prof, 6, 2.0 * np * h->P.nnz, acc_bytes, st, [&]() {
+        NDSI_CK(timed(h->prof, "accumulate", 2.0 * np * h->P.nnz, acc_bytes, st, [&]() {
             return launch_accumulate(h->P, h->T, h->W, np, h->cw + q0, Sd, rho_d, q0 > 0 ? 1 : 0,
                                      last, h->partials, st);
         }));
     }
     const int nblk = accumulate_blocks(h->P.nnz);
-    NDSI_CK(timed(h->prof, 7, static_cast<double>(nblk), 8.0 * nblk, st,
+    NDSI_CK(timed(h->prof, "reduce", static_cast<double>(nblk), 8.0 * nblk, st,
                   [&]() { return launch_reduce(h->partials, nblk, ne_d, st); }));
     if (!rho_dev) NDSI_CK(cudaMemcpyAsync(rho_out, rho_d, sizeof(double) * h->P.nnz, cudaMemcpyDeviceToHost, st));
     if (n_elec_out && !ne_dev) NDSI_CK(cudaMemcpyAsync(n_elec_out, ne_d, sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -607,10 +648,8 @@ int ndsi_profile_enable(ndsi_plan* h, int32_t enable) {
     Profiler& pf = h->prof;
     pf.on = enable != 0;
     if (pf.on) {
-        std::fill(pf.ms, pf.ms + kFamiliesAll, 0.0);
-        std::fill(pf.flops, pf.flops + kFamiliesAll, 0.0);
-        std::fill(pf.bytes, pf.bytes + kFamiliesAll, 0.0);
-        std::fill(pf.launches, pf.launches + kFamiliesAll, int64_t(0));
+        pf.names.clear();
+        pf.stats.clear();
         pf.pending.clear();
         pf.used = 0;
     }
@@ -622,15 +661,17 @@ int ndsi_profile_read(const ndsi_plan* h, ndsi_profile_entry* out, int32_t max_e
         return fail(NDSI_ERR_INVALID, "ndsi_profile_read: invalid argument");
     const Profiler& pf = h->prof;
     int32_t n = 0;
-    for (int f = 0; f < kFamiliesAll && n < max_entries; ++f) {
-        if (pf.launches[f] == 0) continue;
+    for (size_t f = 0; f < pf.names.size() && n < max_entries; ++f) {
+        const ProfStat& st = pf.stats[f];
+        if (st.launches == 0) continue;
         ndsi_profile_entry& e = out[n++];
         std::memset(&e, 0, sizeof(e));
-        std::strncpy(e.name, kFamilyName[f], sizeof(e.name) - 1);
-        e.launches = pf.launches[f];
-        e.ms = pf.ms[f];
-        e.flops = pf.flops[f];
-        e.bytes = pf.bytes[f];
+        std::strncpy(e.name, pf.names[f].c_str(), sizeof(e.name) - 1);
+        e.launches = st.launches;
+        e.ms = st.ms;
+        e.flops = st.flops;
+        e.bytes = st.bytes;
+        e.tensor_flops = st.tensor_flops;
     }
     *n_out = n;
     return NDSI_OK;

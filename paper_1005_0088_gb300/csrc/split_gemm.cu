@@ -679,11 +679,10 @@ cudaError_t split_alloc(SplitBuffers& B, const std::vector<SplitStep>& steps, in
 }
 
 template <int S>
-static cudaError_t run_step(const Launch& l, int step_index, const GemmItem* items_dev,
-                            const SplitItem* sitems_dev, const GemmTile* stiles_dev,
-                            const SliceBlock* blocks_dev, const SplitStep& step, const SplitBuffers& B,
-                            const double2* Abuf, int64_t sA, const double2* Bbuf, int64_t sB, double2* Cbuf,
-                            int64_t sC, int np, int* status, cudaStream_t st) {
+static cudaError_t run_slice(const Launch& l, const GemmItem* items_dev, const SplitItem* sitems_dev,
+                             const SliceBlock* blocks_dev, const SplitStep& step, const SplitBuffers& B,
+                             const double2* Abuf, int64_t sA, const double2* Bbuf, int64_t sB, int np,
+                             cudaStream_t st) {
     SliceArgs sa{items_dev, sitems_dev, blocks_dev, step.sa_first, l.first, Abuf, sA, l.opA, 0,
                  B.sliceA, step.rowsA, step.Kcols, B.expA, step.erowsA};
     k_slice<S><<<dim3(static_cast<unsigned>(step.sa_count), np), 256, 0, st>>>(sa);
@@ -692,7 +691,14 @@ static cudaError_t run_step(const Launch& l, int step_index, const GemmItem* ite
     SliceArgs sb{items_dev, sitems_dev, blocks_dev, step.sb_first, l.first, Bbuf, sB, l.opB, 1,
                  B.sliceB, step.rowsB, step.Kcols, B.expB, step.erowsB};
     k_slice<S><<<dim3(static_cast<unsigned>(step.sb_count), np), 256, 0, st>>>(sb);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    return cudaGetLastError();
+}
+
+template <int S>
+static cudaError_t run_mma(const Launch& l, int step_index, const GemmItem* items_dev,
+                           const SplitItem* sitems_dev, const GemmTile* stiles_dev, const SplitStep& step,
+                           const SplitBuffers& B, double2* Cbuf, int64_t sC, int np, int* status,
+                           cudaStream_t st) {
     GemmArgs ga{items_dev, sitems_dev, stiles_dev, step.tfirst, l.first, step.rowsA, step.rowsB,
                 step.erowsA, step.erowsB, B.expA, B.expB, Cbuf, sC, l.alpha, l.beta, l.lower, status};
     k_gemm_split<S><<<dim3(static_cast<unsigned>(step.tcount), np), kThreads, split_smem_bytes<S>(), st>>>(
@@ -700,19 +706,43 @@ static cudaError_t run_step(const Launch& l, int step_index, const GemmItem* ite
     return cudaGetLastError();
 }
 
-cudaError_t split_gemm_step(const Launch& l, int step_index, const GemmItem* items_dev,
-                            const SplitItem* sitems_dev, const GemmTile* stiles_dev,
-                            const SliceBlock* blocks_dev, const SplitStep& step,
-                            const SplitBuffers& B, int slices, const double2* Abuf, int64_t sA,
-                            const double2* Bbuf, int64_t sB, double2* Cbuf, int64_t sC, int np,
-                            int* status, cudaStream_t st) {
+cudaError_t split_slice_step(const Launch& l, const GemmItem* items_dev, const SplitItem* sitems_dev,
+                             const SliceBlock* blocks_dev, const SplitStep& step, const SplitBuffers& B,
+                             int slices, const double2* Abuf, int64_t sA, const double2* Bbuf, int64_t sB,
+                             int np, cudaStream_t st) {
     switch (slices) {
-        case 4: return run_step<4>(l, step_index, items_dev, sitems_dev, stiles_dev, blocks_dev, step, B, Abuf, sA, Bbuf, sB, Cbuf, sC, np, status, st);
-        case 5: return run_step<5>(l, step_index, items_dev, sitems_dev, stiles_dev, blocks_dev, step, B, Abuf, sA, Bbuf, sB, Cbuf, sC, np, status, st);
-        case 6: return run_step<6>(l, step_index, items_dev, sitems_dev, stiles_dev, blocks_dev, step, B, Abuf, sA, Bbuf, sB, Cbuf, sC, np, status, st);
-        case 7: return run_step<7>(l, step_index, items_dev, sitems_dev, stiles_dev, blocks_dev, step, B, Abuf, sA, Bbuf, sB, Cbuf, sC, np, status, st);
+        case 4: return run_slice<4>(l, items_dev, sitems_dev, blocks_dev, step, B, Abuf, sA, Bbuf, sB, np, st);
+        case 5: return run_slice<5>(l, items_dev, sitems_dev, blocks_dev, step, B, Abuf, sA, Bbuf, sB, np, st);
+        case 6: return run_slice<6>(l, items_dev, sitems_dev, blocks_dev, step, B, Abuf, sA, Bbuf, sB, np, st);
+        case 7: return run_slice<7>(l, items_dev, sitems_dev, blocks_dev, step, B, Abuf, sA, Bbuf, sB, np, st);
         default: return cudaErrorInvalidValue;
     }
+}
+
+cudaError_t split_mma_step(const Launch& l, int step_index, const GemmItem* items_dev,
+                           const SplitItem* sitems_dev, const GemmTile* stiles_dev, const SplitStep& step,
+                           const SplitBuffers& B, int slices, double2* Cbuf, int64_t sC, int np, int* status,
+                           cudaStream_t st) {
+    switch (slices) {
+        case 4: return run_mma<4>(l, step_index, items_dev, sitems_dev, stiles_dev, step, B, Cbuf, sC, np, status, st);
+        case 5: return run_mma<5>(l, step_index, items_dev, sitems_dev, stiles_dev, step, B, Cbuf, sC, np, status, st);
+        case 6: return run_mma<6>(l, step_index, items_dev, sitems_dev, stiles_dev, step, B, Cbuf, sC, np, status, st);
+        case 7: return run_mma<7>(l, step_index, items_dev, sitems_dev, stiles_dev, step, B, Cbuf, sC, np, status, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+double split_executed_flops(const Plan& P, const SplitStep& step, const std::vector<SplitItem>& items,
+                            const std::vector<GemmTile>& tiles, const Launch& l, int slices) {
+    // real MACs issued by the tensor cores: per tile 128 x 128 x (2 Kpad) per slice pair
+    const int pairs = slices * (slices + 1) / 2;
+    double macs = 0;
+    for (int64_t t = step.tfirst; t < step.tfirst + step.tcount; ++t) {
+        const SplitItem& si = items[l.first + tiles[t].item];
+        macs += 128.0 * 128.0 * 2.0 * si.Kpad * pairs;
+    }
+    (void)P;
+    return 2.0 * macs;
 }
 
 }  // namespace ndsi

@@ -63,12 +63,18 @@ cudaError_t split_init();
 cudaError_t split_alloc(SplitBuffers& B, const std::vector<SplitStep>& steps, int slices, int np);
 void split_free(SplitBuffers& B);
 
-// Run one GEMM launch of the schedule in split precision: slice A, slice B, tensor-core GEMM.
-cudaError_t split_gemm_step(const Launch& l, int step_index, const GemmItem* items_dev,
-                            const SplitItem* sitems_dev, const GemmTile* stiles_dev,
-                            const SliceBlock* blocks_dev, const SplitStep& step,
-                            const SplitBuffers& B, int slices, const double2* Abuf, int64_t sA,
-                            const double2* Bbuf, int64_t sB, double2* Cbuf, int64_t sC, int np,
-                            int* status, cudaStream_t st);
+// One GEMM launch of the schedule in split precision: slice A and B (split_slice_step), then the
+// tensor-core product and FP64 epilogue (split_mma_step).
+cudaError_t split_slice_step(const Launch& l, const GemmItem* items_dev, const SplitItem* sitems_dev,
+                             const SliceBlock* blocks_dev, const SplitStep& step, const SplitBuffers& B,
+                             int slices, const double2* Abuf, int64_t sA, const double2* Bbuf, int64_t sB,
+                             int np, cudaStream_t st);
+cudaError_t split_mma_step(const Launch& l, int step_index, const GemmItem* items_dev,
+                           const SplitItem* sitems_dev, const GemmTile* stiles_dev, const SplitStep& step,
+                           const SplitBuffers& B, int slices, double2* Cbuf, int64_t sC, int np, int* status,
+                           cudaStream_t st);
+// Tensor-core flops one pole of the step issues (tiles x 128 x 128 x 2Kpad x pairs x 2).
+double split_executed_flops(const Plan& P, const SplitStep& step, const std::vector<SplitItem>& items,
+                            const std::vector<GemmTile>& tiles, const Launch& l, int slices);
 
 }  // namespace ndsi

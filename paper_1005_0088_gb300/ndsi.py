@@ -60,7 +60,8 @@ class ndsi_plan_summary(ctypes.Structure):
 
 class ndsi_profile_entry(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_int64), ("ms", ctypes.c_double),
-                ("flops", ctypes.c_double), ("bytes", ctypes.c_double)]
+                ("flops", ctypes.c_double), ("bytes", ctypes.c_double),
+                ("tensor_flops", ctypes.c_double)]
 
 
 _lib = None
@@ -250,11 +251,12 @@ def ndsi_profile_enable(plan: Plan, enable: bool = True):
 
 def ndsi_profile_read(plan: Plan) -> dict:
     """{family: dict(launches, ms, flops, bytes)} accumulated since ndsi_profile_enable."""
-    buf = (ndsi_profile_entry * 16)()
+    buf = (ndsi_profile_entry * 64)()
     n = ctypes.c_int32()
-    _check(load().ndsi_profile_read(plan.handle, buf, 16, ctypes.byref(n)))
+    _check(load().ndsi_profile_read(plan.handle, buf, 64, ctypes.byref(n)))
     return {buf[i].name.decode(): dict(launches=buf[i].launches, ms=buf[i].ms, flops=buf[i].flops,
-                                       bytes=buf[i].bytes) for i in range(n.value)}
+                                       bytes=buf[i].bytes, tensor_flops=buf[i].tensor_flops)
+            for i in range(n.value)}
 
 
 def ndsi_residue_sum_static(G, c, n_points, S, nnz, rho_out, n_elec_out=None, stream=None):
