@@ -239,6 +239,8 @@ def run_ndsi(args):
 
     system = config_system(args.config)
     kT, M = system.meta["kT"], system.meta["poles"]
+    if args.poles:
+        M = args.poles
     prec_code = {"fp64": nd.NDSI_PREC_FP64, "split": nd.NDSI_PREC_SPLIT}
     plan = nd.analyze_system(system, precision=prec_code[args.precision])
     info = nd.ndsi_plan_info(plan)
@@ -344,7 +346,9 @@ def run_ndsi(args):
             "gpu_launches": launches,
             "roofline": roofline, "clocks": clk.summary(), "cpu_baseline": cpu,
             "parity": parity, "other_precision": other,
-            "kernels": {k: {"launches": v["launches"] // args.steps, "ms_per_step": v["ms"] / args.steps}
+            "kernels": {k: {"launches": v["launches"] // args.steps, "ms_per_step": v["ms"] / args.steps,
+                            "gbs": v["bytes"] / max(v["ms"], 1e-9) / 1e6,
+                            "tflops": v["flops"] / max(v["ms"], 1e-9) / 1e9}
                         for k, v in kern.items()},
             "steps_detail": {k: {"launches": v["launches"] // args.steps, "ms_per_step": v["ms"] / args.steps}
                              for k, v in prof.items()}}
@@ -364,6 +368,8 @@ def main():
     ap.add_argument("--precision", default="fp64", choices=["fp64", "split"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-parity", action="store_true", help="skip the sampled-column check")
+    ap.add_argument("--poles", type=int, default=0,
+                    help="override the workload's pole count (small profiling runs only)")
     ap.add_argument("--no-other", action="store_true",
                     help="skip the run of the other precision (split-vs-FP64 speedup)")
     args = ap.parse_args()

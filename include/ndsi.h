@@ -78,6 +78,8 @@ typedef struct {
     int64_t front_elems;       /* sum of front sizes squared (complex elements per pole) */
     double flops_per_pole;     /* algorithmic real FP64 flops of factor + selected inversion */
     double bytes_per_pole;     /* algorithmic front bytes written + read per pole */
+    int32_t n_launches;        /* schedule launches per pole batch (factor + selected inversion) */
+    int32_t pad;
 } ndsi_plan_summary;
 
 /* Items for ndsi_plan_export. */
@@ -88,6 +90,9 @@ typedef struct {
 #define NDSI_EXPORT_STRUCT_PTR   5  /* int64[n_nodes+1]: offsets into NDSI_EXPORT_STRUCT_ATOMS */
 #define NDSI_EXPORT_STRUCT_ATOMS 6  /* int32[...]: struct(J) as atom ids, by structured position */
 #define NDSI_EXPORT_LEVEL        7  /* int32[n_nodes]: tree level of each node */
+#define NDSI_EXPORT_SCHEDULE     8  /* int32[4*n_launches]: (kind, level, step tag, items) per launch
+                                       of one pole batch, in issue order; n_launches from
+                                       ndsi_plan_info.n_launches */
 
 /* Fill *opt with the defaults listed above. */
 void ndsi_default_options(ndsi_options* opt);

@@ -467,6 +467,8 @@ int ndsi_plan_info(const ndsi_plan* h, ndsi_plan_summary* out) {
     out->front_elems = P.front_total;
     out->flops_per_pole = P.flops_per_pole;
     out->bytes_per_pole = P.bytes_per_pole;
+    out->n_launches = static_cast<int32_t>(P.launches.size());
+    out->pad = 0;
     return NDSI_OK;
 }
 
@@ -483,6 +485,16 @@ int ndsi_plan_export(const ndsi_plan* h, int32_t what, void* out) {
             if (!P.struct_atoms.empty()) std::memcpy(out, P.struct_atoms.data(), bytes_of(P.struct_atoms));
             break;
         case NDSI_EXPORT_LEVEL: std::memcpy(out, P.level.data(), bytes_of(P.level)); break;
+        case NDSI_EXPORT_SCHEDULE: {
+            int32_t* o = static_cast<int32_t*>(out);
+            for (size_t i = 0; i < P.launches.size(); ++i) {
+                o[4 * i + 0] = P.launches[i].kind;
+                o[4 * i + 1] = P.launches[i].level;
+                o[4 * i + 2] = P.launches[i].tag;
+                o[4 * i + 3] = static_cast<int32_t>(P.launches[i].count);
+            }
+            break;
+        }
         default: return fail(NDSI_ERR_INVALID, "ndsi_plan_export: unknown item");
     }
     return NDSI_OK;

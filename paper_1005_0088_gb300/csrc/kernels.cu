@@ -131,9 +131,78 @@ __global__ void __launch_bounds__(256) k_diaginv(const DiagItem* __restrict__ it
     }
 }
 
+// Register-resident variant for blocks of up to 32: one warp per (block, pole), lane j holds
+// column j; each pivot's column is broadcast through 512 bytes of shared memory, so a pivot
+// step needs only warp-level synchronisation.  Four warps per CTA take four poles.
+__global__ void __launch_bounds__(128) k_diaginv_warp(const DiagItem* __restrict__ items, int64_t first,
+                                                      double2* __restrict__ F, int64_t stride, int np,
+                                                      int* __restrict__ status) {
+    __shared__ double2 colbuf[4][32];
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    const int pole = blockIdx.y * 4 + warp;
+    if (pole >= np) return;
+    const DiagItem d = items[first + blockIdx.x];
+    double2* A = F + static_cast<int64_t>(pole) * stride + d.off;
+    const int nb = d.nb, ld = d.ld;
+    double2 a[32];
+#pragma unroll
+    for (int i = 0; i < 32; ++i) {
+        a[i] = make_double2(0.0, 0.0);
+        if (i < nb && lane < nb)
+            a[i] = i >= lane ? A[i + static_cast<int64_t>(lane) * ld] : A[lane + static_cast<int64_t>(i) * ld];
+    }
+    bool bad = false;
+#pragma unroll
+    for (int t = 0; t < 32; ++t) {
+        if (t < nb) {
+            // pivot column t to shared memory, pivot broadcast
+            if (lane == t) {
+#pragma unroll
+                for (int i = 0; i < 32; ++i) colbuf[warp][i] = a[i];
+            }
+            __syncwarp();
+            const double2 p = colbuf[warp][t];
+            const double den = p.x * p.x + p.y * p.y;
+            bad |= !(den > 0.0 && isfinite(den));
+            const double2 ip = make_double2(p.x / den, -p.y / den);
+            if (lane == t) {
+#pragma unroll
+                for (int i = 0; i < 32; ++i) {
+                    if (i == t) {
+                        a[i] = ip;
+                    } else {
+                        const double2 v = cmul(a[i], ip);
+                        a[i] = make_double2(-v.x, -v.y);
+                    }
+                }
+            } else {
+                const double2 r = cmul(a[t], ip);  // scaled pivot-row element of this column
+#pragma unroll
+                for (int i = 0; i < 32; ++i) {
+                    if (i == t) {
+                        a[i] = r;
+                    } else {
+                        const double2 c = colbuf[warp][i];
+                        a[i].x -= c.x * r.x - c.y * r.y;
+                        a[i].y -= c.x * r.y + c.y * r.x;
+                    }
+                }
+            }
+            __syncwarp();
+        }
+    }
+    if (bad && lane == 0) atomicOr(status, kStatusSingular);
+#pragma unroll
+    for (int i = 0; i < 32; ++i)
+        if (i < nb && lane < nb && i >= lane) A[i + static_cast<int64_t>(lane) * ld] = a[i];
+}
+
 // ---------------------------------------------------------------------------------------------
 // Batched complex FP64 GEMM on the CUDA cores: C = alpha op(A) op(B) + beta C for every tile of
-// a schedule step.  64 x 64 output tile, K step 16, 256 threads with 4 x 4 outputs each.
+// a schedule step.  32 x 32 output tile, K step 16, 64 threads with 4 x 4 outputs each.  The
+// complex product uses three real products per element (Re = P1 - P2, Im = P3 - P1 - P2 with
+// P1 = Ar Br, P2 = Ai Bi, P3 = (Ar + Ai)(Br + Bi)): GB300's FP64 rate is the bound here, and
+// the third real product saves a quarter of the DFMAs.
 constexpr int BM = kGemmTile, BN = kGemmTile, BK = 16;
 
 template <int OP>
@@ -145,14 +214,14 @@ __device__ __forceinline__ double2 load_op(const double2* __restrict__ X, int ld
 }
 
 template <int OPA, int OPB>
-__global__ void __launch_bounds__(256) k_gemm_f64(const GemmItem* __restrict__ items,
-                                                  const GemmTile* __restrict__ tiles, int64_t tfirst,
-                                                  int64_t ifirst, const double2* __restrict__ Abuf,
-                                                  int64_t sA, const double2* __restrict__ Bbuf,
-                                                  int64_t sB, double2* __restrict__ Cbuf, int64_t sC,
-                                                  double alpha, double beta, int lower) {
-    __shared__ double2 As[BK][BM + 1];
-    __shared__ double2 Bs[BK][BN + 1];
+__global__ void __launch_bounds__(64) k_gemm_f64(const GemmItem* __restrict__ items,
+                                                 const GemmTile* __restrict__ tiles, int64_t tfirst,
+                                                 int64_t ifirst, const double2* __restrict__ Abuf,
+                                                 int64_t sA, const double2* __restrict__ Bbuf,
+                                                 int64_t sB, double2* __restrict__ Cbuf, int64_t sC,
+                                                 double alpha, double beta, int lower) {
+    __shared__ double As[3][BK][BM + 1];
+    __shared__ double Bs[3][BK][BN + 1];
     const GemmTile t = tiles[tfirst + blockIdx.x];
     const GemmItem it = items[ifirst + t.item];
     const int64_t pole = blockIdx.y;
@@ -160,69 +229,85 @@ __global__ void __launch_bounds__(256) k_gemm_f64(const GemmItem* __restrict__ i
     const double2* B = Bbuf + pole * sB + it.b_off;
     double2* C = Cbuf + pole * sC + it.c_off;
     const int tid = threadIdx.x;
-    const int tx = tid % 16, ty = tid / 16;
-    double2 acc[4][4];
-    #pragma unroll
+    const int tx = tid % 8, ty = tid / 8;
+    double p1[4][4], p2[4][4], p3[4][4];
+#pragma unroll
     for (int i = 0; i < 4; ++i)
-        #pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = make_double2(0.0, 0.0);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) p1[i][j] = p2[i][j] = p3[i][j] = 0.0;
     for (int k0 = 0; k0 < it.K; k0 += BK) {
-        // A tile (BM x BK): coalesced along the contiguous index of the stored operand
-        #pragma unroll
-        for (int u = 0; u < 4; ++u) {
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int e = tid + 64 * u;
             int lm, lk;
             if (OPA == OP_T) {
-                lk = tid % BK;
-                lm = tid / BK + 16 * u;
+                lk = e % BK;
+                lm = e / BK;
             } else {
-                lm = tid % BM;
-                lk = tid / BM + 4 * u;
+                lm = e % BM;
+                lk = e / BM;
             }
             const int m = t.m0 + lm, k = k0 + lk;
-            As[lk][lm] = (m < it.M && k < it.K) ? load_op<OPA>(A, it.lda, m, k) : make_double2(0.0, 0.0);
+            const double2 v = (m < it.M && k < it.K) ? load_op<OPA>(A, it.lda, m, k) : make_double2(0.0, 0.0);
+            As[0][lk][lm] = v.x;
+            As[1][lk][lm] = v.y;
+            As[2][lk][lm] = v.x + v.y;
         }
-        #pragma unroll
-        for (int u = 0; u < 4; ++u) {
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int e = tid + 64 * u;
             int ln, lk;
             if (OPB == OP_T) {
-                ln = tid % BN;
-                lk = tid / BN + 4 * u;
+                ln = e % BN;
+                lk = e / BN;
             } else {
-                lk = tid % BK;
-                ln = tid / BK + 16 * u;
+                lk = e % BK;
+                ln = e / BK;
             }
             const int n = t.n0 + ln, k = k0 + lk;
-            Bs[lk][ln] = (n < it.N && k < it.K) ? load_op<OPB>(B, it.ldb, k, n) : make_double2(0.0, 0.0);
+            const double2 v = (n < it.N && k < it.K) ? load_op<OPB>(B, it.ldb, k, n) : make_double2(0.0, 0.0);
+            Bs[0][lk][ln] = v.x;
+            Bs[1][lk][ln] = v.y;
+            Bs[2][lk][ln] = v.x + v.y;
         }
         __syncthreads();
-        #pragma unroll 4
+#pragma unroll 2
         for (int kk = 0; kk < BK; ++kk) {
-            double2 av[4], bv[4];
-            #pragma unroll
-            for (int i = 0; i < 4; ++i) av[i] = As[kk][tx + 16 * i];
-            #pragma unroll
-            for (int j = 0; j < 4; ++j) bv[j] = Bs[kk][ty + 16 * j];
-            #pragma unroll
+            double ar[4], ai[4], as[4], br[4], bi[4], bs[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                ar[i] = As[0][kk][tx + 8 * i];
+                ai[i] = As[1][kk][tx + 8 * i];
+                as[i] = As[2][kk][tx + 8 * i];
+            }
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                br[j] = Bs[0][kk][ty + 8 * j];
+                bi[j] = Bs[1][kk][ty + 8 * j];
+                bs[j] = Bs[2][kk][ty + 8 * j];
+            }
+#pragma unroll
             for (int i = 0; i < 4; ++i)
-                #pragma unroll
+#pragma unroll
                 for (int j = 0; j < 4; ++j) {
-                    acc[i][j].x = fma(av[i].x, bv[j].x, acc[i][j].x);
-                    acc[i][j].x = fma(-av[i].y, bv[j].y, acc[i][j].x);
-                    acc[i][j].y = fma(av[i].x, bv[j].y, acc[i][j].y);
-                    acc[i][j].y = fma(av[i].y, bv[j].x, acc[i][j].y);
+                    p1[i][j] = fma(ar[i], br[j], p1[i][j]);
+                    p2[i][j] = fma(ai[i], bi[j], p2[i][j]);
+                    p3[i][j] = fma(as[i], bs[j], p3[i][j]);
                 }
         }
         __syncthreads();
     }
-    #pragma unroll
+#pragma unroll
     for (int j = 0; j < 4; ++j) {
-        const int n = t.n0 + ty + 16 * j;
-        #pragma unroll
+        const int n = t.n0 + ty + 8 * j;
+#pragma unroll
         for (int i = 0; i < 4; ++i) {
-            const int m = t.m0 + tx + 16 * i;
+            const int m = t.m0 + tx + 8 * i;
             if (m < it.M && n < it.N && (!lower || m >= n)) {
                 double2* c = C + m + static_cast<int64_t>(n) * it.ldc;
-                double2 v = make_double2(alpha * acc[i][j].x, alpha * acc[i][j].y);
+                const double re = p1[i][j] - p2[i][j];
+                const double im = p3[i][j] - p1[i][j] - p2[i][j];
+                double2 v = make_double2(alpha * re, alpha * im);
                 if (beta != 0.0) {
                     const double2 old = *c;
                     v.x += beta * old.x;
@@ -345,7 +430,7 @@ cudaError_t gemm_launch(const Plan& P, const DevTables& T, const Launch& l, cons
     const double2* bufs[2] = {W.fronts, W.scr};
     const int64_t strides[2] = {W.front_stride, W.scr_stride};
     dim3 grid(static_cast<unsigned>(l.tcount), static_cast<unsigned>(np));
-    k_gemm_f64<OPA, OPB><<<grid, 256, 0, st>>>(T.gemm_items, T.gemm_tiles, l.tfirst, l.first,
+    k_gemm_f64<OPA, OPB><<<grid, 64, 0, st>>>(T.gemm_items, T.gemm_tiles, l.tfirst, l.first,
                                                bufs[l.bufA], strides[l.bufA], bufs[l.bufB],
                                                strides[l.bufB], const_cast<double2*>(bufs[l.bufC]),
                                                strides[l.bufC], l.alpha, l.beta, l.lower);
@@ -375,9 +460,12 @@ cudaError_t launch_step(const Plan& P, const DevTables& T, const Launch& l, cons
             dim3 grid(static_cast<unsigned>(l.count), static_cast<unsigned>(np));
             const int b = P.block;
             const size_t sm = static_cast<size_t>(b) * (b + 1) * sizeof(double2);
-            if (b <= 16) k_diaginv<16><<<grid, 256, sm, st>>>(T.diag_items, l.first, W.fronts, W.front_stride, T.status);
-            else if (b <= 32) k_diaginv<32><<<grid, 256, sm, st>>>(T.diag_items, l.first, W.fronts, W.front_stride, T.status);
-            else k_diaginv<64><<<grid, 256, sm, st>>>(T.diag_items, l.first, W.fronts, W.front_stride, T.status);
+            if (b <= 32) {
+                dim3 g2(static_cast<unsigned>(l.count), static_cast<unsigned>((np + 3) / 4));
+                k_diaginv_warp<<<g2, 128, 0, st>>>(T.diag_items, l.first, W.fronts, W.front_stride, np, T.status);
+            } else {
+                k_diaginv<64><<<grid, 256, sm, st>>>(T.diag_items, l.first, W.fronts, W.front_stride, T.status);
+            }
             return cudaGetLastError();
         }
         case L_GEMM: {

@@ -143,7 +143,7 @@ int analyze(const ndsi_pattern* pat, int32_t n_atoms, const double* centers,
 int cf_poles(int32_t M, double* z, double* R, std::string& err);
 
 // Tile sizes shared by the schedule and the kernels.
-constexpr int kGemmTile = 64;     // FP64 GEMM output tile (rows and columns)
+constexpr int kGemmTile = 32;     // FP64 GEMM output tile (rows and columns)
 constexpr int kNodeTile = 32;     // assembly / gather tile
 
 void set_last_error(const std::string& msg);

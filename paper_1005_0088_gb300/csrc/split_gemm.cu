@@ -69,13 +69,13 @@ void build_split_schedule(const Plan& P, int slices, std::vector<SplitItem>& ite
         st.tcount = static_cast<int64_t>(tiles.size()) - st.tfirst;
         for (int64_t i = 0; i < l.count; ++i) {
             const GemmItem& g = P.gemm_items[l.first + i];
-            for (int32_t r0 = 0; r0 < g.M; r0 += 64) blocks.push_back(SliceBlock{static_cast<int32_t>(i), r0});
+            for (int32_t r0 = 0; r0 < g.M; r0 += 32) blocks.push_back(SliceBlock{static_cast<int32_t>(i), r0});
         }
         st.sa_count = static_cast<int64_t>(blocks.size()) - st.sa_first;
         st.sb_first = static_cast<int64_t>(blocks.size());
         for (int64_t i = 0; i < l.count; ++i) {
             const GemmItem& g = P.gemm_items[l.first + i];
-            for (int32_t n0 = 0; n0 < g.N; n0 += 64) blocks.push_back(SliceBlock{static_cast<int32_t>(i), n0});
+            for (int32_t n0 = 0; n0 < g.N; n0 += 32) blocks.push_back(SliceBlock{static_cast<int32_t>(i), n0});
         }
         st.sb_count = static_cast<int64_t>(blocks.size()) - st.sb_first;
         st.Kcols = std::max(64, 2 * kmax);
@@ -214,6 +214,75 @@ __device__ __forceinline__ void ff_add(float& hi, float& lo, float v) {
     lo += e;
 }
 
+// (hi + lo) * 2^e rounded to nearest double, using integer operations only (GB300's FP64 pipe is
+// the scarce unit): both floats become signed integer mantissas at a common exponent, their
+// exact sum (an int64) is rounded to 53 bits and packed with the combined exponent.  Out of the
+// normal double range it falls back to FP64 arithmetic.
+__device__ __forceinline__ double ff_to_double_scaled(float hi, float lo, int e) {
+    const uint32_t bh = __float_as_uint(hi), bl = __float_as_uint(lo);
+    const int eh = static_cast<int>((bh >> 23) & 0xFF), el = static_cast<int>((bl >> 23) & 0xFF);
+    int64_t mh = eh ? static_cast<int64_t>((bh & 0x7FFFFFu) | 0x800000u) : 0;
+    int64_t ml = el ? static_cast<int64_t>((bl & 0x7FFFFFu) | 0x800000u) : 0;
+    if (bh >> 31) mh = -mh;
+    if (bl >> 31) ml = -ml;
+    int64_t S;
+    int E0;
+    if (ml == 0) {
+        if (mh == 0) return 0.0;
+        S = mh;
+        E0 = eh - 150;
+    } else if (mh == 0) {
+        S = ml;
+        E0 = el - 150;
+    } else {
+        int64_t big = mh, small = ml;
+        int ebig = eh, esmall = el;
+        if (el > eh) {
+            big = ml;
+            small = mh;
+            ebig = el;
+            esmall = eh;
+        }
+        const int d = ebig - esmall;
+        if (d <= 38) {
+            S = (big << d) + small;
+            E0 = esmall - 150;
+        } else {
+            S = (big << 38) + (small >> (d - 38));
+            E0 = ebig - 150 - 38;
+        }
+    }
+    const bool neg = S < 0;
+    uint64_t u = static_cast<uint64_t>(neg ? -S : S);
+    if (u == 0) return 0.0;
+    const int nbits = 64 - __clzll(static_cast<long long>(u));
+    int exp2;
+    uint64_t mant;
+    if (nbits > 53) {
+        int sh = nbits - 53;
+        mant = u >> sh;
+        const uint64_t rem = u & ((uint64_t(1) << sh) - 1);
+        const uint64_t half = uint64_t(1) << (sh - 1);
+        if (rem > half || (rem == half && (mant & 1))) ++mant;
+        if (mant >> 53) {
+            mant >>= 1;
+            ++sh;
+        }
+        exp2 = E0 + e + sh + 52;
+    } else {
+        mant = u << (53 - nbits);
+        exp2 = E0 + e - (53 - nbits) + 52;
+    }
+    const int biased = exp2 + 1023;
+    if (biased <= 0 || biased >= 2047) {
+        const double v = static_cast<double>(hi) + static_cast<double>(lo);
+        return ldexp(v, e);
+    }
+    const uint64_t bits = (static_cast<uint64_t>(neg) << 63) | (static_cast<uint64_t>(biased) << 52) |
+                          (mant & ((uint64_t(1) << 52) - 1));
+    return __longlong_as_double(static_cast<long long>(bits));
+}
+
 // ----------------------------------------------------------------------------- slicing -----
 // Biased FP64 exponent of x with zero mapped to -1 (and subnormals to 1).
 __device__ __forceinline__ int fp64_expo(double x) {
@@ -249,6 +318,45 @@ __device__ __forceinline__ void fp64_digits(double x, int E, int* d) {
     d[0] = static_cast<int>(F);
 }
 
+// Same digits with 32-bit integer work: the fixed-point value is split into 24-bit halves
+// (S <= 6: F < 2^47), the low half's balanced digits carry into the high half.
+template <int S>
+__device__ __forceinline__ void fp64_digits32(double x, int E, int* d) {
+    if (S > 6) {
+        fp64_digits<S>(x, E, d);
+        return;
+    }
+    const int64_t b = __double_as_longlong(x);
+    int ex = static_cast<int>((b >> 52) & 0x7FF);
+    int64_t mant = b & 0xFFFFFFFFFFFFFLL;
+    if (ex) mant |= 0x10000000000000LL; else ex = 1;
+    const int rsh = 1076 + E - 8 * S - ex;  // >= 6 for S <= 6
+    const uint64_t F = rsh >= 62 ? 0 : (((static_cast<uint64_t>(mant) >> (rsh - 1)) + 1) >> 1);
+    int lo = static_cast<int>(F & 0xFFFFFF);
+    int hi = static_cast<int>(F >> 24);
+    const bool neg = b < 0;
+    if (neg) {
+        // -(hi*2^24 + lo) = (-hi-1)*2^24 + (2^24 - lo), keeping lo in [0, 2^24)
+        if (lo) {
+            hi = -hi - 1;
+            lo = 0x1000000 - lo;
+        } else {
+            hi = -hi;
+        }
+    }
+    // digits S-1 .. S-3 from lo (0-based index), the rest from hi
+#pragma unroll
+    for (int t = S - 1; t >= 1; --t) {
+        int& v = (t >= S - 3) ? lo : hi;
+        int low = v & 0xFF;
+        if (low >= 128) low -= 256;
+        d[t] = low;
+        v = (v - low) >> 8;
+        if (t == S - 3) hi += lo;  // carry out of the low half
+    }
+    d[0] = hi;
+}
+
 // BF16 bit pattern of d * 2^(-8t), |d| <= 128 (exact).
 __device__ __forceinline__ uint16_t bf16_digit(int d, int t) {
     if (d == 0) return 0;
@@ -276,11 +384,18 @@ struct SliceArgs {
     int64_t erows_pole;
 };
 
-// Slices of one 64-row block of the stacked operand (A: rows m of op(A); B: columns n of op(B)).
+// Slices of one 32-row block of the stacked operand (A: rows m of op(A); B: columns n of op(B)).
+// A 32 x 64 complex tile is staged in shared memory with loads coalesced along whichever index
+// is contiguous in memory.  Pass 1 finds the row exponents (eight threads per row); pass 2 turns
+// two consecutive k per thread into digits, 32 threads per row, so every 4-byte store
+// instruction of a warp fills one whole 128-byte line of a slice.
+constexpr int kSliceRows = 32;
+constexpr int kSliceK = 64;
+
 template <int S>
-__global__ void __launch_bounds__(256) k_slice(const SliceArgs p) {
-    __shared__ double2 tile[64][33];
-    __shared__ int rowmax[64];
+__global__ void __launch_bounds__(256, 3) k_slice(const SliceArgs p) {
+    __shared__ double2 tile[kSliceRows][kSliceK + 1];
+    __shared__ int rowmax[kSliceRows];
     const SliceBlock blk = p.blocks[p.bfirst + blockIdx.x];
     const GemmItem it = p.items[p.ifirst + blk.item];
     const SplitItem si = p.sitems[p.ifirst + blk.item];
@@ -292,85 +407,105 @@ __global__ void __launch_bounds__(256) k_slice(const SliceArgs p) {
     const bool sym = p.op == OP_S;
     const bool rows_contig = !sym && (p.isB ? p.op == OP_T : p.op == OP_N);
     const int tid = threadIdx.x;
-    const int r0 = blk.r0;
-    if (tid < 64) rowmax[tid] = -1;
-    auto elem = [&](int row, int k) -> double2 {
-        if (sym) {
-            const int hi = row > k ? row : k, lo = row > k ? k : row;
-            return base[hi + static_cast<int64_t>(lo) * ld];
-        }
-        return rows_contig ? base[row + static_cast<int64_t>(k) * ld] : base[k + static_cast<int64_t>(row) * ld];
-    };
+    const int r = tid / 8, kg = tid % 8;
+    const int row = blk.r0 + r;
+    if (tid < kSliceRows) rowmax[tid] = -1;
     auto load_tile = [&](int k0) {
-        // 64 rows x 32 k, coalesced along the stored contiguous index
-        for (int e = tid; e < 64 * 32; e += 256) {
-            int r, kk;
+#pragma unroll
+        for (int u = 0; u < kSliceRows * kSliceK / 256; ++u) {
+            const int e = tid + 256 * u;
+            int rr, kk;
             if (rows_contig) {
-                r = e % 64;
-                kk = e / 64;
+                rr = e % kSliceRows;
+                kk = e / kSliceRows;
             } else {
-                kk = e % 32;
-                r = e / 32;
+                kk = e % kSliceK;
+                rr = e / kSliceK;
             }
-            const int row = r0 + r, k = k0 + kk;
-            tile[r][kk] = (row < nrows && k < K) ? elem(row, k) : make_double2(0.0, 0.0);
+            const int gr = blk.r0 + rr, k = k0 + kk;
+            double2 x = make_double2(0.0, 0.0);
+            if (gr < nrows && k < K) {
+                if (sym) {
+                    const int hi = gr > k ? gr : k, lo = gr > k ? k : gr;
+                    x = base[hi + static_cast<int64_t>(lo) * ld];
+                } else if (rows_contig) {
+                    x = base[gr + static_cast<int64_t>(k) * ld];
+                } else {
+                    x = base[k + static_cast<int64_t>(gr) * ld];
+                }
+            }
+            tile[rr][kk] = x;
         }
     };
-    // phase 1: row exponents
     __syncthreads();
     int lmax = -1;
-    const int my_r = tid % 64, my_k = (tid / 64) * 8;
-    for (int k0 = 0; k0 < K; k0 += 32) {
+    for (int k0 = 0; k0 < K; k0 += kSliceK) {
         load_tile(k0);
         __syncthreads();
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
-            const double2 v = tile[my_r][my_k + j];
+            const double2 v = tile[r][kg * 8 + j];
             lmax = max(lmax, max(fp64_expo(v.x), fp64_expo(v.y)));
         }
         __syncthreads();
     }
-    atomicMax(&rowmax[my_r], lmax);
+    atomicMax(&rowmax[r], lmax);
     __syncthreads();
-    // phase 2: digits
-    const int kk = tid % 32;
-    for (int k0 = 0; k0 < si.Kpad; k0 += 32) {
+    const bool live = row < nrows;
+    const int E = rowmax[r] < 0 ? -1021 : rowmax[r] - 1022;
+    for (int k0 = 0; k0 < si.Kpad; k0 += kSliceK) {
         load_tile(k0);
         __syncthreads();
-        for (int r = tid / 32; r < 64; r += 8) {
-            const int row = r0 + r;
-            if (row >= nrows) continue;
-            const int E = rowmax[r] < 0 ? -1021 : rowmax[r] - 1022;
-            const double2 v = tile[r][kk];
-            int dr[S], di[S];
-            fp64_digits<S>(v.x, E, dr);
-            fp64_digits<S>(v.y, E, di);
-            const int64_t col = k0 + kk;
+        // 32 threads per row, two consecutive k each: one 128-byte line per warp store
+        const int kk = (tid % 32) * 2;
+        const int col = k0 + kk;
+#pragma unroll 1
+        for (int pass = 0; pass < kSliceRows / 8; ++pass) {
+            const int rr = pass * 8 + tid / 32;
+            const int grow = blk.r0 + rr;
+            if (grow >= nrows || col >= si.Kpad) continue;
+            const int Er = rowmax[rr] < 0 ? -1021 : rowmax[rr] - 1022;
+            int64_t o0, ost;
+            if (!p.isB) {
+                o0 = pole * p.rows_pole + si.rowA + grow;
+                ost = si.Mpad;
+            } else {
+                o0 = pole * p.rows_pole + si.rowB + (grow / 64) * 128 + (grow % 64);
+                ost = 2 * si.Npad;
+            }
+            const double2 v0 = tile[rr][kk];
+            const double2 v1 = tile[rr][kk + 1];
+            int d0[S], d1[S];
+            uint32_t wre[S], wim[S];
+            fp64_digits32<S>(v0.x, Er, d0);
+            fp64_digits32<S>(v1.x, Er, d1);
+#pragma unroll
+            for (int t = 0; t < S; ++t)
+                wre[t] = static_cast<uint32_t>(bf16_digit(d0[t], t)) | (static_cast<uint32_t>(bf16_digit(d1[t], t)) << 16);
+            fp64_digits32<S>(v0.y, Er, d0);
+            fp64_digits32<S>(v1.y, Er, d1);
+#pragma unroll
+            for (int t = 0; t < S; ++t)
+                wim[t] = static_cast<uint32_t>(bf16_digit(d0[t], t)) | (static_cast<uint32_t>(bf16_digit(d1[t], t)) << 16);
 #pragma unroll
             for (int t = 0; t < S; ++t) {
+                uint16_t* o1 = p.out + (o0 + t * ost) * p.Kcols;
                 if (!p.isB) {
-                    const int64_t orow = pole * p.rows_pole + si.rowA + static_cast<int64_t>(t) * si.Mpad + row;
-                    uint16_t* o = p.out + orow * p.Kcols;
-                    o[col] = bf16_digit(dr[t], t);
-                    o[si.Kpad + col] = bf16_digit(di[t], t);
+                    *reinterpret_cast<uint32_t*>(o1 + col) = wre[t];
+                    *reinterpret_cast<uint32_t*>(o1 + si.Kpad + col) = wim[t];
                 } else {
-                    const int64_t orow = pole * p.rows_pole + si.rowB + static_cast<int64_t>(t) * 2 * si.Npad +
-                                         (row / 64) * 128 + (row % 64);
-                    uint16_t* o1 = p.out + orow * p.Kcols;
-                    uint16_t* o2 = p.out + (orow + 64) * p.Kcols;
-                    o1[col] = bf16_digit(dr[t], t);
-                    o1[si.Kpad + col] = bf16_digit(-di[t], t);
-                    o2[col] = bf16_digit(di[t], t);
-                    o2[si.Kpad + col] = bf16_digit(dr[t], t);
+                    // rows [Re | -Im] and [Im | Re]; negation flips the BF16 sign bits
+                    uint16_t* o2 = o1 + 64 * static_cast<int64_t>(p.Kcols);
+                    *reinterpret_cast<uint32_t*>(o1 + col) = wre[t];
+                    *reinterpret_cast<uint32_t*>(o1 + si.Kpad + col) = wim[t] ^ 0x80008000u;
+                    *reinterpret_cast<uint32_t*>(o2 + col) = wim[t];
+                    *reinterpret_cast<uint32_t*>(o2 + si.Kpad + col) = wre[t];
                 }
             }
         }
         __syncthreads();
     }
-    if (tid < 64 && r0 + tid < nrows) {
-        const int E = rowmax[tid] < 0 ? -1021 : rowmax[tid] - 1022;
-        p.expo[pole * p.erows_pole + (p.isB ? si.erowB : si.erowA) + r0 + tid] = E;
-    }
+    if (live && kg == 0) p.expo[pole * p.erows_pole + (p.isB ? si.erowB : si.erowA) + row] = E;
 }
 
 // ---------------------------------------------------------------------------- the GEMM -----
@@ -573,20 +708,30 @@ __global__ void __launch_bounds__(kThreads, 1)
                 const int r = idx % 128, j = idx / 128;
                 const int m = tile.m0 + r, n = tile.n0 + j;
                 if (m >= it.M || n >= it.N || (p.lower && n > m)) continue;
-                const int e0 = p.expA[pole * p.erowsA + si.erowA + m] + p.expB[pole * p.erowsB + si.erowB + n] - 14;
-                const int e = e0 < -1022 ? -1022 : (e0 > 1023 ? 1023 : e0);
-                const double scale = __longlong_as_double(static_cast<int64_t>(e + 1023) << 52) * p.alpha;
-                const double re = (static_cast<double>(sm_hi[j * 128 + r]) + static_cast<double>(sm_lo[j * 128 + r])) * scale;
-                const double im = (static_cast<double>(sm_hi[(64 + j) * 128 + r]) +
-                                   static_cast<double>(sm_lo[(64 + j) * 128 + r])) * scale;
+                const int e = p.expA[pole * p.erowsA + si.erowA + m] + p.expB[pole * p.erowsB + si.erowB + n] - 14;
+                double re = ff_to_double_scaled(sm_hi[j * 128 + r], sm_lo[j * 128 + r], e);
+                double im = ff_to_double_scaled(sm_hi[(64 + j) * 128 + r], sm_lo[(64 + j) * 128 + r], e);
+                if (p.alpha != 1.0) {
+                    if (p.alpha == -1.0) {
+                        re = -re;
+                        im = -im;
+                    } else {
+                        re *= p.alpha;
+                        im *= p.alpha;
+                    }
+                }
                 double2* dst = Cp + m + static_cast<int64_t>(n) * it.ldc;
-                double2 v = make_double2(re, im);
                 if (p.beta != 0.0) {
                     const double2 old = *dst;
-                    v.x += p.beta * old.x;
-                    v.y += p.beta * old.y;
+                    if (p.beta == 1.0) {
+                        re += old.x;
+                        im += old.y;
+                    } else {
+                        re = fma(p.beta, old.x, re);
+                        im = fma(p.beta, old.y, im);
+                    }
                 }
-                *dst = v;
+                *dst = make_double2(re, im);
             }
         }
     }

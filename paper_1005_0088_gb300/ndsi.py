@@ -24,7 +24,7 @@ NDSI_ERR_UNSUPPORTED = 6
 NDSI_PREC_FP64 = 0
 NDSI_PREC_SPLIT = 1
 EXPORT = dict(perm_atoms=1, perm_basis=2, node_atoms=3, parent=4, struct_ptr=5, struct_atoms=6,
-              level=7)
+              level=7, schedule=8)
 
 # Every function declared in include/ndsi.h.
 EXPORTED_SYMBOLS = (
@@ -55,7 +55,8 @@ class ndsi_plan_summary(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int64), ("nnz", ctypes.c_int64), ("n_atoms", ctypes.c_int32),
                 ("n_nodes", ctypes.c_int32), ("n_levels", ctypes.c_int32),
                 ("max_front", ctypes.c_int32), ("front_elems", ctypes.c_int64),
-                ("flops_per_pole", ctypes.c_double), ("bytes_per_pole", ctypes.c_double)]
+                ("flops_per_pole", ctypes.c_double), ("bytes_per_pole", ctypes.c_double),
+                ("n_launches", ctypes.c_int32), ("pad", ctypes.c_int32)]
 
 
 class ndsi_profile_entry(ctypes.Structure):
@@ -209,10 +210,13 @@ def ndsi_plan_export(plan: Plan, what: str) -> np.ndarray:
         return out[:int(ptr[-1])]
     sizes = dict(perm_atoms=(info["n_atoms"], np.int32), perm_basis=(info["n"], np.int32),
                  node_atoms=(nn + 1, np.int32), parent=(nn, np.int32),
-                 struct_ptr=(nn + 1, np.int64), level=(nn, np.int32))
+                 struct_ptr=(nn + 1, np.int64), level=(nn, np.int32),
+                 schedule=(4 * info["n_launches"], np.int32))
     cnt, dt = sizes[what]
     out = np.zeros(cnt, dtype=dt)
     _check(load().ndsi_plan_export(plan.handle, EXPORT[what], _ptr(out)))
+    if what == "schedule":
+        return out.reshape(-1, 4)
     return out
 
 
