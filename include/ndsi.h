@@ -199,6 +199,58 @@ int ndsi_profile_read(const ndsi_plan* plan, ndsi_profile_entry* out, int32_t ma
 int ndsi_residue_sum_static(const double* G, const double* c, int32_t n_points, const double* S,
                             int64_t nnz, double* rho_out, double* n_elec_out, void* stream);
 
+/* Chemical-potential search (Sec. II.C.3): find mu with
+ *   DeltaN(mu) = Tr(rho(mu) S) - n_electrons = 0      (Eq. 40)
+ * to |DeltaN| < tol_electrons.  Every trial mu is one full contour evaluation (ndsi_density).
+ * The bracket [mu_lo, mu_hi] (e.g. from a learned seed) is checked first and, if it does not
+ * enclose the root, widened step by step towards the Gershgorin bounds of the pencil (H, S);
+ * pass mu_lo >= mu_hi to start from those bounds.  Inside the bracket each step takes the
+ * paper's Muller step (procedure (4), Eqs. 45-46: the positive-slope root of the quadratic
+ * through the three evaluations with the smallest |DeltaN| and both signs), else the linear
+ * interpolation of procedure (3) between the bracket ends (Eq. 44 with the denominator read as
+ * DeltaN_i - DeltaN_j, Illinois-weighted), and bisects whenever a step would leave the
+ * bracket's central 98% or two steps fail to halve it.
+ *   H, S            - values on the pattern, device or host.
+ *   rho_out         - rho at the returned mu, device or host (double[nnz]).
+ *   mu_out, n_elec_out, iters_out - host scalars (iters = contour evaluations used).
+ * Errors: NDSI_ERR_INVALID (kT <= 0, n_poles < 1, tol <= 0, no sign change within the bounds),
+ * NDSI_ERR_TIMEOUT if max_iter evaluations do not converge (the best mu is still returned),
+ * and every error of ndsi_density. */
+int ndsi_find_mu(ndsi_plan* plan, const double* H, const double* S, double kT, int32_t n_poles,
+                 double n_electrons, double mu_lo, double mu_hi, double tol_electrons,
+                 int32_t max_iter, double* rho_out, double* mu_out, double* n_elec_out,
+                 int32_t* iters_out, void* stream);
+
+/* ---- Learned seed for the chemical-potential search (not in the paper; it only proposes the
+ * starting bracket of ndsi_find_mu, whose bisection stays the judge of the result). ----
+ * Network: 32 inputs -> 64 tanh -> 64 tanh -> 1 output, FP32, parameters packed as
+ * [W1 (64x32 row-major), b1 (64), W2 (64x64), b2 (64), W3 (64), b3 (1)]. */
+#define NDSI_MLP_INPUTS 32
+#define NDSI_MLP_HIDDEN 64
+#define NDSI_MLP_PARAMS 6337
+
+/* Input features of a system (device or host float[32]):
+ *   [0..23]  Chebyshev moments (1/N) Tr T_k(H/4), k = 1..24 (fixed window [-4, 4] Ha),
+ *   [24..29] Chebyshev moments (1/N) Tr T_k((S - I)/0.75), k = 1..6,
+ *   [30] filling n_electrons/(2N), [31] 10*kT (Ha),
+ * traces estimated with n_vectors Rademacher vectors from a counter-based generator (seed).
+ * Errors: NDSI_ERR_INVALID, NDSI_ERR_OOM, NDSI_ERR_CUDA. */
+int ndsi_mu_features(ndsi_plan* plan, const double* H, const double* S, double n_electrons,
+                     double kT, int32_t n_vectors, uint64_t seed, float* feat_out, void* stream);
+
+/* params (device float[NDSI_MLP_PARAMS]) <- Glorot-uniform weights, zero biases. */
+int ndsi_mlp_init(float* params, uint64_t seed, void* stream);
+/* Y[s] = network(X[s, :]) for s < n; X device float[n*32], Y device float[n]. */
+int ndsi_mlp_forward(const float* params, const float* X, int32_t n, float* Y, void* stream);
+/* grad (device float[NDSI_MLP_PARAMS]) and loss (device float, may be NULL) of the mean squared
+ * error (1/n) sum_s (network(X_s) - T_s)^2.  Synchronises the stream. */
+int ndsi_mlp_grad(const float* params, const float* X, const float* T, int32_t n, float* grad,
+                  float* loss, void* stream);
+/* `steps` full-batch Adam steps (beta1 0.9, beta2 0.999) on the mean squared error; final loss
+ * to *loss_out (host, may be NULL).  Synchronises the stream. */
+int ndsi_mlp_train(float* params, const float* X, const float* T, int32_t n, int32_t steps,
+                   float lr, float* loss_out, void* stream);
+
 void ndsi_plan_destroy(ndsi_plan* plan);
 void ndsi_factors_destroy(ndsi_factors* f);
 

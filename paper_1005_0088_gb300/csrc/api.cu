@@ -139,6 +139,8 @@ int upload_tables(ndsi_plan* h) {
         {P.copy_items.data(), bytes_of(P.copy_items), reinterpret_cast<void**>(&T.copy_items)},
         {P.diag_items.data(), bytes_of(P.diag_items), reinterpret_cast<void**>(&T.diag_items)},
         {P.node_tiles.data(), bytes_of(P.node_tiles), reinterpret_cast<void**>(&T.node_tiles)},
+        {P.rowptr.data(), bytes_of(P.rowptr), reinterpret_cast<void**>(&T.rowptr)},
+        {P.col.data(), bytes_of(P.col), reinterpret_cast<void**>(&T.col)},
         {nullptr, sizeof(int) * 4, reinterpret_cast<void**>(&T.status)},
     };
     size_t total = 0;
@@ -578,6 +580,12 @@ int ndsi_selinv(ndsi_factors* f, double* G_out, void* stream) {
     return check_status(h, st);
 }
 
+namespace ndsi {
+// rho(mu) and Tr(rho S) for device inputs and outputs; synchronises the stream.
+int density_impl(ndsi_plan* h, const double* Hd, const double* Sd, double mu, double kT, int32_t n_poles,
+                 double* rho_d, double* ne_d, cudaStream_t st);
+}  // namespace ndsi
+
 int ndsi_density(ndsi_plan* h, const double* H, const double* S, double mu, double kT, int32_t n_poles,
                  double* rho_out, double* n_elec_out, void* stream) {
     if (!h || !H || !S || !rho_out || n_poles < 1 || !(kT > 0) || !std::isfinite(mu))
@@ -585,6 +593,27 @@ int ndsi_density(ndsi_plan* h, const double* H, const double* S, double mu, doub
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     int rc = upload_tables(h);
     if (rc) return rc;
+    const double *Hd, *Sd;
+    rc = device_inputs(h, H, S, &Hd, &Sd, st);
+    if (rc) return rc;
+    const bool rho_dev = is_device_ptr(rho_out);
+    const bool ne_dev = n_elec_out && is_device_ptr(n_elec_out);
+    rc = ensure_stage(h, 3 * h->P.nnz + 8);
+    if (rc) return rc;
+    double* rho_d = rho_dev ? rho_out : h->stage + 2 * h->P.nnz;
+    double* ne_d = ne_dev ? n_elec_out : h->stage + 3 * h->P.nnz;
+    rc = density_impl(h, Hd, Sd, mu, kT, n_poles, rho_d, ne_d, st);
+    if (rc) return rc;
+    if (!rho_dev) NDSI_CK(cudaMemcpyAsync(rho_out, rho_d, sizeof(double) * h->P.nnz, cudaMemcpyDeviceToHost, st));
+    if (n_elec_out && !ne_dev) NDSI_CK(cudaMemcpyAsync(n_elec_out, ne_d, sizeof(double), cudaMemcpyDeviceToHost, st));
+    NDSI_CK(cudaStreamSynchronize(st));
+    return NDSI_OK;
+}
+
+namespace ndsi {
+int density_impl(ndsi_plan* h, const double* Hd, const double* Sd, double mu, double kT, int32_t n_poles,
+                 double* rho_d, double* ne_d, cudaStream_t st) {
+    int rc;
     // poles of Eq. 7 (cached per M) -> points alpha_p and weights w_p of Eq. 8, plus iR for M0
     if (h->pole_M != n_poles) {
         h->pole_z.assign(n_poles, 0.0);
@@ -623,17 +652,6 @@ int ndsi_density(ndsi_plan* h, const double* H, const double* S, double mu, doub
     if (!h->partials) NDSI_CK(cudaMalloc(&h->partials, sizeof(double) * (accumulate_blocks(h->P.nnz) + 1)));
     NDSI_CK(cudaMemcpyAsync(h->zw, zq.data(), sizeof(double2) * nq, cudaMemcpyHostToDevice, st));
     NDSI_CK(cudaMemcpyAsync(h->cw, cq.data(), sizeof(double2) * nq, cudaMemcpyHostToDevice, st));
-    const double *Hd, *Sd;
-    rc = device_inputs(h, H, S, &Hd, &Sd, st);
-    if (rc) return rc;
-    const bool rho_dev = is_device_ptr(rho_out);
-    const bool ne_dev = n_elec_out && is_device_ptr(n_elec_out);
-    if (!rho_dev || (n_elec_out && !ne_dev)) {
-        rc = ensure_stage(h, 3 * h->P.nnz + 8);
-        if (rc) return rc;
-    }
-    double* rho_d = rho_dev ? rho_out : h->stage + 2 * h->P.nnz;
-    double* ne_d = ne_dev ? n_elec_out : h->stage + 3 * h->P.nnz;
     for (int32_t q0 = 0; q0 < nq; q0 += chunk) {
         const int32_t np = std::min(chunk, nq - q0);
         rc = run_phase(h, h->W, h->SB, 0, Hd, Sd, h->zw + q0, np, st);
@@ -650,9 +668,230 @@ int ndsi_density(ndsi_plan* h, const double* H, const double* S, double mu, doub
     const int nblk = accumulate_blocks(h->P.nnz);
     NDSI_CK(timed(h->prof, "reduce", static_cast<double>(nblk), 8.0 * nblk, st,
                   [&]() { return launch_reduce(h->partials, nblk, ne_d, st); }));
-    if (!rho_dev) NDSI_CK(cudaMemcpyAsync(rho_out, rho_d, sizeof(double) * h->P.nnz, cudaMemcpyDeviceToHost, st));
-    if (n_elec_out && !ne_dev) NDSI_CK(cudaMemcpyAsync(n_elec_out, ne_d, sizeof(double), cudaMemcpyDeviceToHost, st));
     return check_status(h, st);
+}
+}  // namespace ndsi
+
+int ndsi_find_mu(ndsi_plan* h, const double* H, const double* S, double kT, int32_t n_poles,
+                 double n_electrons, double mu_lo, double mu_hi, double tol_electrons, int32_t max_iter,
+                 double* rho_out, double* mu_out, double* n_elec_out, int32_t* iters_out, void* stream) {
+    if (!h || !H || !S || !rho_out || !mu_out || n_poles < 1 || !(kT > 0) || !(tol_electrons > 0) ||
+        max_iter < 1 || !std::isfinite(n_electrons))
+        return fail(NDSI_ERR_INVALID, "ndsi_find_mu: invalid argument");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    int rc = upload_tables(h);
+    if (rc) return rc;
+    const int64_t nnz = h->P.nnz;
+    const double *Hd, *Sd;
+    rc = device_inputs(h, H, S, &Hd, &Sd, st);
+    if (rc) return rc;
+    // Gershgorin bounds of H and S -> bounds of the pencil's spectrum (host, O(nnz))
+    std::vector<double> hv(nnz), sv(nnz);
+    NDSI_CK(cudaMemcpyAsync(hv.data(), Hd, sizeof(double) * nnz, cudaMemcpyDeviceToHost, st));
+    NDSI_CK(cudaMemcpyAsync(sv.data(), Sd, sizeof(double) * nnz, cudaMemcpyDeviceToHost, st));
+    NDSI_CK(cudaStreamSynchronize(st));
+    double hlo = 1e300, hhi = -1e300, slo = 1e300, shi = -1e300;
+    for (int64_t i = 0; i < h->P.n; ++i) {
+        double hd = 0, sd = 0, hr = 0, sr = 0;
+        for (int64_t k = h->P.rowptr[i]; k < h->P.rowptr[i + 1]; ++k) {
+            if (h->P.col[k] == i) {
+                hd = hv[k];
+                sd = sv[k];
+            } else {
+                hr += std::fabs(hv[k]);
+                sr += std::fabs(sv[k]);
+            }
+        }
+        hlo = std::min(hlo, hd - hr);
+        hhi = std::max(hhi, hd + hr);
+        slo = std::min(slo, sd - sr);
+        shi = std::max(shi, sd + sr);
+    }
+    double elo, ehi;
+    if (slo > 0) {
+        elo = hlo / (hlo < 0 ? slo : shi);
+        ehi = hhi / (hhi > 0 ? slo : shi);
+    } else {
+        elo = hlo < 0 ? hlo * 4 : -1.0;  // S not diagonally dominant: generous guess
+        ehi = hhi > 0 ? hhi * 4 : 1.0;
+    }
+    rc = ensure_stage(h, 3 * nnz + 8);
+    if (rc) return rc;
+    const bool rho_dev = is_device_ptr(rho_out);
+    double* rho_d = rho_dev ? rho_out : h->stage + 2 * nnz;
+    double* ne_d = h->stage + 3 * nnz;
+    int iters = 0;
+    double best_mu = 0, best_dn = 1e300;
+    auto eval = [&](double mu, double& dn) -> int {
+        int r = density_impl(h, Hd, Sd, mu, kT, n_poles, rho_d, ne_d, st);
+        if (r) return r;
+        double ne = 0;
+        cudaError_t e = cudaMemcpy(&ne, ne_d, sizeof(double), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return fail(NDSI_ERR_CUDA, "ndsi_find_mu: readback failed");
+        ++iters;
+        dn = ne - n_electrons;
+        if (std::fabs(dn) < std::fabs(best_dn)) {
+            best_dn = dn;
+            best_mu = mu;
+        }
+        return NDSI_OK;
+    };
+    double a, b, fa, fb;
+    if (mu_lo < mu_hi) {
+        a = std::max(mu_lo, elo);
+        b = std::min(mu_hi, ehi);
+        if (!(a < b)) {
+            a = elo;
+            b = ehi;
+        }
+    } else {
+        a = elo;
+        b = ehi;
+    }
+    if ((rc = eval(a, fa))) return rc;
+    if (std::fabs(fa) >= tol_electrons) {
+        if ((rc = eval(b, fb))) return rc;
+    } else {
+        fb = fa;
+        b = a;
+    }
+    // widen towards the spectral bounds until the bracket encloses the root
+    double grow = std::max(b - a, 1e-3);
+    while (std::fabs(fa) >= tol_electrons && std::fabs(fb) >= tol_electrons && fa * fb > 0) {
+        if (iters >= max_iter) break;
+        if (fa > 0) {
+            if (a <= elo) return fail(NDSI_ERR_INVALID, "ndsi_find_mu: no root above the lower spectral bound");
+            b = a;
+            fb = fa;
+            a = std::max(elo, a - grow);
+            if ((rc = eval(a, fa))) return rc;
+        } else {
+            if (b >= ehi) return fail(NDSI_ERR_INVALID, "ndsi_find_mu: no root below the upper spectral bound");
+            a = b;
+            fa = fb;
+            b = std::min(ehi, b + grow);
+            if ((rc = eval(b, fb))) return rc;
+        }
+        grow *= 2;
+    }
+    // Inside the bracket: the paper's Muller step (procedure (4), Eqs. 45-46) through the three
+    // evaluated points with the smallest |DeltaN| (both signs present), else the linear
+    // interpolation of procedure (3) between the bracket ends (Illinois-weighted), else bisection.
+    std::vector<std::pair<double, double>> pts;  // (mu, DeltaN) of every evaluation in the bracket
+    pts.emplace_back(a, fa);
+    pts.emplace_back(b, fb);
+    int side = 0;
+    double ga = fa, gb = fb;
+    double width_prev = 2.0 * (b - a), width_prev2 = 4.0 * (b - a);
+    while (std::fabs(best_dn) >= tol_electrons && iters < max_iter) {
+        const double w = b - a;
+        if (w <= 1e-15 * std::max(1.0, std::fabs(a))) break;
+        double c = std::nan("");
+        if (pts.size() >= 3) {
+            std::vector<std::pair<double, double>> q(pts);
+            std::sort(q.begin(), q.end(), [](const std::pair<double, double>& x, const std::pair<double, double>& y) {
+                return std::fabs(x.second) < std::fabs(y.second);
+            });
+            std::vector<std::pair<double, double>> sel(q.begin(), q.begin() + 3);
+            bool pos = false, neg = false;
+            for (auto& t : sel) (t.second > 0 ? pos : neg) = true;
+            if (!(pos && neg)) {
+                for (size_t i = 3; i < q.size(); ++i)
+                    if ((q[i].second > 0) != pos || (q[i].second < 0) != neg) {
+                        sel[2] = q[i];
+                        break;
+                    }
+            }
+            std::sort(sel.begin(), sel.end());
+            const double m0 = sel[0].first, m1 = sel[1].first, m2 = sel[2].first;
+            const double h1 = m1 - m0, h2 = m2 - m1;
+            if (h1 > 0 && h2 > 0) {
+                const double d1 = (sel[1].second - sel[0].second) / h1;
+                const double d2 = (sel[2].second - sel[1].second) / h2;
+                const double qa = (d2 - d1) / (h1 + h2);       // DeltaN ~ qa t^2 + qb t + qc, t = mu - m2
+                const double qb = qa * h2 + d2;
+                const double qc = sel[2].second;
+                const double disc = qb * qb - 4.0 * qa * qc;
+                if (disc >= 0) {
+                    const double sq = std::sqrt(disc);
+                    double t;
+                    if (qb >= 0) t = -2.0 * qc / (qb + sq);                       // Eq. 46, b >= 0
+                    else t = (std::fabs(qa) > 0) ? (-qb + sq) / (2.0 * qa) : std::nan("");  // b < 0
+                    c = m2 + t;
+                }
+            }
+        }
+        if (!(c > a + 0.01 * w && c < b - 0.01 * w)) c = b - gb * (b - a) / (gb - ga);
+        if (!(c > a + 0.01 * w && c < b - 0.01 * w)) c = 0.5 * (a + b);
+        double fc;
+        if ((rc = eval(c, fc))) return rc;
+        pts.emplace_back(c, fc);
+        width_prev2 = width_prev;
+        width_prev = w;
+        if (fc < 0) {
+            a = c;
+            fa = ga = fc;
+            if (side == -1) gb *= 0.5;
+            side = -1;
+        } else {
+            b = c;
+            fb = gb = fc;
+            if (side == 1) ga *= 0.5;
+            side = 1;
+        }
+        if (b - a > 0.5 * width_prev2 && std::fabs(best_dn) >= tol_electrons && iters < max_iter) {
+            // two steps did not halve the bracket: bisect once
+            const double m = 0.5 * (a + b);
+            double fm;
+            if ((rc = eval(m, fm))) return rc;
+            pts.emplace_back(m, fm);
+            if (fm < 0) {
+                a = m;
+                fa = ga = fm;
+            } else {
+                b = m;
+                fb = gb = fm;
+            }
+            side = 0;
+            width_prev2 = width_prev = b - a;
+        }
+    }
+    // rho_out must hold rho(best_mu): re-evaluate if the last trial was not the best
+    double last_dn = 0;
+    if ((rc = eval(best_mu, last_dn))) return rc;
+    --iters;  // the re-evaluation is bookkeeping, not a search step
+    *mu_out = best_mu;
+    if (n_elec_out) *n_elec_out = n_electrons + best_dn;
+    if (iters_out) *iters_out = iters;
+    if (!rho_dev) NDSI_CK(cudaMemcpyAsync(rho_out, rho_d, sizeof(double) * nnz, cudaMemcpyDeviceToHost, st));
+    NDSI_CK(cudaStreamSynchronize(st));
+    if (std::fabs(best_dn) >= tol_electrons)
+        return fail(NDSI_ERR_TIMEOUT, "ndsi_find_mu: not converged within max_iter evaluations");
+    return NDSI_OK;
+}
+
+int ndsi_mu_features(ndsi_plan* h, const double* H, const double* S, double n_electrons, double kT,
+                     int32_t n_vectors, uint64_t seed, float* feat_out, void* stream) {
+    if (!h || !H || !S || !feat_out || n_vectors < 1 || !(kT > 0))
+        return fail(NDSI_ERR_INVALID, "ndsi_mu_features: invalid argument");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    int rc = upload_tables(h);
+    if (rc) return rc;
+    const double *Hd, *Sd;
+    rc = device_inputs(h, H, S, &Hd, &Sd, st);
+    if (rc) return rc;
+    const bool dev = is_device_ptr(feat_out);
+    float* fd = feat_out;
+    if (!dev) NDSI_CK(cudaMalloc(&fd, sizeof(float) * NDSI_MLP_INPUTS));
+    rc = mlp_features(h->P, Hd, Sd, h->T.rowptr, h->T.col, n_electrons, kT, n_vectors, seed, fd, st);
+    if (!dev) {
+        if (!rc) {
+            cudaError_t e = cudaMemcpy(feat_out, fd, sizeof(float) * NDSI_MLP_INPUTS, cudaMemcpyDeviceToHost);
+            if (e != cudaSuccess) rc = fail(NDSI_ERR_CUDA, "ndsi_mu_features: readback failed");
+        }
+        cudaFree(fd);
+    }
+    return rc;
 }
 
 int ndsi_profile_enable(ndsi_plan* h, int32_t enable) {

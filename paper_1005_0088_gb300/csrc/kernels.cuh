@@ -23,6 +23,8 @@ struct DevTables {
     CopyItem* copy_items = nullptr;
     DiagItem* diag_items = nullptr;
     NodeTile* node_tiles = nullptr;
+    int64_t* rowptr = nullptr;   // CSR pattern (original order), for the moment features
+    int32_t* col = nullptr;
     int* status = nullptr;
     void* blob = nullptr;  // single allocation holding all of the above
 };
@@ -35,6 +37,11 @@ struct Workspace {
     int64_t scr_stride = 0;
     int32_t np_cap = 0;         // poles the buffers hold
 };
+
+// Spectral-moment features of (H, S) for the learned mu seed (mlp.cu).
+int mlp_features(const Plan& P, const double* Hd, const double* Sd, const int64_t* rowptr_d,
+                 const int32_t* col_d, double n_electrons, double kT, int R, uint64_t seed, float* feat_d,
+                 cudaStream_t st);
 
 // One-time kernel attributes (large dynamic shared memory).
 cudaError_t kernels_init();

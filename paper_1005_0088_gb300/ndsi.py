@@ -31,8 +31,12 @@ EXPORTED_SYMBOLS = (
     "ndsi_default_options", "ndsi_poles", "ndsi_analyze", "ndsi_plan_info", "ndsi_plan_export",
     "ndsi_factor_poles", "ndsi_selinv", "ndsi_density", "ndsi_plan_destroy",
     "ndsi_factors_destroy", "ndsi_last_error", "ndsi_profile_enable", "ndsi_profile_read",
-    "ndsi_residue_sum_static",
+    "ndsi_residue_sum_static", "ndsi_find_mu", "ndsi_mu_features", "ndsi_mlp_init",
+    "ndsi_mlp_forward", "ndsi_mlp_grad", "ndsi_mlp_train",
 )
+NDSI_MLP_INPUTS = 32
+NDSI_MLP_HIDDEN = 64
+NDSI_MLP_PARAMS = 6337
 
 
 class NdsiError(RuntimeError):
@@ -97,6 +101,17 @@ def load(path: str = LIB_PATH):
                                       ctypes.POINTER(i32)]
     lib.ndsi_residue_sum_static.argtypes = [vp, vp, i32, vp, i64, vp, vp, vp]
     lib.ndsi_residue_sum_static.restype = ctypes.c_int
+    lib.ndsi_find_mu.argtypes = [vp, vp, vp, dbl, i32, dbl, dbl, dbl, dbl, i32, vp,
+                                 ctypes.POINTER(dbl), ctypes.POINTER(dbl), ctypes.POINTER(i32), vp]
+    lib.ndsi_find_mu.restype = ctypes.c_int
+    lib.ndsi_mu_features.argtypes = [vp, vp, vp, dbl, dbl, i32, ctypes.c_uint64, vp, vp]
+    lib.ndsi_mlp_init.argtypes = [vp, ctypes.c_uint64, vp]
+    lib.ndsi_mlp_forward.argtypes = [vp, vp, i32, vp, vp]
+    lib.ndsi_mlp_grad.argtypes = [vp, vp, vp, i32, vp, vp, vp]
+    lib.ndsi_mlp_train.argtypes = [vp, vp, vp, i32, i32, ctypes.c_float, vp, vp]
+    for name in ("ndsi_mu_features", "ndsi_mlp_init", "ndsi_mlp_forward", "ndsi_mlp_grad",
+                 "ndsi_mlp_train"):
+        getattr(lib, name).restype = ctypes.c_int
     lib.ndsi_last_error.argtypes = []
     lib.ndsi_last_error.restype = ctypes.c_char_p
     for name in ("ndsi_poles", "ndsi_analyze", "ndsi_plan_info", "ndsi_plan_export",
@@ -268,3 +283,47 @@ def ndsi_residue_sum_static(G, c, n_points, S, nnz, rho_out, n_elec_out=None, st
     _check(load().ndsi_residue_sum_static(_ptr(G), _ptr(c), int(n_points), _ptr(S), int(nnz),
                                           _ptr(rho_out), _ptr(n_elec_out), _stream(stream)))
     return rho_out
+
+
+def ndsi_find_mu(plan: Plan, H, S, kT, n_poles, n_electrons, rho_out, mu_lo=0.0, mu_hi=0.0,
+                 tol_electrons=1e-8, max_iter=100, stream=None):
+    """(mu, N_e, evaluations): Eq. 40 solved by bracketed interpolation/bisection."""
+    mu = ctypes.c_double()
+    ne = ctypes.c_double()
+    it = ctypes.c_int32()
+    _check(load().ndsi_find_mu(plan.handle, _ptr(H), _ptr(S), float(kT), int(n_poles),
+                               float(n_electrons), float(mu_lo), float(mu_hi), float(tol_electrons),
+                               int(max_iter), _ptr(rho_out), ctypes.byref(mu), ctypes.byref(ne),
+                               ctypes.byref(it), _stream(stream)))
+    return mu.value, ne.value, it.value
+
+
+def ndsi_mu_features(plan: Plan, H, S, n_electrons, kT, feat_out, n_vectors=16, seed=12345,
+                     stream=None):
+    _check(load().ndsi_mu_features(plan.handle, _ptr(H), _ptr(S), float(n_electrons), float(kT),
+                                   int(n_vectors), int(seed), _ptr(feat_out), _stream(stream)))
+    return feat_out
+
+
+def ndsi_mlp_init(params, seed=0, stream=None):
+    _check(load().ndsi_mlp_init(_ptr(params), int(seed), _stream(stream)))
+    return params
+
+
+def ndsi_mlp_forward(params, X, n, Y, stream=None):
+    _check(load().ndsi_mlp_forward(_ptr(params), _ptr(X), int(n), _ptr(Y), _stream(stream)))
+    return Y
+
+
+def ndsi_mlp_grad(params, X, T, n, grad, loss=None, stream=None):
+    _check(load().ndsi_mlp_grad(_ptr(params), _ptr(X), _ptr(T), int(n), _ptr(grad), _ptr(loss),
+                                _stream(stream)))
+    return grad
+
+
+def ndsi_mlp_train(params, X, T, n, steps, lr, stream=None):
+    """Full-batch Adam on the mean squared error; returns the final loss."""
+    loss = np.zeros(1, dtype=np.float32)
+    _check(load().ndsi_mlp_train(_ptr(params), _ptr(X), _ptr(T), int(n), int(steps), float(lr),
+                                 _ptr(loss), _stream(stream)))
+    return float(loss[0])

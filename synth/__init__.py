@@ -13,4 +13,5 @@ from .lattice import (  # noqa: F401
     config_system,
     batched_systems,
     csr_from_dense,
+    mu_training_systems,
 )

@@ -239,3 +239,27 @@ def batched_systems(count=None):
         s.meta.update(name=f"C4.{i}", kT=0.01, poles=120)
         out.append(s)
     return out
+
+
+def mu_training_systems(count, seed):
+    """Small seeded systems with varied recipe parameters for the chemical-potential seed.
+
+    Shapes, orbital counts, onsite range, hopping spread, overlap scale, filling and kT are
+    drawn per system; every system uses the lattice recipe above.  Returns (System, kT) pairs.
+    """
+    rng = np.random.Generator(np.random.PCG64(seed))
+    shapes = [((3, 3, 3), "3d"), ((4, 3, 2), "3d"), ((6, 5, 1), "2d"), ((5, 5, 1), "2d"),
+              ((24, 1, 1), "1d")]
+    out = []
+    for i in range(count):
+        shape, nb = shapes[int(rng.integers(len(shapes)))]
+        o = int(rng.integers(2, 5))
+        n = int(np.prod(shape)) * o
+        filling = float(rng.uniform(0.15, 0.85))
+        sysm = lattice_system(shape, o, nb, int(rng.integers(1 << 30)),
+                              onsite_range=float(rng.uniform(0.5, 1.5)),
+                              hop_std=float(rng.uniform(0.05, 0.2)),
+                              overlap=float(rng.uniform(0.01, 0.08)),
+                              electrons=round(2.0 * n * filling))
+        out.append((sysm, float(rng.uniform(0.005, 0.02))))
+    return out
