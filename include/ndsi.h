@@ -79,7 +79,7 @@ typedef struct {
     double flops_per_pole;     /* algorithmic real FP64 flops of factor + selected inversion */
     double bytes_per_pole;     /* algorithmic front bytes written + read per pole */
     int32_t n_launches;        /* schedule launches per pole batch (factor + selected inversion) */
-    int32_t pad;
+    int32_t n_systems;         /* systems in the plan (1 unless built by ndsi_analyze_batched) */
 } ndsi_plan_summary;
 
 /* Items for ndsi_plan_export. */
@@ -117,6 +117,26 @@ int ndsi_poles(int32_t M, double* z_out, double* R_out);
  * Errors: NDSI_ERR_INVALID for a malformed pattern, NDSI_ERR_OOM. */
 int ndsi_analyze(const ndsi_pattern* pat, int32_t n_atoms, const double* centers,
                  const int32_t* atom_of_basis, const ndsi_options* opt, ndsi_plan** plan_out);
+
+/* Batched analysis: n_systems independent systems of uneven size in one plan.  Each system is
+ * dissected on its own (as by ndsi_analyze); the supernodes of all systems are then merged level by
+ * level (level = height above the innermost domains), so every launch of the factor and of the
+ * selected inversion processes one tree level of every system and every pole at once.  Pattern
+ * arrays of the batch are the systems' arrays concatenated in order.
+ *   pats[i], n_atoms[i], centers[i], atom_of_basis[i] - as for ndsi_analyze, per system.
+ * ndsi_density_batched, ndsi_factor_poles and ndsi_selinv accept the plan; ndsi_density,
+ * ndsi_find_mu and ndsi_mu_features need a single-system plan (NDSI_ERR_INVALID otherwise). */
+int ndsi_analyze_batched(int32_t n_systems, const ndsi_pattern* pats, const int32_t* n_atoms,
+                         const double* const* centers, const int32_t* const* atom_of_basis,
+                         const ndsi_options* opt, ndsi_plan** plan_out);
+
+/* Density matrices of every system of a batched plan, each at its own mu[i] and kT[i] (host
+ * arrays of n_systems), with the same pole count: as ndsi_density, with H, S and rho_out the
+ * systems' pattern arrays concatenated (device or host) and n_elec_out[i] = Tr(rho_i S_i)
+ * (device or host array of n_systems, may be NULL).  Synchronises `stream`. */
+int ndsi_density_batched(ndsi_plan* plan, const double* H, const double* S, const double* mu,
+                         const double* kT, int32_t n_poles, double* rho_out, double* n_elec_out,
+                         void* stream);
 
 int ndsi_plan_info(const ndsi_plan* plan, ndsi_plan_summary* out);
 

@@ -375,20 +375,7 @@ int analyze(const ndsi_pattern* pat, int32_t n_atoms, const double* centers,
         P.max_front = std::max(P.max_front, P.f[j]);
     }
     P.front_total = std::max<int64_t>(off, 1);
-    // scratch per level
-    const int32_t b = P.block;
-    P.scr_off.assign(nn, 0);
-    P.scr_total = 1;
-    for (int32_t L = 0; L < P.n_levels; ++L) {
-        int64_t acc = 0;
-        for (int32_t j : P.level_nodes[L]) {
-            P.scr_off[j] = acc;
-            const int64_t need = std::max<int64_t>(static_cast<int64_t>(P.s[j]) * b,
-                                                   static_cast<int64_t>(P.r[j]) * P.s[j]);
-            acc += need;
-        }
-        P.scr_total = std::max(P.scr_total, acc);
-    }
+    compute_scratch(P);
     // ---- rel / inv maps
     std::vector<int32_t> node_of_pos(n);
     for (int32_t j = 0; j < nn; ++j)
@@ -450,7 +437,8 @@ int analyze(const ndsi_pattern* pat, int32_t n_atoms, const double* centers,
     // ---- assembly and output maps
     P.asm_map.assign(nnz, -1);
     P.out_map.assign(nnz, -1);
-    std::vector<std::vector<int64_t>> lvl_entries(P.n_levels);
+    P.level_entries.assign(P.n_levels, {});
+    auto& lvl_entries = P.level_entries;
     for (int64_t i = 0; i < n; ++i) {
         for (int64_t k = P.rowptr[i]; k < P.rowptr[i + 1]; ++k) {
             const int32_t gi = P.ipos_basis[i];
@@ -483,7 +471,35 @@ int analyze(const ndsi_pattern* pat, int32_t n_atoms, const double* centers,
             if (P.asm_map[k] >= 0) lvl_entries[P.level[J]].push_back(k);
         }
     }
-    // ---- schedule
+    P.n_systems = 1;
+    P.sys_nnz_first = {0, nnz};
+    P.sys_n_first = {0, n};
+    P.entry_sys.assign(nnz, 0);
+    build_schedule(P);
+    return NDSI_OK;
+}
+
+void compute_scratch(Plan& P) {
+    const int32_t b = P.block;
+    P.scr_off.assign(P.n_nodes, 0);
+    P.scr_total = 1;
+    for (int32_t L = 0; L < P.n_levels; ++L) {
+        int64_t acc = 0;
+        for (int32_t j : P.level_nodes[L]) {
+            P.scr_off[j] = acc;
+            const int64_t need = std::max<int64_t>(static_cast<int64_t>(P.s[j]) * b,
+                                                   static_cast<int64_t>(P.r[j]) * P.s[j]);
+            acc += need;
+        }
+        P.scr_total = std::max(P.scr_total, acc);
+    }
+}
+
+// Per-level launch schedule of the factor (bottom-up) and the selected inversion (top-down),
+// from the node structure of a plan (one system or several merged level by level).
+void build_schedule(Plan& P) {
+    const int32_t b = P.block;
+    const auto& lvl_entries = P.level_entries;
     P.launches.clear();
     P.gemm_items.clear();
     P.gemm_tiles.clear();
@@ -684,7 +700,84 @@ int analyze(const ndsi_pattern* pat, int32_t n_atoms, const double* centers,
         emit_copy(L, 1, T_SEL_COPY, -1.0, copies);
     }
     // the accumulation reads each pattern value of G once per pole
-    P.bytes_per_pole += 16.0 * static_cast<double>(nnz);
+    P.bytes_per_pole += 16.0 * static_cast<double>(P.nnz);
+}
+
+// Merge per-system plans into one: nodes, fronts and index tables are concatenated with
+// offsets, tree levels are aligned (level = height above the innermost domains), and one
+// schedule covers every system, so each launch processes a level of all systems at once.
+int merge_plans(std::vector<Plan>& parts, Plan& M, std::string& err) {
+    if (parts.empty()) {
+        err = "ndsi_analyze_batched: no systems";
+        return NDSI_ERR_INVALID;
+    }
+    M = Plan{};
+    M.opt = parts[0].opt;
+    M.block = parts[0].block;
+    M.n_systems = static_cast<int32_t>(parts.size());
+    M.sys_nnz_first.assign(parts.size() + 1, 0);
+    M.sys_n_first.assign(parts.size() + 1, 0);
+    int32_t node_base = 0;
+    int64_t front_base = 0, nnz_base = 0, n_base = 0, inv_base = 0, rel_base = 0;
+    for (const Plan& Q : parts) M.n_levels = std::max(M.n_levels, Q.n_levels);
+    M.level_entries.assign(M.n_levels, {});
+    M.level_nodes.assign(M.n_levels, {});
+    M.rowptr.assign(1, 0);
+    for (size_t si = 0; si < parts.size(); ++si) {
+        const Plan& Q = parts[si];
+        M.sys_nnz_first[si] = nnz_base;
+        M.sys_n_first[si] = n_base;
+        for (int32_t j = 0; j < Q.n_nodes; ++j) {
+            NodeDev d = Q.nodes[j];
+            d.front_off += front_base;
+            for (int t = 0; t < 2; ++t) {
+                if (d.inv_off[t] >= 0) d.inv_off[t] += inv_base;
+                if (d.child[t] >= 0) d.child[t] += node_base;
+            }
+            if (d.rel_off >= 0) d.rel_off += rel_base;
+            if (d.parent >= 0) d.parent += node_base;
+            M.nodes.push_back(d);
+            M.f.push_back(Q.f[j]);
+            M.s.push_back(Q.s[j]);
+            M.r.push_back(Q.r[j]);
+            M.front_off.push_back(Q.front_off[j] + front_base);
+            M.parent.push_back(Q.parent[j] >= 0 ? Q.parent[j] + node_base : -1);
+            M.child0.push_back(Q.child0[j] >= 0 ? Q.child0[j] + node_base : -1);
+            M.child1.push_back(Q.child1[j] >= 0 ? Q.child1[j] + node_base : -1);
+            M.nchild.push_back(Q.nchild[j]);
+            M.level.push_back(Q.level[j]);
+            M.level_nodes[Q.level[j]].push_back(node_base + j);
+            M.max_front = std::max(M.max_front, Q.f[j]);
+        }
+        for (int64_t k = 0; k < Q.nnz; ++k) {
+            M.asm_map.push_back(Q.asm_map[k] >= 0 ? Q.asm_map[k] + front_base : -1);
+            M.out_map.push_back(Q.out_map[k] + front_base);
+            M.entry_sys.push_back(static_cast<int32_t>(si));
+        }
+        for (int32_t L = 0; L < Q.n_levels; ++L)
+            for (int64_t k : Q.level_entries[L]) M.level_entries[L].push_back(k + nnz_base);
+        for (int32_t v : Q.inv_map) M.inv_map.push_back(v);
+        for (int32_t v : Q.rel_map) M.rel_map.push_back(v);
+        for (int64_t i = 0; i < Q.n; ++i) M.rowptr.push_back(Q.rowptr[i + 1] + nnz_base);
+        for (int32_t c : Q.col) M.col.push_back(static_cast<int32_t>(c + n_base));
+        node_base += Q.n_nodes;
+        front_base += Q.front_total;
+        nnz_base += Q.nnz;
+        n_base += Q.n;
+        inv_base += static_cast<int64_t>(Q.inv_map.size());
+        rel_base += static_cast<int64_t>(Q.rel_map.size());
+        M.n_atoms += Q.n_atoms;
+    }
+    M.sys_nnz_first[parts.size()] = nnz_base;
+    M.sys_n_first[parts.size()] = n_base;
+    M.n_nodes = node_base;
+    M.front_total = std::max<int64_t>(front_base, 1);
+    M.nnz = nnz_base;
+    M.n = n_base;
+    // per-node level lists must follow the merged ids in ascending order
+    for (auto& v : M.level_nodes) std::sort(v.begin(), v.end());
+    compute_scratch(M);
+    build_schedule(M);
     return NDSI_OK;
 }
 

@@ -139,6 +139,7 @@ int upload_tables(ndsi_plan* h) {
         {P.copy_items.data(), bytes_of(P.copy_items), reinterpret_cast<void**>(&T.copy_items)},
         {P.diag_items.data(), bytes_of(P.diag_items), reinterpret_cast<void**>(&T.diag_items)},
         {P.node_tiles.data(), bytes_of(P.node_tiles), reinterpret_cast<void**>(&T.node_tiles)},
+        {P.entry_sys.data(), bytes_of(P.entry_sys), reinterpret_cast<void**>(&T.entry_sys)},
         {P.rowptr.data(), bytes_of(P.rowptr), reinterpret_cast<void**>(&T.rowptr)},
         {P.col.data(), bytes_of(P.col), reinterpret_cast<void**>(&T.col)},
         {nullptr, sizeof(int) * 4, reinterpret_cast<void**>(&T.status)},
@@ -267,7 +268,7 @@ void prof_resolve(Profiler& pf) {
 }
 
 int run_phase(ndsi_plan* h, const Workspace& W, const SplitBuffers& SB, int phase, const double* H,
-              const double* S, const double2* z, int np, cudaStream_t st) {
+              const double* S, const double2* z, int64_t zstride, int np, cudaStream_t st) {
     const Plan& P = h->P;
     const bool split = P.opt.precision == NDSI_PREC_SPLIT;
     for (size_t li = 0; li < P.launches.size(); ++li) {
@@ -296,7 +297,7 @@ int run_phase(ndsi_plan* h, const Workspace& W, const SplitBuffers& SB, int phas
                     h->SP.tensor_flops[si] * np);
         } else {
             e = timed(h->prof, family_of(l), l.flops * np, l.bytes * np, st,
-                      [&]() { return launch_step(P, h->T, l, W, H, S, z, np, st); });
+                      [&]() { return launch_step(P, h->T, l, W, H, S, z, zstride, np, st); });
         }
         if (e != cudaSuccess)
             return fail(NDSI_ERR_CUDA, std::string("kernel launch (step ") + std::to_string(l.tag) +
@@ -381,6 +382,11 @@ int64_t workspace_cap(const ndsi_plan* h) {
 }  // namespace
 }  // namespace ndsi
 
+namespace ndsi {
+int density_impl(ndsi_plan* h, const double* Hd, const double* Sd, const double* mu, const double* kT,
+                 int32_t n_poles, double* rho_d, double* ne_d, cudaStream_t st);
+}  // namespace ndsi
+
 using namespace ndsi;
 
 extern "C" {
@@ -457,6 +463,88 @@ int ndsi_analyze(const ndsi_pattern* pat, int32_t n_atoms, const double* centers
     return NDSI_OK;
 }
 
+int ndsi_analyze_batched(int32_t n_systems, const ndsi_pattern* pats, const int32_t* n_atoms,
+                         const double* const* centers, const int32_t* const* atom_of_basis,
+                         const ndsi_options* opt, ndsi_plan** plan_out) {
+    if (!plan_out || n_systems < 1 || !pats || !n_atoms || !centers || !atom_of_basis)
+        return fail(NDSI_ERR_INVALID, "ndsi_analyze_batched: invalid argument");
+    *plan_out = nullptr;
+    ndsi_options o;
+    ndsi_default_options(&o);
+    if (opt) o = *opt;
+    if (o.m0_radius <= 0) o.m0_radius = 1e7;
+    std::vector<Plan> parts(n_systems);
+    std::string err;
+    try {
+        for (int32_t i = 0; i < n_systems; ++i) {
+            int rc = analyze(&pats[i], n_atoms[i], centers[i], atom_of_basis[i], o, parts[i], err);
+            if (rc) return fail(rc, "system " + std::to_string(i) + ": " + err);
+        }
+        ndsi_plan* h = new ndsi_plan();
+        int rc = merge_plans(parts, h->P, err);
+        if (rc) {
+            delete h;
+            return fail(rc, err);
+        }
+        if (o.precision == NDSI_PREC_SPLIT) {
+            if (o.split_slices < 4 || o.split_slices > kSplitMaxSlices) {
+                delete h;
+                return fail(NDSI_ERR_INVALID, "ndsi_analyze_batched: split_slices must be in [4, 7]");
+            }
+            SplitPlan& S = h->SP;
+            build_split_schedule(h->P, o.split_slices, S.items, S.steps, S.tiles, S.blocks);
+            S.step_of_launch.assign(h->P.launches.size(), -1);
+            int k = 0;
+            for (size_t li = 0; li < h->P.launches.size(); ++li) {
+                const Launch& l = h->P.launches[li];
+                if (l.kind != L_GEMM) continue;
+                const SplitStep& st = S.steps[k];
+                S.tensor_flops.push_back(split_executed_flops(h->P, st, S.items, S.tiles, l, o.split_slices));
+                double sb = 0;
+                for (int64_t i = 0; i < l.count; ++i) {
+                    const GemmItem& g = h->P.gemm_items[l.first + i];
+                    sb += 2.0 * 16.0 * (static_cast<double>(g.M) * g.K + static_cast<double>(g.N) * g.K);
+                }
+                sb += 2.0 * (static_cast<double>(st.rowsA) + st.rowsB) * st.Kcols;
+                S.slice_bytes.push_back(sb);
+                S.step_of_launch[li] = k++;
+            }
+        }
+        *plan_out = h;
+    } catch (const std::bad_alloc&) {
+        return fail(NDSI_ERR_OOM, "ndsi_analyze_batched: out of host memory");
+    }
+    return NDSI_OK;
+}
+
+int ndsi_density_batched(ndsi_plan* h, const double* H, const double* S, const double* mu, const double* kT,
+                         int32_t n_poles, double* rho_out, double* n_elec_out, void* stream) {
+    if (!h || !H || !S || !mu || !kT || !rho_out || n_poles < 1)
+        return fail(NDSI_ERR_INVALID, "ndsi_density_batched: invalid argument");
+    const int32_t ns = h->P.n_systems;
+    for (int32_t i = 0; i < ns; ++i)
+        if (!(kT[i] > 0) || !std::isfinite(mu[i])) return fail(NDSI_ERR_INVALID, "ndsi_density_batched: bad mu/kT");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    int rc = upload_tables(h);
+    if (rc) return rc;
+    const double *Hd, *Sd;
+    rc = device_inputs(h, H, S, &Hd, &Sd, st);
+    if (rc) return rc;
+    const bool rho_dev = is_device_ptr(rho_out);
+    const bool ne_dev = n_elec_out && is_device_ptr(n_elec_out);
+    rc = ensure_stage(h, 3 * h->P.nnz + 8 + ns);
+    if (rc) return rc;
+    double* rho_d = rho_dev ? rho_out : h->stage + 2 * h->P.nnz;
+    double* ne_d = ne_dev ? n_elec_out : h->stage + 3 * h->P.nnz;
+    std::vector<double> muv(mu, mu + ns), ktv(kT, kT + ns);
+    rc = density_impl(h, Hd, Sd, muv.data(), ktv.data(), n_poles, rho_d, ne_d, st);
+    if (rc) return rc;
+    if (!rho_dev) NDSI_CK(cudaMemcpyAsync(rho_out, rho_d, sizeof(double) * h->P.nnz, cudaMemcpyDeviceToHost, st));
+    if (n_elec_out && !ne_dev) NDSI_CK(cudaMemcpyAsync(n_elec_out, ne_d, sizeof(double) * ns, cudaMemcpyDeviceToHost, st));
+    NDSI_CK(cudaStreamSynchronize(st));
+    return NDSI_OK;
+}
+
 int ndsi_plan_info(const ndsi_plan* h, ndsi_plan_summary* out) {
     if (!h || !out) return fail(NDSI_ERR_INVALID, "ndsi_plan_info: NULL argument");
     const Plan& P = h->P;
@@ -470,13 +558,15 @@ int ndsi_plan_info(const ndsi_plan* h, ndsi_plan_summary* out) {
     out->flops_per_pole = P.flops_per_pole;
     out->bytes_per_pole = P.bytes_per_pole;
     out->n_launches = static_cast<int32_t>(P.launches.size());
-    out->pad = 0;
+    out->n_systems = P.n_systems;
     return NDSI_OK;
 }
 
 int ndsi_plan_export(const ndsi_plan* h, int32_t what, void* out) {
     if (!h || !out) return fail(NDSI_ERR_INVALID, "ndsi_plan_export: NULL argument");
     const Plan& P = h->P;
+    if (P.n_systems != 1 && what != NDSI_EXPORT_SCHEDULE && what != NDSI_EXPORT_LEVEL && what != NDSI_EXPORT_PARENT)
+        return fail(NDSI_ERR_INVALID, "ndsi_plan_export: ordering tables are per system; not available for a batch");
     switch (what) {
         case NDSI_EXPORT_PERM_ATOMS: std::memcpy(out, P.perm_atoms.data(), bytes_of(P.perm_atoms)); break;
         case NDSI_EXPORT_PERM_BASIS: std::memcpy(out, P.perm_basis.data(), bytes_of(P.perm_basis)); break;
@@ -547,7 +637,7 @@ int ndsi_factor_poles(ndsi_plan* h, const double* H, const double* S, const doub
     }
     const double *Hd, *Sd;
     rc = device_inputs(h, H, S, &Hd, &Sd, st);
-    if (!rc) rc = run_phase(h, f->W, f->SB, 0, Hd, Sd, f->zd, n_poles, st);
+    if (!rc) rc = run_phase(h, f->W, f->SB, 0, Hd, Sd, f->zd, 0, n_poles, st);
     if (rc) {
         cleanup();
         return rc;
@@ -560,7 +650,7 @@ int ndsi_selinv(ndsi_factors* f, double* G_out, void* stream) {
     if (!f || !f->plan) return fail(NDSI_ERR_INVALID, "ndsi_selinv: NULL factors");
     ndsi_plan* h = f->plan;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    int rc = run_phase(h, f->W, f->SB, 1, nullptr, nullptr, f->zd, f->np, st);
+    int rc = run_phase(h, f->W, f->SB, 1, nullptr, nullptr, f->zd, 0, f->np, st);
     if (rc) return rc;
     if (G_out) {
         const bool dev = is_device_ptr(G_out);
@@ -580,12 +670,6 @@ int ndsi_selinv(ndsi_factors* f, double* G_out, void* stream) {
     return check_status(h, st);
 }
 
-namespace ndsi {
-// rho(mu) and Tr(rho S) for device inputs and outputs; synchronises the stream.
-int density_impl(ndsi_plan* h, const double* Hd, const double* Sd, double mu, double kT, int32_t n_poles,
-                 double* rho_d, double* ne_d, cudaStream_t st);
-}  // namespace ndsi
-
 int ndsi_density(ndsi_plan* h, const double* H, const double* S, double mu, double kT, int32_t n_poles,
                  double* rho_out, double* n_elec_out, void* stream) {
     if (!h || !H || !S || !rho_out || n_poles < 1 || !(kT > 0) || !std::isfinite(mu))
@@ -602,7 +686,8 @@ int ndsi_density(ndsi_plan* h, const double* H, const double* S, double mu, doub
     if (rc) return rc;
     double* rho_d = rho_dev ? rho_out : h->stage + 2 * h->P.nnz;
     double* ne_d = ne_dev ? n_elec_out : h->stage + 3 * h->P.nnz;
-    rc = density_impl(h, Hd, Sd, mu, kT, n_poles, rho_d, ne_d, st);
+    if (h->P.n_systems != 1) return fail(NDSI_ERR_INVALID, "ndsi_density: batched plan, use ndsi_density_batched");
+    rc = density_impl(h, Hd, Sd, &mu, &kT, n_poles, rho_d, ne_d, st);
     if (rc) return rc;
     if (!rho_dev) NDSI_CK(cudaMemcpyAsync(rho_out, rho_d, sizeof(double) * h->P.nnz, cudaMemcpyDeviceToHost, st));
     if (n_elec_out && !ne_dev) NDSI_CK(cudaMemcpyAsync(n_elec_out, ne_d, sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -610,10 +695,15 @@ int ndsi_density(ndsi_plan* h, const double* H, const double* S, double mu, doub
     return NDSI_OK;
 }
 
+}  // extern "C"
+
 namespace ndsi {
-int density_impl(ndsi_plan* h, const double* Hd, const double* Sd, double mu, double kT, int32_t n_poles,
-                 double* rho_d, double* ne_d, cudaStream_t st) {
+// rho(mu) and Tr(rho S) of every system of the plan (mu[s], kT[s]) for device inputs and
+// outputs (ne_d[s] per system); synchronises the stream.
+int density_impl(ndsi_plan* h, const double* Hd, const double* Sd, const double* mu, const double* kT,
+                 int32_t n_poles, double* rho_d, double* ne_d, cudaStream_t st) {
     int rc;
+    const int32_t ns = h->P.n_systems;
     // poles of Eq. 7 (cached per M) -> points alpha_p and weights w_p of Eq. 8, plus iR for M0
     if (h->pole_M != n_poles) {
         h->pole_z.assign(n_poles, 0.0);
@@ -624,14 +714,18 @@ int density_impl(ndsi_plan* h, const double* Hd, const double* Sd, double mu, do
         h->pole_M = n_poles;
     }
     const int32_t nq = n_poles + 1;
-    std::vector<double2> zq(nq), cq(nq);
-    for (int32_t p = 0; p < n_poles; ++p) {
-        zq[p] = make_double2(mu, h->pole_z[p] * kT);
-        cq[p] = make_double2(-4.0 * h->pole_R[p] * kT, 0.0);
-    }
+    std::vector<double2> zq(static_cast<size_t>(ns) * nq), cq(static_cast<size_t>(ns) * nq);
     const double R = h->P.opt.m0_radius;
-    zq[n_poles] = make_double2(0.0, R);
-    cq[n_poles] = make_double2(0.0, R);
+    for (int32_t sy = 0; sy < ns; ++sy) {
+        double2* z = zq.data() + static_cast<size_t>(sy) * nq;
+        double2* c = cq.data() + static_cast<size_t>(sy) * nq;
+        for (int32_t p = 0; p < n_poles; ++p) {
+            z[p] = make_double2(mu[sy], h->pole_z[p] * kT[sy]);
+            c[p] = make_double2(-4.0 * h->pole_R[p] * kT[sy], 0.0);
+        }
+        z[n_poles] = make_double2(0.0, R);
+        c[n_poles] = make_double2(0.0, R);
+    }
     // chunk the points to the workspace cap
     const int64_t per_pole = bytes_per_pole(h);
     int64_t cap = workspace_cap(h);
@@ -640,43 +734,53 @@ int density_impl(ndsi_plan* h, const double* Hd, const double* Sd, double mu, do
     rc = alloc_workspace(h->W, h->P, chunk);
     if (rc) return rc;
     if (h->P.opt.precision == NDSI_PREC_SPLIT) NDSI_CK(split_alloc(h->SB, h->SP.steps, h->P.opt.split_slices, chunk));
-    if (h->cw_cap < nq) {
+    if (h->cw_cap < ns * nq) {
         if (h->cw) cudaFree(h->cw);
         if (h->zw) cudaFree(h->zw);
         h->cw = h->zw = nullptr;
         h->cw_cap = 0;
-        NDSI_CK(cudaMalloc(&h->cw, sizeof(double2) * nq));
-        NDSI_CK(cudaMalloc(&h->zw, sizeof(double2) * nq));
-        h->cw_cap = nq;
+        NDSI_CK(cudaMalloc(&h->cw, sizeof(double2) * ns * nq));
+        NDSI_CK(cudaMalloc(&h->zw, sizeof(double2) * ns * nq));
+        h->cw_cap = ns * nq;
     }
-    if (!h->partials) NDSI_CK(cudaMalloc(&h->partials, sizeof(double) * (accumulate_blocks(h->P.nnz) + 1)));
-    NDSI_CK(cudaMemcpyAsync(h->zw, zq.data(), sizeof(double2) * nq, cudaMemcpyHostToDevice, st));
-    NDSI_CK(cudaMemcpyAsync(h->cw, cq.data(), sizeof(double2) * nq, cudaMemcpyHostToDevice, st));
+    // per-system partial-trace ranges of the reduction scratch
+    std::vector<int> part_off(ns + 1, 0);
+    for (int32_t sy = 0; sy < ns; ++sy)
+        part_off[sy + 1] = part_off[sy] + accumulate_blocks(h->P.sys_nnz_first[sy + 1] - h->P.sys_nnz_first[sy]);
+    if (!h->partials) NDSI_CK(cudaMalloc(&h->partials, sizeof(double) * (part_off[ns] + 1)));
+    NDSI_CK(cudaMemcpyAsync(h->zw, zq.data(), sizeof(double2) * ns * nq, cudaMemcpyHostToDevice, st));
+    NDSI_CK(cudaMemcpyAsync(h->cw, cq.data(), sizeof(double2) * ns * nq, cudaMemcpyHostToDevice, st));
     for (int32_t q0 = 0; q0 < nq; q0 += chunk) {
         const int32_t np = std::min(chunk, nq - q0);
-        rc = run_phase(h, h->W, h->SB, 0, Hd, Sd, h->zw + q0, np, st);
-        if (!rc) rc = run_phase(h, h->W, h->SB, 1, Hd, Sd, h->zw + q0, np, st);
+        rc = run_phase(h, h->W, h->SB, 0, Hd, Sd, h->zw + q0, nq, np, st);
+        if (!rc) rc = run_phase(h, h->W, h->SB, 1, Hd, Sd, h->zw + q0, nq, np, st);
         if (rc) return rc;
         const int last = q0 + np >= nq;
-        const double acc_bytes = static_cast<double>(h->P.nnz) * (8.0 + 16.0 * np + 8.0 + 8.0 +
-                                                                  (q0 > 0 ? 8.0 : 0.0));
-        NDSI_CK(timed(h->prof, "accumulate", 2.0 * np * h->P.nnz, acc_bytes, st, [&]() {
-            return launch_accumulate(h->P, h->T, h->W, np, h->cw + q0, Sd, rho_d, q0 > 0 ? 1 : 0,
-                                     last, h->partials, st);
-        }));
+        for (int32_t sy = 0; sy < ns; ++sy) {
+            const int64_t k0 = h->P.sys_nnz_first[sy], cnt = h->P.sys_nnz_first[sy + 1] - k0;
+            const double acc_bytes = static_cast<double>(cnt) * (8.0 + 16.0 * np + 8.0 + 8.0 + (q0 > 0 ? 8.0 : 0.0));
+            NDSI_CK(timed(h->prof, "accumulate", 2.0 * np * cnt, acc_bytes, st, [&]() {
+                return launch_accumulate(h->P, h->T, h->W, np, h->cw + static_cast<size_t>(sy) * nq + q0, Sd, rho_d,
+                                         q0 > 0 ? 1 : 0, last, h->partials + part_off[sy], st, k0, cnt);
+            }));
+        }
     }
-    const int nblk = accumulate_blocks(h->P.nnz);
-    NDSI_CK(timed(h->prof, "reduce", static_cast<double>(nblk), 8.0 * nblk, st,
-                  [&]() { return launch_reduce(h->partials, nblk, ne_d, st); }));
+    for (int32_t sy = 0; sy < ns; ++sy) {
+        const int nblk = part_off[sy + 1] - part_off[sy];
+        NDSI_CK(timed(h->prof, "reduce", static_cast<double>(nblk), 8.0 * nblk, st,
+                      [&]() { return launch_reduce(h->partials + part_off[sy], nblk, ne_d + sy, st); }));
+    }
     return check_status(h, st);
 }
 }  // namespace ndsi
+
+extern "C" {
 
 int ndsi_find_mu(ndsi_plan* h, const double* H, const double* S, double kT, int32_t n_poles,
                  double n_electrons, double mu_lo, double mu_hi, double tol_electrons, int32_t max_iter,
                  double* rho_out, double* mu_out, double* n_elec_out, int32_t* iters_out, void* stream) {
     if (!h || !H || !S || !rho_out || !mu_out || n_poles < 1 || !(kT > 0) || !(tol_electrons > 0) ||
-        max_iter < 1 || !std::isfinite(n_electrons))
+        max_iter < 1 || !std::isfinite(n_electrons) || h->P.n_systems != 1)
         return fail(NDSI_ERR_INVALID, "ndsi_find_mu: invalid argument");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     int rc = upload_tables(h);
@@ -723,7 +827,7 @@ int ndsi_find_mu(ndsi_plan* h, const double* H, const double* S, double kT, int3
     int iters = 0;
     double best_mu = 0, best_dn = 1e300;
     auto eval = [&](double mu, double& dn) -> int {
-        int r = density_impl(h, Hd, Sd, mu, kT, n_poles, rho_d, ne_d, st);
+        int r = density_impl(h, Hd, Sd, &mu, &kT, n_poles, rho_d, ne_d, st);
         if (r) return r;
         double ne = 0;
         cudaError_t e = cudaMemcpy(&ne, ne_d, sizeof(double), cudaMemcpyDeviceToHost);
@@ -872,7 +976,7 @@ int ndsi_find_mu(ndsi_plan* h, const double* H, const double* S, double kT, int3
 
 int ndsi_mu_features(ndsi_plan* h, const double* H, const double* S, double n_electrons, double kT,
                      int32_t n_vectors, uint64_t seed, float* feat_out, void* stream) {
-    if (!h || !H || !S || !feat_out || n_vectors < 1 || !(kT > 0))
+    if (!h || !H || !S || !feat_out || n_vectors < 1 || !(kT > 0) || h->P.n_systems != 1)
         return fail(NDSI_ERR_INVALID, "ndsi_mu_features: invalid argument");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     int rc = upload_tables(h);

@@ -53,18 +53,21 @@ __global__ void __launch_bounds__(256) k_assemble(const NodeDev* __restrict__ no
 }
 
 // X = z S - H on the level's entries (each front element receives at most one entry).
+// z[sys * zstride + pole] is the point of the entry's system (systems of a batch have their own
+// mu and kT).
 __global__ void __launch_bounds__(256) k_scatter(const int64_t* __restrict__ idx, int64_t first,
                                                  int64_t count, const int64_t* __restrict__ asm_map,
+                                                 const int32_t* __restrict__ entry_sys,
                                                  const double* __restrict__ H,
                                                  const double* __restrict__ S,
-                                                 const double2* __restrict__ z,
+                                                 const double2* __restrict__ z, int64_t zstride,
                                                  double2* __restrict__ F, int64_t stride) {
-    const double2 zq = z[blockIdx.y];
     double2* Fp = F + static_cast<int64_t>(blockIdx.y) * stride;
     for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < count;
          e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
         const int64_t k = idx[first + e];
         const int64_t off = asm_map[k];
+        const double2 zq = z[entry_sys[k] * zstride + blockIdx.y];
         const double h = H[k], s = S[k];
         double2 v = Fp[off];
         v.x += zq.x * s - h;
@@ -361,7 +364,7 @@ __global__ void __launch_bounds__(256) k_gather(const NodeDev* __restrict__ node
 constexpr int kAccThreads = 256;
 
 __global__ void __launch_bounds__(kAccThreads) k_accumulate(const int64_t* __restrict__ out_map,
-                                                            int64_t nnz,
+                                                            int64_t k0, int64_t nnz,
                                                             const double2* __restrict__ F,
                                                             int64_t stride, int np,
                                                             const double2* __restrict__ c,
@@ -370,9 +373,9 @@ __global__ void __launch_bounds__(kAccThreads) k_accumulate(const int64_t* __res
                                                             int want_trace,
                                                             double* __restrict__ partials) {
     __shared__ double red[kAccThreads / 32];
-    const int64_t k = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+    const int64_t k = k0 + blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
     double tr = 0.0;
-    if (k < nnz) {
+    if (k < k0 + nnz) {
         const int64_t off = out_map[k];
         double sum = accumulate ? rho[k] : 0.0;
         for (int q = 0; q < np; ++q) {
@@ -441,7 +444,8 @@ cudaError_t gemm_launch(const Plan& P, const DevTables& T, const Launch& l, cons
 }  // namespace
 
 cudaError_t launch_step(const Plan& P, const DevTables& T, const Launch& l, const Workspace& W,
-                        const double* H, const double* S, const double2* z, int np, cudaStream_t st) {
+                        const double* H, const double* S, const double2* z, int64_t zstride, int np,
+                        cudaStream_t st) {
     switch (l.kind) {
         case L_ASSEMBLE: {
             dim3 grid(static_cast<unsigned>(l.count), static_cast<unsigned>(np));
@@ -452,8 +456,8 @@ cudaError_t launch_step(const Plan& P, const DevTables& T, const Launch& l, cons
         case L_SCATTER: {
             const int64_t blocks = (l.count + 255) / 256;
             dim3 grid(static_cast<unsigned>(blocks < 4096 ? blocks : 4096), static_cast<unsigned>(np));
-            k_scatter<<<grid, 256, 0, st>>>(T.scatter_idx, l.first, l.count, T.asm_map, H, S, z, W.fronts,
-                                            W.front_stride);
+            k_scatter<<<grid, 256, 0, st>>>(T.scatter_idx, l.first, l.count, T.asm_map, T.entry_sys, H, S, z,
+                                            zstride, W.fronts, W.front_stride);
             return cudaGetLastError();
         }
         case L_DIAGINV: {
@@ -501,9 +505,13 @@ int accumulate_blocks(int64_t nnz) { return static_cast<int>((nnz + kAccThreads 
 
 cudaError_t launch_accumulate(const Plan& P, const DevTables& T, const Workspace& W, int np,
                               const double2* c, const double* S, double* rho, int accumulate,
-                              int want_trace, double* partials, cudaStream_t st) {
-    const int blocks = accumulate_blocks(P.nnz);
-    k_accumulate<<<blocks, kAccThreads, 0, st>>>(T.out_map, P.nnz, W.fronts, W.front_stride, np, c, S, rho,
+                              int want_trace, double* partials, cudaStream_t st, int64_t k0, int64_t count) {
+    if (count < 0) {
+        k0 = 0;
+        count = P.nnz;
+    }
+    const int blocks = accumulate_blocks(count);
+    k_accumulate<<<blocks, kAccThreads, 0, st>>>(T.out_map, k0, count, W.fronts, W.front_stride, np, c, S, rho,
                                                  accumulate, want_trace, partials);
     return cudaGetLastError();
 }

@@ -23,6 +23,7 @@ struct DevTables {
     CopyItem* copy_items = nullptr;
     DiagItem* diag_items = nullptr;
     NodeTile* node_tiles = nullptr;
+    int32_t* entry_sys = nullptr;  // system of each pattern entry
     int64_t* rowptr = nullptr;   // CSR pattern (original order), for the moment features
     int32_t* col = nullptr;
     int* status = nullptr;
@@ -47,14 +48,18 @@ int mlp_features(const Plan& P, const double* Hd, const double* Sd, const int64_
 cudaError_t kernels_init();
 
 // Launch one schedule step over `np` poles whose slabs start at the workspace base.
+// z holds the points of every system: z[sys * zstride + pole].
 cudaError_t launch_step(const Plan& P, const DevTables& T, const Launch& l, const Workspace& W,
-                        const double* H, const double* S, const double2* z, int np, cudaStream_t st);
+                        const double* H, const double* S, const double2* z, int64_t zstride, int np,
+                        cudaStream_t st);
 
 // rho(k) (+)= sum_q Re(c_q G_q(k)) over the pattern; `partials` receives per-block sums of
 // rho(k) S(k) when `want_trace` is set (nblocks = accumulate_blocks(nnz)).
+// (entries [k0, k0+count); count < 0 = the whole pattern)
 cudaError_t launch_accumulate(const Plan& P, const DevTables& T, const Workspace& W, int np,
                               const double2* c, const double* S, double* rho, int accumulate,
-                              int want_trace, double* partials, cudaStream_t st);
+                              int want_trace, double* partials, cudaStream_t st, int64_t k0 = 0,
+                              int64_t count = -1);
 int accumulate_blocks(int64_t nnz);
 cudaError_t launch_reduce(const double* partials, int nblocks, double* out, cudaStream_t st);
 

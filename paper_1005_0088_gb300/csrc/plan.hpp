@@ -131,6 +131,12 @@ struct Plan {
     std::vector<Launch> launches;
     double flops_per_pole = 0, bytes_per_pole = 0;
     int32_t block = 32;
+    std::vector<std::vector<int64_t>> level_entries;  // CSR entries scattered per level
+    // systems of a batched plan (one for a plain plan)
+    int32_t n_systems = 1;
+    std::vector<int64_t> sys_nnz_first;   // [n_systems+1] pattern-entry offsets
+    std::vector<int64_t> sys_n_first;     // [n_systems+1] basis offsets
+    std::vector<int32_t> entry_sys;       // [nnz] system of each pattern entry
     // device-side state (owned by the numeric phase)
     void* dev = nullptr;
 };
@@ -138,6 +144,11 @@ struct Plan {
 // Host analysis entry (analyze.cpp).  Returns NDSI_OK or an error code, with `err` set.
 int analyze(const ndsi_pattern* pat, int32_t n_atoms, const double* centers,
             const int32_t* atom_of_basis, const ndsi_options& opt, Plan& plan, std::string& err);
+
+// Schedule and scratch layout from the node structure; merging of per-system plans.
+void compute_scratch(Plan& P);
+void build_schedule(Plan& P);
+int merge_plans(std::vector<Plan>& parts, Plan& merged, std::string& err);
 
 // Continued-fraction poles (analyze.cpp).
 int cf_poles(int32_t M, double* z, double* R, std::string& err);

@@ -32,7 +32,8 @@ EXPORTED_SYMBOLS = (
     "ndsi_factor_poles", "ndsi_selinv", "ndsi_density", "ndsi_plan_destroy",
     "ndsi_factors_destroy", "ndsi_last_error", "ndsi_profile_enable", "ndsi_profile_read",
     "ndsi_residue_sum_static", "ndsi_find_mu", "ndsi_mu_features", "ndsi_mlp_init",
-    "ndsi_mlp_forward", "ndsi_mlp_grad", "ndsi_mlp_train",
+    "ndsi_mlp_forward", "ndsi_mlp_grad", "ndsi_mlp_train", "ndsi_analyze_batched",
+    "ndsi_density_batched",
 )
 NDSI_MLP_INPUTS = 32
 NDSI_MLP_HIDDEN = 64
@@ -60,7 +61,7 @@ class ndsi_plan_summary(ctypes.Structure):
                 ("n_nodes", ctypes.c_int32), ("n_levels", ctypes.c_int32),
                 ("max_front", ctypes.c_int32), ("front_elems", ctypes.c_int64),
                 ("flops_per_pole", ctypes.c_double), ("bytes_per_pole", ctypes.c_double),
-                ("n_launches", ctypes.c_int32), ("pad", ctypes.c_int32)]
+                ("n_launches", ctypes.c_int32), ("n_systems", ctypes.c_int32)]
 
 
 class ndsi_profile_entry(ctypes.Structure):
@@ -112,6 +113,11 @@ def load(path: str = LIB_PATH):
     for name in ("ndsi_mu_features", "ndsi_mlp_init", "ndsi_mlp_forward", "ndsi_mlp_grad",
                  "ndsi_mlp_train"):
         getattr(lib, name).restype = ctypes.c_int
+    lib.ndsi_analyze_batched.argtypes = [i32, vp, vp, vp, vp, ctypes.POINTER(ndsi_options),
+                                         ctypes.POINTER(vp)]
+    lib.ndsi_density_batched.argtypes = [vp, vp, vp, vp, vp, i32, vp, vp, vp]
+    lib.ndsi_analyze_batched.restype = ctypes.c_int
+    lib.ndsi_density_batched.restype = ctypes.c_int
     lib.ndsi_last_error.argtypes = []
     lib.ndsi_last_error.restype = ctypes.c_char_p
     for name in ("ndsi_poles", "ndsi_analyze", "ndsi_plan_info", "ndsi_plan_export",
@@ -327,3 +333,39 @@ def ndsi_mlp_train(params, X, T, n, steps, lr, stream=None):
     _check(load().ndsi_mlp_train(_ptr(params), _ptr(X), _ptr(T), int(n), int(steps), float(lr),
                                  _ptr(loss), _stream(stream)))
     return float(loss[0])
+
+
+def analyze_batched(systems, **options) -> Plan:
+    """ndsi_analyze_batched over synth.System-like objects."""
+    opt = ndsi_default_options()
+    for k, v in options.items():
+        setattr(opt, k, v)
+    ns = len(systems)
+    keep = []
+    pats = (ndsi_pattern * ns)()
+    na = np.zeros(ns, dtype=np.int32)
+    cen_ptrs = (ctypes.c_void_p * ns)()
+    aob_ptrs = (ctypes.c_void_p * ns)()
+    for i, sy in enumerate(systems):
+        rp = np.ascontiguousarray(sy.rowptr, dtype=np.int64)
+        cl = np.ascontiguousarray(sy.col, dtype=np.int32)
+        ce = np.ascontiguousarray(sy.centers, dtype=np.float64)
+        ab = np.ascontiguousarray(sy.atom_of_basis, dtype=np.int32)
+        keep += [rp, cl, ce, ab]
+        pats[i] = ndsi_pattern(int(sy.n), rp.ctypes.data, cl.ctypes.data)
+        na[i] = sy.centers.shape[0]
+        cen_ptrs[i] = ce.ctypes.data
+        aob_ptrs[i] = ab.ctypes.data
+    h = ctypes.c_void_p()
+    _check(load().ndsi_analyze_batched(ns, pats, _ptr(na), cen_ptrs, aob_ptrs, ctypes.byref(opt),
+                                       ctypes.byref(h)))
+    return Plan(h)
+
+
+def ndsi_density_batched(plan: Plan, H, S, mu, kT, n_poles, rho_out, n_elec_out=None, stream=None):
+    mu = np.ascontiguousarray(mu, dtype=np.float64)
+    kT = np.ascontiguousarray(kT, dtype=np.float64)
+    _check(load().ndsi_density_batched(plan.handle, _ptr(H), _ptr(S), _ptr(mu), _ptr(kT),
+                                       int(n_poles), _ptr(rho_out), _ptr(n_elec_out),
+                                       _stream(stream)))
+    return rho_out

@@ -117,3 +117,20 @@ def test_invalid_patterns_rejected():
     assert _raw_analyze(3, [0, 1, 2, 3], [0, 1, 2], 4, np.zeros((4, 3)), aob) == nd.ndsi.NDSI_ERR_INVALID
     with pytest.raises(nd.NdsiError):
         nd.ndsi_poles(0)
+
+
+def test_batched_plan_merges_levels():
+    # Three uneven systems in one plan: one schedule, levels aligned, fewer launches than
+    # the three plans run one after another.
+    nd = lib()
+    systems = [lattice_system((30, 1, 1), 3, "1d", 1), lattice_system((7, 6, 1), 2, "2d", 2),
+               lattice_system((4, 4, 3), 2, "3d", 3)]
+    singles = [nd.ndsi_plan_info(nd.analyze_system(s)) for s in systems]
+    info = nd.ndsi_plan_info(nd.analyze_batched(systems))
+    assert info["n_systems"] == 3
+    assert info["n"] == sum(s.n for s in systems) and info["nnz"] == sum(s.nnz for s in systems)
+    assert info["n_nodes"] == sum(i["n_nodes"] for i in singles)
+    assert info["n_levels"] == max(i["n_levels"] for i in singles)
+    assert info["front_elems"] == sum(i["front_elems"] for i in singles)
+    assert info["n_launches"] < sum(i["n_launches"] for i in singles)
+    assert abs(info["flops_per_pole"] - sum(i["flops_per_pole"] for i in singles)) < 1e-6 * info["flops_per_pole"]

@@ -1,0 +1,47 @@
+"""Batched plans: several uneven systems (own mu and kT) in one launch per tree level."""
+import numpy as np
+import pytest
+
+from synth import lattice_system
+from oracle.dense import generalized_eig, density_eig, on_pattern, electron_count_pattern
+from tests.libtools import lib
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("precision,tol", [(0, 1e-10), (1, 1e-9)])
+def test_batched_density_matches_single_and_oracle(precision, tol):
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    nd = lib()
+    systems = [lattice_system((60, 1, 1), 3, "1d", 11), lattice_system((9, 8, 1), 2, "2d", 12),
+               lattice_system((5, 4, 4), 2, "3d", 13)]
+    mus = [-0.2, 0.05, 0.1]
+    kTs = [0.01, 0.02, 0.015]
+    M = 40
+    plan = nd.analyze_batched(systems, precision=precision)
+    H = torch.as_tensor(np.concatenate([s.H for s in systems]), device="cuda")
+    S = torch.as_tensor(np.concatenate([s.S for s in systems]), device="cuda")
+    nnz = sum(s.nnz for s in systems)
+    rho = torch.zeros(nnz, dtype=torch.float64, device="cuda")
+    ne = torch.zeros(3, dtype=torch.float64, device="cuda")
+    nd.ndsi_density_batched(plan, H, S, mus, kTs, M, rho, ne)
+    torch.cuda.synchronize()
+    rho = rho.cpu().numpy()
+    ne = ne.cpu().numpy()
+    off = 0
+    for i, sy in enumerate(systems):
+        r_b = rho[off:off + sy.nnz]
+        off += sy.nnz
+        p1 = nd.analyze_system(sy, precision=precision)
+        r1 = torch.zeros(sy.nnz, dtype=torch.float64, device="cuda")
+        n1 = torch.zeros(1, dtype=torch.float64, device="cuda")
+        nd.ndsi_density(p1, torch.as_tensor(sy.H, device="cuda"), torch.as_tensor(sy.S, device="cuda"),
+                        mus[i], kTs[i], M, r1, n1)
+        assert np.max(np.abs(r_b - r1.cpu().numpy())) < 1e-13
+        Hd, Sd = sy.dense()
+        eps, C = generalized_eig(Hd, Sd)
+        ref = on_pattern(density_eig(eps, C, mus[i], kTs[i], M), sy)
+        assert np.max(np.abs(r_b - ref)) < tol
+        assert abs(ne[i] - electron_count_pattern(r_b, sy)) < 1e-9
