@@ -237,11 +237,13 @@ def run_ndsi(args):
     import paper_1005_0088_gb300 as nd
     from synth import config_system
 
+    prec_code = {"fp64": nd.NDSI_PREC_FP64, "split": nd.NDSI_PREC_SPLIT}
+    if args.config == "C4":
+        return run_batched(args, nd, torch, dist, rank, world, local, prec_code)
     system = config_system(args.config)
     kT, M = system.meta["kT"], system.meta["poles"]
     if args.poles:
         M = args.poles
-    prec_code = {"fp64": nd.NDSI_PREC_FP64, "split": nd.NDSI_PREC_SPLIT}
     plan = nd.analyze_system(system, precision=prec_code[args.precision])
     info = nd.ndsi_plan_info(plan)
     dev = torch.device("cuda", local)
@@ -358,13 +360,76 @@ def run_ndsi(args):
     return 0
 
 
+def run_batched(args, nd, torch, dist, rank, world, local, prec_code):
+    """C4: twelve uneven systems (1D/2D/3D, N 2048..32768) in one batched plan, 120 poles."""
+    import numpy as np
+    from synth import batched_systems
+    systems = batched_systems()
+    M = args.poles or 120
+    kT = 0.01
+    plan = nd.analyze_batched(systems, precision=prec_code[args.precision])
+    info = nd.ndsi_plan_info(plan)
+    dev = torch.device("cuda", local)
+    H = torch.as_tensor(np.concatenate([s.H for s in systems]), device=dev)
+    S = torch.as_tensor(np.concatenate([s.S for s in systems]), device=dev)
+    nnz = int(H.shape[0])
+    rho = torch.zeros(nnz, dtype=torch.float64, device=dev)
+    ne = torch.zeros(len(systems), dtype=torch.float64, device=dev)
+    mus = np.full(len(systems), MU)
+    kts = np.full(len(systems), kT)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        nd.ndsi_density_batched(plan, H, S, mus, kts, M, rho, ne, stream=stream)
+    for _ in range(max(args.warmup, 3)):
+        step()
+    nd.ndsi_profile_enable(plan, True)
+    times = []
+    with ClockSampler(local) as clk:
+        for _ in range(args.steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            step()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1))
+    prof = nd.ndsi_profile_read(plan)
+    ms = sum(times) / len(times)
+    ntot = sum(s.n for s in systems)
+    roofline, kern = _roofline(prof, args.steps, _peaks())
+    line = {"metric": METRIC, "value": world * M * ntot / (ms * 1e-3), "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if args.precision == "fp64" else "bf16x6->f64", "data": "synthetic",
+            "config": {"workload": f"batched: {M} poles x {len(systems)} uneven systems "
+                                   f"(N {min(s.n for s in systems)}..{max(s.n for s in systems)}), "
+                                   f"{args.precision} path, one launch per tree level",
+                       "n_total": ntot, "poles": M, "kT": kT, "nnz": nnz, "precision": args.precision,
+                       "flops_per_pole": info["flops_per_pole"], "n_levels": info["n_levels"],
+                       "l2": "flushed (256 MB write) before every timed step"},
+            "gpu_launches": sum(v["launches"] for v in kern.values()),
+            "roofline": roofline, "clocks": clk.summary(),
+            "n_elec": ne.cpu().numpy().tolist(),
+            "kernels": {k: {"launches": v["launches"] // args.steps, "ms_per_step": v["ms"] / args.steps}
+                        for k, v in kern.items()}}
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ndsi", choices=["ndsi", "reference"])
-    ap.add_argument("--config", default="C2", choices=["C1", "C2", "C3"])
+    ap.add_argument("--config", default="C2", choices=["C1", "C2", "C3", "C4"])
     ap.add_argument("--precision", default="fp64", choices=["fp64", "split"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-parity", action="store_true", help="skip the sampled-column check")
