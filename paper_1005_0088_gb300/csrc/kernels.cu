@@ -134,70 +134,81 @@ __global__ void __launch_bounds__(256) k_diaginv(const DiagItem* __restrict__ it
     }
 }
 
-// Register-resident variant for blocks of up to 32: one warp per (block, pole), lane j holds
-// column j; each pivot's column is broadcast through 512 bytes of shared memory, so a pivot
-// step needs only warp-level synchronisation.  Four warps per CTA take four poles.
-__global__ void __launch_bounds__(128) k_diaginv_warp(const DiagItem* __restrict__ items, int64_t first,
-                                                      double2* __restrict__ F, int64_t stride, int np,
+// Register-resident variant for blocks of up to 32: one warp per (block, pole) running the
+// symmetric sweep, the sign convention of Gauss-Jordan elimination that keeps a symmetric matrix
+// symmetric.  Pivoting on t with p = a_tt maps a_tt -> -1/p, a_it and a_ti -> a_it/p and
+// a_ik -> a_ik - a_it a_tk / p; after all pivots the block holds -A^{-1}.  Because every
+// intermediate matrix is symmetric only the 528 lower-triangle elements are updated, half the
+// FP64 work of the full elimination.  They are packed 17 to a lane: lane c (c < 16) holds rows
+// c..31 of column c and then rows 31-c..31 of column 31-c (33 elements), split between lanes c
+// (first 17) and c + 16 (last 16).  Every lane runs the same instruction stream (no divergent
+// pivot lane); column t of the current matrix and its scaled copy pass through shared memory.
+constexpr int kSweepSlots = 17;
+
+__global__ void __launch_bounds__(32) k_diaginv_sweep(const DiagItem* __restrict__ items, int64_t first,
+                                                      double2* __restrict__ F, int64_t stride,
                                                       int* __restrict__ status) {
-    __shared__ double2 colbuf[4][32];
-    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-    const int pole = blockIdx.y * 4 + warp;
-    if (pole >= np) return;
+    __shared__ double2 cs[33], ds[33];
+    const int lane = threadIdx.x;
     const DiagItem d = items[first + blockIdx.x];
-    double2* A = F + static_cast<int64_t>(pole) * stride + d.off;
+    double2* A = F + static_cast<int64_t>(blockIdx.y) * stride + d.off;
     const int nb = d.nb, ld = d.ld;
-    double2 a[32];
+    const int c = lane & 15, vbase = lane < 16 ? 0 : kSweepSlots;
+    int rc[kSweepSlots];  // row | column << 8 of each slot (32 = unused slot)
+    double2 a[kSweepSlots];
 #pragma unroll
-    for (int i = 0; i < 32; ++i) {
-        a[i] = make_double2(0.0, 0.0);
-        if (i < nb && lane < nb)
-            a[i] = i >= lane ? A[i + static_cast<int64_t>(lane) * ld] : A[lane + static_cast<int64_t>(i) * ld];
+    for (int s = 0; s < kSweepSlots; ++s) {
+        const int v = vbase + s;
+        int i = 32, k = 32;
+        if (v < 32 - c) {
+            i = c + v;
+            k = c;
+        } else if (v <= 32) {
+            i = v - 1;
+            k = 31 - c;
+        }
+        rc[s] = i | (k << 8);
+        a[s] = make_double2(0.0, 0.0);
+        if (i < nb && k < nb) a[s] = A[i + static_cast<int64_t>(k) * ld];
+    }
+    if (lane == 0) {
+        cs[32] = make_double2(0.0, 0.0);
+        ds[32] = make_double2(0.0, 0.0);
     }
     bool bad = false;
+    for (int t = 0; t < nb; ++t) {
+        // column t (= row t) of the current matrix
 #pragma unroll
-    for (int t = 0; t < 32; ++t) {
-        if (t < nb) {
-            // pivot column t to shared memory, pivot broadcast
-            if (lane == t) {
-#pragma unroll
-                for (int i = 0; i < 32; ++i) colbuf[warp][i] = a[i];
-            }
-            __syncwarp();
-            const double2 p = colbuf[warp][t];
-            const double den = p.x * p.x + p.y * p.y;
-            bad |= !(den > 0.0 && isfinite(den));
-            const double2 ip = make_double2(p.x / den, -p.y / den);
-            if (lane == t) {
-#pragma unroll
-                for (int i = 0; i < 32; ++i) {
-                    if (i == t) {
-                        a[i] = ip;
-                    } else {
-                        const double2 v = cmul(a[i], ip);
-                        a[i] = make_double2(-v.x, -v.y);
-                    }
-                }
-            } else {
-                const double2 r = cmul(a[t], ip);  // scaled pivot-row element of this column
-#pragma unroll
-                for (int i = 0; i < 32; ++i) {
-                    if (i == t) {
-                        a[i] = r;
-                    } else {
-                        const double2 c = colbuf[warp][i];
-                        a[i].x -= c.x * r.x - c.y * r.y;
-                        a[i].y -= c.x * r.y + c.y * r.x;
-                    }
-                }
-            }
-            __syncwarp();
+        for (int s = 0; s < kSweepSlots; ++s) {
+            const int i = rc[s] & 255, k = rc[s] >> 8;
+            if (k == t) cs[i] = a[s];
+            if (i == t) cs[k] = a[s];
         }
+        __syncwarp();
+        const double2 p = cs[t];
+        const double den = p.x * p.x + p.y * p.y;
+        bad |= !(den > 0.0 && isfinite(den));
+        const double rden = 1.0 / den;
+        const double2 ip = make_double2(p.x * rden, -p.y * rden);
+        ds[lane] = cmul(cs[lane], ip);
+        __syncwarp();
+#pragma unroll
+        for (int s = 0; s < kSweepSlots; ++s) {
+            const int i = rc[s] & 255, k = rc[s] >> 8;
+            const double2 cv = cs[i], dk = ds[k];
+            double2 g = make_double2(a[s].x - (cv.x * dk.x - cv.y * dk.y), a[s].y - (cv.x * dk.y + cv.y * dk.x));
+            if (k == t) g = i == t ? make_double2(-ip.x, -ip.y) : ds[i];
+            else if (i == t) g = dk;
+            a[s] = g;
+        }
+        __syncwarp();
     }
     if (bad && lane == 0) atomicOr(status, kStatusSingular);
 #pragma unroll
-    for (int i = 0; i < 32; ++i)
-        if (i < nb && lane < nb && i >= lane) A[i + static_cast<int64_t>(lane) * ld] = a[i];
+    for (int s = 0; s < kSweepSlots; ++s) {
+        const int i = rc[s] & 255, k = rc[s] >> 8;
+        if (i < nb && k < nb) A[i + static_cast<int64_t>(k) * ld] = make_double2(-a[s].x, -a[s].y);
+    }
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -465,8 +476,7 @@ cudaError_t launch_step(const Plan& P, const DevTables& T, const Launch& l, cons
             const int b = P.block;
             const size_t sm = static_cast<size_t>(b) * (b + 1) * sizeof(double2);
             if (b <= 32) {
-                dim3 g2(static_cast<unsigned>(l.count), static_cast<unsigned>((np + 3) / 4));
-                k_diaginv_warp<<<g2, 128, 0, st>>>(T.diag_items, l.first, W.fronts, W.front_stride, np, T.status);
+                k_diaginv_sweep<<<grid, 32, 0, st>>>(T.diag_items, l.first, W.fronts, W.front_stride, T.status);
             } else {
                 k_diaginv<64><<<grid, 256, sm, st>>>(T.diag_items, l.first, W.fronts, W.front_stride, T.status);
             }
