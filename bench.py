@@ -198,26 +198,33 @@ def _roofline(prof, steps, peaks):
 
 
 def _measure(nd, torch, plan, H, S, rho, ne, kT, M, steps, warmup, stream, flush, clocks=None):
+    """Time `steps` density sweeps as the library runs them (one captured CUDA graph per sweep),
+    then repeat them with direct launches and per-launch CUDA events for the kernel breakdown."""
     def step():
         nd.ndsi_density(plan, H, S, MU, kT, M, rho, ne, stream=stream)
+
+    def timed_steps():
+        out = []
+        for _ in range(steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            step()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            out.append(e0.elapsed_time(e1))
+        return out
     for _ in range(max(warmup, 3)):
         step()
     torch.cuda.synchronize()
+    times = timed_steps()
     nd.ndsi_profile_enable(plan, True)
-    times = []
-    torch.cuda.synchronize()
-    for _ in range(steps):
-        flush.zero_()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        step()
-        e1.record(stream)
-        torch.cuda.synchronize()
-        times.append(e0.elapsed_time(e1))
+    prof_times = timed_steps()
     prof = nd.ndsi_profile_read(plan)
     nd.ndsi_profile_enable(plan, False)
-    return times, prof
+    return times, prof, prof_times
 
 
 def run_ndsi(args):
@@ -257,8 +264,9 @@ def run_ndsi(args):
     if world > 1:
         dist.barrier()
     with ClockSampler(local) as clk:
-        times, prof = _measure(nd, torch, plan, H, S, rho, ne, kT, M, args.steps, args.warmup, stream,
-                               flush)
+        times, prof, prof_times = _measure(nd, torch, plan, H, S, rho, ne, kT, M, args.steps,
+                                           args.warmup, stream, flush)
+        graph_nodes = nd.ndsi_graph_info(plan)
     if world > 1:
         dist.barrier()
     total_ms = sum(times)
@@ -294,8 +302,8 @@ def run_ndsi(args):
         plan2 = nd.analyze_system(system, precision=prec_code[oprec])
         rho2 = torch.zeros_like(rho)
         ne2 = torch.zeros_like(ne)
-        t2, prof2 = _measure(nd, torch, plan2, H, S, rho2, ne2, kT, M, args.steps, args.warmup, stream,
-                             flush)
+        t2, prof2, _ = _measure(nd, torch, plan2, H, S, rho2, ne2, kT, M, args.steps, args.warmup,
+                                stream, flush)
         ms2 = sum(t2) / len(t2)
         ms_split, ms_fp64 = (ms2, ms_step) if oprec == "split" else (ms_step, ms2)
         rl2, k2 = _roofline(prof2, args.steps, _peaks())
@@ -346,6 +354,11 @@ def run_ndsi(args):
                     "h2d_bytes_per_step": 2 * 8 * system.nnz,
                     "d2h_bytes_per_step": 8 * system.nnz + 8},
             "gpu_launches": launches,
+            "graph": {"kernel_nodes": graph_nodes,
+                      "ms_per_step_direct_launches": sum(prof_times) / len(prof_times),
+                      "note": "timed steps replay one captured CUDA graph per sweep; the kernel "
+                              "breakdown and roofline come from the same steps repeated with direct "
+                              "launches bracketed by CUDA events on the launch stream"},
             "roofline": roofline, "clocks": clk.summary(), "cpu_baseline": cpu,
             "parity": parity, "other_precision": other,
             "kernels": {k: {"launches": v["launches"] // args.steps, "ms_per_step": v["ms"] / args.steps,
@@ -384,9 +397,9 @@ def run_batched(args, nd, torch, dist, rank, world, local, prec_code):
         nd.ndsi_density_batched(plan, H, S, mus, kts, M, rho, ne, stream=stream)
     for _ in range(max(args.warmup, 3)):
         step()
-    nd.ndsi_profile_enable(plan, True)
-    times = []
-    with ClockSampler(local) as clk:
+
+    def timed_steps():
+        out = []
         for _ in range(args.steps):
             flush.zero_()
             torch.cuda.synchronize()
@@ -396,8 +409,15 @@ def run_batched(args, nd, torch, dist, rank, world, local, prec_code):
             step()
             e1.record(stream)
             torch.cuda.synchronize()
-            times.append(e0.elapsed_time(e1))
+            out.append(e0.elapsed_time(e1))
+        return out
+    with ClockSampler(local) as clk:
+        times = timed_steps()
+    graph_nodes = nd.ndsi_graph_info(plan)
+    nd.ndsi_profile_enable(plan, True)
+    prof_times = timed_steps()
     prof = nd.ndsi_profile_read(plan)
+    nd.ndsi_profile_enable(plan, False)
     ms = sum(times) / len(times)
     ntot = sum(s.n for s in systems)
     roofline, kern = _roofline(prof, args.steps, _peaks())
@@ -412,6 +432,8 @@ def run_batched(args, nd, torch, dist, rank, world, local, prec_code):
                        "flops_per_pole": info["flops_per_pole"], "n_levels": info["n_levels"],
                        "l2": "flushed (256 MB write) before every timed step"},
             "gpu_launches": sum(v["launches"] for v in kern.values()),
+            "graph": {"kernel_nodes": graph_nodes,
+                      "ms_per_step_direct_launches": sum(prof_times) / len(prof_times)},
             "roofline": roofline, "clocks": clk.summary(),
             "n_elec": ne.cpu().numpy().tolist(),
             "kernels": {k: {"launches": v["launches"] // args.steps, "ms_per_step": v["ms"] / args.steps}

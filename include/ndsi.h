@@ -193,6 +193,19 @@ typedef struct {
 
 int ndsi_profile_enable(ndsi_plan* plan, int32_t enable);
 
+/* CUDA graphs.  While enabled (the default) and profiling is off, ndsi_density,
+ * ndsi_density_batched and ndsi_find_mu run each density sweep (all chunks of points: assembly,
+ * factorisation, selected inversion, residue sum and electron counts) as one CUDA graph,
+ * captured on a private stream at the first call and replayed by later calls on the caller's
+ * stream.  A graph is recaptured when a buffer it names changes (H, S or output pointers, the
+ * workspace, the number of points); the chemical potential and temperature are read from device
+ * memory at run time and need no recapture.  ndsi_graph_enable(plan, 0) launches every kernel
+ * directly instead and frees the graph.  Errors: NDSI_ERR_INVALID for a NULL plan. */
+int ndsi_graph_enable(ndsi_plan* plan, int32_t enable);
+
+/* Kernel nodes of the plan's current captured sweep in *nodes_out (0 when none is held). */
+int ndsi_graph_info(const ndsi_plan* plan, int64_t* nodes_out);
+
 /* Copy up to max_entries families into `out` (host) and their number into *n_out.
  * Errors: NDSI_ERR_INVALID for NULL arguments. */
 int ndsi_profile_read(const ndsi_plan* plan, ndsi_profile_entry* out, int32_t max_entries,

@@ -530,14 +530,29 @@ void build_schedule(Plan& P) {
         l.alpha = alpha; l.beta = beta; l.lower = lower ? 1 : 0;
         l.first = static_cast<int64_t>(P.gemm_items.size());
         l.tfirst = static_cast<int64_t>(P.gemm_tiles.size());
+        // Output tile edge: the small tile when the large one would spend more than 10% of the
+        // launch's multiply-adds on padding (ragged edges of small fronts).
+        auto padded = [&](int32_t T) {
+            double e = 0;
+            for (const GSpec& g : specs) {
+                if (g.M <= 0 || g.N <= 0 || g.K <= 0) continue;
+                double nt = 0;
+                for (int32_t m0 = 0; m0 < g.M; m0 += T)
+                    for (int32_t n0 = 0; n0 < g.N; n0 += T)
+                        if (!(lower && n0 > m0 + T - 1)) nt += 1;
+                e += nt * T * T * g.K;
+            }
+            return e;
+        };
+        l.tile = padded(kGemmTile) > 1.1 * padded(kGemmTileSmall) ? kGemmTileSmall : kGemmTile;
         double fl = 0;
         for (const GSpec& g : specs) {
             if (g.M <= 0 || g.N <= 0 || g.K <= 0) continue;
             const int32_t it = static_cast<int32_t>(P.gemm_items.size() - l.first);
             P.gemm_items.push_back(GemmItem{g.a_off, g.b_off, g.c_off, g.lda, g.ldb, g.ldc, g.M, g.N, g.K, 0});
-            for (int32_t m0 = 0; m0 < g.M; m0 += kGemmTile)
-                for (int32_t n0 = 0; n0 < g.N; n0 += kGemmTile) {
-                    if (lower && n0 > m0 + kGemmTile - 1) continue;
+            for (int32_t m0 = 0; m0 < g.M; m0 += l.tile)
+                for (int32_t n0 = 0; n0 < g.N; n0 += l.tile) {
+                    if (lower && n0 > m0 + l.tile - 1) continue;
                     P.gemm_tiles.push_back(GemmTile{it, m0, n0, 0});
                 }
             const double mn = lower ? 0.5 * g.M * (g.M + 1.0) : static_cast<double>(g.M) * g.N;

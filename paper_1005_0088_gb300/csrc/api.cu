@@ -75,6 +75,13 @@ struct ndsi_plan {
     int64_t stage_cap = 0;
     std::vector<double> pole_z, pole_R;  // cached continued-fraction poles
     int32_t pole_M = 0;
+    // CUDA graph of one density sweep (every chunk's factor, selected inversion and residue
+    // sum), captured on first use and replayed while the buffers it names stay the same
+    bool graphs = true;
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t graph = nullptr;
+    std::vector<const void*> graph_key;
+    int64_t graph_nodes = 0;
 };
 
 struct ndsi_factors {
@@ -385,6 +392,8 @@ int64_t workspace_cap(const ndsi_plan* h) {
 namespace ndsi {
 int density_impl(ndsi_plan* h, const double* Hd, const double* Sd, const double* mu, const double* kT,
                  int32_t n_poles, double* rho_d, double* ne_d, cudaStream_t st);
+int sweep(ndsi_plan* h, const double* Hd, const double* Sd, int32_t nq, int32_t chunk,
+          const std::vector<int>& part_off, double* rho_d, double* ne_d, cudaStream_t st);
 }  // namespace ndsi
 
 using namespace ndsi;
@@ -750,6 +759,48 @@ int density_impl(ndsi_plan* h, const double* Hd, const double* Sd, const double*
     if (!h->partials) NDSI_CK(cudaMalloc(&h->partials, sizeof(double) * (part_off[ns] + 1)));
     NDSI_CK(cudaMemcpyAsync(h->zw, zq.data(), sizeof(double2) * ns * nq, cudaMemcpyHostToDevice, st));
     NDSI_CK(cudaMemcpyAsync(h->cw, cq.data(), sizeof(double2) * ns * nq, cudaMemcpyHostToDevice, st));
+    if (h->graphs && !h->prof.on) {
+        // replay the captured sweep; points and weights are read from zw / cw at run time
+        const std::vector<const void*> key = {Hd, Sd, rho_d, ne_d, h->W.fronts, h->W.scr, h->SB.sliceA,
+                                              h->SB.sliceB, h->cw, h->zw, h->partials,
+                                              reinterpret_cast<const void*>(static_cast<intptr_t>(nq)),
+                                              reinterpret_cast<const void*>(static_cast<intptr_t>(chunk))};
+        if (!h->graph || h->graph_key != key) {
+            if (h->graph) cudaGraphExecDestroy(h->graph);
+            h->graph = nullptr;
+            if (!h->cap_stream) NDSI_CK(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+            NDSI_CK(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
+            rc = sweep(h, Hd, Sd, nq, chunk, part_off, rho_d, ne_d, h->cap_stream);
+            cudaGraph_t g = nullptr;
+            const cudaError_t ec = cudaStreamEndCapture(h->cap_stream, &g);
+            if (rc || ec != cudaSuccess) {
+                if (g) cudaGraphDestroy(g);
+                if (rc) return rc;
+                NDSI_CK(ec);
+            }
+            size_t nodes = 0;
+            cudaGraphGetNodes(g, nullptr, &nodes);
+            const cudaError_t ei = cudaGraphInstantiate(&h->graph, g, 0);
+            cudaGraphDestroy(g);
+            NDSI_CK(ei);
+            h->graph_key = key;
+            h->graph_nodes = static_cast<int64_t>(nodes);
+        }
+        NDSI_CK(cudaGraphLaunch(h->graph, st));
+        return check_status(h, st);
+    }
+    rc = sweep(h, Hd, Sd, nq, chunk, part_off, rho_d, ne_d, st);
+    if (rc) return rc;
+    return check_status(h, st);
+}
+
+// One density sweep over all points, chunked: factor, selected inversion and residue sum per
+// chunk, then the per-system electron counts.  Only stream-ordered work: it is also the body of
+// the captured graph.
+int sweep(ndsi_plan* h, const double* Hd, const double* Sd, int32_t nq, int32_t chunk,
+          const std::vector<int>& part_off, double* rho_d, double* ne_d, cudaStream_t st) {
+    int rc;
+    const int32_t ns = h->P.n_systems;
     for (int32_t q0 = 0; q0 < nq; q0 += chunk) {
         const int32_t np = std::min(chunk, nq - q0);
         rc = run_phase(h, h->W, h->SB, 0, Hd, Sd, h->zw + q0, nq, np, st);
@@ -770,7 +821,7 @@ int density_impl(ndsi_plan* h, const double* Hd, const double* Sd, const double*
         NDSI_CK(timed(h->prof, "reduce", static_cast<double>(nblk), 8.0 * nblk, st,
                       [&]() { return launch_reduce(h->partials + part_off[sy], nblk, ne_d + sy, st); }));
     }
-    return check_status(h, st);
+    return NDSI_OK;
 }
 }  // namespace ndsi
 
@@ -1051,7 +1102,27 @@ void ndsi_plan_destroy(ndsi_plan* h) {
     if (h->zw) cudaFree(h->zw);
     if (h->partials) cudaFree(h->partials);
     if (h->stage) cudaFree(h->stage);
+    if (h->graph) cudaGraphExecDestroy(h->graph);
+    if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
     delete h;
+}
+
+int ndsi_graph_enable(ndsi_plan* h, int32_t enable) {
+    if (!h) return fail(NDSI_ERR_INVALID, "ndsi_graph_enable: NULL plan");
+    h->graphs = enable != 0;
+    if (!h->graphs && h->graph) {
+        cudaGraphExecDestroy(h->graph);
+        h->graph = nullptr;
+        h->graph_key.clear();
+        h->graph_nodes = 0;
+    }
+    return NDSI_OK;
+}
+
+int ndsi_graph_info(const ndsi_plan* h, int64_t* nodes_out) {
+    if (!h || !nodes_out) return fail(NDSI_ERR_INVALID, "ndsi_graph_info: NULL argument");
+    *nodes_out = h->graph ? h->graph_nodes : 0;
+    return NDSI_OK;
 }
 
 const char* ndsi_last_error(void) { return g_last_error.c_str(); }

@@ -213,11 +213,12 @@ __global__ void __launch_bounds__(32) k_diaginv_sweep(const DiagItem* __restrict
 
 // ---------------------------------------------------------------------------------------------
 // Batched complex FP64 GEMM on the CUDA cores: C = alpha op(A) op(B) + beta C for every tile of
-// a schedule step.  32 x 32 output tile, K step 16, 64 threads with 4 x 4 outputs each.  The
-// complex product uses three real products per element (Re = P1 - P2, Im = P3 - P1 - P2 with
-// P1 = Ar Br, P2 = Ai Bi, P3 = (Ar + Ai)(Br + Bi)): GB300's FP64 rate is the bound here, and
-// the third real product saves a quarter of the DFMAs.
-constexpr int BM = kGemmTile, BN = kGemmTile, BK = 16;
+// a schedule step.  TILE x TILE output tile (32, or 16 for launches of small items, where a 32
+// tile would spend its multiply-adds on padding), K step 16, 64 threads with (TILE/8)^2 outputs
+// each.  The complex product uses three real products per element (Re = P1 - P2,
+// Im = P3 - P1 - P2 with P1 = Ar Br, P2 = Ai Bi, P3 = (Ar + Ai)(Br + Bi)): GB300's FP64 rate is
+// the bound here, and the third real product saves a quarter of the DFMAs.
+constexpr int BK = 16;
 
 template <int OP>
 __device__ __forceinline__ double2 load_op(const double2* __restrict__ X, int ld, int r, int c) {
@@ -227,15 +228,17 @@ __device__ __forceinline__ double2 load_op(const double2* __restrict__ X, int ld
     return X[hi + static_cast<int64_t>(lo) * ld];
 }
 
-template <int OPA, int OPB>
+template <int OPA, int OPB, int TILE>
 __global__ void __launch_bounds__(64) k_gemm_f64(const GemmItem* __restrict__ items,
                                                  const GemmTile* __restrict__ tiles, int64_t tfirst,
                                                  int64_t ifirst, const double2* __restrict__ Abuf,
                                                  int64_t sA, const double2* __restrict__ Bbuf,
                                                  int64_t sB, double2* __restrict__ Cbuf, int64_t sC,
                                                  double alpha, double beta, int lower) {
-    __shared__ double As[3][BK][BM + 1];
-    __shared__ double Bs[3][BK][BN + 1];
+    constexpr int MT = TILE / 8;           // outputs per thread along each edge
+    constexpr int LD = TILE * BK / 64;     // operand elements each thread stages per K step
+    __shared__ double As[3][BK][TILE + 1];
+    __shared__ double Bs[3][BK][TILE + 1];
     const GemmTile t = tiles[tfirst + blockIdx.x];
     const GemmItem it = items[ifirst + t.item];
     const int64_t pole = blockIdx.y;
@@ -244,22 +247,22 @@ __global__ void __launch_bounds__(64) k_gemm_f64(const GemmItem* __restrict__ it
     double2* C = Cbuf + pole * sC + it.c_off;
     const int tid = threadIdx.x;
     const int tx = tid % 8, ty = tid / 8;
-    double p1[4][4], p2[4][4], p3[4][4];
+    double p1[MT][MT], p2[MT][MT], p3[MT][MT];
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
+    for (int i = 0; i < MT; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) p1[i][j] = p2[i][j] = p3[i][j] = 0.0;
+        for (int j = 0; j < MT; ++j) p1[i][j] = p2[i][j] = p3[i][j] = 0.0;
     for (int k0 = 0; k0 < it.K; k0 += BK) {
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
+        for (int u = 0; u < LD; ++u) {
             const int e = tid + 64 * u;
             int lm, lk;
             if (OPA == OP_T) {
                 lk = e % BK;
                 lm = e / BK;
             } else {
-                lm = e % BM;
-                lk = e / BM;
+                lm = e % TILE;
+                lk = e / TILE;
             }
             const int m = t.m0 + lm, k = k0 + lk;
             const double2 v = (m < it.M && k < it.K) ? load_op<OPA>(A, it.lda, m, k) : make_double2(0.0, 0.0);
@@ -268,12 +271,12 @@ __global__ void __launch_bounds__(64) k_gemm_f64(const GemmItem* __restrict__ it
             As[2][lk][lm] = v.x + v.y;
         }
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
+        for (int u = 0; u < LD; ++u) {
             const int e = tid + 64 * u;
             int ln, lk;
             if (OPB == OP_T) {
-                ln = e % BN;
-                lk = e / BN;
+                ln = e % TILE;
+                lk = e / TILE;
             } else {
                 lk = e % BK;
                 ln = e / BK;
@@ -287,23 +290,23 @@ __global__ void __launch_bounds__(64) k_gemm_f64(const GemmItem* __restrict__ it
         __syncthreads();
 #pragma unroll 2
         for (int kk = 0; kk < BK; ++kk) {
-            double ar[4], ai[4], as[4], br[4], bi[4], bs[4];
+            double ar[MT], ai[MT], as[MT], br[MT], bi[MT], bs[MT];
 #pragma unroll
-            for (int i = 0; i < 4; ++i) {
+            for (int i = 0; i < MT; ++i) {
                 ar[i] = As[0][kk][tx + 8 * i];
                 ai[i] = As[1][kk][tx + 8 * i];
                 as[i] = As[2][kk][tx + 8 * i];
             }
 #pragma unroll
-            for (int j = 0; j < 4; ++j) {
+            for (int j = 0; j < MT; ++j) {
                 br[j] = Bs[0][kk][ty + 8 * j];
                 bi[j] = Bs[1][kk][ty + 8 * j];
                 bs[j] = Bs[2][kk][ty + 8 * j];
             }
 #pragma unroll
-            for (int i = 0; i < 4; ++i)
+            for (int i = 0; i < MT; ++i)
 #pragma unroll
-                for (int j = 0; j < 4; ++j) {
+                for (int j = 0; j < MT; ++j) {
                     p1[i][j] = fma(ar[i], br[j], p1[i][j]);
                     p2[i][j] = fma(ai[i], bi[j], p2[i][j]);
                     p3[i][j] = fma(as[i], bs[j], p3[i][j]);
@@ -312,10 +315,10 @@ __global__ void __launch_bounds__(64) k_gemm_f64(const GemmItem* __restrict__ it
         __syncthreads();
     }
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
+    for (int j = 0; j < MT; ++j) {
         const int n = t.n0 + ty + 8 * j;
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
+        for (int i = 0; i < MT; ++i) {
             const int m = t.m0 + tx + 8 * i;
             if (m < it.M && n < it.N && (!lower || m >= n)) {
                 double2* c = C + m + static_cast<int64_t>(n) * it.ldc;
@@ -444,10 +447,14 @@ cudaError_t gemm_launch(const Plan& P, const DevTables& T, const Launch& l, cons
     const double2* bufs[2] = {W.fronts, W.scr};
     const int64_t strides[2] = {W.front_stride, W.scr_stride};
     dim3 grid(static_cast<unsigned>(l.tcount), static_cast<unsigned>(np));
-    k_gemm_f64<OPA, OPB><<<grid, 64, 0, st>>>(T.gemm_items, T.gemm_tiles, l.tfirst, l.first,
-                                               bufs[l.bufA], strides[l.bufA], bufs[l.bufB],
-                                               strides[l.bufB], const_cast<double2*>(bufs[l.bufC]),
-                                               strides[l.bufC], l.alpha, l.beta, l.lower);
+    if (l.tile == kGemmTileSmall)
+        k_gemm_f64<OPA, OPB, kGemmTileSmall><<<grid, 64, 0, st>>>(
+            T.gemm_items, T.gemm_tiles, l.tfirst, l.first, bufs[l.bufA], strides[l.bufA], bufs[l.bufB],
+            strides[l.bufB], const_cast<double2*>(bufs[l.bufC]), strides[l.bufC], l.alpha, l.beta, l.lower);
+    else
+        k_gemm_f64<OPA, OPB, kGemmTile><<<grid, 64, 0, st>>>(
+            T.gemm_items, T.gemm_tiles, l.tfirst, l.first, bufs[l.bufA], strides[l.bufA], bufs[l.bufB],
+            strides[l.bufB], const_cast<double2*>(bufs[l.bufC]), strides[l.bufC], l.alpha, l.beta, l.lower);
     (void)P;
     return cudaGetLastError();
 }

@@ -75,6 +75,7 @@ struct Launch {
     double alpha, beta;
     int64_t first, count;    // range in the item array of this kind
     int64_t tfirst, tcount;  // GEMM tiles range
+    int32_t tile;            // FP64 GEMM output tile edge of this launch (16 or 32)
     int32_t phase;           // 0 factor, 1 selinv
     int32_t tag;             // which formula the step implements (for profiling names)
     double flops;            // algorithmic real flops per pole of this launch
@@ -154,7 +155,8 @@ int merge_plans(std::vector<Plan>& parts, Plan& merged, std::string& err);
 int cf_poles(int32_t M, double* z, double* R, std::string& err);
 
 // Tile sizes shared by the schedule and the kernels.
-constexpr int kGemmTile = 32;     // FP64 GEMM output tile (rows and columns)
+constexpr int kGemmTile = 32;     // largest FP64 GEMM output tile (rows and columns)
+constexpr int kGemmTileSmall = 16;  // output tile for launches whose items are small
 constexpr int kNodeTile = 32;     // assembly / gather tile
 
 void set_last_error(const std::string& msg);

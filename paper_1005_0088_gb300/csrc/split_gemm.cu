@@ -597,7 +597,6 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
     } else if (warp == 1) {
         if (lane == 0) {
-            bool tail_started = false;
             int issued = 0;
             for (int kb = 0; kb < nkb; ++kb) {
                 const int stage = kb & 1;
@@ -606,40 +605,44 @@ __global__ void __launch_bounds__(kThreads, 1)
                 const int chunk = kb / kSplitChunkKB;
                 const bool first_in_chunk = (kb % kSplitChunkKB) == 0;
                 if (first_in_chunk) {
-                    tail_started = false;
                     if (chunk > 0) {
                         if (!mbar_wait(tmem_free, (chunk - 1) & 1, abort)) break;
                         tc_fence_after();
                     }
                 }
+                // Descriptors of this stage's slice tiles: the start-address field is the low 14
+                // bits (address >> 4), so tile t and K16 half ks are compile-time offsets from the
+                // stage's first tile.  The pair loops unroll completely (S is a template
+                // parameter), leaving one 64-bit add and one tcgen05.mma per product.
+                const uint64_t da0 = sdesc_sw64(smem_u32(a_tile(stage, 0)));
+                const uint64_t db0 = sdesc_sw64(smem_u32(b_tile(stage, 0)));
+                const uint32_t fresh = first_in_chunk ? 0u : 1u;
                 // band 3: slice pairs with t+u >= 5 (1-based), read out per chunk like the others
-#pragma unroll 1
+#pragma unroll
                 for (int t = 0; t < S; ++t)
-#pragma unroll 1
+#pragma unroll
                     for (int u = 0; u < S; ++u) {
                         if (t + u > S - 1 || t + u < 3) continue;
+                        const bool lead = (t + u == 3) && t == 0;  // first tail product of a K-tile
 #pragma unroll
                         for (int ks = 0; ks < 2; ++ks) {
-                            const uint64_t da = sdesc_sw64(smem_u32(a_tile(stage, t)) + ks * 32);
-                            const uint64_t db = sdesc_sw64(smem_u32(b_tile(stage, u)) + ks * 32);
-                            umma_bf16(tmem + 3 * 128, da, db, kIdesc, tail_started ? 1u : 0u);
-                            tail_started = true;
+                            const uint64_t da = da0 + static_cast<uint64_t>((t * kTileBytes + ks * 32) >> 4);
+                            const uint64_t db = db0 + static_cast<uint64_t>((u * kTileBytes + ks * 32) >> 4);
+                            umma_bf16(tmem + 3 * 128, da, db, kIdesc, (lead && ks == 0) ? fresh : 1u);
                         }
                     }
                 // bands 0..2: t+u = 2, 3, 4 (1-based), exact within a chunk
-#pragma unroll 1
+#pragma unroll
                 for (int band = 0; band < 3; ++band) {
-                    bool first = first_in_chunk;
-#pragma unroll 1
+#pragma unroll
                     for (int t = 0; t < S; ++t) {
                         const int u = band - t;
                         if (u < 0 || u >= S) continue;
 #pragma unroll
                         for (int ks = 0; ks < 2; ++ks) {
-                            const uint64_t da = sdesc_sw64(smem_u32(a_tile(stage, t)) + ks * 32);
-                            const uint64_t db = sdesc_sw64(smem_u32(b_tile(stage, u)) + ks * 32);
-                            umma_bf16(tmem + band * 128, da, db, kIdesc, first ? 0u : 1u);
-                            first = false;
+                            const uint64_t da = da0 + static_cast<uint64_t>((t * kTileBytes + ks * 32) >> 4);
+                            const uint64_t db = db0 + static_cast<uint64_t>((u * kTileBytes + ks * 32) >> 4);
+                            umma_bf16(tmem + band * 128, da, db, kIdesc, (t == 0 && ks == 0) ? fresh : 1u);
                         }
                     }
                 }

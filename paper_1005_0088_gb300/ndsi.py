@@ -33,7 +33,7 @@ EXPORTED_SYMBOLS = (
     "ndsi_factors_destroy", "ndsi_last_error", "ndsi_profile_enable", "ndsi_profile_read",
     "ndsi_residue_sum_static", "ndsi_find_mu", "ndsi_mu_features", "ndsi_mlp_init",
     "ndsi_mlp_forward", "ndsi_mlp_grad", "ndsi_mlp_train", "ndsi_analyze_batched",
-    "ndsi_density_batched",
+    "ndsi_density_batched", "ndsi_graph_enable", "ndsi_graph_info",
 )
 NDSI_MLP_INPUTS = 32
 NDSI_MLP_HIDDEN = 64
@@ -98,6 +98,10 @@ def load(path: str = LIB_PATH):
     lib.ndsi_factors_destroy.argtypes = [vp]
     lib.ndsi_factors_destroy.restype = None
     lib.ndsi_profile_enable.argtypes = [vp, i32]
+    lib.ndsi_graph_enable.argtypes = [vp, i32]
+    lib.ndsi_graph_info.argtypes = [vp, ctypes.POINTER(ctypes.c_int64)]
+    lib.ndsi_graph_enable.restype = ctypes.c_int
+    lib.ndsi_graph_info.restype = ctypes.c_int
     lib.ndsi_profile_read.argtypes = [vp, ctypes.POINTER(ndsi_profile_entry), i32,
                                       ctypes.POINTER(i32)]
     lib.ndsi_residue_sum_static.argtypes = [vp, vp, i32, vp, i64, vp, vp, vp]
@@ -268,6 +272,18 @@ def analyze_system(system, **options) -> Plan:
         setattr(opt, k, v)
     return ndsi_analyze(system.n, system.rowptr, system.col, system.centers.shape[0],
                         system.centers, system.atom_of_basis, opt)
+
+
+def ndsi_graph_enable(plan: Plan, enable: bool = True):
+    """Run density sweeps as one captured CUDA graph (default) or as direct launches."""
+    _check(load().ndsi_graph_enable(plan.handle, 1 if enable else 0))
+
+
+def ndsi_graph_info(plan: Plan) -> int:
+    """Kernel nodes of the plan's captured sweep (0 when none is held)."""
+    n = ctypes.c_int64(0)
+    _check(load().ndsi_graph_info(plan.handle, ctypes.byref(n)))
+    return n.value
 
 
 def ndsi_profile_enable(plan: Plan, enable: bool = True):
