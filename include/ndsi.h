@@ -65,6 +65,11 @@ typedef struct {
     int32_t block;               /* FP64 pivot block size, 16/32/64 (0 = default 32) */
     double m0_radius;            /* R of the zeroth-moment point Z = iR (default 1e7) */
     int64_t max_workspace_bytes; /* device workspace cap; poles are chunked to fit (0 = auto) */
+    int32_t outer_block;         /* diagonal-block size of the two-level factorisation of A_J: the
+                                    block's own LDL^T and inverse run in FP64 pivot blocks, the
+                                    panel, trailing update and inverse assembly outside it are the
+                                    GEMMs that split mode moves to the tensor cores; a multiple of
+                                    `block` (0 = default 128) */
 } ndsi_options;
 
 /* Summary of a plan, filled by ndsi_plan_info. */

@@ -192,6 +192,11 @@ int analyze(const ndsi_pattern* pat, int32_t n_atoms, const double* centers,
         err = "ndsi_analyze: block must be 16, 32 or 64";
         return NDSI_ERR_INVALID;
     }
+    P.outer = opt.outer_block > 0 ? opt.outer_block : 128;
+    if (P.outer % P.block != 0 || P.outer > 4096) {
+        err = "ndsi_analyze: outer_block must be a multiple of block, at most 4096";
+        return NDSI_ERR_INVALID;
+    }
     P.rowptr.assign(pat->rowptr, pat->rowptr + n + 1);
     P.col.assign(pat->col, pat->col + nnz);
     // ---- pattern checks: monotone rows, sorted columns, diagonal present, symmetric
@@ -487,7 +492,7 @@ void compute_scratch(Plan& P) {
         int64_t acc = 0;
         for (int32_t j : P.level_nodes[L]) {
             P.scr_off[j] = acc;
-            const int64_t need = std::max<int64_t>(static_cast<int64_t>(P.s[j]) * b,
+            const int64_t need = std::max<int64_t>(static_cast<int64_t>(P.s[j]) * std::max(b, std::min(P.outer, P.s[j])),
                                                    static_cast<int64_t>(P.r[j]) * P.s[j]);
             acc += need;
         }
@@ -523,9 +528,10 @@ void build_schedule(Plan& P) {
     };
     auto emit_gemm = [&](int32_t L, int32_t phase, int32_t tag, int32_t opA, int32_t opB,
                          int32_t bufA, int32_t bufB, int32_t bufC, double alpha, double beta,
-                         bool lower, const std::vector<GSpec>& specs) {
+                         bool lower, const std::vector<GSpec>& specs, bool exact = false) {
         if (specs.empty()) return;
         Launch l = new_launch(L_GEMM, L, phase, tag);
+        l.exact = exact ? 1 : 0;
         l.opA = opA; l.opB = opB; l.bufA = bufA; l.bufB = bufB; l.bufC = bufC;
         l.alpha = alpha; l.beta = beta; l.lower = lower ? 1 : 0;
         l.first = static_cast<int64_t>(P.gemm_items.size());
@@ -608,64 +614,124 @@ void build_schedule(Plan& P) {
             P.bytes_per_pole += l.bytes;
             if (l.count > 0) P.launches.push_back(l);
         }
-        int32_t nbmax = 0;
-        for (int32_t j : nodesL) nbmax = std::max<int32_t>(nbmax, static_cast<int32_t>(ceil_div(P.s[j], b)));
-        // F2: block LDL^T of the diagonal block A_J (Eqs. 18-20 on b x b blocks)
-        for (int32_t t = 0; t < nbmax; ++t) {
-            Launch ld = new_launch(L_DIAGINV, L, 0, T_DINV);
-            ld.first = static_cast<int64_t>(P.diag_items.size());
-            std::vector<GSpec> panel, update;
-            std::vector<CopyItem> copies;
-            for (int32_t j : nodesL) {
-                const int32_t s = P.s[j], f = P.f[j];
-                const int32_t k0 = t * b;
-                if (k0 >= s) continue;
-                const int32_t nb = std::min(b, s - k0);
-                const int32_t k1 = k0 + nb;
-                const int64_t fo = P.front_off[j];
-                P.diag_items.push_back(DiagItem{fo + k0 + static_cast<int64_t>(k0) * f, f, nb});
-                ld.flops += 8.0 * nb * nb * nb;
-                ld.bytes += 16.0 * nb * (nb + 1.0);
-                if (k1 < s) {
-                    const int32_t m = s - k1;
-                    panel.push_back(GSpec{fo + k1 + static_cast<int64_t>(k0) * f, fo + k0 + static_cast<int64_t>(k0) * f,
-                                          P.scr_off[j], f, f, m, m, nb, nb});
-                    update.push_back(GSpec{P.scr_off[j], fo + k1 + static_cast<int64_t>(k0) * f,
-                                           fo + k1 + static_cast<int64_t>(k1) * f, m, f, f, m, m, nb});
+        // F2/F3: block LDL^T of A_J (Eqs. 18-20) and its inverse (Eqs. 38-39 inside the block), in
+        // two levels.  A_J is cut into diagonal blocks of `outer` columns; each block, once its
+        // trailing update has arrived, is factored in b x b pivot blocks and inverted in place
+        // (FP64, marked exact), then the panel below it is scaled by that inverse and the
+        // trailing matrix updated with inner dimension `outer`.  The inverse of A_J is assembled
+        // block by block from the last one backwards.  The outer GEMMs are few and large, which
+        // is what split mode needs; the pivot-level work stays in FP64.
+        const int32_t Bo = P.outer;
+        int32_t nob = 0;
+        for (int32_t j : nodesL) nob = std::max<int32_t>(nob, static_cast<int32_t>(ceil_div(P.s[j], Bo)));
+        for (int32_t T = 0; T < nob; ++T) {
+            // (i) block LDL^T of diagonal block T in pivot blocks of b
+            for (int32_t t = 0; t < Bo / b; ++t) {
+                Launch ld = new_launch(L_DIAGINV, L, 0, T_DINV);
+                ld.first = static_cast<int64_t>(P.diag_items.size());
+                std::vector<GSpec> panel, update;
+                std::vector<CopyItem> copies;
+                for (int32_t j : nodesL) {
+                    const int32_t s = P.s[j], f = P.f[j];
+                    const int32_t K0 = T * Bo;
+                    if (K0 >= s) continue;
+                    const int32_t K1 = std::min(K0 + Bo, s);
+                    const int32_t k0 = K0 + t * b;
+                    if (k0 >= K1) continue;
+                    const int32_t nb = std::min(b, K1 - k0);
+                    const int32_t k1 = k0 + nb;
+                    const int64_t fo = P.front_off[j];
+                    P.diag_items.push_back(DiagItem{fo + k0 + static_cast<int64_t>(k0) * f, f, nb});
+                    ld.flops += 8.0 * nb * nb * nb;
+                    ld.bytes += 16.0 * nb * (nb + 1.0);
+                    if (k1 < K1) {
+                        const int32_t m = K1 - k1;
+                        panel.push_back(GSpec{fo + k1 + static_cast<int64_t>(k0) * f, fo + k0 + static_cast<int64_t>(k0) * f,
+                                              P.scr_off[j], f, f, m, m, nb, nb});
+                        update.push_back(GSpec{P.scr_off[j], fo + k1 + static_cast<int64_t>(k0) * f,
+                                               fo + k1 + static_cast<int64_t>(k1) * f, m, f, f, m, m, nb});
+                        copies.push_back(CopyItem{P.scr_off[j], fo + k1 + static_cast<int64_t>(k0) * f, m, f, m, nb});
+                    }
+                }
+                ld.count = static_cast<int64_t>(P.diag_items.size()) - ld.first;
+                if (ld.count > 0) {
+                    P.flops_per_pole += ld.flops;
+                    P.launches.push_back(ld);
+                }
+                emit_gemm(L, 0, T_PANEL, OP_N, OP_S, BUF_FRONT, BUF_FRONT, BUF_SCR, 1.0, 0.0, false, panel, true);
+                emit_gemm(L, 0, T_UPDATE, OP_N, OP_T, BUF_SCR, BUF_FRONT, BUF_FRONT, -1.0, 1.0, true, update, true);
+                emit_copy(L, 0, T_PCOPY, 1.0, copies);
+            }
+            // (ii) inverse of diagonal block T in place, from its pivot blocks backwards
+            for (int32_t t = Bo / b - 1; t >= 0; --t) {
+                std::vector<GSpec> tg, dg;
+                std::vector<CopyItem> copies;
+                for (int32_t j : nodesL) {
+                    const int32_t s = P.s[j], f = P.f[j];
+                    const int32_t K0 = T * Bo;
+                    if (K0 >= s) continue;
+                    const int32_t K1 = std::min(K0 + Bo, s);
+                    const int32_t k0 = K0 + t * b;
+                    if (k0 >= K1) continue;
+                    const int32_t nb = std::min(b, K1 - k0);
+                    const int32_t k1 = k0 + nb;
+                    if (k1 >= K1) continue;
+                    const int32_t m = K1 - k1;
+                    const int64_t fo = P.front_off[j];
+                    tg.push_back(GSpec{fo + k1 + static_cast<int64_t>(k1) * f, fo + k1 + static_cast<int64_t>(k0) * f,
+                                       P.scr_off[j], f, f, m, m, nb, m});
+                    dg.push_back(GSpec{fo + k1 + static_cast<int64_t>(k0) * f, P.scr_off[j],
+                                       fo + k0 + static_cast<int64_t>(k0) * f, f, m, f, nb, nb, m});
                     copies.push_back(CopyItem{P.scr_off[j], fo + k1 + static_cast<int64_t>(k0) * f, m, f, m, nb});
                 }
+                emit_gemm(L, 0, T_AINV_T, OP_S, OP_N, BUF_FRONT, BUF_FRONT, BUF_SCR, 1.0, 0.0, false, tg, true);
+                emit_gemm(L, 0, T_AINV_D, OP_T, OP_N, BUF_FRONT, BUF_SCR, BUF_FRONT, 1.0, 1.0, true, dg, true);
+                emit_copy(L, 0, T_AINV_COPY, -1.0, copies);
             }
-            ld.count = static_cast<int64_t>(P.diag_items.size()) - ld.first;
-            if (ld.count > 0) {
-                P.flops_per_pole += ld.flops;
-                P.launches.push_back(ld);
+            // (iii) panel below the block scaled by its inverse, trailing update, store the panel
+            {
+                std::vector<GSpec> panel, update;
+                std::vector<CopyItem> copies;
+                for (int32_t j : nodesL) {
+                    const int32_t s = P.s[j], f = P.f[j];
+                    const int32_t K0 = T * Bo;
+                    if (K0 >= s) continue;
+                    const int32_t K1 = std::min(K0 + Bo, s);
+                    if (K1 >= s) continue;
+                    const int32_t m = s - K1, w = K1 - K0;
+                    const int64_t fo = P.front_off[j];
+                    panel.push_back(GSpec{fo + K1 + static_cast<int64_t>(K0) * f, fo + K0 + static_cast<int64_t>(K0) * f,
+                                          P.scr_off[j], f, f, m, m, w, w});
+                    update.push_back(GSpec{P.scr_off[j], fo + K1 + static_cast<int64_t>(K0) * f,
+                                           fo + K1 + static_cast<int64_t>(K1) * f, m, f, f, m, m, w});
+                    copies.push_back(CopyItem{P.scr_off[j], fo + K1 + static_cast<int64_t>(K0) * f, m, f, m, w});
+                }
+                emit_gemm(L, 0, T_OPANEL, OP_N, OP_S, BUF_FRONT, BUF_FRONT, BUF_SCR, 1.0, 0.0, false, panel);
+                emit_gemm(L, 0, T_OUPDATE, OP_N, OP_T, BUF_SCR, BUF_FRONT, BUF_FRONT, -1.0, 1.0, true, update);
+                emit_copy(L, 0, T_OPCOPY, 1.0, copies);
             }
-            emit_gemm(L, 0, T_PANEL, OP_N, OP_S, BUF_FRONT, BUF_FRONT, BUF_SCR, 1.0, 0.0, false, panel);
-            emit_gemm(L, 0, T_UPDATE, OP_N, OP_T, BUF_SCR, BUF_FRONT, BUF_FRONT, -1.0, 1.0, true, update);
-            emit_copy(L, 0, T_PCOPY, 1.0, copies);
         }
-        // F3: inverse of A_J from its block LDL^T (Eqs. 38-39 inside the block)
-        for (int32_t t = nbmax - 1; t >= 0; --t) {
+        // inverse of A_J assembled from the diagonal-block inverses, last block first
+        for (int32_t T = nob - 1; T >= 0; --T) {
             std::vector<GSpec> tg, dg;
             std::vector<CopyItem> copies;
             for (int32_t j : nodesL) {
                 const int32_t s = P.s[j], f = P.f[j];
-                const int32_t k0 = t * b;
-                if (k0 >= s) continue;
-                const int32_t nb = std::min(b, s - k0);
-                const int32_t k1 = k0 + nb;
-                if (k1 >= s) continue;
-                const int32_t m = s - k1;
+                const int32_t K0 = T * Bo;
+                if (K0 >= s) continue;
+                const int32_t K1 = std::min(K0 + Bo, s);
+                if (K1 >= s) continue;
+                const int32_t m = s - K1, w = K1 - K0;
                 const int64_t fo = P.front_off[j];
-                tg.push_back(GSpec{fo + k1 + static_cast<int64_t>(k1) * f, fo + k1 + static_cast<int64_t>(k0) * f,
-                                   P.scr_off[j], f, f, m, m, nb, m});
-                dg.push_back(GSpec{fo + k1 + static_cast<int64_t>(k0) * f, P.scr_off[j],
-                                   fo + k0 + static_cast<int64_t>(k0) * f, f, m, f, nb, nb, m});
-                copies.push_back(CopyItem{P.scr_off[j], fo + k1 + static_cast<int64_t>(k0) * f, m, f, m, nb});
+                tg.push_back(GSpec{fo + K1 + static_cast<int64_t>(K1) * f, fo + K1 + static_cast<int64_t>(K0) * f,
+                                   P.scr_off[j], f, f, m, m, w, m});
+                dg.push_back(GSpec{fo + K1 + static_cast<int64_t>(K0) * f, P.scr_off[j],
+                                   fo + K0 + static_cast<int64_t>(K0) * f, f, m, f, w, w, m});
+                copies.push_back(CopyItem{P.scr_off[j], fo + K1 + static_cast<int64_t>(K0) * f, m, f, m, w});
             }
-            emit_gemm(L, 0, T_AINV_T, OP_S, OP_N, BUF_FRONT, BUF_FRONT, BUF_SCR, 1.0, 0.0, false, tg);
-            emit_gemm(L, 0, T_AINV_D, OP_T, OP_N, BUF_FRONT, BUF_SCR, BUF_FRONT, 1.0, 1.0, true, dg);
-            emit_copy(L, 0, T_AINV_COPY, -1.0, copies);
+            emit_gemm(L, 0, T_OAINV_T, OP_S, OP_N, BUF_FRONT, BUF_FRONT, BUF_SCR, 1.0, 0.0, false, tg);
+            emit_gemm(L, 0, T_OAINV_D, OP_T, OP_N, BUF_FRONT, BUF_SCR, BUF_FRONT, 1.0, 1.0, true, dg);
+            emit_copy(L, 0, T_OAINV_COPY, -1.0, copies);
         }
         // F4-F6: L_RJ = B A_J^{-1}; Schur update of the separator front (Eq. 32); store L
         {
@@ -729,6 +795,7 @@ int merge_plans(std::vector<Plan>& parts, Plan& M, std::string& err) {
     M = Plan{};
     M.opt = parts[0].opt;
     M.block = parts[0].block;
+    M.outer = parts[0].outer;
     M.n_systems = static_cast<int32_t>(parts.size());
     M.sys_nnz_first.assign(parts.size() + 1, 0);
     M.sys_n_first.assign(parts.size() + 1, 0);

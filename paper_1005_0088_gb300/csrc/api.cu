@@ -212,10 +212,12 @@ void free_workspace(Workspace& W) {
 }
 
 const char* tag_name(int tag) {
-    static const char* const names[] = {"assemble", "scatter", "dinv", "panel", "update", "pcopy", "ainv_t",
-                                        "ainv_d", "ainv_copy", "lrj", "schur", "lcopy", "gather", "sel_t",
-                                        "sel_d", "sel_copy"};
-    return (tag >= 0 && tag < 16) ? names[tag] : "other";
+    static const char* const names[] = {"assemble", "scatter", "dinv",  "panel",    "update",  "pcopy",
+                                        "ainv_t",   "ainv_d",  "ainv_copy", "lrj",   "schur",   "lcopy",
+                                        "gather",   "sel_t",   "sel_d",   "sel_copy", "opanel",  "oupdate",
+                                        "opcopy",   "oainv_t", "oainv_d", "oainv_copy"};
+    constexpr int n = static_cast<int>(sizeof(names) / sizeof(names[0]));
+    return (tag >= 0 && tag < n) ? names[tag] : "other";
 }
 
 std::string family_of(const Launch& l) {
@@ -282,7 +284,7 @@ int run_phase(ndsi_plan* h, const Workspace& W, const SplitBuffers& SB, int phas
         const Launch& l = P.launches[li];
         if (l.phase != phase) continue;
         cudaError_t e;
-        if (split && l.kind == L_GEMM) {
+        if (split && split_eligible(l)) {
             const int si = h->SP.steps.empty() ? 0 : h->SP.step_of_launch[li];
             const SplitStep& step = h->SP.steps[si];
             const double2* bufs[2] = {W.fronts, W.scr};
@@ -408,6 +410,7 @@ void ndsi_default_options(ndsi_options* opt) {
     opt->block = 32;
     opt->m0_radius = 1e7;
     opt->max_workspace_bytes = 0;
+    opt->outer_block = 128;
 }
 
 int ndsi_poles(int32_t M, double* z_out, double* R_out) {
@@ -455,7 +458,7 @@ int ndsi_analyze(const ndsi_pattern* pat, int32_t n_atoms, const double* centers
         int k = 0;
         for (size_t li = 0; li < h->P.launches.size(); ++li) {
             const Launch& l = h->P.launches[li];
-            if (l.kind != L_GEMM) continue;
+            if (!split_eligible(l)) continue;
             const SplitStep& st = S.steps[k];
             S.tensor_flops.push_back(split_executed_flops(h->P, st, S.items, S.tiles, l, o.split_slices));
             double sb = 0;
@@ -506,7 +509,7 @@ int ndsi_analyze_batched(int32_t n_systems, const ndsi_pattern* pats, const int3
             int k = 0;
             for (size_t li = 0; li < h->P.launches.size(); ++li) {
                 const Launch& l = h->P.launches[li];
-                if (l.kind != L_GEMM) continue;
+                if (!split_eligible(l)) continue;
                 const SplitStep& st = S.steps[k];
                 S.tensor_flops.push_back(split_executed_flops(h->P, st, S.items, S.tiles, l, o.split_slices));
                 double sb = 0;

@@ -76,6 +76,7 @@ struct Launch {
     int64_t first, count;    // range in the item array of this kind
     int64_t tfirst, tcount;  // GEMM tiles range
     int32_t tile;            // FP64 GEMM output tile edge of this launch (16 or 32)
+    int32_t exact;           // 1: FP64 CUDA-core GEMM in every precision mode (diagonal blocks)
     int32_t phase;           // 0 factor, 1 selinv
     int32_t tag;             // which formula the step implements (for profiling names)
     double flops;            // algorithmic real flops per pole of this launch
@@ -85,8 +86,12 @@ struct Launch {
 // Tags of the schedule steps.
 enum StepTag : int32_t {
     T_ASSEMBLE = 0, T_SCATTER, T_DINV, T_PANEL, T_UPDATE, T_PCOPY, T_AINV_T, T_AINV_D,
-    T_AINV_COPY, T_LRJ, T_SCHUR, T_LCOPY, T_GATHER, T_SEL_T, T_SEL_D, T_SEL_COPY
+    T_AINV_COPY, T_LRJ, T_SCHUR, T_LCOPY, T_GATHER, T_SEL_T, T_SEL_D, T_SEL_COPY,
+    T_OPANEL, T_OUPDATE, T_OPCOPY, T_OAINV_T, T_OAINV_D, T_OAINV_COPY
 };
+
+// GEMM launches that split mode runs on the tensor cores.
+inline bool split_eligible(const Launch& l) { return l.kind == L_GEMM && !l.exact; }
 
 struct Plan {
     // input structure
@@ -132,6 +137,7 @@ struct Plan {
     std::vector<Launch> launches;
     double flops_per_pole = 0, bytes_per_pole = 0;
     int32_t block = 32;
+    int32_t outer = 128;   // diagonal-block size of the two-level factorisation of A_J
     std::vector<std::vector<int64_t>> level_entries;  // CSR entries scattered per level
     // systems of a batched plan (one for a plain plan)
     int32_t n_systems = 1;

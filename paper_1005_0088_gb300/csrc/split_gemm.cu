@@ -40,7 +40,7 @@ void build_split_schedule(const Plan& P, int slices, std::vector<SplitItem>& ite
     tiles.clear();
     blocks.clear();
     for (const Launch& l : P.launches) {
-        if (l.kind != L_GEMM) continue;
+        if (!split_eligible(l)) continue;
         SplitStep st{};
         int32_t kmax = 0;
         st.tfirst = static_cast<int64_t>(tiles.size());

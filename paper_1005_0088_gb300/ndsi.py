@@ -53,7 +53,8 @@ class ndsi_pattern(ctypes.Structure):
 class ndsi_options(ctypes.Structure):
     _fields_ = [("leaf_atoms", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("split_slices", ctypes.c_int32), ("block", ctypes.c_int32),
-                ("m0_radius", ctypes.c_double), ("max_workspace_bytes", ctypes.c_int64)]
+                ("m0_radius", ctypes.c_double), ("max_workspace_bytes", ctypes.c_int64),
+                ("outer_block", ctypes.c_int32)]
 
 
 class ndsi_plan_summary(ctypes.Structure):

@@ -119,6 +119,33 @@ def test_invalid_patterns_rejected():
         nd.ndsi_poles(0)
 
 
+def test_invalid_options_rejected():
+    nd = lib()
+    sysm = lattice_system((4, 4, 1), 2, "2d", 3)
+    for opts in (dict(block=24), dict(outer_block=48), dict(outer_block=40, block=16),
+                 dict(precision=1, split_slices=3)):
+        with pytest.raises(nd.NdsiError) as ei:
+            nd.analyze_system(sysm, **opts)
+        assert ei.value.code == nd.ndsi.NDSI_ERR_INVALID
+
+
+def test_two_level_schedule():
+    # diagonal blocks of outer_block columns: exactly ceil(s / outer) - 1 outer panel steps for
+    # the widest node of a level, and the pivot-level GEMMs never leave the diagonal blocks
+    nd = lib()
+    sysm = lattice_system((6, 6, 5), 3, "3d", 5)
+    for outer in (32, 64, 128):
+        p = nd.analyze_system(sysm, leaf_atoms=12, outer_block=outer)
+        sch = nd.ndsi_plan_export(p, "schedule")
+        na = nd.ndsi_plan_export(p, "node_atoms")
+        lv = nd.ndsi_plan_export(p, "level")
+        s = np.diff(na) * 3
+        for L in range(lv.max() + 1):
+            smax = s[lv == L].max()
+            n_outer = sum(1 for k, l, t, c in sch if k == 3 and l == L and t == 16)  # opanel
+            assert n_outer == -(-smax // outer) - 1, (outer, L, smax, n_outer)
+
+
 def test_batched_plan_merges_levels():
     # Three uneven systems in one plan: one schedule, levels aligned, fewer launches than
     # the three plans run one after another.

@@ -112,6 +112,20 @@ def test_pivot_block_sizes(block):
     assert np.max(np.abs(g - ref)) < 1e-11 * np.max(np.abs(ref))
 
 
+@pytest.mark.parametrize("block,outer", [(32, 32), (16, 48), (32, 64), (16, 128)])
+def test_outer_block_sizes(block, outer):
+    # two-level factorisation of A_J: diagonal blocks of `outer` columns factored and inverted in
+    # pivot blocks of `block`, outer panel / trailing update / inverse assembly between them;
+    # the separators here (up to 108 columns) span several outer blocks
+    sysm = lattice_system((6, 6, 5), 3, "3d", 5)
+    Hd, Sd = sysm.dense()
+    Z = [-0.2 + 0.05j, 0.3 + 1.5j]
+    g = _selinv(sysm, Z, leaf_atoms=12, block=block, outer_block=outer)
+    for q, z in enumerate(Z):
+        ref = on_pattern(green_dense(Hd, Sd, z), sysm)
+        assert np.max(np.abs(g[q] - ref)) < 1e-11 * np.max(np.abs(ref))
+
+
 def _rho_check(sysm, kT, M, leaf=20, host=False):
     Hd, Sd = sysm.dense()
     eps, C = generalized_eig(Hd, Sd)

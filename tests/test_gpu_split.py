@@ -32,6 +32,20 @@ def test_split_selected_inverse_matches_dense(shape, o, nb, leaf):
         assert rel < 1e-9
 
 
+@pytest.mark.parametrize("outer", [32, 64])
+def test_split_outer_blocks(outer):
+    # outer panel, trailing update and inverse-assembly GEMMs on the tensor cores between FP64
+    # diagonal blocks of `outer` columns
+    sysm = lattice_system((6, 6, 5), 3, "3d", 5)
+    Hd, Sd = sysm.dense()
+    Z = [-0.2 + 0.05j, 0.3 + 1.5j]
+    g = _selinv(sysm, Z, leaf_atoms=12, outer_block=outer, precision=lib().NDSI_PREC_SPLIT)
+    for q, z in enumerate(Z):
+        ref = on_pattern(green_dense(Hd, Sd, z), sysm)
+        rel = np.max(np.abs(g[q] - ref)) / np.max(np.abs(ref))
+        assert rel < 1e-9
+
+
 def _rho_split(sysm, kT, M, leaf=20, slices=6):
     Hd, Sd = sysm.dense()
     eps, C = generalized_eig(Hd, Sd)
