@@ -218,7 +218,14 @@ __device__ __forceinline__ void ff_add(float& hi, float& lo, float v) {
 // the scarce unit): both floats become signed integer mantissas at a common exponent, their
 // exact sum (an int64) is rounded to 53 bits and packed with the combined exponent.  Out of the
 // normal double range it falls back to FP64 arithmetic.
-__device__ __forceinline__ double ff_to_double_scaled(float hi, float lo, int e) {
+// Out-of-range results (never produced by finite fronts in practice) take the FP64 route in a
+// separate function so that the common path carries no FP64 instructions, even predicated ones.
+__device__ __noinline__ double ff_to_double_slow(float hi, float lo, int e, bool negate) {
+    const double v = ldexp(static_cast<double>(hi) + static_cast<double>(lo), e);
+    return negate ? -v : v;
+}
+
+__device__ __forceinline__ double ff_to_double_scaled(float hi, float lo, int e, bool negate = false) {
     const uint32_t bh = __float_as_uint(hi), bl = __float_as_uint(lo);
     const int eh = static_cast<int>((bh >> 23) & 0xFF), el = static_cast<int>((bl >> 23) & 0xFF);
     int64_t mh = eh ? static_cast<int64_t>((bh & 0x7FFFFFu) | 0x800000u) : 0;
@@ -252,8 +259,8 @@ __device__ __forceinline__ double ff_to_double_scaled(float hi, float lo, int e)
             E0 = ebig - 150 - 38;
         }
     }
-    const bool neg = S < 0;
-    uint64_t u = static_cast<uint64_t>(neg ? -S : S);
+    const bool neg = (S < 0) != negate;
+    uint64_t u = static_cast<uint64_t>(S < 0 ? -S : S);
     if (u == 0) return 0.0;
     const int nbits = 64 - __clzll(static_cast<long long>(u));
     int exp2;
@@ -274,10 +281,7 @@ __device__ __forceinline__ double ff_to_double_scaled(float hi, float lo, int e)
         exp2 = E0 + e - (53 - nbits) + 52;
     }
     const int biased = exp2 + 1023;
-    if (biased <= 0 || biased >= 2047) {
-        const double v = static_cast<double>(hi) + static_cast<double>(lo);
-        return ldexp(v, e);
-    }
+    if (biased <= 0 || biased >= 2047) return ff_to_double_slow(hi, lo, e, negate);
     const uint64_t bits = (static_cast<uint64_t>(neg) << 63) | (static_cast<uint64_t>(biased) << 52) |
                           (mant & ((uint64_t(1) << 52) - 1));
     return __longlong_as_double(static_cast<long long>(bits));
@@ -519,7 +523,7 @@ struct GemmArgs {
     const int32_t* expB;
     double2* C;
     int64_t sC;
-    double alpha, beta;
+    int neg_alpha, add_c;  // alpha = -1 / +1; beta = 1 / 0
     int lower;
     int* status;
 };
@@ -530,7 +534,9 @@ constexpr int kEpiWarps = 16;
 
 template <int S>
 constexpr int split_smem_bytes() {
-    return 2 * 2 * S * kTileBytes + 128 + 1024;
+    // pipeline tiles, then barriers (128 B) and the tile's row / column exponents (768 B), plus
+    // up to 1 KB lost to aligning the tiles to 1024 bytes
+    return 2 * 2 * S * kTileBytes + 128 + 768 + 1024;
 }
 
 template <int S>
@@ -546,6 +552,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     uint64_t* mma_done = bars + 6;
     uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(bars + 8);
     volatile int* abort = reinterpret_cast<volatile int*>(bars + 9);
+    int* sm_ea = reinterpret_cast<int*>(bars + 16);  // [128] exponents of the tile's rows
+    int* sm_eb = sm_ea + 128;                         // [64] exponents of its complex columns
 
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
     const int64_t pole = blockIdx.y;
@@ -658,6 +666,32 @@ __global__ void __launch_bounds__(kThreads, 1)
         // columns 32cg..32cg+31 (cg 0,1: Re C; cg 2,3: Im C of the same 64 complex columns)
         const int q = warp & 3;
         const int cg = (warp - 2) >> 2;
+        const int et = threadIdx.x - 64;
+        {
+            // while the main loop runs: the tile's scale exponents into shared memory, and the C
+            // block the final update reads pulled towards L2
+            const GemmTile tile = p.tiles[p.tfirst + blockIdx.x];
+            const GemmItem it = p.items[p.ifirst + tile.item];
+            const SplitItem si = p.sitems[p.ifirst + tile.item];
+            if (et < 128) {
+                const int m = tile.m0 + et;
+                sm_ea[et] = m < it.M ? p.expA[pole * p.erowsA + si.erowA + m] : 0;
+            } else if (et < 192) {
+                const int n = tile.n0 + et - 128;
+                sm_eb[et - 128] = n < it.N ? p.expB[pole * p.erowsB + si.erowB + n] : 0;
+            }
+            if (p.add_c) {
+                const double2* Cp = p.C + pole * p.sC + it.c_off;
+#pragma unroll
+                for (int u = 0; u < 2; ++u) {
+                    const int line = et + u * kEpiWarps * 32;  // 64 columns x 16 lines of 128 B
+                    const int j = line >> 4, r = (line & 15) * 8;
+                    const int m = tile.m0 + r, n = tile.n0 + j;
+                    if (m < it.M && n < it.N && !(p.lower && n > tile.m0 + 127))
+                        asm volatile("prefetch.global.L2 [%0];" ::"l"(Cp + m + static_cast<int64_t>(n) * it.ldc));
+                }
+            }
+        }
         float hi[32], lo[32];
 #pragma unroll
         for (int j = 0; j < 32; ++j) {
@@ -704,37 +738,40 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (ok && !*abort) {
             const GemmTile tile = p.tiles[p.tfirst + blockIdx.x];
             const GemmItem it = p.items[p.ifirst + tile.item];
-            const SplitItem si = p.sitems[p.ifirst + tile.item];
-            const int et = threadIdx.x - 64;
             double2* Cp = p.C + pole * p.sC + it.c_off;
-            for (int idx = et; idx < 128 * 64; idx += kEpiWarps * 32) {
-                const int r = idx % 128, j = idx / 128;
-                const int m = tile.m0 + r, n = tile.n0 + j;
-                if (m >= it.M || n >= it.N || (p.lower && n > m)) continue;
-                const int e = p.expA[pole * p.erowsA + si.erowA + m] + p.expB[pole * p.erowsB + si.erowB + n] - 14;
-                double re = ff_to_double_scaled(sm_hi[j * 128 + r], sm_lo[j * 128 + r], e);
-                double im = ff_to_double_scaled(sm_hi[(64 + j) * 128 + r], sm_lo[(64 + j) * 128 + r], e);
-                if (p.alpha != 1.0) {
-                    if (p.alpha == -1.0) {
-                        re = -re;
-                        im = -im;
-                    } else {
-                        re *= p.alpha;
-                        im *= p.alpha;
-                    }
+            // four outputs per thread per round: their C loads are in flight together.  alpha is
+            // +-1 and beta 0 or 1 (checked at launch): the sign is applied to the integer result,
+            // and beta = 1 costs the only FP64 instructions of the epilogue.
+            const bool neg_alpha = p.neg_alpha != 0, add_c = p.add_c != 0;
+            constexpr int kRound = 4, kStride = kEpiWarps * 32;
+#pragma unroll 1
+            for (int base = et; base < 128 * 64; base += kRound * kStride) {
+                double2 old[kRound];
+                bool live[kRound];
+#pragma unroll
+                for (int u = 0; u < kRound; ++u) {
+                    const int idx = base + u * kStride;
+                    const int r = idx % 128, j = idx / 128;
+                    const int m = tile.m0 + r, n = tile.n0 + j;
+                    live[u] = idx < 128 * 64 && m < it.M && n < it.N && !(p.lower && n > m);
+                    old[u] = make_double2(0.0, 0.0);
+                    if (live[u] && add_c) old[u] = Cp[m + static_cast<int64_t>(n) * it.ldc];
                 }
-                double2* dst = Cp + m + static_cast<int64_t>(n) * it.ldc;
-                if (p.beta != 0.0) {
-                    const double2 old = *dst;
-                    if (p.beta == 1.0) {
-                        re += old.x;
-                        im += old.y;
-                    } else {
-                        re = fma(p.beta, old.x, re);
-                        im = fma(p.beta, old.y, im);
+#pragma unroll
+                for (int u = 0; u < kRound; ++u) {
+                    if (!live[u]) continue;
+                    const int idx = base + u * kStride;
+                    const int r = idx % 128, j = idx / 128;
+                    const int m = tile.m0 + r, n = tile.n0 + j;
+                    const int e = sm_ea[r] + sm_eb[j] - 14;
+                    double re = ff_to_double_scaled(sm_hi[j * 128 + r], sm_lo[j * 128 + r], e, neg_alpha);
+                    double im = ff_to_double_scaled(sm_hi[(64 + j) * 128 + r], sm_lo[(64 + j) * 128 + r], e, neg_alpha);
+                    if (add_c) {
+                        re += old[u].x;
+                        im += old[u].y;
                     }
+                    Cp[m + static_cast<int64_t>(n) * it.ldc] = make_double2(re, im);
                 }
-                *dst = make_double2(re, im);
             }
         }
     }
@@ -847,8 +884,10 @@ static cudaError_t run_mma(const Launch& l, int step_index, const GemmItem* item
                            const SplitItem* sitems_dev, const GemmTile* stiles_dev, const SplitStep& step,
                            const SplitBuffers& B, double2* Cbuf, int64_t sC, int np, int* status,
                            cudaStream_t st) {
+    if ((l.alpha != 1.0 && l.alpha != -1.0) || (l.beta != 0.0 && l.beta != 1.0)) return cudaErrorInvalidValue;
     GemmArgs ga{items_dev, sitems_dev, stiles_dev, step.tfirst, l.first, step.rowsA, step.rowsB,
-                step.erowsA, step.erowsB, B.expA, B.expB, Cbuf, sC, l.alpha, l.beta, l.lower, status};
+                step.erowsA, step.erowsB, B.expA, B.expB, Cbuf, sC, l.alpha < 0 ? 1 : 0, l.beta != 0.0 ? 1 : 0,
+                l.lower, status};
     k_gemm_split<S><<<dim3(static_cast<unsigned>(step.tcount), np), kThreads, split_smem_bytes<S>(), st>>>(
         B.tmA[step_index], B.tmB[step_index], ga);
     return cudaGetLastError();
