@@ -197,6 +197,14 @@ def _roofline(prof, steps, peaks):
     return r, kern
 
 
+def _autotune(nd, args, plan, H, S, kT, M):
+    """Per-step tensor-core / FP64 choice of a split plan, made once before any timing."""
+    if args.no_autotune:
+        return None
+    n_split, n_fp64 = nd.ndsi_autotune(plan, H, S, MU, kT, M)
+    return {"tensor_core_steps": n_split, "fp64_steps": n_fp64}
+
+
 def _measure(nd, torch, plan, H, S, rho, ne, kT, M, steps, warmup, stream, flush, clocks=None):
     """Time `steps` density sweeps as the library runs them (one captured CUDA graph per sweep),
     then repeat them with direct launches and per-launch CUDA events for the kernel breakdown."""
@@ -251,11 +259,12 @@ def run_ndsi(args):
     kT, M = system.meta["kT"], system.meta["poles"]
     if args.poles:
         M = args.poles
-    plan = nd.analyze_system(system, precision=prec_code[args.precision])
+    plan = nd.analyze_system(system, precision=prec_code[args.precision], split_slices=args.slices)
     info = nd.ndsi_plan_info(plan)
     dev = torch.device("cuda", local)
     H = torch.as_tensor(system.H, device=dev)
     S = torch.as_tensor(system.S, device=dev)
+    tune = _autotune(nd, args, plan, H, S, kT, M)
     rho = torch.zeros(system.nnz, dtype=torch.float64, device=dev)
     ne = torch.zeros(1, dtype=torch.float64, device=dev)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > L2
@@ -299,7 +308,8 @@ def run_ndsi(args):
     other = None
     if not args.no_other and rank == 0:
         oprec = "split" if args.precision == "fp64" else "fp64"
-        plan2 = nd.analyze_system(system, precision=prec_code[oprec])
+        plan2 = nd.analyze_system(system, precision=prec_code[oprec], split_slices=args.slices)
+        tune2 = _autotune(nd, args, plan2, H, S, kT, M)
         rho2 = torch.zeros_like(rho)
         ne2 = torch.zeros_like(ne)
         t2, prof2, _ = _measure(nd, torch, plan2, H, S, rho2, ne2, kT, M, args.steps, args.warmup,
@@ -308,7 +318,7 @@ def run_ndsi(args):
         ms_split, ms_fp64 = (ms2, ms_step) if oprec == "split" else (ms_step, ms2)
         rl2, k2 = _roofline(prof2, args.steps, _peaks())
         other = {"precision": oprec, "ms_per_step": ms2, "value": M * system.n / (ms2 * 1e-3),
-                 "split_speedup_vs_fp64": ms_fp64 / ms_split,
+                 "split_speedup_vs_fp64": ms_fp64 / ms_split, "autotune": tune2,
                  "max_abs_rho_diff_vs_headline": float(np.max(np.abs(rho2.cpu().numpy() - rho_main))),
                  "roofline": rl2,
                  "kernels": {k: {"launches": v["launches"] // args.steps, "ms_per_step": v["ms"] / args.steps}
@@ -343,17 +353,18 @@ def run_ndsi(args):
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": ms_step,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f64" if args.precision == "fp64" else "bf16x6->f64",
+            "dtype": "f64" if args.precision == "fp64" else f"bf16x{args.slices}->f64",
             "data": "synthetic",
             "config": {"workload": system.meta["label"] + f", {M} poles, {args.precision} path",
                        "n": system.n, "poles": M, "kT": kT, "mu": MU, "nnz": system.nnz,
-                       "precision": args.precision,
+                       "precision": args.precision, "split_slices": args.slices,
                        "l2": "flushed (256 MB write) before every timed step",
                        "flops_per_pole": info["flops_per_pole"], "parallelism": f"replicas x{world}"},
             "e2e": {"value": world * M * system.n / e2e_s, "unit": UNIT,
                     "h2d_bytes_per_step": 2 * 8 * system.nnz,
                     "d2h_bytes_per_step": 8 * system.nnz + 8},
             "gpu_launches": launches,
+            "autotune": tune,
             "graph": {"kernel_nodes": graph_nodes,
                       "ms_per_step_direct_launches": sum(prof_times) / len(prof_times),
                       "note": "timed steps replay one captured CUDA graph per sweep; the kernel "
@@ -380,7 +391,7 @@ def run_batched(args, nd, torch, dist, rank, world, local, prec_code):
     systems = batched_systems()
     M = args.poles or 120
     kT = 0.01
-    plan = nd.analyze_batched(systems, precision=prec_code[args.precision])
+    plan = nd.analyze_batched(systems, precision=prec_code[args.precision], split_slices=args.slices)
     info = nd.ndsi_plan_info(plan)
     dev = torch.device("cuda", local)
     H = torch.as_tensor(np.concatenate([s.H for s in systems]), device=dev)
@@ -424,7 +435,7 @@ def run_batched(args, nd, torch, dist, rank, world, local, prec_code):
     line = {"metric": METRIC, "value": world * M * ntot / (ms * 1e-3), "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f64" if args.precision == "fp64" else "bf16x6->f64", "data": "synthetic",
+            "dtype": "f64" if args.precision == "fp64" else f"bf16x{args.slices}->f64", "data": "synthetic",
             "config": {"workload": f"batched: {M} poles x {len(systems)} uneven systems "
                                    f"(N {min(s.n for s in systems)}..{max(s.n for s in systems)}), "
                                    f"{args.precision} path, one launch per tree level",
@@ -455,6 +466,10 @@ def main():
     ap.add_argument("--precision", default="fp64", choices=["fp64", "split"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-parity", action="store_true", help="skip the sampled-column check")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep every eligible GEMM of a split plan on the tensor cores")
+    ap.add_argument("--slices", type=int, default=6,
+                    help="BF16 slices per operand of the split path (4-7)")
     ap.add_argument("--poles", type=int, default=0,
                     help="override the workload's pole count (small profiling runs only)")
     ap.add_argument("--no-other", action="store_true",

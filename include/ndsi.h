@@ -198,6 +198,19 @@ typedef struct {
 
 int ndsi_profile_enable(ndsi_plan* plan, int32_t enable);
 
+/* Autotuner for split-precision plans: times every GEMM step of one density sweep at (mu, kT,
+ * n_poles) on H, S (device or host) both on the tensor cores (slicing + emulated-FP64 GEMM) and
+ * on the FP64 CUDA cores, with CUDA events per launch after an untimed warm-up of each, and keeps
+ * the faster path per step for all later calls on the plan.  Both paths meet the split-mode
+ * tolerance, so only speed changes.  Small steps (few tiles, short inner dimension) usually go
+ * to the CUDA cores, separator-sized ones to the tensor cores.  Counts of the steps left on each
+ * path in *n_split_out / *n_fp64_out (either may be NULL).  Runs four sweeps; the profiler
+ * counters are unchanged and any captured graph is dropped.  FP64 plans: no-op (all steps
+ * counted as FP64).  Errors: NDSI_ERR_INVALID for bad arguments or a batched plan; as
+ * ndsi_density otherwise. */
+int ndsi_autotune(ndsi_plan* plan, const double* H, const double* S, double mu, double kT, int32_t n_poles,
+                  int32_t* n_split_out, int32_t* n_fp64_out, void* stream);
+
 /* CUDA graphs.  While enabled (the default) and profiling is off, ndsi_density,
  * ndsi_density_batched and ndsi_find_mu run each density sweep (all chunks of points: assembly,
  * factorisation, selected inversion, residue sum and electron counts) as one CUDA graph,

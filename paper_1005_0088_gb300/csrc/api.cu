@@ -25,9 +25,12 @@ struct ProfRec {
     int key;
     double flops, bytes, tensor_flops;
     cudaEvent_t e0, e1;
+    int64_t launch;  // schedule launch index, or -1
 };
 struct Profiler {
     bool on = false;
+    int64_t cur_launch = -1;                // schedule launch being issued (run_phase)
+    std::vector<double>* per_launch = nullptr;  // when set: ms accumulated per launch index
     std::vector<cudaEvent_t> pool;
     size_t used = 0;
     std::vector<ProfRec> pending;
@@ -51,6 +54,7 @@ struct SplitPlan {
     std::vector<int32_t> step_of_launch;
     std::vector<double> tensor_flops;   // per step, one pole
     std::vector<double> slice_bytes;    // per step, one pole: FP64 operand reads + BF16 slice writes
+    std::vector<char> use_split;        // per launch: 1 = tensor-core path (autotuner may clear)
     SplitItem* d_items = nullptr;
     GemmTile* d_tiles = nullptr;
     SliceBlock* d_blocks = nullptr;
@@ -253,7 +257,7 @@ cudaError_t timed(Profiler& pf, const std::string& family, double flops, double 
     if (e0) cudaEventRecord(e0, st);
     cudaError_t e = fn();
     if (e1) cudaEventRecord(e1, st);
-    if (e0 && e1) pf.pending.push_back(ProfRec{pf.key(family), flops, bytes, tensor_flops, e0, e1});
+    if (e0 && e1) pf.pending.push_back(ProfRec{pf.key(family), flops, bytes, tensor_flops, e0, e1, pf.cur_launch});
     return e;
 }
 
@@ -268,6 +272,8 @@ void prof_resolve(Profiler& pf) {
             st.bytes += r.bytes;
             st.tensor_flops += r.tensor_flops;
             st.launches += 1;
+            if (pf.per_launch && r.launch >= 0 && r.launch < static_cast<int64_t>(pf.per_launch->size()))
+                (*pf.per_launch)[r.launch] += ms;
         } else {
             cudaGetLastError();
         }
@@ -284,7 +290,8 @@ int run_phase(ndsi_plan* h, const Workspace& W, const SplitBuffers& SB, int phas
         const Launch& l = P.launches[li];
         if (l.phase != phase) continue;
         cudaError_t e;
-        if (split && split_eligible(l)) {
+        h->prof.cur_launch = static_cast<int64_t>(li);
+        if (split && split_eligible(l) && h->SP.use_split[li]) {
             const int si = h->SP.steps.empty() ? 0 : h->SP.step_of_launch[li];
             const SplitStep& step = h->SP.steps[si];
             const double2* bufs[2] = {W.fronts, W.scr};
@@ -394,6 +401,29 @@ int64_t workspace_cap(const ndsi_plan* h) {
 namespace ndsi {
 int density_impl(ndsi_plan* h, const double* Hd, const double* Sd, const double* mu, const double* kT,
                  int32_t n_poles, double* rho_d, double* ne_d, cudaStream_t st);
+
+// Split-precision metadata of a plan: tensor-core steps, their tile lists and cost figures.
+void setup_split(ndsi_plan* h, const ndsi_options& o) {
+    SplitPlan& S = h->SP;
+    build_split_schedule(h->P, o.split_slices, S.items, S.steps, S.tiles, S.blocks);
+    S.step_of_launch.assign(h->P.launches.size(), -1);
+    S.use_split.assign(h->P.launches.size(), 1);
+    int k = 0;
+    for (size_t li = 0; li < h->P.launches.size(); ++li) {
+        const Launch& l = h->P.launches[li];
+        if (!split_eligible(l)) continue;
+        const SplitStep& st = S.steps[k];
+        S.tensor_flops.push_back(split_executed_flops(h->P, st, S.items, S.tiles, l, o.split_slices));
+        double sb = 0;
+        for (int64_t i = 0; i < l.count; ++i) {
+            const GemmItem& g = h->P.gemm_items[l.first + i];
+            sb += 2.0 * 16.0 * (static_cast<double>(g.M) * g.K + static_cast<double>(g.N) * g.K);
+        }
+        sb += 2.0 * (static_cast<double>(st.rowsA) + st.rowsB) * st.Kcols;
+        S.slice_bytes.push_back(sb);
+        S.step_of_launch[li] = k++;
+    }
+}
 int sweep(ndsi_plan* h, const double* Hd, const double* Sd, int32_t nq, int32_t chunk,
           const std::vector<int>& part_off, double* rho_d, double* ne_d, cudaStream_t st);
 }  // namespace ndsi
@@ -452,24 +482,7 @@ int ndsi_analyze(const ndsi_pattern* pat, int32_t n_atoms, const double* centers
             delete h;
             return fail(NDSI_ERR_INVALID, "ndsi_analyze: split_slices must be in [4, 7]");
         }
-        SplitPlan& S = h->SP;
-        build_split_schedule(h->P, o.split_slices, S.items, S.steps, S.tiles, S.blocks);
-        S.step_of_launch.assign(h->P.launches.size(), -1);
-        int k = 0;
-        for (size_t li = 0; li < h->P.launches.size(); ++li) {
-            const Launch& l = h->P.launches[li];
-            if (!split_eligible(l)) continue;
-            const SplitStep& st = S.steps[k];
-            S.tensor_flops.push_back(split_executed_flops(h->P, st, S.items, S.tiles, l, o.split_slices));
-            double sb = 0;
-            for (int64_t i = 0; i < l.count; ++i) {
-                const GemmItem& g = h->P.gemm_items[l.first + i];
-                sb += 2.0 * 16.0 * (static_cast<double>(g.M) * g.K + static_cast<double>(g.N) * g.K);
-            }
-            sb += 2.0 * (static_cast<double>(st.rowsA) + st.rowsB) * st.Kcols;
-            S.slice_bytes.push_back(sb);
-            S.step_of_launch[li] = k++;
-        }
+        setup_split(h, o);
     }
     *plan_out = h;
     return NDSI_OK;
@@ -503,24 +516,7 @@ int ndsi_analyze_batched(int32_t n_systems, const ndsi_pattern* pats, const int3
                 delete h;
                 return fail(NDSI_ERR_INVALID, "ndsi_analyze_batched: split_slices must be in [4, 7]");
             }
-            SplitPlan& S = h->SP;
-            build_split_schedule(h->P, o.split_slices, S.items, S.steps, S.tiles, S.blocks);
-            S.step_of_launch.assign(h->P.launches.size(), -1);
-            int k = 0;
-            for (size_t li = 0; li < h->P.launches.size(); ++li) {
-                const Launch& l = h->P.launches[li];
-                if (!split_eligible(l)) continue;
-                const SplitStep& st = S.steps[k];
-                S.tensor_flops.push_back(split_executed_flops(h->P, st, S.items, S.tiles, l, o.split_slices));
-                double sb = 0;
-                for (int64_t i = 0; i < l.count; ++i) {
-                    const GemmItem& g = h->P.gemm_items[l.first + i];
-                    sb += 2.0 * 16.0 * (static_cast<double>(g.M) * g.K + static_cast<double>(g.N) * g.K);
-                }
-                sb += 2.0 * (static_cast<double>(st.rowsA) + st.rowsB) * st.Kcols;
-                S.slice_bytes.push_back(sb);
-                S.step_of_launch[li] = k++;
-            }
+            setup_split(h, o);
         }
         *plan_out = h;
     } catch (const std::bad_alloc&) {
@@ -1108,6 +1104,68 @@ void ndsi_plan_destroy(ndsi_plan* h) {
     if (h->graph) cudaGraphExecDestroy(h->graph);
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
     delete h;
+}
+
+int ndsi_autotune(ndsi_plan* h, const double* H, const double* S, double mu, double kT, int32_t n_poles,
+                  int32_t* n_split_out, int32_t* n_fp64_out, void* stream) {
+    if (!h || !H || !S || n_poles < 1 || !(kT > 0) || !std::isfinite(mu) || h->P.n_systems != 1)
+        return fail(NDSI_ERR_INVALID, "ndsi_autotune: invalid argument");
+    const size_t nl = h->P.launches.size();
+    auto report = [&]() {
+        int32_t ns = 0, nf = 0;
+        for (size_t li = 0; li < nl; ++li) {
+            if (!split_eligible(h->P.launches[li])) continue;
+            if (h->P.opt.precision == NDSI_PREC_SPLIT && h->SP.use_split[li]) ++ns;
+            else ++nf;
+        }
+        if (n_split_out) *n_split_out = ns;
+        if (n_fp64_out) *n_fp64_out = nf;
+    };
+    if (h->P.opt.precision != NDSI_PREC_SPLIT) {
+        report();
+        return NDSI_OK;
+    }
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    int rc = upload_tables(h);
+    if (rc) return rc;
+    const double *Hd, *Sd;
+    rc = device_inputs(h, H, S, &Hd, &Sd, st);
+    if (rc) return rc;
+    rc = ensure_stage(h, 3 * h->P.nnz + 8);
+    if (rc) return rc;
+    double* rho_d = h->stage + 2 * h->P.nnz;
+    double* ne_d = h->stage + 3 * h->P.nnz;
+    // Per-launch event timing of one sweep with every eligible GEMM on the tensor cores and one
+    // with every eligible GEMM on the FP64 CUDA cores (each after an untimed warm-up sweep); each
+    // launch then keeps the faster of the two.  Both choices meet the split tolerance, so the
+    // result only changes speed.  The profiler's own counters are left as they were.
+    Profiler saved = h->prof;
+    h->prof.pending.clear();
+    h->prof.used = 0;
+    h->prof.on = true;
+    std::vector<double> t_split(nl, 0.0), t_fp64(nl, 0.0);
+    for (int pass = 0; pass < 4 && !rc; ++pass) {
+        const bool on_tensor = (pass % 2) == 0;
+        std::fill(h->SP.use_split.begin(), h->SP.use_split.end(), on_tensor ? 1 : 0);
+        h->prof.per_launch = pass < 2 ? nullptr : (on_tensor ? &t_split : &t_fp64);
+        rc = density_impl(h, Hd, Sd, &mu, &kT, n_poles, rho_d, ne_d, st);
+    }
+    h->prof.per_launch = nullptr;
+    for (size_t li = 0; li < nl; ++li)
+        h->SP.use_split[li] = !rc && split_eligible(h->P.launches[li]) ? (t_split[li] <= t_fp64[li] ? 1 : 0) : 1;
+    saved.pool = h->prof.pool;  // events created meanwhile stay owned by the plan
+    h->prof = saved;
+    h->prof.pending.clear();
+    h->prof.used = 0;
+    if (h->graph) {
+        cudaGraphExecDestroy(h->graph);
+        h->graph = nullptr;
+        h->graph_key.clear();
+        h->graph_nodes = 0;
+    }
+    if (rc) return rc;
+    report();
+    return NDSI_OK;
 }
 
 int ndsi_graph_enable(ndsi_plan* h, int32_t enable) {

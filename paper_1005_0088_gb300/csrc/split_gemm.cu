@@ -69,13 +69,13 @@ void build_split_schedule(const Plan& P, int slices, std::vector<SplitItem>& ite
         st.tcount = static_cast<int64_t>(tiles.size()) - st.tfirst;
         for (int64_t i = 0; i < l.count; ++i) {
             const GemmItem& g = P.gemm_items[l.first + i];
-            for (int32_t r0 = 0; r0 < g.M; r0 += 32) blocks.push_back(SliceBlock{static_cast<int32_t>(i), r0});
+            for (int32_t r0 = 0; r0 < g.M; r0 += kSplitSliceRows) blocks.push_back(SliceBlock{static_cast<int32_t>(i), r0});
         }
         st.sa_count = static_cast<int64_t>(blocks.size()) - st.sa_first;
         st.sb_first = static_cast<int64_t>(blocks.size());
         for (int64_t i = 0; i < l.count; ++i) {
             const GemmItem& g = P.gemm_items[l.first + i];
-            for (int32_t n0 = 0; n0 < g.N; n0 += 32) blocks.push_back(SliceBlock{static_cast<int32_t>(i), n0});
+            for (int32_t n0 = 0; n0 < g.N; n0 += kSplitSliceRows) blocks.push_back(SliceBlock{static_cast<int32_t>(i), n0});
         }
         st.sb_count = static_cast<int64_t>(blocks.size()) - st.sb_first;
         st.Kcols = std::max(64, 2 * kmax);
@@ -388,13 +388,15 @@ struct SliceArgs {
     int64_t erows_pole;
 };
 
-// Slices of one 32-row block of the stacked operand (A: rows m of op(A); B: columns n of op(B)).
-// A 32 x 64 complex tile is staged in shared memory with loads coalesced along whichever index
-// is contiguous in memory.  Pass 1 finds the row exponents (eight threads per row); pass 2 turns
-// two consecutive k per thread into digits, 32 threads per row, so every 4-byte store
-// instruction of a warp fills one whole 128-byte line of a slice.
-constexpr int kSliceRows = 32;
+// Slices of one block of kSplitSliceRows rows of the stacked operand (A: rows m of op(A); B:
+// columns n of op(B)).  A rows x 64 complex tile is staged in shared memory with loads coalesced
+// along whichever index is contiguous in memory.  Pass 1 finds the row exponents; pass 2 reads
+// the rows again and turns two consecutive k per thread into digits, 32 threads per row, so every
+// 4-byte store instruction of a warp fills one whole 128-byte line of a slice.  Blocks are few
+// rows high so that the rows pass 1 read are still in L2 when pass 2 reads them.
+constexpr int kSliceRows = kSplitSliceRows;
 constexpr int kSliceK = 64;
+constexpr int kSliceTPR = 256 / kSliceRows;  // pass-1 threads per row
 
 template <int S>
 __global__ void __launch_bounds__(256, 3) k_slice(const SliceArgs p) {
@@ -411,7 +413,7 @@ __global__ void __launch_bounds__(256, 3) k_slice(const SliceArgs p) {
     const bool sym = p.op == OP_S;
     const bool rows_contig = !sym && (p.isB ? p.op == OP_T : p.op == OP_N);
     const int tid = threadIdx.x;
-    const int r = tid / 8, kg = tid % 8;
+    const int r = tid / kSliceTPR, kg = tid % kSliceTPR;
     const int row = blk.r0 + r;
     if (tid < kSliceRows) rowmax[tid] = -1;
     auto load_tile = [&](int k0) {
@@ -447,8 +449,8 @@ __global__ void __launch_bounds__(256, 3) k_slice(const SliceArgs p) {
         load_tile(k0);
         __syncthreads();
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            const double2 v = tile[r][kg * 8 + j];
+        for (int j = 0; j < kSliceK / kSliceTPR; ++j) {
+            const double2 v = tile[r][kg * (kSliceK / kSliceTPR) + j];
             lmax = max(lmax, max(fp64_expo(v.x), fp64_expo(v.y)));
         }
         __syncthreads();

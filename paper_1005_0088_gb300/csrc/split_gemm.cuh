@@ -13,6 +13,7 @@ namespace ndsi {
 // Tile of the split GEMM: 128 output rows x 64 complex output columns.
 constexpr int kSplitBM = 128;
 constexpr int kSplitBNc = 64;      // complex columns per tile (128 rows of the stacked B operand)
+constexpr int kSplitSliceRows = 32;  // operand rows per slicing block
 constexpr int kSplitKB = 32;       // K per pipeline stage (64-byte rows, 64B swizzle)
 #ifdef NDSI_SPLIT_CHUNK_KB
 constexpr int kSplitChunkKB = NDSI_SPLIT_CHUNK_KB;

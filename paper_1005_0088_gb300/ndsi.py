@@ -33,7 +33,7 @@ EXPORTED_SYMBOLS = (
     "ndsi_factors_destroy", "ndsi_last_error", "ndsi_profile_enable", "ndsi_profile_read",
     "ndsi_residue_sum_static", "ndsi_find_mu", "ndsi_mu_features", "ndsi_mlp_init",
     "ndsi_mlp_forward", "ndsi_mlp_grad", "ndsi_mlp_train", "ndsi_analyze_batched",
-    "ndsi_density_batched", "ndsi_graph_enable", "ndsi_graph_info",
+    "ndsi_density_batched", "ndsi_graph_enable", "ndsi_graph_info", "ndsi_autotune",
 )
 NDSI_MLP_INPUTS = 32
 NDSI_MLP_HIDDEN = 64
@@ -100,6 +100,9 @@ def load(path: str = LIB_PATH):
     lib.ndsi_factors_destroy.restype = None
     lib.ndsi_profile_enable.argtypes = [vp, i32]
     lib.ndsi_graph_enable.argtypes = [vp, i32]
+    lib.ndsi_autotune.argtypes = [vp, vp, vp, ctypes.c_double, ctypes.c_double, i32,
+                                  ctypes.POINTER(i32), ctypes.POINTER(i32), vp]
+    lib.ndsi_autotune.restype = ctypes.c_int
     lib.ndsi_graph_info.argtypes = [vp, ctypes.POINTER(ctypes.c_int64)]
     lib.ndsi_graph_enable.restype = ctypes.c_int
     lib.ndsi_graph_info.restype = ctypes.c_int
@@ -273,6 +276,15 @@ def analyze_system(system, **options) -> Plan:
         setattr(opt, k, v)
     return ndsi_analyze(system.n, system.rowptr, system.col, system.centers.shape[0],
                         system.centers, system.atom_of_basis, opt)
+
+
+def ndsi_autotune(plan: Plan, H, S, mu, kT, n_poles, stream=None):
+    """Per-step choice between tensor-core and FP64 GEMMs by timing; returns (n_split, n_fp64)."""
+    ns = ctypes.c_int32(0)
+    nf = ctypes.c_int32(0)
+    _check(load().ndsi_autotune(plan.handle, _ptr(H), _ptr(S), float(mu), float(kT), int(n_poles),
+                                ctypes.byref(ns), ctypes.byref(nf), _stream(stream)))
+    return ns.value, nf.value
 
 
 def ndsi_graph_enable(plan: Plan, enable: bool = True):

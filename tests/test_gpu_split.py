@@ -93,3 +93,29 @@ def test_split_matches_fp64_path_C2():
     err = np.max(np.abs(rs - r64))
     print(f"split vs fp64 C2: rho {err:.2e}, N_e {abs(ns - n64):.2e}")
     assert err < RHO_TOL_SPLIT
+
+
+def test_autotune_keeps_accuracy():
+    # the autotuner moves each GEMM step to whichever of the tensor-core and FP64 paths is faster;
+    # the density must stay within the split tolerance and the graph path must keep working
+    import torch
+    nd = lib()
+    sysm = lattice_system((6, 6, 6), 2, "3d", 123)
+    kT, M = 0.01, 40
+    Hd, Sd = sysm.dense()
+    eps, C = generalized_eig(Hd, Sd)
+    mu = find_mu_eig(eps, kT, sysm.n_electrons, M)
+    ref = on_pattern(density_eig(eps, C, mu, kT, M), sysm)
+    plan = nd.analyze_system(sysm, precision=nd.NDSI_PREC_SPLIT)
+    H = torch.as_tensor(sysm.H, device="cuda")
+    S = torch.as_tensor(sysm.S, device="cuda")
+    n_split, n_fp64 = nd.ndsi_autotune(plan, H, S, mu, kT, M)
+    sched = nd.ndsi_plan_export(plan, "schedule")
+    assert n_split + n_fp64 == sum(1 for k, l, t, c in sched if k == 3 and t not in (3, 4, 6, 7))
+    rho = torch.zeros(sysm.nnz, dtype=torch.float64, device="cuda")
+    ne = torch.zeros(1, dtype=torch.float64, device="cuda")
+    for _ in range(2):
+        nd.ndsi_density(plan, H, S, mu, kT, M, rho, ne)
+    torch.cuda.synchronize()
+    assert nd.ndsi_graph_info(plan) > 0
+    assert np.max(np.abs(rho.cpu().numpy() - ref)) < RHO_TOL_SPLIT
