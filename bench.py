@@ -369,6 +369,7 @@ def run_ndsi(args):
                     "h2d_bytes_per_step": 2 * 8 * system.nnz,
                     "d2h_bytes_per_step": 8 * system.nnz + 8},
             "gpu_launches": launches,
+            "step_ms": [round(t, 4) for t in times],
             "autotune": tune,
             "graph": {"kernel_nodes": graph_nodes,
                       "ms_per_step_direct_launches": sum(prof_times) / len(prof_times),

@@ -528,6 +528,8 @@ struct GemmArgs {
     int neg_alpha, add_c;  // alpha = -1 / +1; beta = 1 / 0
     int lower;
     int* status;
+    int64_t tcount;        // tiles per pole
+    int np;                // poles
 };
 
 constexpr int kTileBytes = kSplitBM * kSplitKB * 2;  // 128 rows x 64 bytes
@@ -554,14 +556,15 @@ __global__ void __launch_bounds__(kThreads, 1)
     uint64_t* mma_done = bars + 6;
     uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(bars + 8);
     volatile int* abort = reinterpret_cast<volatile int*>(bars + 9);
-    int* sm_ea = reinterpret_cast<int*>(bars + 16);  // [128] exponents of the tile's rows
+    int* sm_ea = reinterpret_cast<int*>(bars + 16);  // [128] exponents of the current tile's rows
     int* sm_eb = sm_ea + 128;                         // [64] exponents of its complex columns
 
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-    const int64_t pole = blockIdx.y;
-    const int tile_item = p.tiles[p.tfirst + blockIdx.x].item;
-    const int nkb = 2 * p.sitems[p.ifirst + tile_item].Kpad / kSplitKB;
-    const int nchunks = (nkb + kSplitChunkKB - 1) / kSplitChunkKB;
+    // Persistent: CTA b takes work items b, b + gridDim.x, ... (work = pole * tcount + tile), so
+    // the CTAs running at the same time share the A and B slices of one pole in L2.
+    const int64_t n_work = p.tcount * p.np;
+    auto tile_of = [&](int64_t w) { return p.tiles[p.tfirst + w % p.tcount]; };
+    auto nkb_of = [&](const GemmTile& t) { return 2 * p.sitems[p.ifirst + t.item].Kpad / kSplitKB; };
 
     if (threadIdx.x == 0) {
         mbar_init(&full[0], 1);
@@ -583,98 +586,129 @@ __global__ void __launch_bounds__(kThreads, 1)
 
     if (warp == 0) {
         if (lane == 0) {
-            const GemmTile tile = p.tiles[p.tfirst + blockIdx.x];
-            const SplitItem si = p.sitems[p.ifirst + tile.item];
-            const int yA0 = static_cast<int>(pole * p.rowsA + si.rowA + tile.m0);
-            const int yB0 = static_cast<int>(pole * p.rowsB + si.rowB + (tile.n0 / kSplitBNc) * 128);
-            int armed = 0;  // k-blocks whose loads were issued
-            for (int kb = 0; kb < nkb; ++kb) {
-                const int stage = kb & 1;
-                if (kb >= 2 && !mbar_wait(&empty[stage], ((kb >> 1) - 1) & 1, abort)) break;
-                mbar_expect_tx(&full[stage], 2 * S * kTileBytes);
+            // producer: one ring of two stages across all of this CTA's tiles
+            int64_t g = 0;      // K-blocks issued so far (all tiles)
+            int64_t armed = 0;
+            for (int64_t w = blockIdx.x; w < n_work && !*abort; w += gridDim.x) {
+                const GemmTile tile = tile_of(w);
+                const int64_t pole = w / p.tcount;
+                const SplitItem si = p.sitems[p.ifirst + tile.item];
+                const int nkb = nkb_of(tile);
+                const int yA0 = static_cast<int>(pole * p.rowsA + si.rowA + tile.m0);
+                const int yB0 = static_cast<int>(pole * p.rowsB + si.rowB + (tile.n0 / kSplitBNc) * 128);
+                bool ok = true;
+                for (int kb = 0; kb < nkb; ++kb, ++g) {
+                    const int stage = static_cast<int>(g & 1);
+                    if (g >= 2 && !mbar_wait(&empty[stage], static_cast<uint32_t>(((g >> 1) - 1) & 1), abort)) {
+                        ok = false;
+                        break;
+                    }
+                    mbar_expect_tx(&full[stage], 2 * S * kTileBytes);
 #pragma unroll
-                for (int t = 0; t < S; ++t) tma_load_2d(a_tile(stage, t), &tmA, kb * kSplitKB, yA0 + t * si.Mpad, &full[stage]);
+                    for (int t = 0; t < S; ++t)
+                        tma_load_2d(a_tile(stage, t), &tmA, kb * kSplitKB, yA0 + t * si.Mpad, &full[stage]);
 #pragma unroll
-                for (int u = 0; u < S; ++u)
-                    tma_load_2d(b_tile(stage, u), &tmB, kb * kSplitKB, yB0 + u * 2 * si.Npad, &full[stage]);
-                armed = kb + 1;
+                    for (int u = 0; u < S; ++u)
+                        tma_load_2d(b_tile(stage, u), &tmB, kb * kSplitKB, yB0 + u * 2 * si.Npad, &full[stage]);
+                    armed = g + 1;
+                }
+                if (!ok) break;
             }
             if (*abort) {
                 // drain: wait for the last (up to two) armed stages' copies to land
-                for (int kb = armed > 2 ? armed - 2 : 0; kb < armed; ++kb)
-                    mbar_wait_drain(&full[kb & 1], (kb >> 1) & 1);
+                for (int64_t k = armed > 2 ? armed - 2 : 0; k < armed; ++k)
+                    mbar_wait_drain(&full[k & 1], static_cast<uint32_t>((k >> 1) & 1));
             }
         }
     } else if (warp == 1) {
         if (lane == 0) {
-            int issued = 0;
-            for (int kb = 0; kb < nkb; ++kb) {
-                const int stage = kb & 1;
-                if (!mbar_wait(&full[stage], (kb >> 1) & 1, abort)) break;
-                tc_fence_after();
-                const int chunk = kb / kSplitChunkKB;
-                const bool first_in_chunk = (kb % kSplitChunkKB) == 0;
-                if (first_in_chunk) {
-                    if (chunk > 0) {
-                        if (!mbar_wait(tmem_free, (chunk - 1) & 1, abort)) break;
+            // MMA issue: chunks are numbered across tiles; chunk c > 0 starts once the epilogue
+            // has read chunk c - 1 out of TMEM (which may belong to the previous tile)
+            int64_t g = 0, c = 0;
+            bool ok = true;
+            for (int64_t w = blockIdx.x; w < n_work && ok; w += gridDim.x) {
+                const int nkb = nkb_of(tile_of(w));
+                for (int kb = 0; kb < nkb; ++kb, ++g) {
+                    const int stage = static_cast<int>(g & 1);
+                    if (!mbar_wait(&full[stage], static_cast<uint32_t>((g >> 1) & 1), abort)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const bool first_in_chunk = (kb % kSplitChunkKB) == 0;
+                    if (first_in_chunk && c > 0) {
+                        if (!mbar_wait(tmem_free, static_cast<uint32_t>((c - 1) & 1), abort)) {
+                            ok = false;
+                            break;
+                        }
                         tc_fence_after();
                     }
-                }
-                // Descriptors of this stage's slice tiles: the start-address field is the low 14
-                // bits (address >> 4), so tile t and K16 half ks are compile-time offsets from the
-                // stage's first tile.  The pair loops unroll completely (S is a template
-                // parameter), leaving one 64-bit add and one tcgen05.mma per product.
-                const uint64_t da0 = sdesc_sw64(smem_u32(a_tile(stage, 0)));
-                const uint64_t db0 = sdesc_sw64(smem_u32(b_tile(stage, 0)));
-                const uint32_t fresh = first_in_chunk ? 0u : 1u;
-                // band 3: slice pairs with t+u >= 5 (1-based), read out per chunk like the others
+                    // Descriptors of this stage's slice tiles: the start-address field is the low
+                    // 14 bits (address >> 4), so tile t and K16 half ks are compile-time offsets
+                    // from the stage's first tile.  The pair loops unroll completely (S is a
+                    // template parameter), leaving one 64-bit add and one tcgen05.mma per product.
+                    const uint64_t da0 = sdesc_sw64(smem_u32(a_tile(stage, 0)));
+                    const uint64_t db0 = sdesc_sw64(smem_u32(b_tile(stage, 0)));
+                    const uint32_t fresh = first_in_chunk ? 0u : 1u;
+                    // band 3: slice pairs with t+u >= 5 (1-based), read out per chunk like the others
 #pragma unroll
-                for (int t = 0; t < S; ++t)
+                    for (int t = 0; t < S; ++t)
 #pragma unroll
-                    for (int u = 0; u < S; ++u) {
-                        if (t + u > S - 1 || t + u < 3) continue;
-                        const bool lead = (t + u == 3) && t == 0;  // first tail product of a K-tile
+                        for (int u = 0; u < S; ++u) {
+                            if (t + u > S - 1 || t + u < 3) continue;
+                            const bool lead = (t + u == 3) && t == 0;  // first tail product of a K-block
 #pragma unroll
-                        for (int ks = 0; ks < 2; ++ks) {
-                            const uint64_t da = da0 + static_cast<uint64_t>((t * kTileBytes + ks * 32) >> 4);
-                            const uint64_t db = db0 + static_cast<uint64_t>((u * kTileBytes + ks * 32) >> 4);
-                            umma_bf16(tmem + 3 * 128, da, db, kIdesc, (lead && ks == 0) ? fresh : 1u);
+                            for (int ks = 0; ks < 2; ++ks) {
+                                const uint64_t da = da0 + static_cast<uint64_t>((t * kTileBytes + ks * 32) >> 4);
+                                const uint64_t db = db0 + static_cast<uint64_t>((u * kTileBytes + ks * 32) >> 4);
+                                umma_bf16(tmem + 3 * 128, da, db, kIdesc, (lead && ks == 0) ? fresh : 1u);
+                            }
+                        }
+                    // bands 0..2: t+u = 2, 3, 4 (1-based), exact within a chunk
+#pragma unroll
+                    for (int band = 0; band < 3; ++band) {
+#pragma unroll
+                        for (int t = 0; t < S; ++t) {
+                            const int u = band - t;
+                            if (u < 0 || u >= S) continue;
+#pragma unroll
+                            for (int ks = 0; ks < 2; ++ks) {
+                                const uint64_t da = da0 + static_cast<uint64_t>((t * kTileBytes + ks * 32) >> 4);
+                                const uint64_t db = db0 + static_cast<uint64_t>((u * kTileBytes + ks * 32) >> 4);
+                                umma_bf16(tmem + band * 128, da, db, kIdesc, (t == 0 && ks == 0) ? fresh : 1u);
+                            }
                         }
                     }
-                // bands 0..2: t+u = 2, 3, 4 (1-based), exact within a chunk
-#pragma unroll
-                for (int band = 0; band < 3; ++band) {
-#pragma unroll
-                    for (int t = 0; t < S; ++t) {
-                        const int u = band - t;
-                        if (u < 0 || u >= S) continue;
-#pragma unroll
-                        for (int ks = 0; ks < 2; ++ks) {
-                            const uint64_t da = da0 + static_cast<uint64_t>((t * kTileBytes + ks * 32) >> 4);
-                            const uint64_t db = db0 + static_cast<uint64_t>((u * kTileBytes + ks * 32) >> 4);
-                            umma_bf16(tmem + band * 128, da, db, kIdesc, (t == 0 && ks == 0) ? fresh : 1u);
-                        }
+                    umma_commit(&empty[stage]);
+                    if ((kb % kSplitChunkKB) == kSplitChunkKB - 1 || kb == nkb - 1) {
+                        umma_commit(chunk_full);
+                        ++c;
                     }
                 }
-                umma_commit(&empty[stage]);
-                if ((kb % kSplitChunkKB) == kSplitChunkKB - 1 || kb == nkb - 1) umma_commit(chunk_full);
-                issued = kb + 1;
             }
             umma_commit(mma_done);
-            (void)issued;
         }
     } else {
-        // epilogue: warp quarter q reads TMEM lanes 32q..32q+31; column group cg the accumulator
-        // columns 32cg..32cg+31 (cg 0,1: Re C; cg 2,3: Im C of the same 64 complex columns)
+        // epilogue: warp quarter q reads TMEM lanes 32q..32q+31 (tile rows); column group cg the
+        // complex columns 16cg..16cg+15, i.e. accumulator columns 16cg.. (Re) and 64+16cg.. (Im),
+        // so that every thread holds whole complex elements.  After a tile's last chunk TMEM is
+        // released at once and the conversion to FP64 and the store run from registers while
+        // the MMAs of the next tile proceed.
         const int q = warp & 3;
         const int cg = (warp - 2) >> 2;
         const int et = threadIdx.x - 64;
-        {
-            // while the main loop runs: the tile's scale exponents into shared memory, and the C
-            // block the final update reads pulled towards L2
-            const GemmTile tile = p.tiles[p.tfirst + blockIdx.x];
+        const bool neg_alpha = p.neg_alpha != 0, add_c = p.add_c != 0;
+        int64_t c = 0;  // chunks consumed (all tiles)
+        bool ok = true;
+        for (int64_t w = blockIdx.x; w < n_work && ok; w += gridDim.x) {
+            const GemmTile tile = tile_of(w);
+            const int64_t pole = w / p.tcount;
             const GemmItem it = p.items[p.ifirst + tile.item];
             const SplitItem si = p.sitems[p.ifirst + tile.item];
+            const int nchunks = (nkb_of(tile) + kSplitChunkKB - 1) / kSplitChunkKB;
+            double2* Cp = p.C + pole * p.sC + it.c_off;
+            // this tile's scale exponents (the previous tile's are no longer read)
+            asm volatile("bar.sync 1, %0;" ::"n"(kEpiWarps * 32) : "memory");
             if (et < 128) {
                 const int m = tile.m0 + et;
                 sm_ea[et] = m < it.M ? p.expA[pole * p.erowsA + si.erowA + m] : 0;
@@ -682,8 +716,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                 const int n = tile.n0 + et - 128;
                 sm_eb[et - 128] = n < it.N ? p.expB[pole * p.erowsB + si.erowB + n] : 0;
             }
-            if (p.add_c) {
-                const double2* Cp = p.C + pole * p.sC + it.c_off;
+            if (add_c) {
+                // pull the C block the final update reads towards L2 while the MMAs run
 #pragma unroll
                 for (int u = 0; u < 2; ++u) {
                     const int line = et + u * kEpiWarps * 32;  // 64 columns x 16 lines of 128 B
@@ -693,86 +727,59 @@ __global__ void __launch_bounds__(kThreads, 1)
                         asm volatile("prefetch.global.L2 [%0];" ::"l"(Cp + m + static_cast<int64_t>(n) * it.ldc));
                 }
             }
-        }
-        float hi[32], lo[32];
+            asm volatile("bar.sync 1, %0;" ::"n"(kEpiWarps * 32) : "memory");
+            float hi[32], lo[32];
 #pragma unroll
-        for (int j = 0; j < 32; ++j) {
-            hi[j] = 0.f;
-            lo[j] = 0.f;
-        }
-        bool ok = true;
-        for (int c = 0; c < nchunks; ++c) {
-            if (!mbar_wait(chunk_full, c & 1, abort)) {
-                ok = false;
-                break;
+            for (int j = 0; j < 32; ++j) {
+                hi[j] = 0.f;
+                lo[j] = 0.f;
             }
-            tc_fence_after();
-            const int nb = 4;
+            for (int k = 0; k < nchunks; ++k, ++c) {
+                if (!mbar_wait(chunk_full, static_cast<uint32_t>(c & 1), abort)) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
 #pragma unroll
-            for (int band = 0; band < 4; ++band) {
-                if (band < nb) {
+                for (int band = 0; band < 4; ++band) {
 #pragma unroll
                     for (int j2 = 0; j2 < 4; ++j2) {
+                        // j2 0,1: Re columns 16cg + 0..15; j2 2,3: the matching Im columns
                         float v[8];
-                        tmem_ld8(tmem + (static_cast<uint32_t>(32 * q) << 16) + band * 128 + cg * 32 + j2 * 8, v);
+                        const int col = (j2 >> 1) * 64 + cg * 16 + (j2 & 1) * 8;
+                        tmem_ld8(tmem + (static_cast<uint32_t>(32 * q) << 16) + band * 128 + col, v);
 #pragma unroll
                         for (int i = 0; i < 8; ++i) ff_add(hi[j2 * 8 + i], lo[j2 * 8 + i], v[i]);
                     }
                 }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(tmem_free);
             }
-            tc_fence_before();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(tmem_free);
-        }
-        // stage (hi, lo) in the pipeline shared memory (idle once the last chunk completed), then
-        // all epilogue warps form C = alpha*scale*(hi+lo) + beta*C with coalesced complex stores
-        float* sm_hi = reinterpret_cast<float*>(smem);          // [128 columns][128 rows]
-        float* sm_lo = sm_hi + 128 * 128;
-        if (ok && !*abort) {
+            if (!ok || *abort) break;
+            // C = alpha * 2^e (hi + lo) + beta * C for this thread's row and 16 complex columns:
+            // alpha is +-1 and beta 0 or 1 (checked at launch), the sign goes onto the integer
+            // result and beta = 1 costs the only FP64 instructions.  A warp stores one column's
+            // 32 consecutive rows (512 contiguous bytes) per instruction.
+            const int r = 32 * q + lane;
+            const int m = tile.m0 + r;
+            if (m < it.M) {
+                const int ea = sm_ea[r] - 14;
 #pragma unroll
-            for (int j = 0; j < 32; ++j) {
-                const int col = cg * 32 + j;
-                sm_hi[col * 128 + 32 * q + lane] = hi[j];
-                sm_lo[col * 128 + 32 * q + lane] = lo[j];
-            }
-        }
-        asm volatile("bar.sync 1, %0;" ::"n"(kEpiWarps * 32) : "memory");
-        if (ok && !*abort) {
-            const GemmTile tile = p.tiles[p.tfirst + blockIdx.x];
-            const GemmItem it = p.items[p.ifirst + tile.item];
-            double2* Cp = p.C + pole * p.sC + it.c_off;
-            // four outputs per thread per round: their C loads are in flight together.  alpha is
-            // +-1 and beta 0 or 1 (checked at launch): the sign is applied to the integer result,
-            // and beta = 1 costs the only FP64 instructions of the epilogue.
-            const bool neg_alpha = p.neg_alpha != 0, add_c = p.add_c != 0;
-            constexpr int kRound = 4, kStride = kEpiWarps * 32;
-#pragma unroll 1
-            for (int base = et; base < 128 * 64; base += kRound * kStride) {
-                double2 old[kRound];
-                bool live[kRound];
-#pragma unroll
-                for (int u = 0; u < kRound; ++u) {
-                    const int idx = base + u * kStride;
-                    const int r = idx % 128, j = idx / 128;
-                    const int m = tile.m0 + r, n = tile.n0 + j;
-                    live[u] = idx < 128 * 64 && m < it.M && n < it.N && !(p.lower && n > m);
-                    old[u] = make_double2(0.0, 0.0);
-                    if (live[u] && add_c) old[u] = Cp[m + static_cast<int64_t>(n) * it.ldc];
-                }
-#pragma unroll
-                for (int u = 0; u < kRound; ++u) {
-                    if (!live[u]) continue;
-                    const int idx = base + u * kStride;
-                    const int r = idx % 128, j = idx / 128;
-                    const int m = tile.m0 + r, n = tile.n0 + j;
-                    const int e = sm_ea[r] + sm_eb[j] - 14;
-                    double re = ff_to_double_scaled(sm_hi[j * 128 + r], sm_lo[j * 128 + r], e, neg_alpha);
-                    double im = ff_to_double_scaled(sm_hi[(64 + j) * 128 + r], sm_lo[(64 + j) * 128 + r], e, neg_alpha);
+                for (int j = 0; j < 16; ++j) {
+                    const int jc = cg * 16 + j;
+                    const int n = tile.n0 + jc;
+                    if (n >= it.N || (p.lower && n > m)) continue;
+                    double2* dst = Cp + m + static_cast<int64_t>(n) * it.ldc;
+                    const int e = ea + sm_eb[jc];
+                    double re = ff_to_double_scaled(hi[j], lo[j], e, neg_alpha);
+                    double im = ff_to_double_scaled(hi[16 + j], lo[16 + j], e, neg_alpha);
                     if (add_c) {
-                        re += old[u].x;
-                        im += old[u].y;
+                        const double2 old = *dst;
+                        re += old.x;
+                        im += old.y;
                     }
-                    Cp[m + static_cast<int64_t>(n) * it.ldc] = make_double2(re, im);
+                    *dst = make_double2(re, im);
                 }
             }
         }
@@ -790,6 +797,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+int g_num_sms = 148;  // multiprocessors of the current device (persistent grid size)
 
 template <int S>
 cudaError_t set_attrs() {
@@ -808,6 +816,10 @@ cudaError_t split_init() {
         g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
     }
     cudaError_t e;
+    int dev = 0, sms = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    if (sms > 0) g_num_sms = sms;
     if ((e = set_attrs<4>()) != cudaSuccess) return e;
     if ((e = set_attrs<5>()) != cudaSuccess) return e;
     if ((e = set_attrs<6>()) != cudaSuccess) return e;
@@ -890,8 +902,11 @@ static cudaError_t run_mma(const Launch& l, int step_index, const GemmItem* item
     GemmArgs ga{items_dev, sitems_dev, stiles_dev, step.tfirst, l.first, step.rowsA, step.rowsB,
                 step.erowsA, step.erowsB, B.expA, B.expB, Cbuf, sC, l.alpha < 0 ? 1 : 0, l.beta != 0.0 ? 1 : 0,
                 l.lower, status};
-    k_gemm_split<S><<<dim3(static_cast<unsigned>(step.tcount), np), kThreads, split_smem_bytes<S>(), st>>>(
-        B.tmA[step_index], B.tmB[step_index], ga);
+    ga.tcount = step.tcount;
+    ga.np = np;
+    const int64_t work = step.tcount * np;
+    const unsigned grid = static_cast<unsigned>(std::max<int64_t>(1, std::min<int64_t>(work, g_num_sms)));
+    k_gemm_split<S><<<grid, kThreads, split_smem_bytes<S>(), st>>>(B.tmA[step_index], B.tmB[step_index], ga);
     return cudaGetLastError();
 }
 
