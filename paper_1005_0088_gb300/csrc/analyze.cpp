@@ -654,6 +654,10 @@ void build_schedule(Plan& P) {
                     }
                 }
                 ld.count = static_cast<int64_t>(P.diag_items.size()) - ld.first;
+                // pivot-sweep variant: 16 when every block of the launch is at most 16 wide
+                ld.tile = 16;
+                for (int64_t i = ld.first; i < ld.first + ld.count; ++i)
+                    if (P.diag_items[i].nb > 16) ld.tile = 32;
                 if (ld.count > 0) {
                     P.flops_per_pole += ld.flops;
                     P.launches.push_back(ld);

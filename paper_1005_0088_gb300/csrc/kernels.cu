@@ -134,38 +134,42 @@ __global__ void __launch_bounds__(256) k_diaginv(const DiagItem* __restrict__ it
     }
 }
 
-// Register-resident variant for blocks of up to 32: one warp per (block, pole) running the
-// symmetric sweep, the sign convention of Gauss-Jordan elimination that keeps a symmetric matrix
-// symmetric.  Pivoting on t with p = a_tt maps a_tt -> -1/p, a_it and a_ti -> a_it/p and
+// Register-resident variant for blocks of up to N = 16 or 32: one warp per (block, pole) running
+// the symmetric sweep, the sign convention of Gauss-Jordan elimination that keeps a symmetric
+// matrix symmetric.  Pivoting on t with p = a_tt maps a_tt -> -1/p, a_it and a_ti -> a_it/p and
 // a_ik -> a_ik - a_it a_tk / p; after all pivots the block holds -A^{-1}.  Because every
-// intermediate matrix is symmetric only the 528 lower-triangle elements are updated, half the
-// FP64 work of the full elimination.  They are packed 17 to a lane: lane c (c < 16) holds rows
-// c..31 of column c and then rows 31-c..31 of column 31-c (33 elements), split between lanes c
-// (first 17) and c + 16 (last 16).  Every lane runs the same instruction stream (no divergent
-// pivot lane); column t of the current matrix and its scaled copy pass through shared memory.
-constexpr int kSweepSlots = 17;
-
+// intermediate matrix is symmetric only the N(N+1)/2 lower-triangle elements are updated, half
+// the FP64 work of the full elimination.  They are packed onto the lanes: virtual column c
+// (c < N/2) is rows c..N-1 of column c followed by rows N-1-c..N-1 of column N-1-c (N+1
+// elements), split evenly over 64/N lanes.  Every lane runs the same instruction stream (no
+// divergent pivot lane); column t of the current matrix and its scaled copy pass through shared
+// memory.  N = 16 serves launches whose pivot blocks are all at most 16 wide (small separators
+// and the ragged last block of a front) at about a third of the N = 32 cost.
+template <int N>
 __global__ void __launch_bounds__(32) k_diaginv_sweep(const DiagItem* __restrict__ items, int64_t first,
                                                       double2* __restrict__ F, int64_t stride,
                                                       int* __restrict__ status) {
+    constexpr int VC = N / 2;                  // virtual columns
+    constexpr int LPC = 32 / VC;               // lanes per virtual column
+    constexpr int SLOTS = (N + 1 + LPC - 1) / LPC;
     __shared__ double2 cs[33], ds[33];
     const int lane = threadIdx.x;
     const DiagItem d = items[first + blockIdx.x];
     double2* A = F + static_cast<int64_t>(blockIdx.y) * stride + d.off;
     const int nb = d.nb, ld = d.ld;
-    const int c = lane & 15, vbase = lane < 16 ? 0 : kSweepSlots;
-    int rc[kSweepSlots];  // row | column << 8 of each slot (32 = unused slot)
-    double2 a[kSweepSlots];
+    const int c = lane % VC, vbase = (lane / VC) * SLOTS;
+    int rc[SLOTS];  // row | column << 8 of each slot (32 = unused slot)
+    double2 a[SLOTS];
 #pragma unroll
-    for (int s = 0; s < kSweepSlots; ++s) {
+    for (int s = 0; s < SLOTS; ++s) {
         const int v = vbase + s;
         int i = 32, k = 32;
-        if (v < 32 - c) {
+        if (v < N - c) {
             i = c + v;
             k = c;
-        } else if (v <= 32) {
+        } else if (v <= N) {
             i = v - 1;
-            k = 31 - c;
+            k = N - 1 - c;
         }
         rc[s] = i | (k << 8);
         a[s] = make_double2(0.0, 0.0);
@@ -179,7 +183,7 @@ __global__ void __launch_bounds__(32) k_diaginv_sweep(const DiagItem* __restrict
     for (int t = 0; t < nb; ++t) {
         // column t (= row t) of the current matrix
 #pragma unroll
-        for (int s = 0; s < kSweepSlots; ++s) {
+        for (int s = 0; s < SLOTS; ++s) {
             const int i = rc[s] & 255, k = rc[s] >> 8;
             if (k == t) cs[i] = a[s];
             if (i == t) cs[k] = a[s];
@@ -190,10 +194,10 @@ __global__ void __launch_bounds__(32) k_diaginv_sweep(const DiagItem* __restrict
         bad |= !(den > 0.0 && isfinite(den));
         const double rden = 1.0 / den;
         const double2 ip = make_double2(p.x * rden, -p.y * rden);
-        ds[lane] = cmul(cs[lane], ip);
+        if (lane < N) ds[lane] = cmul(cs[lane], ip);
         __syncwarp();
 #pragma unroll
-        for (int s = 0; s < kSweepSlots; ++s) {
+        for (int s = 0; s < SLOTS; ++s) {
             const int i = rc[s] & 255, k = rc[s] >> 8;
             const double2 cv = cs[i], dk = ds[k];
             double2 g = make_double2(a[s].x - (cv.x * dk.x - cv.y * dk.y), a[s].y - (cv.x * dk.y + cv.y * dk.x));
@@ -205,7 +209,7 @@ __global__ void __launch_bounds__(32) k_diaginv_sweep(const DiagItem* __restrict
     }
     if (bad && lane == 0) atomicOr(status, kStatusSingular);
 #pragma unroll
-    for (int s = 0; s < kSweepSlots; ++s) {
+    for (int s = 0; s < SLOTS; ++s) {
         const int i = rc[s] & 255, k = rc[s] >> 8;
         if (i < nb && k < nb) A[i + static_cast<int64_t>(k) * ld] = make_double2(-a[s].x, -a[s].y);
     }
@@ -483,7 +487,10 @@ cudaError_t launch_step(const Plan& P, const DevTables& T, const Launch& l, cons
             const int b = P.block;
             const size_t sm = static_cast<size_t>(b) * (b + 1) * sizeof(double2);
             if (b <= 32) {
-                k_diaginv_sweep<<<grid, 32, 0, st>>>(T.diag_items, l.first, W.fronts, W.front_stride, T.status);
+                if (l.tile == 16)
+                    k_diaginv_sweep<16><<<grid, 32, 0, st>>>(T.diag_items, l.first, W.fronts, W.front_stride, T.status);
+                else
+                    k_diaginv_sweep<32><<<grid, 32, 0, st>>>(T.diag_items, l.first, W.fronts, W.front_stride, T.status);
             } else {
                 k_diaginv<64><<<grid, 256, sm, st>>>(T.diag_items, l.first, W.fronts, W.front_stride, T.status);
             }

@@ -75,7 +75,7 @@ struct Launch {
     double alpha, beta;
     int64_t first, count;    // range in the item array of this kind
     int64_t tfirst, tcount;  // GEMM tiles range
-    int32_t tile;            // FP64 GEMM output tile edge of this launch (16 or 32)
+    int32_t tile;            // FP64 GEMM output tile edge (16 or 32); pivot-sweep width of a diag launch
     int32_t exact;           // 1: FP64 CUDA-core GEMM in every precision mode (diagonal blocks)
     int32_t phase;           // 0 factor, 1 selinv
     int32_t tag;             // which formula the step implements (for profiling names)
