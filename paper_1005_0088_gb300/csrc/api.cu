@@ -417,7 +417,8 @@ void setup_split(ndsi_plan* h, const ndsi_options& o) {
         double sb = 0;
         for (int64_t i = 0; i < l.count; ++i) {
             const GemmItem& g = h->P.gemm_items[l.first + i];
-            sb += 2.0 * 16.0 * (static_cast<double>(g.M) * g.K + static_cast<double>(g.N) * g.K);
+            // FP64 operand reads: once (one-pass slicer) or twice (two-pass)
+            sb += (st.slice_ldt > 0 ? 1.0 : 2.0) * 16.0 * (static_cast<double>(g.M) * g.K + static_cast<double>(g.N) * g.K);
         }
         sb += 2.0 * (static_cast<double>(st.rowsA) + st.rowsB) * st.Kcols;
         S.slice_bytes.push_back(sb);

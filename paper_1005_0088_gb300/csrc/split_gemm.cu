@@ -67,15 +67,27 @@ void build_split_schedule(const Plan& P, int slices, std::vector<SplitItem>& ite
                 }
         }
         st.tcount = static_cast<int64_t>(tiles.size()) - st.tfirst;
+        // slicing: one pass over the operand when a block of rows x K fits the shared-memory
+        // budget (32, 16, 8 or 4 rows), else two passes over 32-row blocks
+        int32_t kreal = 0;
+        for (int64_t i = 0; i < l.count; ++i) kreal = std::max(kreal, P.gemm_items[l.first + i].K);
+        st.slice_ldt = kreal + 1;
+        st.slice_rows = 32;
+        while (st.slice_rows > 4 && static_cast<int64_t>(st.slice_rows) * st.slice_ldt * 16 > kSplitSlice1Smem)
+            st.slice_rows /= 2;
+        if (static_cast<int64_t>(st.slice_rows) * st.slice_ldt * 16 > kSplitSlice1Smem) {
+            st.slice_rows = kSplitSliceRows;
+            st.slice_ldt = 0;
+        }
         for (int64_t i = 0; i < l.count; ++i) {
             const GemmItem& g = P.gemm_items[l.first + i];
-            for (int32_t r0 = 0; r0 < g.M; r0 += kSplitSliceRows) blocks.push_back(SliceBlock{static_cast<int32_t>(i), r0});
+            for (int32_t r0 = 0; r0 < g.M; r0 += st.slice_rows) blocks.push_back(SliceBlock{static_cast<int32_t>(i), r0});
         }
         st.sa_count = static_cast<int64_t>(blocks.size()) - st.sa_first;
         st.sb_first = static_cast<int64_t>(blocks.size());
         for (int64_t i = 0; i < l.count; ++i) {
             const GemmItem& g = P.gemm_items[l.first + i];
-            for (int32_t n0 = 0; n0 < g.N; n0 += kSplitSliceRows) blocks.push_back(SliceBlock{static_cast<int32_t>(i), n0});
+            for (int32_t n0 = 0; n0 < g.N; n0 += st.slice_rows) blocks.push_back(SliceBlock{static_cast<int32_t>(i), n0});
         }
         st.sb_count = static_cast<int64_t>(blocks.size()) - st.sb_first;
         st.Kcols = std::max(64, 2 * kmax);
@@ -386,6 +398,7 @@ struct SliceArgs {
     int32_t Kcols;
     int32_t* expo;
     int64_t erows_pole;
+    int rows, ldt;  // one-pass slicer: rows per block and shared-memory row stride
 };
 
 // Slices of one block of kSplitSliceRows rows of the stacked operand (A: rows m of op(A); B:
@@ -512,6 +525,113 @@ __global__ void __launch_bounds__(256, 3) k_slice(const SliceArgs p) {
         __syncthreads();
     }
     if (live && kg == 0) p.expo[pole * p.erows_pole + (p.isB ? si.erowB : si.erowA) + row] = E;
+}
+
+// One-pass slicing: a block of `rows` (32, 16, 8 or 4) operand rows with all K of them resident
+// in shared memory, so every FP64 element is read from HBM once.  Loads are coalesced along the
+// contiguous index; the row maxima come from rows-many thread groups; the digits are written by
+// 32 threads per row with two consecutive k each, one 128-byte line per warp store.
+template <int S>
+__global__ void __launch_bounds__(256) k_slice1(const SliceArgs p) {
+    extern __shared__ double2 t1[];  // [rows][ldt]
+    __shared__ int rowmax[32];
+    const SliceBlock blk = p.blocks[p.bfirst + blockIdx.x];
+    const GemmItem it = p.items[p.ifirst + blk.item];
+    const SplitItem si = p.sitems[p.ifirst + blk.item];
+    const int64_t pole = blockIdx.y;
+    const int nrows = p.isB ? it.N : it.M;
+    const int K = it.K;
+    const int R = p.rows, ldt = p.ldt;
+    const double2* base = p.X + pole * p.sX + (p.isB ? it.b_off : it.a_off);
+    const int ld = p.isB ? it.ldb : it.lda;
+    const bool sym = p.op == OP_S;
+    const bool rows_contig = !sym && (p.isB ? p.op == OP_T : p.op == OP_N);
+    const int tid = threadIdx.x;
+    if (tid < 32) rowmax[tid] = -1;
+    const int total = R * K;
+    for (int e = tid; e < total; e += 256) {
+        int rr, kk;
+        if (rows_contig) {
+            rr = e % R;
+            kk = e / R;
+        } else {
+            kk = e % K;
+            rr = e / K;
+        }
+        const int gr = blk.r0 + rr;
+        double2 x = make_double2(0.0, 0.0);
+        if (gr < nrows) {
+            if (sym) {
+                const int hi = gr > kk ? gr : kk, lo = gr > kk ? kk : gr;
+                x = base[hi + static_cast<int64_t>(lo) * ld];
+            } else if (rows_contig) {
+                x = base[gr + static_cast<int64_t>(kk) * ld];
+            } else {
+                x = base[kk + static_cast<int64_t>(gr) * ld];
+            }
+        }
+        t1[rr * ldt + kk] = x;
+    }
+    __syncthreads();
+    {
+        const int tpr = 256 / R;  // threads per row
+        const int rr = tid / tpr, kg = tid % tpr;
+        int lmax = -1;
+        for (int kk = kg; kk < K; kk += tpr) {
+            const double2 v = t1[rr * ldt + kk];
+            lmax = max(lmax, max(fp64_expo(v.x), fp64_expo(v.y)));
+        }
+        atomicMax(&rowmax[rr], lmax);
+    }
+    __syncthreads();
+    const int half = si.Kpad / 2;  // k pairs per row
+    for (int idx = tid; idx < R * half; idx += 256) {
+        const int rr = idx / half, kk = 2 * (idx % half);
+        const int grow = blk.r0 + rr;
+        if (grow >= nrows) continue;
+        const int Er = rowmax[rr] < 0 ? -1021 : rowmax[rr] - 1022;
+        int64_t o0, ost;
+        if (!p.isB) {
+            o0 = pole * p.rows_pole + si.rowA + grow;
+            ost = si.Mpad;
+        } else {
+            o0 = pole * p.rows_pole + si.rowB + (grow / 64) * 128 + (grow % 64);
+            ost = 2 * si.Npad;
+        }
+        const double2 v0 = kk < K ? t1[rr * ldt + kk] : make_double2(0.0, 0.0);
+        const double2 v1 = kk + 1 < K ? t1[rr * ldt + kk + 1] : make_double2(0.0, 0.0);
+        int d0[S], d1[S];
+        uint32_t wre[S], wim[S];
+        fp64_digits32<S>(v0.x, Er, d0);
+        fp64_digits32<S>(v1.x, Er, d1);
+#pragma unroll
+        for (int t = 0; t < S; ++t)
+            wre[t] = static_cast<uint32_t>(bf16_digit(d0[t], t)) | (static_cast<uint32_t>(bf16_digit(d1[t], t)) << 16);
+        fp64_digits32<S>(v0.y, Er, d0);
+        fp64_digits32<S>(v1.y, Er, d1);
+#pragma unroll
+        for (int t = 0; t < S; ++t)
+            wim[t] = static_cast<uint32_t>(bf16_digit(d0[t], t)) | (static_cast<uint32_t>(bf16_digit(d1[t], t)) << 16);
+#pragma unroll
+        for (int t = 0; t < S; ++t) {
+            uint16_t* o1 = p.out + (o0 + t * ost) * p.Kcols;
+            if (!p.isB) {
+                *reinterpret_cast<uint32_t*>(o1 + kk) = wre[t];
+                *reinterpret_cast<uint32_t*>(o1 + si.Kpad + kk) = wim[t];
+            } else {
+                // rows [Re | -Im] and [Im | Re]; negation flips the BF16 sign bits
+                uint16_t* o2 = o1 + 64 * static_cast<int64_t>(p.Kcols);
+                *reinterpret_cast<uint32_t*>(o1 + kk) = wre[t];
+                *reinterpret_cast<uint32_t*>(o1 + si.Kpad + kk) = wim[t] ^ 0x80008000u;
+                *reinterpret_cast<uint32_t*>(o2 + kk) = wim[t];
+                *reinterpret_cast<uint32_t*>(o2 + si.Kpad + kk) = wre[t];
+            }
+        }
+    }
+    if (tid < R && blk.r0 + tid < nrows) {
+        const int E = rowmax[tid] < 0 ? -1021 : rowmax[tid] - 1022;
+        p.expo[pole * p.erows_pole + (p.isB ? si.erowB : si.erowA) + blk.r0 + tid] = E;
+    }
 }
 
 // ---------------------------------------------------------------------------- the GEMM -----
@@ -801,7 +921,10 @@ int g_num_sms = 148;  // multiprocessors of the current device (persistent grid 
 
 template <int S>
 cudaError_t set_attrs() {
-    return cudaFuncSetAttribute(k_gemm_split<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, split_smem_bytes<S>());
+    cudaError_t e = cudaFuncSetAttribute(k_gemm_split<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         split_smem_bytes<S>());
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_slice1<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSplitSlice1Smem);
 }
 
 }  // namespace
@@ -883,12 +1006,20 @@ static cudaError_t run_slice(const Launch& l, const GemmItem* items_dev, const S
                              const double2* Abuf, int64_t sA, const double2* Bbuf, int64_t sB, int np,
                              cudaStream_t st) {
     SliceArgs sa{items_dev, sitems_dev, blocks_dev, step.sa_first, l.first, Abuf, sA, l.opA, 0,
-                 B.sliceA, step.rowsA, step.Kcols, B.expA, step.erowsA};
+                 B.sliceA, step.rowsA, step.Kcols, B.expA, step.erowsA, step.slice_rows, step.slice_ldt};
+    SliceArgs sb{items_dev, sitems_dev, blocks_dev, step.sb_first, l.first, Bbuf, sB, l.opB, 1,
+                 B.sliceB, step.rowsB, step.Kcols, B.expB, step.erowsB, step.slice_rows, step.slice_ldt};
+    if (step.slice_ldt > 0) {
+        const size_t sm = static_cast<size_t>(step.slice_rows) * step.slice_ldt * sizeof(double2);
+        k_slice1<S><<<dim3(static_cast<unsigned>(step.sa_count), np), 256, sm, st>>>(sa);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        k_slice1<S><<<dim3(static_cast<unsigned>(step.sb_count), np), 256, sm, st>>>(sb);
+        return cudaGetLastError();
+    }
     k_slice<S><<<dim3(static_cast<unsigned>(step.sa_count), np), 256, 0, st>>>(sa);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    SliceArgs sb{items_dev, sitems_dev, blocks_dev, step.sb_first, l.first, Bbuf, sB, l.opB, 1,
-                 B.sliceB, step.rowsB, step.Kcols, B.expB, step.erowsB};
     k_slice<S><<<dim3(static_cast<unsigned>(step.sb_count), np), 256, 0, st>>>(sb);
     return cudaGetLastError();
 }

@@ -13,7 +13,8 @@ namespace ndsi {
 // Tile of the split GEMM: 128 output rows x 64 complex output columns.
 constexpr int kSplitBM = 128;
 constexpr int kSplitBNc = 64;      // complex columns per tile (128 rows of the stacked B operand)
-constexpr int kSplitSliceRows = 32;  // operand rows per slicing block
+constexpr int kSplitSliceRows = 32;  // operand rows per slicing block (two-pass slicer)
+constexpr int kSplitSlice1Smem = 72 * 1024;  // shared-memory budget of the one-pass slicer
 constexpr int kSplitKB = 32;       // K per pipeline stage (64-byte rows, 64B swizzle)
 #ifdef NDSI_SPLIT_CHUNK_KB
 constexpr int kSplitChunkKB = NDSI_SPLIT_CHUNK_KB;
@@ -33,10 +34,13 @@ struct SplitItem {
 // Per GEMM launch: sizes of one pole's block in the step buffers, and the split tile range.
 struct SplitStep {
     int64_t rowsA, rowsB, erowsA, erowsB;  // per pole
-    int32_t Kcols, pad;                    // row length of the slice buffers (2*max Kpad)
+    int32_t Kcols;                         // row length of the slice buffers (2*max Kpad)
+    int32_t slice_rows;                    // operand rows per slicing block
+    int32_t slice_ldt;                     // one-pass slicing: shared-memory row stride (0: two passes)
+    int32_t pad;
     int64_t tfirst, tcount;                // tiles in the split tile list
-    int64_t sa_first, sa_count;            // 64-row slicing blocks of A in the block list
-    int64_t sb_first, sb_count;            // 64-column slicing blocks of B
+    int64_t sa_first, sa_count;            // slicing blocks of A (rows of op(A)) in the block list
+    int64_t sb_first, sb_count;            // slicing blocks of B (columns of op(B))
 };
 
 // A slicing block: item (relative to the launch) and its first row (A) or complex column (B).
