@@ -37,6 +37,21 @@ def _env_rank():
             int(os.environ.get("LOCAL_RANK", "0")))
 
 
+def _max_over_ranks(x, dist, world, device):
+    """Largest value of x over all ranks (the slowest replica sets the job's time)."""
+    if world <= 1:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def _job_value(units_per_rank, world, ms_per_step):
+    """Whole-job throughput: every replica processes units_per_rank per step."""
+    return world * units_per_rank / (ms_per_step * 1e-3)
+
+
 def _peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -283,13 +298,9 @@ def run_ndsi(args):
         graph_nodes = nd.ndsi_graph_info(plan)
     if world > 1:
         dist.barrier()
-    total_ms = sum(times)
-    if world > 1:
-        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = _max_over_ranks(sum(times), dist, world, dev)
     ms_step = total_ms / args.steps
-    value = world * M * system.n / (ms_step * 1e-3)
+    value = _job_value(M * system.n, world, ms_step)
     rho_main = rho.cpu().numpy()
     # end to end through the public API with pinned host buffers (copies inside the call)
     Hh = torch.as_tensor(system.H).pin_memory()
@@ -304,11 +315,7 @@ def run_ndsi(args):
         t0 = time.perf_counter()
         nd.ndsi_density(plan, Hh, Sh, MU, kT, M, rho_h, ne_h, stream=stream)
         e2e_times.append(time.perf_counter() - t0)
-    e2e_s = sum(e2e_times) / len(e2e_times)
-    if world > 1:
-        t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = _max_over_ranks(sum(e2e_times) / len(e2e_times), dist, world, dev)
     # the other precision on the same workload: split-vs-FP64 speedup and rho difference
     other = None
     if not args.no_other and rank == 0:
@@ -437,10 +444,41 @@ def run_batched(args, nd, torch, dist, rank, world, local, prec_code):
     prof_times = timed_steps()
     prof = nd.ndsi_profile_read(plan)
     nd.ndsi_profile_enable(plan, False)
-    ms = sum(times) / len(times)
+    ms = _max_over_ranks(sum(times), dist, world, dev) / len(times)
     ntot = sum(s.n for s in systems)
+    # end to end through the public API with pinned host buffers (copies inside the call)
+    Hh = H.cpu().pin_memory()
+    Sh = S.cpu().pin_memory()
+    rho_h = torch.zeros(nnz, dtype=torch.float64).pin_memory()
+    ne_h = torch.zeros(len(systems), dtype=torch.float64).pin_memory()
+    nd.ndsi_density_batched(plan, Hh, Sh, mus, kts, M, rho_h, ne_h, stream=stream)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    nd.ndsi_density_batched(plan, Hh, Sh, mus, kts, M, rho_h, ne_h, stream=stream)
+    e2e_s = _max_over_ranks(time.perf_counter() - t0, dist, world, dev)
+    # parity outside the timed region: sampled columns of the three smallest systems by sparse
+    # solves per pole (the oracle's column route)
+    parity = None
+    if not args.no_parity and rank == 0:
+        from oracle.dense import density_columns
+        rho_all = rho.cpu().numpy()
+        offs = np.cumsum([0] + [s_.nnz for s_ in systems])
+        rng = np.random.default_rng(12)
+        err, checked = 0.0, []
+        for i in sorted(range(len(systems)), key=lambda i: systems[i].n)[:3]:
+            sy = systems[i]
+            cols = sorted(rng.choice(sy.n, 2, replace=False).tolist())
+            ref = density_columns(sy, MU, kT, M, cols)
+            rows = sy.rows()
+            r_i = rho_all[offs[i]:offs[i + 1]]
+            for t_, j in enumerate(cols):
+                sel = np.nonzero(sy.col == j)[0]
+                err = max(err, float(np.max(np.abs(r_i[sel] - ref[rows[sel], t_]))))
+            checked.append({"system": i, "n": sy.n, "columns": cols})
+        parity = {"max_abs_err_rho": err, "checked": checked,
+                  "tolerance": 1e-10 if args.precision == "fp64" else 1e-9}
     roofline, kern = _roofline(prof, args.steps, _peaks())
-    line = {"metric": METRIC, "value": world * M * ntot / (ms * 1e-3), "unit": UNIT, "n_gpus": world,
+    line = {"metric": METRIC, "value": _job_value(M * ntot, world, ms), "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64" if args.precision == "fp64" else f"bf16x{args.slices}->f64", "data": "synthetic",
@@ -450,11 +488,14 @@ def run_batched(args, nd, torch, dist, rank, world, local, prec_code):
                        "n_total": ntot, "poles": M, "kT": kT, "nnz": nnz, "precision": args.precision,
                        "flops_per_pole": info["flops_per_pole"], "n_levels": info["n_levels"],
                        "l2": "flushed (256 MB write) before every timed step"},
+            "e2e": {"value": _job_value(M * ntot, world, e2e_s * 1e3), "unit": UNIT,
+                    "h2d_bytes_per_step": 2 * 8 * nnz, "d2h_bytes_per_step": 8 * nnz + 8 * len(systems)},
             "gpu_launches": sum(v["launches"] for v in kern.values()),
             "graph": {"kernel_nodes": graph_nodes,
                       "ms_per_step_direct_launches": sum(prof_times) / len(prof_times)},
             "roofline": roofline, "clocks": clk.summary(),
             "n_elec": ne.cpu().numpy().tolist(),
+            "parity": parity,
             "kernels": {k: {"launches": v["launches"] // args.steps, "ms_per_step": v["ms"] / args.steps}
                         for k, v in kern.items()}}
     if rank == 0:
@@ -470,7 +511,7 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ndsi", choices=["ndsi", "reference"])
-    ap.add_argument("--config", default="C2", choices=["C1", "C2", "C3", "C4"])
+    ap.add_argument("--config", default="C2", choices=["C1", "C2", "C3", "C4", "C5"])
     ap.add_argument("--precision", default="fp64", choices=["fp64", "split"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-parity", action="store_true", help="skip the sampled-column check")
