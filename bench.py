@@ -220,7 +220,7 @@ def _autotune(nd, args, plan, H, S, kT, M):
     return {"tensor_core_steps": n_split, "fp64_steps": n_fp64}
 
 
-def _measure(nd, torch, plan, H, S, rho, ne, kT, M, steps, warmup, stream, flush, clocks=None):
+def _measure(nd, torch, plan, H, S, rho, ne, kT, M, steps, warmup, stream, flush, by_level=False):
     """Time `steps` density sweeps as the library runs them (one captured CUDA graph per sweep),
     then repeat them with direct launches and per-launch CUDA events for the kernel breakdown."""
     def step():
@@ -246,7 +246,7 @@ def _measure(nd, torch, plan, H, S, rho, ne, kT, M, steps, warmup, stream, flush
     torch.cuda.profiler.start()
     times = timed_steps()
     torch.cuda.profiler.stop()
-    nd.ndsi_profile_enable(plan, True)
+    nd.ndsi_profile_enable(plan, True, by_level=by_level)
     prof_times = timed_steps()
     prof = nd.ndsi_profile_read(plan)
     nd.ndsi_profile_enable(plan, False)
@@ -277,7 +277,8 @@ def run_ndsi(args):
     kT, M = system.meta["kT"], system.meta["poles"]
     if args.poles:
         M = args.poles
-    plan = nd.analyze_system(system, precision=prec_code[args.precision], split_slices=args.slices)
+    plan = nd.analyze_system(system, precision=prec_code[args.precision], split_slices=args.slices,
+                             outer_block=args.outer, block=args.block)
     info = nd.ndsi_plan_info(plan)
     dev = torch.device("cuda", local)
     H = torch.as_tensor(system.H, device=dev)
@@ -294,7 +295,7 @@ def run_ndsi(args):
         dist.barrier()
     with ClockSampler(local) as clk:
         times, prof, prof_times = _measure(nd, torch, plan, H, S, rho, ne, kT, M, args.steps,
-                                           args.warmup, stream, flush)
+                                           args.warmup, stream, flush, by_level=args.by_level)
         graph_nodes = nd.ndsi_graph_info(plan)
     if world > 1:
         dist.barrier()
@@ -320,7 +321,8 @@ def run_ndsi(args):
     other = None
     if not args.no_other and rank == 0:
         oprec = "split" if args.precision == "fp64" else "fp64"
-        plan2 = nd.analyze_system(system, precision=prec_code[oprec], split_slices=args.slices)
+        plan2 = nd.analyze_system(system, precision=prec_code[oprec], split_slices=args.slices,
+                                  outer_block=args.outer, block=args.block)
         tune2 = _autotune(nd, args, plan2, H, S, kT, M)
         rho2 = torch.zeros_like(rho)
         ne2 = torch.zeros_like(ne)
@@ -404,7 +406,8 @@ def run_batched(args, nd, torch, dist, rank, world, local, prec_code):
     systems = batched_systems()
     M = args.poles or 120
     kT = 0.01
-    plan = nd.analyze_batched(systems, precision=prec_code[args.precision], split_slices=args.slices)
+    plan = nd.analyze_batched(systems, precision=prec_code[args.precision], split_slices=args.slices,
+                              outer_block=args.outer, block=args.block)
     info = nd.ndsi_plan_info(plan)
     dev = torch.device("cuda", local)
     H = torch.as_tensor(np.concatenate([s.H for s in systems]), device=dev)
@@ -505,6 +508,59 @@ def run_batched(args, nd, torch, dist, rank, world, local, prec_code):
     return 0
 
 
+def run_mu_search(args):
+    """Chemical-potential search on the workload, plain (spectral bounds) and seeded by the
+    network trained here on exact-method mu of generated systems: exact density evaluations and
+    wall time per solve.  One JSON line; not part of the default run."""
+    import numpy as np
+    import torch
+    from paper_1005_0088_gb300.build import build
+    build()
+    import paper_1005_0088_gb300 as nd
+    from paper_1005_0088_gb300.mu_seed import MuSeed, build_dataset, features
+    from synth import config_system, mu_training_systems
+    torch.cuda.set_device(0)
+    t0 = time.perf_counter()
+    X, T = build_dataset(mu_training_systems(args.mu_train, 1))
+    t_data = time.perf_counter() - t0
+    model = MuSeed(seed=5)
+    t0 = time.perf_counter()
+    model.train(X, T, steps=3000, lr=3e-3)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    system = config_system(args.config)
+    kT, M = system.meta["kT"], args.poles or system.meta["poles"]
+    plan = nd.analyze_system(system, precision={"fp64": nd.NDSI_PREC_FP64, "split": nd.NDSI_PREC_SPLIT}[args.precision],
+                             split_slices=args.slices)
+    H = torch.as_tensor(system.H, device="cuda")
+    S = torch.as_tensor(system.S, device="cuda")
+    rho = torch.zeros(system.nnz, dtype=torch.float64, device="cuda")
+    ne = torch.zeros(1, dtype=torch.float64, device="cuda")
+    nd.ndsi_density(plan, H, S, MU, kT, M, rho, ne)   # warm: tables, workspace, graph
+    torch.cuda.synchronize()
+    out = {}
+    for mode in ("plain", "seeded"):
+        t0 = time.perf_counter()
+        lo = hi = 0.0
+        if mode == "seeded":
+            lo, hi = model.bracket(features(plan, H, S, system.n_electrons, kT))
+        mu, n_e, it = nd.ndsi_find_mu(plan, H, S, kT, M, system.n_electrons, rho, mu_lo=lo, mu_hi=hi)
+        torch.cuda.synchronize()
+        out[mode] = {"evaluations": it, "ms": (time.perf_counter() - t0) * 1e3, "mu": mu,
+                     "electron_error": n_e - system.n_electrons}
+    line = {"metric": "chemical-potential search: exact density evaluations per solve",
+            "value": out["seeded"]["evaluations"], "unit": "evaluations", "higher_is_better": False,
+            "n_gpus": 1, "data": "synthetic",
+            "config": {"workload": system.meta["label"], "poles": M, "kT": kT, "precision": args.precision,
+                       "n_electrons": system.n_electrons, "tolerance_electrons": 1e-8},
+            "plain": out["plain"], "seeded": out["seeded"],
+            "seed_model": {"training_systems": args.mu_train, "train_rmse_mu": model.rmse,
+                           "dataset_s": t_data, "train_s": t_train,
+                           "bracket_half_width": 3.0 * max(model.rmse or 0.05, 1e-3)}}
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -519,15 +575,27 @@ def main():
                     help="launch every kernel directly instead of replaying a captured CUDA graph")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep every eligible GEMM of a split plan on the tensor cores")
+    ap.add_argument("--by-level", action="store_true",
+                    help="kernel breakdown of GEMM and slicing steps per tree level")
+    ap.add_argument("--outer", type=int, default=0,
+                    help="diagonal-block size of the two-level factorisation (0: library default)")
+    ap.add_argument("--block", type=int, default=0,
+                    help="FP64 pivot block size 16/32/64 (0: library default)")
     ap.add_argument("--slices", type=int, default=6,
                     help="BF16 slices per operand of the split path (4-7)")
     ap.add_argument("--poles", type=int, default=0,
                     help="override the workload's pole count (small profiling runs only)")
     ap.add_argument("--no-other", action="store_true",
                     help="skip the run of the other precision (split-vs-FP64 speedup)")
+    ap.add_argument("--mu-search", action="store_true",
+                    help="time the chemical-potential search, plain and seeded by the trained network")
+    ap.add_argument("--mu-train", type=int, default=2000,
+                    help="generated systems the mu-search network is trained on")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.mu_search:
+        return run_mu_search(args)
     return run_ndsi(args)
 
 

@@ -184,7 +184,8 @@ int ndsi_density(ndsi_plan* plan, const double* H, const double* S, double mu, d
 /* Per-kernel timing.  While enabled, every launch made for this plan by ndsi_factor_poles,
  * ndsi_selinv and ndsi_density is bracketed by CUDA events on its stream; durations, launch
  * counts and the algorithmic flops and bytes of the launches accumulate per kernel family.
- * ndsi_profile_enable(plan, 1) also clears the counters; 0 stops recording. */
+ * ndsi_profile_enable(plan, 1) also clears the counters; 2 does the same and splits the GEMM and
+ * slicing families by tree level (":L<level>" appended to the name); 0 stops recording. */
 typedef struct {
     char name[32];        /* kernel family and schedule step: "gemm_f64:<step>", "slice:<step>",
                              "gemm_split:<step>", diaginv, assemble, scatter, copy, gather,

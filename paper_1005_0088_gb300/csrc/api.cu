@@ -29,6 +29,7 @@ struct ProfRec {
 };
 struct Profiler {
     bool on = false;
+    bool by_level = false;                  // family names carry the tree level (":L<level>")
     int64_t cur_launch = -1;                // schedule launch being issued (run_phase)
     std::vector<double>* per_launch = nullptr;  // when set: ms accumulated per launch index
     std::vector<cudaEvent_t> pool;
@@ -296,7 +297,8 @@ int run_phase(ndsi_plan* h, const Workspace& W, const SplitBuffers& SB, int phas
             const SplitStep& step = h->SP.steps[si];
             const double2* bufs[2] = {W.fronts, W.scr};
             const int64_t strides[2] = {W.front_stride, W.scr_stride};
-            const std::string tg = tag_name(l.tag);
+            const std::string tg = std::string(tag_name(l.tag)) +
+                                   (h->prof.by_level ? ":L" + std::to_string(l.level) : std::string());
             e = timed(h->prof, "slice:" + tg, 0.0, h->SP.slice_bytes[si] * np, st, [&]() {
                 return split_slice_step(l, h->T.gemm_items, h->SP.d_items, h->SP.d_blocks, step, SB,
                                         P.opt.split_slices, bufs[l.bufA], strides[l.bufA], bufs[l.bufB],
@@ -312,7 +314,9 @@ int run_phase(ndsi_plan* h, const Workspace& W, const SplitBuffers& SB, int phas
                     },
                     h->SP.tensor_flops[si] * np);
         } else {
-            e = timed(h->prof, family_of(l), l.flops * np, l.bytes * np, st,
+            e = timed(h->prof,
+                      family_of(l) + (h->prof.by_level && l.kind == L_GEMM ? ":L" + std::to_string(l.level) : std::string()),
+                      l.flops * np, l.bytes * np, st,
                       [&]() { return launch_step(P, h->T, l, W, H, S, z, zstride, np, st); });
         }
         if (e != cudaSuccess)
@@ -1053,6 +1057,7 @@ int ndsi_profile_enable(ndsi_plan* h, int32_t enable) {
     if (!h) return fail(NDSI_ERR_INVALID, "ndsi_profile_enable: NULL plan");
     Profiler& pf = h->prof;
     pf.on = enable != 0;
+    pf.by_level = enable == 2;
     if (pf.on) {
         pf.names.clear();
         pf.stats.clear();

@@ -299,8 +299,8 @@ def ndsi_graph_info(plan: Plan) -> int:
     return n.value
 
 
-def ndsi_profile_enable(plan: Plan, enable: bool = True):
-    _check(load().ndsi_profile_enable(plan.handle, 1 if enable else 0))
+def ndsi_profile_enable(plan: Plan, enable=True, by_level: bool = False):
+    _check(load().ndsi_profile_enable(plan.handle, (2 if by_level else 1) if enable else 0))
 
 
 def ndsi_profile_read(plan: Plan) -> dict:
