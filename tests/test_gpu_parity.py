@@ -198,3 +198,46 @@ def test_singular_pivot_reported():
     with pytest.raises(nd.NdsiError) as ei:
         _selinv(sysm, [0.0])
     assert ei.value.code == nd.ndsi.NDSI_ERR_SINGULAR
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_degenerate_systems(precision):
+    # one atom with one orbital (a 1 x 1 front, no separator), one innermost domain holding the
+    # whole system (no dissection step), and a 2-atom chain split into three one-atom nodes
+    for sysm, leaf in ((lattice_system((1, 1, 1), 1, "1d", 41), 20),
+                       (lattice_system((4, 3, 1), 3, "2d", 42), 20),
+                       (lattice_system((3, 1, 1), 2, "1d", 43), 1)):
+        Hd, Sd = sysm.dense()
+        Z = [0.2 + 0.01j, -1.3 + 0.7j]
+        g = _selinv(sysm, Z, leaf_atoms=leaf, precision=precision)
+        for q, z in enumerate(Z):
+            ref = on_pattern(green_dense(Hd, Sd, z), sysm)
+            assert np.max(np.abs(g[q] - ref)) < 1e-9 * np.max(np.abs(ref))
+
+
+@pytest.mark.parametrize("precision,tol", [(0, RHO_TOL), (1, 1e-9)])
+def test_density_empty_and_full_bands(precision, tol):
+    # mu well below the spectrum: no electrons (rho ~ 0); well above: every state doubly
+    # occupied, rho = 2 S^{-1} on the pattern and Tr(rho S) = 2N (the full-band closed form).
+    # |eps - mu| / kT stays within 120..300, where the 40-pole fraction equals the Fermi
+    # function to ~1e-14 and exp(-120) is negligible.
+    sysm = lattice_system((6, 5, 1), 2, "2d", 44)
+    Hd, Sd = sysm.dense()
+    eps, _ = generalized_eig(Hd, Sd)
+    assert eps.min() > -1.6 and eps.max() < 1.6
+    rho_lo, ne_lo = _density(sysm, -4.0, 0.02, 40, precision=precision)
+    assert np.max(np.abs(rho_lo)) < tol and abs(ne_lo) < 1e-8
+    rho_hi, ne_hi = _density(sysm, 4.0, 0.02, 40, precision=precision)
+    ref = on_pattern(2.0 * np.linalg.inv(Sd), sysm)
+    assert np.max(np.abs(rho_hi - ref)) < tol
+    assert abs(ne_hi - 2 * sysm.n) < 1e-7
+
+
+def test_density_single_pole():
+    # M = 1: one pole pair plus the M0 point, against the oracle's one-pole Fermi function
+    sysm = lattice_system((5, 4, 1), 2, "2d", 45)
+    Hd, Sd = sysm.dense()
+    eps, C = generalized_eig(Hd, Sd)
+    rho_ref = on_pattern(density_eig(eps, C, 0.05, 0.05, 1), sysm)
+    rho, ne = _density(sysm, 0.05, 0.05, 1)
+    assert np.max(np.abs(rho - rho_ref)) < RHO_TOL
