@@ -61,8 +61,10 @@ typedef struct {
 typedef struct {
     int32_t leaf_atoms;          /* innermost-domain threshold of the dissection (default 20) */
     int32_t precision;           /* NDSI_PREC_FP64 or NDSI_PREC_SPLIT (default FP64) */
-    int32_t split_slices;        /* BF16 slices per operand in split mode (default 6) */
-    int32_t block;               /* FP64 pivot block size, 16/32/64 (0 = default 32) */
+    int32_t split_slices;        /* BF16 slices per operand in split mode, 4..7; 0 (default) = by
+                                    plan size: 6, or 7 when the largest front exceeds 4096 (the
+                                    accumulated digit error grows with the inner dimension) */
+    int32_t block;               /* FP64 pivot block size, 16/32/64 (0 = default 16) */
     double m0_radius;            /* R of the zeroth-moment point Z = iR (default 1e7) */
     int64_t max_workspace_bytes; /* device workspace cap; poles are chunked to fit (0 = auto) */
     int32_t outer_block;         /* diagonal-block size of the two-level factorisation of A_J: the
@@ -85,6 +87,7 @@ typedef struct {
     double bytes_per_pole;     /* algorithmic front bytes written + read per pole */
     int32_t n_launches;        /* schedule launches per pole batch (factor + selected inversion) */
     int32_t n_systems;         /* systems in the plan (1 unless built by ndsi_analyze_batched) */
+    int32_t split_slices;      /* slices per operand of a split plan (0 for an FP64 plan) */
 } ndsi_plan_summary;
 
 /* Items for ndsi_plan_export. */

@@ -187,7 +187,7 @@ int analyze(const ndsi_pattern* pat, int32_t n_atoms, const double* centers,
     P.nnz = nnz;
     P.n_atoms = n_atoms;
     P.opt = opt;
-    P.block = opt.block > 0 ? opt.block : 32;
+    P.block = opt.block > 0 ? opt.block : 16;
     if (P.block != 16 && P.block != 32 && P.block != 64) {
         err = "ndsi_analyze: block must be 16, 32 or 64";
         return NDSI_ERR_INVALID;

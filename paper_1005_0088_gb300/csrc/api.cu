@@ -406,6 +406,11 @@ namespace ndsi {
 int density_impl(ndsi_plan* h, const double* Hd, const double* Sd, const double* mu, const double* kT,
                  int32_t n_poles, double* rho_d, double* ne_d, cudaStream_t st);
 
+// Slice count of a split plan when the caller leaves it to the library: six BF16 digits (47
+// bits) keep rho within 1e-9 of the FP64 path on fronts up to a few thousand; on the 3D metallic
+// lattice (largest front 7016, kT = 0.002) six gave 2.0e-9 and seven are needed.
+int auto_slices(const Plan& P) { return P.max_front > 4096 ? 7 : 6; }
+
 // Split-precision metadata of a plan: tensor-core steps, their tile lists and cost figures.
 void setup_split(ndsi_plan* h, const ndsi_options& o) {
     SplitPlan& S = h->SP;
@@ -441,8 +446,8 @@ void ndsi_default_options(ndsi_options* opt) {
     if (!opt) return;
     opt->leaf_atoms = 20;
     opt->precision = NDSI_PREC_FP64;
-    opt->split_slices = 6;
-    opt->block = 32;
+    opt->split_slices = 0;
+    opt->block = 16;
     opt->m0_radius = 1e7;
     opt->max_workspace_bytes = 0;
     opt->outer_block = 128;
@@ -483,10 +488,12 @@ int ndsi_analyze(const ndsi_pattern* pat, int32_t n_atoms, const double* centers
         return fail(rc, err);
     }
     if (o.precision == NDSI_PREC_SPLIT) {
-        if (o.split_slices < 4 || o.split_slices > kSplitMaxSlices) {
+        if (o.split_slices != 0 && (o.split_slices < 4 || o.split_slices > kSplitMaxSlices)) {
             delete h;
-            return fail(NDSI_ERR_INVALID, "ndsi_analyze: split_slices must be in [4, 7]");
+            return fail(NDSI_ERR_INVALID, "ndsi_analyze: split_slices must be 0 or in [4, 7]");
         }
+        if (o.split_slices == 0) o.split_slices = auto_slices(h->P);
+        h->P.opt.split_slices = o.split_slices;
         setup_split(h, o);
     }
     *plan_out = h;
@@ -517,10 +524,12 @@ int ndsi_analyze_batched(int32_t n_systems, const ndsi_pattern* pats, const int3
             return fail(rc, err);
         }
         if (o.precision == NDSI_PREC_SPLIT) {
-            if (o.split_slices < 4 || o.split_slices > kSplitMaxSlices) {
+            if (o.split_slices != 0 && (o.split_slices < 4 || o.split_slices > kSplitMaxSlices)) {
                 delete h;
-                return fail(NDSI_ERR_INVALID, "ndsi_analyze_batched: split_slices must be in [4, 7]");
+                return fail(NDSI_ERR_INVALID, "ndsi_analyze_batched: split_slices must be 0 or in [4, 7]");
             }
+            if (o.split_slices == 0) o.split_slices = auto_slices(h->P);
+            h->P.opt.split_slices = o.split_slices;
             setup_split(h, o);
         }
         *plan_out = h;
@@ -572,6 +581,7 @@ int ndsi_plan_info(const ndsi_plan* h, ndsi_plan_summary* out) {
     out->bytes_per_pole = P.bytes_per_pole;
     out->n_launches = static_cast<int32_t>(P.launches.size());
     out->n_systems = P.n_systems;
+    out->split_slices = P.opt.precision == NDSI_PREC_SPLIT ? P.opt.split_slices : 0;
     return NDSI_OK;
 }
 

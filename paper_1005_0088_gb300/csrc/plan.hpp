@@ -136,7 +136,7 @@ struct Plan {
     std::vector<NodeTile> node_tiles;      // assembly and gather tiles
     std::vector<Launch> launches;
     double flops_per_pole = 0, bytes_per_pole = 0;
-    int32_t block = 32;
+    int32_t block = 16;
     int32_t outer = 128;   // diagonal-block size of the two-level factorisation of A_J
     std::vector<std::vector<int64_t>> level_entries;  // CSR entries scattered per level
     // systems of a batched plan (one for a plain plan)

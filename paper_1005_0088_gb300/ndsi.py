@@ -62,7 +62,8 @@ class ndsi_plan_summary(ctypes.Structure):
                 ("n_nodes", ctypes.c_int32), ("n_levels", ctypes.c_int32),
                 ("max_front", ctypes.c_int32), ("front_elems", ctypes.c_int64),
                 ("flops_per_pole", ctypes.c_double), ("bytes_per_pole", ctypes.c_double),
-                ("n_launches", ctypes.c_int32), ("n_systems", ctypes.c_int32)]
+                ("n_launches", ctypes.c_int32), ("n_systems", ctypes.c_int32),
+                ("split_slices", ctypes.c_int32)]
 
 
 class ndsi_profile_entry(ctypes.Structure):

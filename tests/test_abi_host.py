@@ -122,7 +122,7 @@ def test_invalid_patterns_rejected():
 def test_invalid_options_rejected():
     nd = lib()
     sysm = lattice_system((4, 4, 1), 2, "2d", 3)
-    for opts in (dict(block=24), dict(outer_block=48), dict(outer_block=40, block=16),
+    for opts in (dict(block=24), dict(outer_block=40), dict(outer_block=48, block=32),
                  dict(precision=1, split_slices=3)):
         with pytest.raises(nd.NdsiError) as ei:
             nd.analyze_system(sysm, **opts)
