@@ -61,9 +61,7 @@ typedef struct {
 typedef struct {
     int32_t leaf_atoms;          /* innermost-domain threshold of the dissection (default 20) */
     int32_t precision;           /* NDSI_PREC_FP64 or NDSI_PREC_SPLIT (default FP64) */
-    int32_t split_slices;        /* BF16 slices per operand in split mode, 4..7; 0 (default) = by
-                                    plan size: 6, or 7 when the largest front exceeds 4096 (the
-                                    accumulated digit error grows with the inner dimension) */
+    int32_t split_slices;        /* BF16 slices per operand in split mode, 4..7; 0 (default) = 6 */
     int32_t block;               /* FP64 pivot block size, 16/32/64 (0 = default 16) */
     double m0_radius;            /* R of the zeroth-moment point Z = iR (default 1e7) */
     int64_t max_workspace_bytes; /* device workspace cap; poles are chunked to fit (0 = auto) */
@@ -72,6 +70,12 @@ typedef struct {
                                     panel, trailing update and inverse assembly outside it are the
                                     GEMMs that split mode moves to the tensor cores; a multiple of
                                     `block` (0 = default 128) */
+    int32_t split_bands;         /* TMEM accumulator bands of the split GEMM: 4 (slice products with
+                                    t+u = 2, 3, 4 exact, the rest in one tail accumulator; 64
+                                    complex columns per tile) or 5 (t+u = 2..5 exact; 48 columns,
+                                    about 2^7 more accurate where the tail dominates the error,
+                                    a little slower); 0 (default) = 5 when the largest front
+                                    exceeds 4096, else 4 */
 } ndsi_options;
 
 /* Summary of a plan, filled by ndsi_plan_info. */
@@ -88,6 +92,7 @@ typedef struct {
     int32_t n_launches;        /* schedule launches per pole batch (factor + selected inversion) */
     int32_t n_systems;         /* systems in the plan (1 unless built by ndsi_analyze_batched) */
     int32_t split_slices;      /* slices per operand of a split plan (0 for an FP64 plan) */
+    int32_t split_bands;       /* accumulator bands of a split plan (0 for an FP64 plan) */
 } ndsi_plan_summary;
 
 /* Items for ndsi_plan_export. */

@@ -407,14 +407,22 @@ int density_impl(ndsi_plan* h, const double* Hd, const double* Sd, const double*
                  int32_t n_poles, double* rho_d, double* ne_d, cudaStream_t st);
 
 // Slice count of a split plan when the caller leaves it to the library: six BF16 digits (47
-// bits) keep rho within 1e-9 of the FP64 path on fronts up to a few thousand; on the 3D metallic
-// lattice (largest front 7016, kT = 0.002) six gave 2.0e-9 and seven are needed.
-int auto_slices(const Plan& P) { return P.max_front > 4096 ? 7 : 6; }
+// bits).  A seventh changes nothing with four accumulator bands (the tail accumulator's floor
+// dominates) and little with five.
+int auto_slices(const Plan&) { return 6; }
+
+// Accumulator bands when the caller leaves it to the library.  With four bands the tail
+// accumulator mixes products 2^8 and 2^16 apart and the tensor core drops the low bits of the
+// smaller ones (a floor near 2^-38 of the result, whatever the slice count); five bands keep
+// t+u = 5 exact and move the floor to ~2^-43.  On the 3D metallic lattice (largest front 7016,
+// kT = 0.002) rho moved from 2.0e-9 to 4.0e-11 of the FP64 path for 2% more time; smaller
+// fronts meet 1e-9 with four.
+int auto_bands(const Plan& P) { return P.max_front > 4096 ? 5 : 4; }
 
 // Split-precision metadata of a plan: tensor-core steps, their tile lists and cost figures.
 void setup_split(ndsi_plan* h, const ndsi_options& o) {
     SplitPlan& S = h->SP;
-    build_split_schedule(h->P, o.split_slices, S.items, S.steps, S.tiles, S.blocks);
+    build_split_schedule(h->P, o.split_slices, o.split_bands, S.items, S.steps, S.tiles, S.blocks);
     S.step_of_launch.assign(h->P.launches.size(), -1);
     S.use_split.assign(h->P.launches.size(), 1);
     int k = 0;
@@ -451,6 +459,7 @@ void ndsi_default_options(ndsi_options* opt) {
     opt->m0_radius = 1e7;
     opt->max_workspace_bytes = 0;
     opt->outer_block = 128;
+    opt->split_bands = 0;
 }
 
 int ndsi_poles(int32_t M, double* z_out, double* R_out) {
@@ -492,8 +501,14 @@ int ndsi_analyze(const ndsi_pattern* pat, int32_t n_atoms, const double* centers
             delete h;
             return fail(NDSI_ERR_INVALID, "ndsi_analyze: split_slices must be 0 or in [4, 7]");
         }
+        if (o.split_bands != 0 && o.split_bands != 4 && o.split_bands != 5) {
+            delete h;
+            return fail(NDSI_ERR_INVALID, "ndsi_analyze: split_bands must be 0, 4 or 5");
+        }
         if (o.split_slices == 0) o.split_slices = auto_slices(h->P);
+        if (o.split_bands == 0) o.split_bands = auto_bands(h->P);
         h->P.opt.split_slices = o.split_slices;
+        h->P.opt.split_bands = o.split_bands;
         setup_split(h, o);
     }
     *plan_out = h;
@@ -528,8 +543,14 @@ int ndsi_analyze_batched(int32_t n_systems, const ndsi_pattern* pats, const int3
                 delete h;
                 return fail(NDSI_ERR_INVALID, "ndsi_analyze_batched: split_slices must be 0 or in [4, 7]");
             }
+            if (o.split_bands != 0 && o.split_bands != 4 && o.split_bands != 5) {
+                delete h;
+                return fail(NDSI_ERR_INVALID, "ndsi_analyze_batched: split_bands must be 0, 4 or 5");
+            }
             if (o.split_slices == 0) o.split_slices = auto_slices(h->P);
+            if (o.split_bands == 0) o.split_bands = auto_bands(h->P);
             h->P.opt.split_slices = o.split_slices;
+            h->P.opt.split_bands = o.split_bands;
             setup_split(h, o);
         }
         *plan_out = h;
@@ -582,6 +603,7 @@ int ndsi_plan_info(const ndsi_plan* h, ndsi_plan_summary* out) {
     out->n_launches = static_cast<int32_t>(P.launches.size());
     out->n_systems = P.n_systems;
     out->split_slices = P.opt.precision == NDSI_PREC_SPLIT ? P.opt.split_slices : 0;
+    out->split_bands = P.opt.precision == NDSI_PREC_SPLIT ? P.opt.split_bands : 0;
     return NDSI_OK;
 }
 

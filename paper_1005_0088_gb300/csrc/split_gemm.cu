@@ -32,9 +32,10 @@
 
 namespace ndsi {
 
-void build_split_schedule(const Plan& P, int slices, std::vector<SplitItem>& items,
+void build_split_schedule(const Plan& P, int slices, int bands, std::vector<SplitItem>& items,
                           std::vector<SplitStep>& steps, std::vector<GemmTile>& tiles,
                           std::vector<SliceBlock>& blocks) {
+    const int32_t nc = bands == 5 ? kSplitBNc5 : kSplitBNc;
     items.assign(P.gemm_items.size(), SplitItem{});
     steps.clear();
     tiles.clear();
@@ -42,6 +43,7 @@ void build_split_schedule(const Plan& P, int slices, std::vector<SplitItem>& ite
     for (const Launch& l : P.launches) {
         if (!split_eligible(l)) continue;
         SplitStep st{};
+        st.nc = nc;
         int32_t kmax = 0;
         st.tfirst = static_cast<int64_t>(tiles.size());
         st.sa_first = static_cast<int64_t>(blocks.size());
@@ -49,7 +51,7 @@ void build_split_schedule(const Plan& P, int slices, std::vector<SplitItem>& ite
             const GemmItem& g = P.gemm_items[l.first + i];
             SplitItem& s = items[l.first + i];
             s.Mpad = (g.M + kSplitBM - 1) / kSplitBM * kSplitBM;
-            s.Npad = (g.N + kSplitBNc - 1) / kSplitBNc * kSplitBNc;
+            s.Npad = (g.N + nc - 1) / nc * nc;
             s.Kpad = (g.K + kSplitKB - 1) / kSplitKB * kSplitKB;
             s.rowA = st.rowsA;
             s.rowB = st.rowsB;
@@ -61,7 +63,7 @@ void build_split_schedule(const Plan& P, int slices, std::vector<SplitItem>& ite
             st.erowsB += s.Npad;
             kmax = std::max(kmax, s.Kpad);
             for (int32_t m0 = 0; m0 < g.M; m0 += kSplitBM)
-                for (int32_t n0 = 0; n0 < g.N; n0 += kSplitBNc) {
+                for (int32_t n0 = 0; n0 < g.N; n0 += nc) {
                     if (l.lower && n0 > m0 + kSplitBM - 1) continue;
                     tiles.push_back(GemmTile{static_cast<int32_t>(i), m0, n0, 0});
                 }
@@ -194,6 +196,15 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
     for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+__device__ __forceinline__ void tmem_ld4(uint32_t taddr, float* v) {
+    uint32_t r[4];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 4; ++i) v[i] = __uint_as_float(r[i]);
+}
 __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float* v) {
     uint32_t r[8];
     asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
@@ -214,8 +225,10 @@ __device__ __forceinline__ uint64_t sdesc_sw64(uint32_t saddr) {
     d |= static_cast<uint64_t>(4) << 61;
     return d;
 }
-// Instruction descriptor: D = F32, A = B = BF16, both K-major, N = 128, M = 128.
-constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((128u >> 3) << 17) | ((128u >> 4) << 24);
+// Instruction descriptor: D = F32, A = B = BF16, both K-major, M = 128, N = n (multiple of 16).
+__host__ __device__ constexpr uint32_t idesc_bf16(uint32_t n) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((n >> 3) << 17) | ((128u >> 4) << 24);
+}
 
 // float-float accumulation hi + lo += v (Knuth's two-sum).
 __device__ __forceinline__ void ff_add(float& hi, float& lo, float v) {
@@ -399,6 +412,7 @@ struct SliceArgs {
     int32_t* expo;
     int64_t erows_pole;
     int rows, ldt;  // one-pass slicer: rows per block and shared-memory row stride
+    int nc;         // complex columns per output tile (B slices: groups of nc [Re|-Im], nc [Im|Re])
 };
 
 // Slices of one block of kSplitSliceRows rows of the stacked operand (A: rows m of op(A); B:
@@ -489,7 +503,7 @@ __global__ void __launch_bounds__(256, 3) k_slice(const SliceArgs p) {
                 o0 = pole * p.rows_pole + si.rowA + grow;
                 ost = si.Mpad;
             } else {
-                o0 = pole * p.rows_pole + si.rowB + (grow / 64) * 128 + (grow % 64);
+                o0 = pole * p.rows_pole + si.rowB + (grow / p.nc) * (2 * p.nc) + (grow % p.nc);
                 ost = 2 * si.Npad;
             }
             const double2 v0 = tile[rr][kk];
@@ -514,7 +528,7 @@ __global__ void __launch_bounds__(256, 3) k_slice(const SliceArgs p) {
                     *reinterpret_cast<uint32_t*>(o1 + si.Kpad + col) = wim[t];
                 } else {
                     // rows [Re | -Im] and [Im | Re]; negation flips the BF16 sign bits
-                    uint16_t* o2 = o1 + 64 * static_cast<int64_t>(p.Kcols);
+                    uint16_t* o2 = o1 + p.nc * static_cast<int64_t>(p.Kcols);
                     *reinterpret_cast<uint32_t*>(o1 + col) = wre[t];
                     *reinterpret_cast<uint32_t*>(o1 + si.Kpad + col) = wim[t] ^ 0x80008000u;
                     *reinterpret_cast<uint32_t*>(o2 + col) = wim[t];
@@ -595,7 +609,7 @@ __global__ void __launch_bounds__(256) k_slice1(const SliceArgs p) {
             o0 = pole * p.rows_pole + si.rowA + grow;
             ost = si.Mpad;
         } else {
-            o0 = pole * p.rows_pole + si.rowB + (grow / 64) * 128 + (grow % 64);
+            o0 = pole * p.rows_pole + si.rowB + (grow / p.nc) * (2 * p.nc) + (grow % p.nc);
             ost = 2 * si.Npad;
         }
         const double2 v0 = kk < K ? t1[rr * ldt + kk] : make_double2(0.0, 0.0);
@@ -620,7 +634,7 @@ __global__ void __launch_bounds__(256) k_slice1(const SliceArgs p) {
                 *reinterpret_cast<uint32_t*>(o1 + si.Kpad + kk) = wim[t];
             } else {
                 // rows [Re | -Im] and [Im | Re]; negation flips the BF16 sign bits
-                uint16_t* o2 = o1 + 64 * static_cast<int64_t>(p.Kcols);
+                uint16_t* o2 = o1 + p.nc * static_cast<int64_t>(p.Kcols);
                 *reinterpret_cast<uint32_t*>(o1 + kk) = wre[t];
                 *reinterpret_cast<uint32_t*>(o1 + si.Kpad + kk) = wim[t] ^ 0x80008000u;
                 *reinterpret_cast<uint32_t*>(o2 + kk) = wim[t];
@@ -656,19 +670,30 @@ constexpr int kTileBytes = kSplitBM * kSplitKB * 2;  // 128 rows x 64 bytes
 constexpr int kThreads = 576;
 constexpr int kEpiWarps = 16;
 
-template <int S>
-constexpr int split_smem_bytes() {
+template <int NC>
+__host__ __device__ constexpr int tile_bytes_b() { return 2 * NC * kSplitKB * 2; }  // 2NC rows x 64 bytes
+template <int S, int NC>
+__host__ __device__ constexpr int stage_bytes() { return S * (kTileBytes + tile_bytes_b<NC>()); }
+template <int S, int NC>
+__host__ __device__ constexpr int split_smem_bytes() {
     // pipeline tiles, then barriers (128 B) and the tile's row / column exponents (768 B), plus
     // up to 1 KB lost to aligning the tiles to 1024 bytes
-    return 2 * 2 * S * kTileBytes + 128 + 768 + 1024;
+    return 2 * stage_bytes<S, NC>() + 128 + 768 + 1024;
 }
 
-template <int S>
+template <int S, int NC>
 __global__ void __launch_bounds__(kThreads, 1)
     k_gemm_split(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const GemmArgs p) {
+    constexpr int BANDS = NC == kSplitBNc ? 4 : 5;  // TMEM accumulators: BANDS x 2NC columns <= 512
+    constexpr int NB = 2 * NC;                       // accumulator columns per band (Re | Im)
+    constexpr int CW = NC / 4;                       // complex columns per epilogue warp
+    constexpr int kTileB = tile_bytes_b<NC>();
+    constexpr int kStage = stage_bytes<S, NC>();
+    constexpr uint32_t kId = idesc_bf16(NB);
+    static_assert(BANDS * NB <= 512, "accumulators exceed TMEM");
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + 2 * 2 * S * kTileBytes);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + 2 * kStage);
     uint64_t* full = bars;            // [2]
     uint64_t* empty = bars + 2;       // [2]
     uint64_t* chunk_full = bars + 4;
@@ -701,8 +726,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tmem_holder;
-    auto a_tile = [&](int stage, int t) { return smem + (stage * 2 * S + t) * kTileBytes; };
-    auto b_tile = [&](int stage, int u) { return smem + (stage * 2 * S + S + u) * kTileBytes; };
+    auto a_tile = [&](int stage, int t) { return smem + stage * kStage + t * kTileBytes; };
+    auto b_tile = [&](int stage, int u) { return smem + stage * kStage + S * kTileBytes + u * kTileB; };
 
     if (warp == 0) {
         if (lane == 0) {
@@ -715,7 +740,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 const SplitItem si = p.sitems[p.ifirst + tile.item];
                 const int nkb = nkb_of(tile);
                 const int yA0 = static_cast<int>(pole * p.rowsA + si.rowA + tile.m0);
-                const int yB0 = static_cast<int>(pole * p.rowsB + si.rowB + (tile.n0 / kSplitBNc) * 128);
+                const int yB0 = static_cast<int>(pole * p.rowsB + si.rowB + (tile.n0 / NC) * NB);
                 bool ok = true;
                 for (int kb = 0; kb < nkb; ++kb, ++g) {
                     const int stage = static_cast<int>(g & 1);
@@ -723,7 +748,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                         ok = false;
                         break;
                     }
-                    mbar_expect_tx(&full[stage], 2 * S * kTileBytes);
+                    mbar_expect_tx(&full[stage], kStage);
 #pragma unroll
                     for (int t = 0; t < S; ++t)
                         tma_load_2d(a_tile(stage, t), &tmA, kb * kSplitKB, yA0 + t * si.Mpad, &full[stage]);
@@ -770,23 +795,24 @@ __global__ void __launch_bounds__(kThreads, 1)
                     const uint64_t da0 = sdesc_sw64(smem_u32(a_tile(stage, 0)));
                     const uint64_t db0 = sdesc_sw64(smem_u32(b_tile(stage, 0)));
                     const uint32_t fresh = first_in_chunk ? 0u : 1u;
-                    // band 3: slice pairs with t+u >= 5 (1-based), read out per chunk like the others
+                    // tail band BANDS-1: slice pairs with t+u >= BANDS+1 (1-based), read out per chunk
+                    // like the others
 #pragma unroll
                     for (int t = 0; t < S; ++t)
 #pragma unroll
                         for (int u = 0; u < S; ++u) {
-                            if (t + u > S - 1 || t + u < 3) continue;
-                            const bool lead = (t + u == 3) && t == 0;  // first tail product of a K-block
+                            if (t + u > S - 1 || t + u < BANDS - 1) continue;
+                            const bool lead = (t + u == BANDS - 1) && t == 0;  // first tail product of a K-block
 #pragma unroll
                             for (int ks = 0; ks < 2; ++ks) {
                                 const uint64_t da = da0 + static_cast<uint64_t>((t * kTileBytes + ks * 32) >> 4);
-                                const uint64_t db = db0 + static_cast<uint64_t>((u * kTileBytes + ks * 32) >> 4);
-                                umma_bf16(tmem + 3 * 128, da, db, kIdesc, (lead && ks == 0) ? fresh : 1u);
+                                const uint64_t db = db0 + static_cast<uint64_t>((u * kTileB + ks * 32) >> 4);
+                                umma_bf16(tmem + (BANDS - 1) * NB, da, db, kId, (lead && ks == 0) ? fresh : 1u);
                             }
                         }
-                    // bands 0..2: t+u = 2, 3, 4 (1-based), exact within a chunk
+                    // exact bands 0..BANDS-2: t+u = 2 .. BANDS (1-based), one scale each
 #pragma unroll
-                    for (int band = 0; band < 3; ++band) {
+                    for (int band = 0; band < BANDS - 1; ++band) {
 #pragma unroll
                         for (int t = 0; t < S; ++t) {
                             const int u = band - t;
@@ -794,8 +820,8 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
                             for (int ks = 0; ks < 2; ++ks) {
                                 const uint64_t da = da0 + static_cast<uint64_t>((t * kTileBytes + ks * 32) >> 4);
-                                const uint64_t db = db0 + static_cast<uint64_t>((u * kTileBytes + ks * 32) >> 4);
-                                umma_bf16(tmem + band * 128, da, db, kIdesc, (t == 0 && ks == 0) ? fresh : 1u);
+                                const uint64_t db = db0 + static_cast<uint64_t>((u * kTileB + ks * 32) >> 4);
+                                umma_bf16(tmem + band * NB, da, db, kId, (t == 0 && ks == 0) ? fresh : 1u);
                             }
                         }
                     }
@@ -832,7 +858,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             if (et < 128) {
                 const int m = tile.m0 + et;
                 sm_ea[et] = m < it.M ? p.expA[pole * p.erowsA + si.erowA + m] : 0;
-            } else if (et < 192) {
+            } else if (et < 128 + NC) {
                 const int n = tile.n0 + et - 128;
                 sm_eb[et - 128] = n < it.N ? p.expB[pole * p.erowsB + si.erowB + n] : 0;
             }
@@ -840,17 +866,17 @@ __global__ void __launch_bounds__(kThreads, 1)
                 // pull the C block the final update reads towards L2 while the MMAs run
 #pragma unroll
                 for (int u = 0; u < 2; ++u) {
-                    const int line = et + u * kEpiWarps * 32;  // 64 columns x 16 lines of 128 B
+                    const int line = et + u * kEpiWarps * 32;  // NC columns x 16 lines of 128 B
                     const int j = line >> 4, r = (line & 15) * 8;
                     const int m = tile.m0 + r, n = tile.n0 + j;
-                    if (m < it.M && n < it.N && !(p.lower && n > tile.m0 + 127))
+                    if (j < NC && m < it.M && n < it.N && !(p.lower && n > tile.m0 + 127))
                         asm volatile("prefetch.global.L2 [%0];" ::"l"(Cp + m + static_cast<int64_t>(n) * it.ldc));
                 }
             }
             asm volatile("bar.sync 1, %0;" ::"n"(kEpiWarps * 32) : "memory");
-            float hi[32], lo[32];
+            float hi[2 * CW], lo[2 * CW];  // [0, CW): Re, [CW, 2CW): Im of this warp's columns
 #pragma unroll
-            for (int j = 0; j < 32; ++j) {
+            for (int j = 0; j < 2 * CW; ++j) {
                 hi[j] = 0.f;
                 lo[j] = 0.f;
             }
@@ -861,15 +887,25 @@ __global__ void __launch_bounds__(kThreads, 1)
                 }
                 tc_fence_after();
 #pragma unroll
-                for (int band = 0; band < 4; ++band) {
+                for (int band = 0; band < BANDS; ++band) {
 #pragma unroll
-                    for (int j2 = 0; j2 < 4; ++j2) {
-                        // j2 0,1: Re columns 16cg + 0..15; j2 2,3: the matching Im columns
-                        float v[8];
-                        const int col = (j2 >> 1) * 64 + cg * 16 + (j2 & 1) * 8;
-                        tmem_ld8(tmem + (static_cast<uint32_t>(32 * q) << 16) + band * 128 + col, v);
+                    for (int part = 0; part < 2; ++part) {  // Re columns, then the matching Im columns
+                        const uint32_t base = tmem + (static_cast<uint32_t>(32 * q) << 16) + band * NB +
+                                              part * NC + cg * CW;
 #pragma unroll
-                        for (int i = 0; i < 8; ++i) ff_add(hi[j2 * 8 + i], lo[j2 * 8 + i], v[i]);
+                        for (int j0 = 0; j0 + 8 <= CW; j0 += 8) {
+                            float v[8];
+                            tmem_ld8(base + j0, v);
+#pragma unroll
+                            for (int i = 0; i < 8; ++i) ff_add(hi[part * CW + j0 + i], lo[part * CW + j0 + i], v[i]);
+                        }
+                        if (CW % 8) {
+                            float v[4];
+                            tmem_ld4(base + (CW / 8) * 8, v);
+#pragma unroll
+                            for (int i = 0; i < 4; ++i)
+                                ff_add(hi[part * CW + (CW / 8) * 8 + i], lo[part * CW + (CW / 8) * 8 + i], v[i]);
+                        }
                     }
                 }
                 tc_fence_before();
@@ -886,14 +922,14 @@ __global__ void __launch_bounds__(kThreads, 1)
             if (m < it.M) {
                 const int ea = sm_ea[r] - 14;
 #pragma unroll
-                for (int j = 0; j < 16; ++j) {
-                    const int jc = cg * 16 + j;
+                for (int j = 0; j < CW; ++j) {
+                    const int jc = cg * CW + j;
                     const int n = tile.n0 + jc;
                     if (n >= it.N || (p.lower && n > m)) continue;
                     double2* dst = Cp + m + static_cast<int64_t>(n) * it.ldc;
                     const int e = ea + sm_eb[jc];
                     double re = ff_to_double_scaled(hi[j], lo[j], e, neg_alpha);
-                    double im = ff_to_double_scaled(hi[16 + j], lo[16 + j], e, neg_alpha);
+                    double im = ff_to_double_scaled(hi[CW + j], lo[CW + j], e, neg_alpha);
                     if (add_c) {
                         const double2 old = *dst;
                         re += old.x;
@@ -921,8 +957,11 @@ int g_num_sms = 148;  // multiprocessors of the current device (persistent grid 
 
 template <int S>
 cudaError_t set_attrs() {
-    cudaError_t e = cudaFuncSetAttribute(k_gemm_split<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         split_smem_bytes<S>());
+    cudaError_t e = cudaFuncSetAttribute(k_gemm_split<S, kSplitBNc>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         split_smem_bytes<S, kSplitBNc>());
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k_gemm_split<S, kSplitBNc5>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             split_smem_bytes<S, kSplitBNc5>());
     if (e != cudaSuccess) return e;
     return cudaFuncSetAttribute(k_slice1<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSplitSlice1Smem);
 }
@@ -958,10 +997,10 @@ void split_free(SplitBuffers& B) {
     B = SplitBuffers{};
 }
 
-static cudaError_t encode(CUtensorMap* map, void* base, int64_t cols, int64_t rows) {
+static cudaError_t encode(CUtensorMap* map, void* base, int64_t cols, int64_t rows, int box_rows) {
     cuuint64_t dims[2] = {static_cast<cuuint64_t>(cols), static_cast<cuuint64_t>(rows)};
     cuuint64_t strides[1] = {static_cast<cuuint64_t>(cols * 2)};
-    cuuint32_t box[2] = {static_cast<cuuint32_t>(kSplitKB), static_cast<cuuint32_t>(kSplitBM)};
+    cuuint32_t box[2] = {static_cast<cuuint32_t>(kSplitKB), static_cast<cuuint32_t>(box_rows)};
     cuuint32_t estr[2] = {1, 1};
     CUresult r = g_encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, base, dims, strides, box, estr,
                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
@@ -994,8 +1033,10 @@ cudaError_t split_alloc(SplitBuffers& B, const std::vector<SplitStep>& steps, in
     B.tmB.assign(steps.size(), CUtensorMap{});
     for (size_t i = 0; i < steps.size(); ++i) {
         const SplitStep& s = steps[i];
-        if ((e = encode(&B.tmA[i], B.sliceA, s.Kcols, std::max<int64_t>(s.rowsA * np, 128))) != cudaSuccess) return e;
-        if ((e = encode(&B.tmB[i], B.sliceB, s.Kcols, std::max<int64_t>(s.rowsB * np, 128))) != cudaSuccess) return e;
+        if ((e = encode(&B.tmA[i], B.sliceA, s.Kcols, std::max<int64_t>(s.rowsA * np, 128), kSplitBM)) != cudaSuccess)
+            return e;
+        if ((e = encode(&B.tmB[i], B.sliceB, s.Kcols, std::max<int64_t>(s.rowsB * np, 128), 2 * s.nc)) != cudaSuccess)
+            return e;
     }
     return cudaSuccess;
 }
@@ -1006,9 +1047,9 @@ static cudaError_t run_slice(const Launch& l, const GemmItem* items_dev, const S
                              const double2* Abuf, int64_t sA, const double2* Bbuf, int64_t sB, int np,
                              cudaStream_t st) {
     SliceArgs sa{items_dev, sitems_dev, blocks_dev, step.sa_first, l.first, Abuf, sA, l.opA, 0,
-                 B.sliceA, step.rowsA, step.Kcols, B.expA, step.erowsA, step.slice_rows, step.slice_ldt};
+                 B.sliceA, step.rowsA, step.Kcols, B.expA, step.erowsA, step.slice_rows, step.slice_ldt, step.nc};
     SliceArgs sb{items_dev, sitems_dev, blocks_dev, step.sb_first, l.first, Bbuf, sB, l.opB, 1,
-                 B.sliceB, step.rowsB, step.Kcols, B.expB, step.erowsB, step.slice_rows, step.slice_ldt};
+                 B.sliceB, step.rowsB, step.Kcols, B.expB, step.erowsB, step.slice_rows, step.slice_ldt, step.nc};
     if (step.slice_ldt > 0) {
         const size_t sm = static_cast<size_t>(step.slice_rows) * step.slice_ldt * sizeof(double2);
         k_slice1<S><<<dim3(static_cast<unsigned>(step.sa_count), np), 256, sm, st>>>(sa);
@@ -1037,7 +1078,12 @@ static cudaError_t run_mma(const Launch& l, int step_index, const GemmItem* item
     ga.np = np;
     const int64_t work = step.tcount * np;
     const unsigned grid = static_cast<unsigned>(std::max<int64_t>(1, std::min<int64_t>(work, g_num_sms)));
-    k_gemm_split<S><<<grid, kThreads, split_smem_bytes<S>(), st>>>(B.tmA[step_index], B.tmB[step_index], ga);
+    if (step.nc == kSplitBNc5)
+        k_gemm_split<S, kSplitBNc5><<<grid, kThreads, split_smem_bytes<S, kSplitBNc5>(), st>>>(B.tmA[step_index],
+                                                                                             B.tmB[step_index], ga);
+    else
+        k_gemm_split<S, kSplitBNc><<<grid, kThreads, split_smem_bytes<S, kSplitBNc>(), st>>>(B.tmA[step_index],
+                                                                                           B.tmB[step_index], ga);
     return cudaGetLastError();
 }
 
@@ -1069,12 +1115,12 @@ cudaError_t split_mma_step(const Launch& l, int step_index, const GemmItem* item
 
 double split_executed_flops(const Plan& P, const SplitStep& step, const std::vector<SplitItem>& items,
                             const std::vector<GemmTile>& tiles, const Launch& l, int slices) {
-    // real MACs issued by the tensor cores: per tile 128 x 128 x (2 Kpad) per slice pair
+    // real MACs issued by the tensor cores: per tile 128 x 2nc x (2 Kpad) per slice pair
     const int pairs = slices * (slices + 1) / 2;
     double macs = 0;
     for (int64_t t = step.tfirst; t < step.tfirst + step.tcount; ++t) {
         const SplitItem& si = items[l.first + tiles[t].item];
-        macs += 128.0 * 128.0 * 2.0 * si.Kpad * pairs;
+        macs += 128.0 * (2.0 * step.nc) * 2.0 * si.Kpad * pairs;
     }
     (void)P;
     return 2.0 * macs;

@@ -10,9 +10,12 @@
 
 namespace ndsi {
 
-// Tile of the split GEMM: 128 output rows x 64 complex output columns.
+// Tile of the split GEMM: 128 output rows x NC complex output columns, NC = 64 with four TMEM
+// accumulator bands (slice products t+u = 2, 3, 4 exact, the rest in a tail band) or NC = 48 with
+// five (t+u = 2..5 exact, the rest in the tail; 5 x 96 TMEM columns), the accurate variant.
 constexpr int kSplitBM = 128;
-constexpr int kSplitBNc = 64;      // complex columns per tile (128 rows of the stacked B operand)
+constexpr int kSplitBNc = 64;      // complex columns per tile, four-band variant
+constexpr int kSplitBNc5 = 48;     // complex columns per tile, five-band variant
 constexpr int kSplitSliceRows = 32;  // operand rows per slicing block (two-pass slicer)
 constexpr int kSplitSlice1Smem = 72 * 1024;  // shared-memory budget of the one-pass slicer
 constexpr int kSplitKB = 32;       // K per pipeline stage (64-byte rows, 64B swizzle)
@@ -27,7 +30,7 @@ constexpr int kSplitMaxSlices = 7;
 struct SplitItem {
     int64_t rowA, rowB;     // first slice row of the item (A: S*Mpad rows, B: S*2*Npad rows)
     int64_t erowA, erowB;   // first exponent of the item
-    int32_t Mpad, Npad;     // Mpad multiple of 128 rows, Npad multiple of 64 complex columns
+    int32_t Mpad, Npad;     // Mpad multiple of 128 rows, Npad multiple of nc complex columns
     int32_t Kpad, pad;      // multiple of 32 (complex K); stacked K is 2*Kpad
 };
 
@@ -35,6 +38,7 @@ struct SplitItem {
 struct SplitStep {
     int64_t rowsA, rowsB, erowsA, erowsB;  // per pole
     int32_t Kcols;                         // row length of the slice buffers (2*max Kpad)
+    int32_t nc;                            // complex columns per output tile (64 or 48)
     int32_t slice_rows;                    // operand rows per slicing block
     int32_t slice_ldt;                     // one-pass slicing: shared-memory row stride (0: two passes)
     int32_t pad;
@@ -49,7 +53,7 @@ struct SliceBlock {
 };
 
 // Build the split metadata of every GEMM launch (called by the analysis in split mode).
-void build_split_schedule(const Plan& P, int slices, std::vector<SplitItem>& items,
+void build_split_schedule(const Plan& P, int slices, int bands, std::vector<SplitItem>& items,
                           std::vector<SplitStep>& steps, std::vector<GemmTile>& tiles,
                           std::vector<SliceBlock>& blocks);
 

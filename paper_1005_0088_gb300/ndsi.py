@@ -54,7 +54,7 @@ class ndsi_options(ctypes.Structure):
     _fields_ = [("leaf_atoms", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("split_slices", ctypes.c_int32), ("block", ctypes.c_int32),
                 ("m0_radius", ctypes.c_double), ("max_workspace_bytes", ctypes.c_int64),
-                ("outer_block", ctypes.c_int32)]
+                ("outer_block", ctypes.c_int32), ("split_bands", ctypes.c_int32)]
 
 
 class ndsi_plan_summary(ctypes.Structure):
@@ -63,7 +63,7 @@ class ndsi_plan_summary(ctypes.Structure):
                 ("max_front", ctypes.c_int32), ("front_elems", ctypes.c_int64),
                 ("flops_per_pole", ctypes.c_double), ("bytes_per_pole", ctypes.c_double),
                 ("n_launches", ctypes.c_int32), ("n_systems", ctypes.c_int32),
-                ("split_slices", ctypes.c_int32)]
+                ("split_slices", ctypes.c_int32), ("split_bands", ctypes.c_int32)]
 
 
 class ndsi_profile_entry(ctypes.Structure):

@@ -119,3 +119,38 @@ def test_autotune_keeps_accuracy():
     torch.cuda.synchronize()
     assert nd.ndsi_graph_info(plan) > 0
     assert np.max(np.abs(rho.cpu().numpy() - ref)) < RHO_TOL_SPLIT
+
+
+def test_five_band_accumulation_is_more_accurate():
+    # Five TMEM bands keep slice products with t+u = 5 exact; four leave them in the tail
+    # accumulator, where the tensor core drops low bits of the smaller products.  Five is markedly
+    # closer to the dense inverse.
+    nd = lib()
+    sysm = lattice_system((6, 6, 5), 3, "3d", 5)
+    Hd, Sd = sysm.dense()
+    Z = [-0.2 + 0.004j, 0.3 + 0.02j]
+    errs = {}
+    for bands in (4, 5):
+        g = _selinv(sysm, Z, leaf_atoms=12, precision=nd.NDSI_PREC_SPLIT, split_bands=bands)
+        errs[bands] = max(np.max(np.abs(g[q] - on_pattern(green_dense(Hd, Sd, z), sysm))) /
+                          np.max(np.abs(on_pattern(green_dense(Hd, Sd, z), sysm))) for q, z in enumerate(Z))
+    print(f"split G rel err: 4 bands {errs[4]:.2e}, 5 bands {errs[5]:.2e}")
+    # Im z = 0.004 is closer to the real axis than any pole of the configs (pi kT >= 0.0063):
+    # four bands lose ~4e-9 here, five stay well inside the tolerance
+    assert errs[5] < 1e-9
+    assert errs[5] < errs[4] / 4
+
+
+@pytest.mark.parametrize("bands", [4, 5])
+def test_split_density_bands(bands):
+    rho, ne, ref = _rho_split_bands(lattice_system((6, 6, 6), 2, "3d", 123), 0.01, 40, bands)
+    assert np.max(np.abs(rho - ref)) < RHO_TOL_SPLIT
+
+
+def _rho_split_bands(sysm, kT, M, bands):
+    Hd, Sd = sysm.dense()
+    eps, C = generalized_eig(Hd, Sd)
+    mu = find_mu_eig(eps, kT, sysm.n_electrons, M)
+    ref = on_pattern(density_eig(eps, C, mu, kT, M), sysm)
+    rho, ne = _density(sysm, mu, kT, M, precision=lib().NDSI_PREC_SPLIT, split_bands=bands)
+    return rho, ne, ref
