@@ -278,7 +278,7 @@ def run_ndsi(args):
     if args.poles:
         M = args.poles
     plan = nd.analyze_system(system, precision=prec_code[args.precision], split_slices=args.slices,
-                             outer_block=args.outer, block=args.block)
+                             outer_block=args.outer, block=args.block, split_bands=args.bands)
     info = nd.ndsi_plan_info(plan)
     dev = torch.device("cuda", local)
     H = torch.as_tensor(system.H, device=dev)
@@ -322,7 +322,7 @@ def run_ndsi(args):
     if not args.no_other and rank == 0:
         oprec = "split" if args.precision == "fp64" else "fp64"
         plan2 = nd.analyze_system(system, precision=prec_code[oprec], split_slices=args.slices,
-                                  outer_block=args.outer, block=args.block)
+                                  outer_block=args.outer, block=args.block, split_bands=args.bands)
         tune2 = _autotune(nd, args, plan2, H, S, kT, M)
         rho2 = torch.zeros_like(rho)
         ne2 = torch.zeros_like(ne)
@@ -367,11 +367,12 @@ def run_ndsi(args):
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": ms_step,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f64" if args.precision == "fp64" else f"bf16x{args.slices}->f64",
+            "dtype": "f64" if args.precision == "fp64" else f"bf16x{info['split_slices']}->f64",
             "data": "synthetic",
             "config": {"workload": system.meta["label"] + f", {M} poles, {args.precision} path",
                        "n": system.n, "poles": M, "kT": kT, "mu": MU, "nnz": system.nnz,
-                       "precision": args.precision, "split_slices": args.slices,
+                       "precision": args.precision, "split_slices": info["split_slices"],
+                       "split_bands": info["split_bands"],
                        "l2": "flushed (256 MB write) before every timed step",
                        "flops_per_pole": info["flops_per_pole"], "parallelism": f"replicas x{world}"},
             "e2e": {"value": world * M * system.n / e2e_s, "unit": UNIT,
@@ -407,7 +408,7 @@ def run_batched(args, nd, torch, dist, rank, world, local, prec_code):
     M = args.poles or 120
     kT = 0.01
     plan = nd.analyze_batched(systems, precision=prec_code[args.precision], split_slices=args.slices,
-                              outer_block=args.outer, block=args.block)
+                              outer_block=args.outer, block=args.block, split_bands=args.bands)
     info = nd.ndsi_plan_info(plan)
     dev = torch.device("cuda", local)
     H = torch.as_tensor(np.concatenate([s.H for s in systems]), device=dev)
@@ -484,7 +485,7 @@ def run_batched(args, nd, torch, dist, rank, world, local, prec_code):
     line = {"metric": METRIC, "value": _job_value(M * ntot, world, ms), "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f64" if args.precision == "fp64" else f"bf16x{args.slices}->f64", "data": "synthetic",
+            "dtype": "f64" if args.precision == "fp64" else f"bf16x{info['split_slices']}->f64", "data": "synthetic",
             "config": {"workload": f"batched: {M} poles x {len(systems)} uneven systems "
                                    f"(N {min(s.n for s in systems)}..{max(s.n for s in systems)}), "
                                    f"{args.precision} path, one launch per tree level",
@@ -581,8 +582,10 @@ def main():
                     help="diagonal-block size of the two-level factorisation (0: library default)")
     ap.add_argument("--block", type=int, default=0,
                     help="FP64 pivot block size 16/32/64 (0: library default)")
-    ap.add_argument("--slices", type=int, default=6,
-                    help="BF16 slices per operand of the split path (4-7)")
+    ap.add_argument("--bands", type=int, default=0,
+                    help="TMEM accumulator bands of the split GEMM, 4 or 5 (0: the library's choice)")
+    ap.add_argument("--slices", type=int, default=0,
+                    help="BF16 slices per operand of the split path (4-7; 0: the library's choice)")
     ap.add_argument("--poles", type=int, default=0,
                     help="override the workload's pole count (small profiling runs only)")
     ap.add_argument("--no-other", action="store_true",

@@ -74,8 +74,7 @@ typedef struct {
                                     t+u = 2, 3, 4 exact, the rest in one tail accumulator; 64
                                     complex columns per tile) or 5 (t+u = 2..5 exact; 48 columns,
                                     about 2^7 more accurate where the tail dominates the error,
-                                    a little slower); 0 (default) = 5 when the largest front
-                                    exceeds 4096, else 4 */
+                                    about as fast); 0 (default) = 5 */
 } ndsi_options;
 
 /* Summary of a plan, filled by ndsi_plan_info. */

@@ -415,9 +415,9 @@ int auto_slices(const Plan&) { return 6; }
 // accumulator mixes products 2^8 and 2^16 apart and the tensor core drops the low bits of the
 // smaller ones (a floor near 2^-38 of the result, whatever the slice count); five bands keep
 // t+u = 5 exact and move the floor to ~2^-43.  On the 3D metallic lattice (largest front 7016,
-// kT = 0.002) rho moved from 2.0e-9 to 4.0e-11 of the FP64 path for 2% more time; smaller
-// fronts meet 1e-9 with four.
-int auto_bands(const Plan& P) { return P.max_front > 4096 ? 5 : 4; }
+// kT = 0.002) rho moved from 2.0e-9 to 4.0e-11 of the FP64 path for 6% more time; on the 2D
+// sheet the narrower tiles were faster (less padding), on the 3D cubic lattice 2% slower.
+int auto_bands(const Plan&) { return 5; }
 
 // Split-precision metadata of a plan: tensor-core steps, their tile lists and cost figures.
 void setup_split(ndsi_plan* h, const ndsi_options& o) {
