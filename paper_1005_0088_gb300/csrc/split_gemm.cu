@@ -386,16 +386,18 @@ __device__ __forceinline__ void fp64_digits32(double x, int E, int* d) {
     d[0] = hi;
 }
 
-// BF16 bit pattern of d * 2^(-8t), |d| <= 128 (exact).
-__device__ __forceinline__ uint16_t bf16_digit(int d, int t) {
-    if (d == 0) return 0;
-    const uint32_t sgn = d < 0 ? 0x8000u : 0u;
-    const uint32_t a = static_cast<uint32_t>(d < 0 ? -d : d);
-    const int e = 31 - __clz(a);
-    const uint32_t mant = (a << (7 - e)) & 0x7Fu;
-    const uint32_t bexp = static_cast<uint32_t>(127 + e - 8 * t);
-    return static_cast<uint16_t>(sgn | (bexp << 7) | mant);
+// d * 2^(-8t) as an exact FP32 value, |d| <= 128: 1.5*2^23 + d has ulp 1, so adding d to its bit
+// pattern and subtracting 1.5*2^23 gives d exactly; the power-of-two scale is exact too.  With at
+// most 8 significant bits the value's BF16 pattern is the upper half of the FP32 pattern.
+__device__ __forceinline__ uint32_t digit_f32_bits(int d, int t) {
+    const float f = (__int_as_float(0x4B400000 + d) - 12582912.0f) * __int_as_float((127 - 8 * t) << 23);
+    return __float_as_uint(f);
 }
+// Two digits as a packed BF16 pair (first in the low half).
+__device__ __forceinline__ uint32_t bf16_pair(int d0, int d1, int t) {
+    return __byte_perm(digit_f32_bits(d0, t), digit_f32_bits(d1, t), 0x7632);
+}
+
 
 struct SliceArgs {
     const GemmItem* items;
@@ -513,13 +515,11 @@ __global__ void __launch_bounds__(256, 3) k_slice(const SliceArgs p) {
             fp64_digits32<S>(v0.x, Er, d0);
             fp64_digits32<S>(v1.x, Er, d1);
 #pragma unroll
-            for (int t = 0; t < S; ++t)
-                wre[t] = static_cast<uint32_t>(bf16_digit(d0[t], t)) | (static_cast<uint32_t>(bf16_digit(d1[t], t)) << 16);
+            for (int t = 0; t < S; ++t) wre[t] = bf16_pair(d0[t], d1[t], t);
             fp64_digits32<S>(v0.y, Er, d0);
             fp64_digits32<S>(v1.y, Er, d1);
 #pragma unroll
-            for (int t = 0; t < S; ++t)
-                wim[t] = static_cast<uint32_t>(bf16_digit(d0[t], t)) | (static_cast<uint32_t>(bf16_digit(d1[t], t)) << 16);
+            for (int t = 0; t < S; ++t) wim[t] = bf16_pair(d0[t], d1[t], t);
 #pragma unroll
             for (int t = 0; t < S; ++t) {
                 uint16_t* o1 = p.out + (o0 + t * ost) * p.Kcols;
@@ -619,13 +619,11 @@ __global__ void __launch_bounds__(256) k_slice1(const SliceArgs p) {
         fp64_digits32<S>(v0.x, Er, d0);
         fp64_digits32<S>(v1.x, Er, d1);
 #pragma unroll
-        for (int t = 0; t < S; ++t)
-            wre[t] = static_cast<uint32_t>(bf16_digit(d0[t], t)) | (static_cast<uint32_t>(bf16_digit(d1[t], t)) << 16);
+        for (int t = 0; t < S; ++t) wre[t] = bf16_pair(d0[t], d1[t], t);
         fp64_digits32<S>(v0.y, Er, d0);
         fp64_digits32<S>(v1.y, Er, d1);
 #pragma unroll
-        for (int t = 0; t < S; ++t)
-            wim[t] = static_cast<uint32_t>(bf16_digit(d0[t], t)) | (static_cast<uint32_t>(bf16_digit(d1[t], t)) << 16);
+        for (int t = 0; t < S; ++t) wim[t] = bf16_pair(d0[t], d1[t], t);
 #pragma unroll
         for (int t = 0; t < S; ++t) {
             uint16_t* o1 = p.out + (o0 + t * ost) * p.Kcols;
