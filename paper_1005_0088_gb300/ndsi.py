@@ -306,9 +306,10 @@ def ndsi_profile_enable(plan: Plan, enable=True, by_level: bool = False):
 
 def ndsi_profile_read(plan: Plan) -> dict:
     """{family: dict(launches, ms, flops, bytes)} accumulated since ndsi_profile_enable."""
-    buf = (ndsi_profile_entry * 64)()
+    cap = 1024
+    buf = (ndsi_profile_entry * cap)()
     n = ctypes.c_int32()
-    _check(load().ndsi_profile_read(plan.handle, buf, 64, ctypes.byref(n)))
+    _check(load().ndsi_profile_read(plan.handle, buf, cap, ctypes.byref(n)))
     return {buf[i].name.decode(): dict(launches=buf[i].launches, ms=buf[i].ms, flops=buf[i].flops,
                                        bytes=buf[i].bytes, tensor_flops=buf[i].tensor_flops)
             for i in range(n.value)}
