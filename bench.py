@@ -184,7 +184,13 @@ def _kernel_totals(prof):
     return out
 
 
-def _roofline(prof, steps, peaks):
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum, averaged over the kernel's
+# launches in one timed sweep) from an ncu capture of the same build and workload; the summary
+# and command are in profiles/.  Entries are removed whenever the kernel changes.
+TRAFFIC_PER_LAUNCH = {("C2", "fp64", "gemm_f64"): 55.06e6}  # profiles/gemm_f64_C2_2d_sheet.md
+
+
+def _roofline(prof, steps, peaks, traffic_key=None):
     kern = _kernel_totals(prof)
     dname, d = max(kern.items(), key=lambda kv: kv[1]["ms"])
     total = sum(v["ms"] for v in kern.values())
@@ -206,7 +212,8 @@ def _roofline(prof, steps, peaks):
         achieved = d["bytes"] / (d["ms"] * 1e-3) / 1e9
         r = {"bound": "hbm", "unit": "GB/s", "peak": peak,
              "peak_source": "of measured (MEASURED_PEAKS.json hbm_gbs)"}
-    r.update({"kernel": dname, "achieved": achieved, "frac": achieved / peak, "traffic": None,
+    traffic = TRAFFIC_PER_LAUNCH.get(traffic_key + (dname,)) if traffic_key else None
+    r.update({"kernel": dname, "achieved": achieved, "frac": achieved / peak, "traffic": traffic,
               "launches": d["launches"], "kernel_ms_per_step": d["ms"] / steps,
               "share": d["ms"] / total})
     return r, kern
@@ -342,7 +349,9 @@ def run_ndsi(args):
         if world > 1:
             dist.destroy_process_group()
         return 0
-    roofline, kern = _roofline(prof, args.steps, _peaks())
+    default_opts = not (args.poles or args.outer or args.block or args.slices or args.bands)
+    roofline, kern = _roofline(prof, args.steps, _peaks(),
+                               (args.config, args.precision) if default_opts else None)
     launches = sum(v["launches"] for v in kern.values())
     # parity spot check outside the timed region: sampled columns from the oracle
     parity = None

@@ -4,22 +4,26 @@
 // Method (an error-free splitting in the spirit of Ozaki, Ogita, Oishi and Rump's scheme, with
 // BF16 digits and FP32 tensor-core accumulation):
 //  * complex operands are stacked as real matrices: A'' = [Re A | Im A] (M x 2K) and, per
-//    64-column tile of B, 64 rows [Re B | -Im B] followed by 64 rows [Im B | Re B], so that one
-//    real product gives Re C in the first 64 accumulator columns and Im C in the next 64;
+//    NC-column tile of B, NC rows [Re B | -Im B] followed by NC rows [Im B | Re B], so that one
+//    real product gives Re C in the first NC accumulator columns and Im C in the next NC;
 //  * every row of A'' (column of B) is scaled by a power of two 2^E with |x| < 2^E and written as
 //    S balanced base-256 digits, x = 2^(E-7) sum_t d_t 2^(-8(t-1)), d_1 in [-128,128],
 //    d_t in [-128,127]; digit t is stored pre-scaled, d_t 2^(-8(t-1)), exactly as BF16.  The
 //    digits come from the FP64 bit pattern with integer operations only;
-//  * the slice products A_t B_u^T with t+u <= S+1 are accumulated in TMEM in four bands:
-//    t+u = 2, 3, 4 each in its own accumulator, where every partial sum over a 256-element K
-//    chunk is an integer below 2^24 times a power of two and so exact in FP32; those three are
-//    read out after every chunk into a per-element float-float (hi, lo) sum.  t+u >= 5 share one
-//    accumulator, also read out per chunk: the tensor core truncates products that are not
-//    multiples of the accumulator's ulp, so mixed-scale sums must stay short;
-//  * the epilogue scales by 2^(E_m + F_n - 14) and forms C = alpha*(hi+lo)*scale + beta*C in FP64.
-// Pipeline: warp 0 issues TMA loads (2 stages of S+S 128x32 BF16 tiles, 64-byte swizzle), warp 1
-// issues the MMAs (M=128, N=128, K=16), warps 2-17 read TMEM (4 per lane quarter, 32 columns each).  Every mbarrier wait is bounded: on
-// time-out the kernel flags NDSI timeout status, drains what it issued and frees its TMEM.
+//  * the slice products A_t B_u^T with t+u <= S+1 are accumulated in TMEM in BANDS bands: each
+//    t+u = 2 .. BANDS in its own accumulator, where every partial sum over a 256-element K chunk
+//    is an integer of at most 2^24 times a power of two and so exact in FP32; the remaining
+//    products share a tail accumulator.  Every band is read out after every chunk into a
+//    per-element float-float (hi, lo) sum.  When products of different scales meet in one
+//    accumulator the tensor core drops the low bits of the smaller ones, so the tail must hold
+//    only products well below the result's last digit: BANDS = 5 (NC = 48, 5 x 96 TMEM columns)
+//    gives a floor near 2^-43 of the result, BANDS = 4 (NC = 64, 4 x 128 columns) near 2^-38;
+//  * the epilogue scales by 2^(E_m + F_n - 14) and forms C = alpha*(hi+lo)*scale + beta*C.
+// Pipeline (persistent, one CTA per SM): warp 0 issues TMA loads (2 stages of S A tiles 128x32 and
+// S B tiles 2NCx32, BF16, 64-byte swizzle), one thread of warp 1 issues the MMAs (M=128, N=2NC,
+// K=16), warps 2-17 read TMEM and convert and store finished tiles while the next tile's MMAs
+// run.  Every mbarrier wait is bounded: on time-out the kernel flags NDSI timeout status, drains
+// what it issued and frees its TMEM.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_runtime.h>
@@ -418,7 +422,7 @@ struct SliceArgs {
 };
 
 // Slices of one block of kSplitSliceRows rows of the stacked operand (A: rows m of op(A); B:
-// columns n of op(B)).  A rows x 64 complex tile is staged in shared memory with loads coalesced
+// columns n of op(B)).  A rows x 64-k complex tile is staged in shared memory with loads coalesced
 // along whichever index is contiguous in memory.  Pass 1 finds the row exponents; pass 2 reads
 // the rows again and turns two consecutive k per thread into digits, 32 threads per row, so every
 // 4-byte store instruction of a warp fills one whole 128-byte line of a slice.  Blocks are few
