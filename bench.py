@@ -185,9 +185,9 @@ def _kernel_totals(prof):
 
 
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum, averaged over the kernel's
-# launches in one timed sweep) from an ncu capture of the same build and workload; the summary
-# and command are in profiles/.  Entries are removed whenever the kernel changes.
-TRAFFIC_PER_LAUNCH = {("C2", "fp64", "gemm_f64"): 55.06e6}  # profiles/gemm_f64_C2_2d_sheet.md
+# launches in one timed sweep) from an ncu capture of the same build and workload with default
+# options.  Entries are removed whenever the kernel changes.
+TRAFFIC_PER_LAUNCH = {("C2", "fp64", "gemm_f64"): 55.06e6}
 
 
 def _roofline(prof, steps, peaks, traffic_key=None):
