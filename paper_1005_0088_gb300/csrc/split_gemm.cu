@@ -402,6 +402,51 @@ __device__ __forceinline__ uint32_t bf16_pair(int d0, int d1, int t) {
     return __byte_perm(digit_f32_bits(d0, t), digit_f32_bits(d1, t), 0x7632);
 }
 
+// x / 2^(E+1) * 2^(8S), rounded to the nearest integer, in two's complement (S <= 6: the shift
+// is at least 6 bits to the right, see fp64_digits32).
+template <int S>
+__device__ __forceinline__ int64_t fp64_scaled(double x, int E) {
+    const int64_t b = __double_as_longlong(x);
+    int ex = static_cast<int>((b >> 52) & 0x7FF);
+    int64_t mant = b & 0xFFFFFFFFFFFFFLL;
+    if (ex) mant |= 0x10000000000000LL; else ex = 1;
+    const int rsh = 1076 + E - 8 * S - ex;
+    const int64_t mag = rsh >= 62 ? 0 : static_cast<int64_t>(((static_cast<uint64_t>(mant) >> (rsh - 1)) + 1) >> 1);
+    return b < 0 ? -mag : mag;
+}
+
+// Packed BF16 pairs w[t] = (digit t of x0 | digit t of x1 << 16), digit t scaled by 2^(-8t): the
+// same balanced base-256 digits as fp64_digits32.  Adding 128 to every digit below the top one
+// turns the balanced digits into the plain bytes of the sum (carries included), so each digit is
+// one byte extract and the exact FP32 conversion of digit_f32_bits with the bias folded in.
+template <int S>
+__device__ __forceinline__ void slice_pair(double x0, double x1, int E, uint32_t* w) {
+    if (S > 6) {
+        int d0[S], d1[S];
+        fp64_digits32<S>(x0, E, d0);
+        fp64_digits32<S>(x1, E, d1);
+#pragma unroll
+        for (int t = 0; t < S; ++t) w[t] = bf16_pair(d0[t], d1[t], t);
+        return;
+    }
+    int64_t bias = 0;
+#pragma unroll
+    for (int t = 0; t < S - 1; ++t) bias |= static_cast<int64_t>(128) << (8 * t);
+    const int64_t g0 = fp64_scaled<S>(x0, E) + bias, g1 = fp64_scaled<S>(x1, E) + bias;
+#pragma unroll
+    for (int t = 1; t < S; ++t) {
+        const int k = S - 1 - t;  // byte of the biased sum holding digit t
+        const int b0 = static_cast<int>((g0 >> (8 * k)) & 0xFF), b1 = static_cast<int>((g1 >> (8 * k)) & 0xFF);
+        const float sc = __int_as_float((127 - 8 * t) << 23);
+        const float f0 = (__int_as_float(0x4B400000 + b0) - 12583040.0f) * sc;
+        const float f1 = (__int_as_float(0x4B400000 + b1) - 12583040.0f) * sc;
+        w[t] = __byte_perm(__float_as_uint(f0), __float_as_uint(f1), 0x7632);
+    }
+    const int t0 = static_cast<int>(g0 >> (8 * (S - 1))), t1 = static_cast<int>(g1 >> (8 * (S - 1)));
+    w[0] = __byte_perm(__float_as_uint(__int_as_float(0x4B400000 + t0) - 12582912.0f),
+                       __float_as_uint(__int_as_float(0x4B400000 + t1) - 12582912.0f), 0x7632);
+}
+
 
 struct SliceArgs {
     const GemmItem* items;
@@ -514,16 +559,9 @@ __global__ void __launch_bounds__(256, 3) k_slice(const SliceArgs p) {
             }
             const double2 v0 = tile[rr][kk];
             const double2 v1 = tile[rr][kk + 1];
-            int d0[S], d1[S];
             uint32_t wre[S], wim[S];
-            fp64_digits32<S>(v0.x, Er, d0);
-            fp64_digits32<S>(v1.x, Er, d1);
-#pragma unroll
-            for (int t = 0; t < S; ++t) wre[t] = bf16_pair(d0[t], d1[t], t);
-            fp64_digits32<S>(v0.y, Er, d0);
-            fp64_digits32<S>(v1.y, Er, d1);
-#pragma unroll
-            for (int t = 0; t < S; ++t) wim[t] = bf16_pair(d0[t], d1[t], t);
+            slice_pair<S>(v0.x, v1.x, Er, wre);
+            slice_pair<S>(v0.y, v1.y, Er, wim);
 #pragma unroll
             for (int t = 0; t < S; ++t) {
                 uint16_t* o1 = p.out + (o0 + t * ost) * p.Kcols;
@@ -618,16 +656,9 @@ __global__ void __launch_bounds__(256) k_slice1(const SliceArgs p) {
         }
         const double2 v0 = kk < K ? t1[rr * ldt + kk] : make_double2(0.0, 0.0);
         const double2 v1 = kk + 1 < K ? t1[rr * ldt + kk + 1] : make_double2(0.0, 0.0);
-        int d0[S], d1[S];
         uint32_t wre[S], wim[S];
-        fp64_digits32<S>(v0.x, Er, d0);
-        fp64_digits32<S>(v1.x, Er, d1);
-#pragma unroll
-        for (int t = 0; t < S; ++t) wre[t] = bf16_pair(d0[t], d1[t], t);
-        fp64_digits32<S>(v0.y, Er, d0);
-        fp64_digits32<S>(v1.y, Er, d1);
-#pragma unroll
-        for (int t = 0; t < S; ++t) wim[t] = bf16_pair(d0[t], d1[t], t);
+        slice_pair<S>(v0.x, v1.x, Er, wre);
+        slice_pair<S>(v0.y, v1.y, Er, wim);
 #pragma unroll
         for (int t = 0; t < S; ++t) {
             uint16_t* o1 = p.out + (o0 + t * ost) * p.Kcols;
