@@ -82,8 +82,13 @@ void build_split_schedule(const Plan& P, int slices, int bands, std::vector<Spli
         while (st.slice_rows > 4 && static_cast<int64_t>(st.slice_rows) * st.slice_ldt * 16 > kSplitSlice1Smem)
             st.slice_rows /= 2;
         if (static_cast<int64_t>(st.slice_rows) * st.slice_ldt * 16 > kSplitSlice1Smem) {
-            st.slice_rows = kSplitSliceRows;
-            st.slice_ldt = 0;
+            // very long rows: one or two rows per block with a larger shared-memory allocation
+            st.slice_rows = 2;
+            if (static_cast<int64_t>(st.slice_rows) * st.slice_ldt * 16 > kSplitSlice1SmemWide) st.slice_rows = 1;
+            if (static_cast<int64_t>(st.slice_rows) * st.slice_ldt * 16 > kSplitSlice1SmemWide) {
+                st.slice_rows = kSplitSliceRows;
+                st.slice_ldt = 0;
+            }
         }
         for (int64_t i = 0; i < l.count; ++i) {
             const GemmItem& g = P.gemm_items[l.first + i];
@@ -583,8 +588,8 @@ __global__ void __launch_bounds__(256, 3) k_slice(const SliceArgs p) {
     if (live && kg == 0) p.expo[pole * p.erows_pole + (p.isB ? si.erowB : si.erowA) + row] = E;
 }
 
-// One-pass slicing: a block of `rows` (32, 16, 8 or 4) operand rows with all K of them resident
-// in shared memory, so every FP64 element is read from HBM once.  Loads are coalesced along the
+// One-pass slicing: a block of `rows` (32, 16, 8, 4, or 2 or 1 for very long rows) operand rows
+// with all K of them resident in shared memory, so every FP64 element is read from HBM once.  Loads are coalesced along the
 // contiguous index; the row maxima come from rows-many thread groups; the digits are written by
 // 32 threads per row with two consecutive k each, one 128-byte line per warp store.
 template <int S>
@@ -996,7 +1001,7 @@ cudaError_t set_attrs() {
     e = cudaFuncSetAttribute(k_gemm_split<S, kSplitBNc5>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              split_smem_bytes<S, kSplitBNc5>());
     if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(k_slice1<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSplitSlice1Smem);
+    return cudaFuncSetAttribute(k_slice1<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSplitSlice1SmemWide);
 }
 
 }  // namespace

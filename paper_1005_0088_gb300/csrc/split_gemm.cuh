@@ -17,7 +17,8 @@ constexpr int kSplitBM = 128;
 constexpr int kSplitBNc = 64;      // complex columns per tile, four-band variant
 constexpr int kSplitBNc5 = 48;     // complex columns per tile, five-band variant
 constexpr int kSplitSliceRows = 32;  // operand rows per slicing block (two-pass slicer)
-constexpr int kSplitSlice1Smem = 72 * 1024;  // shared-memory budget of the one-pass slicer
+constexpr int kSplitSlice1Smem = 72 * 1024;       // one-pass slicer budget, 4..32 rows per block
+constexpr int kSplitSlice1SmemWide = 200 * 1024;  // budget for very long rows, 1 or 2 rows per block
 constexpr int kSplitKB = 32;       // K per pipeline stage (64-byte rows, 64B swizzle)
 #ifdef NDSI_SPLIT_CHUNK_KB
 constexpr int kSplitChunkKB = NDSI_SPLIT_CHUNK_KB;
