@@ -119,8 +119,9 @@ class ClockSampler:
 
 
 def cpu_oracle_rate(system, mu, kT, M, min_seconds=10.0, min_reps=2):
-    """Time the oracle's route 1 (dense eigendecomposition + truncated Fermi sum on the pattern)."""
-    from oracle.dense import generalized_eig, density_eig, on_pattern
+    """Time the oracle's route 1 (dense eigendecomposition + truncated Fermi sum on the pattern);
+    also returns the oracle's Tr(rho S) (Eq. 40)."""
+    from oracle.dense import generalized_eig, density_eig, on_pattern, electron_count_eig
     Hd, Sd = system.dense()
     times = []
     t_all = time.perf_counter()
@@ -132,7 +133,7 @@ def cpu_oracle_rate(system, mu, kT, M, min_seconds=10.0, min_reps=2):
         if len(times) >= 20:
             break
     t = statistics.mean(times)
-    return M * system.n / t, len(times), t
+    return M * system.n / t, len(times), t, electron_count_eig(eps, mu, kT, M)
 
 
 def run_reference(args):
@@ -340,6 +341,7 @@ def run_ndsi(args):
         rl2, k2 = _roofline(prof2, args.steps, _peaks())
         other = {"precision": oprec, "ms_per_step": ms2, "value": M * system.n / (ms2 * 1e-3),
                  "split_speedup_vs_fp64": ms_fp64 / ms_split, "autotune": tune2,
+                 "abs_n_elec_diff_vs_headline": abs(float(ne2.cpu()[0]) - float(ne.cpu()[0])),
                  "max_abs_rho_diff_vs_headline": float(np.max(np.abs(rho2.cpu().numpy() - rho_main))),
                  "roofline": rl2,
                  "kernels": {k: {"launches": v["launches"] // args.steps, "ms_per_step": v["ms"] / args.steps}
@@ -368,8 +370,11 @@ def run_ndsi(args):
         parity = {"max_abs_err_rho": err, "columns": cols,
                   "tolerance": 1e-10 if args.precision == "fp64" else 1e-9}
     cpu = None
+    ne_gpu = float(ne.cpu()[0])
+    n_elec = {"value": ne_gpu}
     if world == 1 and not args.no_cpu:
-        v, reps, t_rep = cpu_oracle_rate(system, MU, kT, M)
+        v, reps, t_rep, ne_oracle = cpu_oracle_rate(system, MU, kT, M)
+        n_elec.update(oracle=ne_oracle, abs_err=abs(ne_gpu - ne_oracle))
         cpu = {"value": v, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
                "sample": f"{reps} full density evaluations of the workload by dense generalized "
                          f"eigendecomposition + {M}-pole Fermi sum ({t_rep:.2f} s each)"}
@@ -396,7 +401,7 @@ def run_ndsi(args):
                               "breakdown and roofline come from the same steps repeated with direct "
                               "launches bracketed by CUDA events on the launch stream"},
             "roofline": roofline, "clocks": clk.summary(), "cpu_baseline": cpu,
-            "parity": parity, "other_precision": other,
+            "parity": parity, "n_elec": n_elec, "other_precision": other,
             "kernels": {k: {"launches": v["launches"] // args.steps, "ms_per_step": v["ms"] / args.steps,
                             "gbs": v["bytes"] / max(v["ms"], 1e-9) / 1e6,
                             "tflops": v["flops"] / max(v["ms"], 1e-9) / 1e9}
