@@ -31,3 +31,10 @@ def chain_density(N, a, b, s, mu, kT, occupation):
     eps, C = chain_spectrum(N, a, b, s)
     occ = occupation(eps, mu, kT)
     return (C * occ[None, :]) @ C.T, eps
+
+
+def chain_energy_density(N, a, b, s, mu, kT, occupation):
+    """e = sum_k eps_k occ(eps_k) c_k c_k^T (the energy density matrix of the chain)."""
+    eps, C = chain_spectrum(N, a, b, s)
+    w = eps * occupation(eps, mu, kT)
+    return (C * w[None, :]) @ C.T, eps

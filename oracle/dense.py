@@ -9,6 +9,8 @@ Route 2 (Eq. 8, dense): rho = M0 + sum_p w_p Re G(alpha_p), G(Z) = (Z S - H)^{-1
 alpha_p = mu + i z_p/beta, w_p = -4 R_p/beta, M0 = S^{-1} (the zeroth moment; the paper
 evaluates it as i R G(iR) with large R, whose real part tends to S^{-1}).
 N_e = Tr(rho S) (Eq. 40) = sum over the pattern of rho_ij S_ij.
+Energy density matrix (Eq. 10): e = 2 sum_nu eps_nu f c_nu c_nu^T by definition, or from G with
+the zeroth and first moments M0 = S^{-1}, M1 = S^{-1} H S^{-1}.
 """
 from __future__ import annotations
 
@@ -59,6 +61,26 @@ def density_inv(Hd, Sd, mu, kT, M):
         alpha = mu + 1j * zp / beta
         rho = rho + (-4.0 * Rp / beta) * np.real(green_dense(Hd, Sd, alpha))
     return rho
+
+
+def energy_density_eig(eps, C, mu, kT, M=None):
+    """Energy density matrix by definition: e = sum_nu eps_nu 2 f(beta(eps_nu - mu)) c c^T."""
+    w = np.asarray(eps) * occupation(eps, mu, kT, M)
+    return (C * w[None, :]) @ C.T
+
+
+def energy_density_inv(Hd, Sd, mu, kT, M):
+    """Energy density matrix by Eq. (10) with exact moments (tiny inputs):
+    e = M1 + kappa M0 - (4/beta) sum_p R_p Re(alpha_p G(alpha_p)), kappa = (4/beta) sum_p R_p,
+    M0 = S^{-1} and M1 = S^{-1} H S^{-1} (the zeroth and first moments of G)."""
+    beta = 1.0 / kT
+    z, R = cf_poles(M)
+    Si = np.linalg.inv(Sd)
+    e = Si @ Hd @ Si + (4.0 / beta) * float(np.sum(R)) * Si
+    for zp, Rp in zip(z, R):
+        alpha = mu + 1j * zp / beta
+        e = e - (4.0 / beta) * Rp * np.real(alpha * green_dense(Hd, Sd, alpha))
+    return e
 
 
 def on_pattern(A, system):
@@ -116,3 +138,19 @@ def density_columns(system, mu, kT, M, cols):
         g = green_columns(system, mu + 1j * zp / beta, cols)
         rho = rho + (-4.0 * Rp / beta) * np.real(g)
     return rho
+
+
+def energy_density_columns(system, mu, kT, M, cols):
+    """Columns e[:, cols] by Eq. (10) with sparse solves per pole; M1 e_j = S^{-1} H S^{-1} e_j."""
+    beta = 1.0 / kT
+    z, R = cf_poles(M)
+    H, S = sparse_matrices(system)
+    lu = scipy.sparse.linalg.splu(S.tocsc())
+    rhs = np.zeros((system.n, len(cols)))
+    rhs[np.asarray(cols), np.arange(len(cols))] = 1.0
+    m0 = lu.solve(rhs)
+    e = lu.solve(H @ m0) + (4.0 / beta) * float(np.sum(R)) * m0
+    for zp, Rp in zip(z, R):
+        alpha = mu + 1j * zp / beta
+        e = e - (4.0 / beta) * Rp * np.real(alpha * green_columns(system, alpha, cols))
+    return e
