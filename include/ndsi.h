@@ -219,6 +219,20 @@ int ndsi_profile_enable(ndsi_plan* plan, int32_t enable);
 int ndsi_autotune(ndsi_plan* plan, const double* H, const double* S, double mu, double kT, int32_t n_poles,
                   int32_t* n_split_out, int32_t* n_fp64_out, void* stream);
 
+/* Density matrix and energy density matrix (Eq. 10) on the pattern in one sweep:
+ *   e = M1 + kappa M0 - (4/beta) sum_p R_p Re(alpha_p G(alpha_p)),  kappa = (4/beta) sum_p R_p,
+ * with M0 = S^{-1} and M1 = S^{-1} H S^{-1} the zeroth and first moments of G.  The poles and the
+ * M0 point are those of ndsi_density (their factors are shared); M1 comes from three more points
+ * z = Re, -Re, i Re as (Re^2/4) [G(Re) + G(-Re) - 2 Re G(i Re)]: with the fourth point -i Re (the
+ * conjugate of i Re) these are the four roots Re i^k, which cancel every moment but M1, M5, ...,
+ * so the truncation is (spectral radius / Re)^4 relative.  Re = 1000 x the Gershgorin bound of
+ * the pencil's spectrum (max_i sum_j |H_ij| over min_i (S_ii - sum_{j!=i} |S_ij|)), computed on
+ * the device; this replaces the two-point moment formula the paper prints (whose truncation is
+ * O(|M2|/R)).  rho_out, e_out: nnz doubles each (device or host); n_elec_out: Tr(rho S) (may be
+ * NULL).  Single-system plans only.  Errors as ndsi_density. */
+int ndsi_density_energy(ndsi_plan* plan, const double* H, const double* S, double mu, double kT,
+                        int32_t n_poles, double* rho_out, double* e_out, double* n_elec_out, void* stream);
+
 /* CUDA graphs.  While enabled (the default) and profiling is off, ndsi_density,
  * ndsi_density_batched and ndsi_find_mu run each density sweep (all chunks of points: assembly,
  * factorisation, selected inversion, residue sum and electron counts) as one CUDA graph,

@@ -74,6 +74,8 @@ struct ndsi_plan {
     ndsi::Workspace W;
     double2* cw = nullptr;       // per-chunk points and weights
     double2* zw = nullptr;
+    double2* cew = nullptr;      // energy-density weights of the same points
+    unsigned long long* gersh = nullptr;  // Gershgorin bound of (H, S) for the moment points
     int32_t cw_cap = 0;
     double* partials = nullptr;  // trace reduction scratch
     double* stage = nullptr;     // staging for host H, S, rho, n_elec
@@ -404,7 +406,7 @@ int64_t workspace_cap(const ndsi_plan* h) {
 
 namespace ndsi {
 int density_impl(ndsi_plan* h, const double* Hd, const double* Sd, const double* mu, const double* kT,
-                 int32_t n_poles, double* rho_d, double* ne_d, cudaStream_t st);
+                 int32_t n_poles, double* rho_d, double* ne_d, cudaStream_t st, double* e_d = nullptr);
 
 // Slice count of a split plan when the caller leaves it to the library: six BF16 digits (47
 // bits).  A seventh changes nothing with four accumulator bands (the tail accumulator's floor
@@ -443,7 +445,7 @@ void setup_split(ndsi_plan* h, const ndsi_options& o) {
     }
 }
 int sweep(ndsi_plan* h, const double* Hd, const double* Sd, int32_t nq, int32_t chunk,
-          const std::vector<int>& part_off, double* rho_d, double* ne_d, cudaStream_t st);
+          const std::vector<int>& part_off, double* rho_d, double* ne_d, double* e_d, cudaStream_t st);
 }  // namespace ndsi
 
 using namespace ndsi;
@@ -740,15 +742,61 @@ int ndsi_density(ndsi_plan* h, const double* H, const double* S, double mu, doub
     return NDSI_OK;
 }
 
+int ndsi_density_energy(ndsi_plan* h, const double* H, const double* S, double mu, double kT, int32_t n_poles,
+                        double* rho_out, double* e_out, double* n_elec_out, void* stream) {
+    if (!h || !H || !S || !rho_out || !e_out || n_poles < 1 || !(kT > 0) || !std::isfinite(mu))
+        return fail(NDSI_ERR_INVALID, "ndsi_density_energy: invalid argument");
+    if (h->P.n_systems != 1) return fail(NDSI_ERR_INVALID, "ndsi_density_energy: batched plan");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    int rc = upload_tables(h);
+    if (rc) return rc;
+    const double *Hd, *Sd;
+    rc = device_inputs(h, H, S, &Hd, &Sd, st);
+    if (rc) return rc;
+    const int64_t nnz = h->P.nnz;
+    const bool rho_dev = is_device_ptr(rho_out), e_dev = is_device_ptr(e_out);
+    const bool ne_dev = n_elec_out && is_device_ptr(n_elec_out);
+    rc = ensure_stage(h, 4 * nnz + 8);
+    if (rc) return rc;
+    double* rho_d = rho_dev ? rho_out : h->stage + 2 * nnz;
+    double* ne_d = ne_dev ? n_elec_out : h->stage + 3 * nnz;
+    double* e_d = e_dev ? e_out : h->stage + 3 * nnz + 8;
+    rc = density_impl(h, Hd, Sd, &mu, &kT, n_poles, rho_d, ne_d, st, e_d);
+    if (rc) return rc;
+    if (!rho_dev) NDSI_CK(cudaMemcpyAsync(rho_out, rho_d, sizeof(double) * nnz, cudaMemcpyDeviceToHost, st));
+    if (!e_dev) NDSI_CK(cudaMemcpyAsync(e_out, e_d, sizeof(double) * nnz, cudaMemcpyDeviceToHost, st));
+    if (n_elec_out && !ne_dev) NDSI_CK(cudaMemcpyAsync(n_elec_out, ne_d, sizeof(double), cudaMemcpyDeviceToHost, st));
+    NDSI_CK(cudaStreamSynchronize(st));
+    return NDSI_OK;
+}
+
 }  // extern "C"
 
 namespace ndsi {
 // rho(mu) and Tr(rho S) of every system of the plan (mu[s], kT[s]) for device inputs and
 // outputs (ne_d[s] per system); synchronises the stream.
 int density_impl(ndsi_plan* h, const double* Hd, const double* Sd, const double* mu, const double* kT,
-                 int32_t n_poles, double* rho_d, double* ne_d, cudaStream_t st) {
+                 int32_t n_poles, double* rho_d, double* ne_d, cudaStream_t st, double* e_d) {
     int rc;
     const int32_t ns = h->P.n_systems;
+    if (e_d && ns != 1) return fail(NDSI_ERR_INVALID, "energy density: single-system plans only");
+    // Energy density matrix (Eq. 10): the same points with weights -4 R_p alpha_p kT, kappa on the
+    // M0 point, and the first moment M1 from three more points z = Re, -Re, i Re with
+    // M1 = (Re^2 / 4) [G(Re) + G(-Re) - 2 Re G(i Re)] (the four points Re i^k annihilate every
+    // moment except M1, M5, ...: truncation ~ (spectral radius / Re)^4 |M1|).  Re is 1000 x the
+    // Gershgorin bound of the pencil's spectrum, computed on the device.
+    double Re = 0.0;
+    if (e_d) {
+        if (!h->gersh) NDSI_CK(cudaMalloc(&h->gersh, 2 * sizeof(unsigned long long)));
+        NDSI_CK(cudaMemsetAsync(h->gersh, 0, 2 * sizeof(unsigned long long), st));
+        NDSI_CK(launch_gershgorin(h->T, h->P.n, Hd, Sd, h->gersh, st));
+        unsigned long long keys[2];
+        NDSI_CK(cudaMemcpyAsync(keys, h->gersh, sizeof(keys), cudaMemcpyDeviceToHost, st));
+        NDSI_CK(cudaStreamSynchronize(st));
+        const double hmax = gershgorin_value(keys[0]), smin = -gershgorin_value(keys[1]);
+        const double radius = hmax / (smin > 1e-3 ? smin : 1e-3);
+        Re = 1000.0 * std::max(radius, 1e-3);
+    }
     // poles of Eq. 7 (cached per M) -> points alpha_p and weights w_p of Eq. 8, plus iR for M0
     if (h->pole_M != n_poles) {
         h->pole_z.assign(n_poles, 0.0);
@@ -758,18 +806,33 @@ int density_impl(ndsi_plan* h, const double* Hd, const double* Sd, const double*
         if (rc) return fail(rc, err);
         h->pole_M = n_poles;
     }
-    const int32_t nq = n_poles + 1;
-    std::vector<double2> zq(static_cast<size_t>(ns) * nq), cq(static_cast<size_t>(ns) * nq);
+    const int32_t nq = n_poles + 1 + (e_d ? 3 : 0);
+    std::vector<double2> zq(static_cast<size_t>(ns) * nq), cq(static_cast<size_t>(ns) * nq),
+        ceq(static_cast<size_t>(ns) * nq, make_double2(0.0, 0.0));
     const double R = h->P.opt.m0_radius;
     for (int32_t sy = 0; sy < ns; ++sy) {
         double2* z = zq.data() + static_cast<size_t>(sy) * nq;
         double2* c = cq.data() + static_cast<size_t>(sy) * nq;
+        double2* ce = ceq.data() + static_cast<size_t>(sy) * nq;
+        double kappa = 0.0;
         for (int32_t p = 0; p < n_poles; ++p) {
             z[p] = make_double2(mu[sy], h->pole_z[p] * kT[sy]);
             c[p] = make_double2(-4.0 * h->pole_R[p] * kT[sy], 0.0);
+            // -4 R_p kT alpha_p: Re(ce G) = -4 R_p kT Re(alpha_p G)
+            ce[p] = make_double2(-4.0 * h->pole_R[p] * kT[sy] * mu[sy], -4.0 * h->pole_R[p] * kT[sy] * z[p].y);
+            kappa += 4.0 * kT[sy] * h->pole_R[p];
         }
         z[n_poles] = make_double2(0.0, R);
         c[n_poles] = make_double2(0.0, R);
+        ce[n_poles] = make_double2(0.0, kappa * R);  // kappa M0, M0 = Re(i R G(i R))
+        if (e_d) {
+            z[n_poles + 1] = make_double2(Re, 0.0);
+            z[n_poles + 2] = make_double2(-Re, 0.0);
+            z[n_poles + 3] = make_double2(0.0, Re);
+            c[n_poles + 1] = c[n_poles + 2] = c[n_poles + 3] = make_double2(0.0, 0.0);
+            ce[n_poles + 1] = ce[n_poles + 2] = make_double2(0.25 * Re * Re, 0.0);
+            ce[n_poles + 3] = make_double2(-0.5 * Re * Re, 0.0);
+        }
     }
     // chunk the points to the workspace cap
     const int64_t per_pole = bytes_per_pole(h);
@@ -782,10 +845,12 @@ int density_impl(ndsi_plan* h, const double* Hd, const double* Sd, const double*
     if (h->cw_cap < ns * nq) {
         if (h->cw) cudaFree(h->cw);
         if (h->zw) cudaFree(h->zw);
-        h->cw = h->zw = nullptr;
+        if (h->cew) cudaFree(h->cew);
+        h->cw = h->zw = h->cew = nullptr;
         h->cw_cap = 0;
         NDSI_CK(cudaMalloc(&h->cw, sizeof(double2) * ns * nq));
         NDSI_CK(cudaMalloc(&h->zw, sizeof(double2) * ns * nq));
+        NDSI_CK(cudaMalloc(&h->cew, sizeof(double2) * ns * nq));
         h->cw_cap = ns * nq;
     }
     // per-system partial-trace ranges of the reduction scratch
@@ -795,10 +860,11 @@ int density_impl(ndsi_plan* h, const double* Hd, const double* Sd, const double*
     if (!h->partials) NDSI_CK(cudaMalloc(&h->partials, sizeof(double) * (part_off[ns] + 1)));
     NDSI_CK(cudaMemcpyAsync(h->zw, zq.data(), sizeof(double2) * ns * nq, cudaMemcpyHostToDevice, st));
     NDSI_CK(cudaMemcpyAsync(h->cw, cq.data(), sizeof(double2) * ns * nq, cudaMemcpyHostToDevice, st));
+    if (e_d) NDSI_CK(cudaMemcpyAsync(h->cew, ceq.data(), sizeof(double2) * ns * nq, cudaMemcpyHostToDevice, st));
     if (h->graphs && !h->prof.on) {
         // replay the captured sweep; points and weights are read from zw / cw at run time
-        const std::vector<const void*> key = {Hd, Sd, rho_d, ne_d, h->W.fronts, h->W.scr, h->SB.sliceA,
-                                              h->SB.sliceB, h->cw, h->zw, h->partials,
+        const std::vector<const void*> key = {Hd, Sd, rho_d, ne_d, e_d, h->W.fronts, h->W.scr, h->SB.sliceA,
+                                              h->SB.sliceB, h->cw, h->zw, h->cew, h->partials,
                                               reinterpret_cast<const void*>(static_cast<intptr_t>(nq)),
                                               reinterpret_cast<const void*>(static_cast<intptr_t>(chunk))};
         if (!h->graph || h->graph_key != key) {
@@ -806,7 +872,7 @@ int density_impl(ndsi_plan* h, const double* Hd, const double* Sd, const double*
             h->graph = nullptr;
             if (!h->cap_stream) NDSI_CK(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
             NDSI_CK(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
-            rc = sweep(h, Hd, Sd, nq, chunk, part_off, rho_d, ne_d, h->cap_stream);
+            rc = sweep(h, Hd, Sd, nq, chunk, part_off, rho_d, ne_d, e_d, h->cap_stream);
             cudaGraph_t g = nullptr;
             const cudaError_t ec = cudaStreamEndCapture(h->cap_stream, &g);
             if (rc || ec != cudaSuccess) {
@@ -825,7 +891,7 @@ int density_impl(ndsi_plan* h, const double* Hd, const double* Sd, const double*
         NDSI_CK(cudaGraphLaunch(h->graph, st));
         return check_status(h, st);
     }
-    rc = sweep(h, Hd, Sd, nq, chunk, part_off, rho_d, ne_d, st);
+    rc = sweep(h, Hd, Sd, nq, chunk, part_off, rho_d, ne_d, e_d, st);
     if (rc) return rc;
     return check_status(h, st);
 }
@@ -834,7 +900,7 @@ int density_impl(ndsi_plan* h, const double* Hd, const double* Sd, const double*
 // chunk, then the per-system electron counts.  Only stream-ordered work: it is also the body of
 // the captured graph.
 int sweep(ndsi_plan* h, const double* Hd, const double* Sd, int32_t nq, int32_t chunk,
-          const std::vector<int>& part_off, double* rho_d, double* ne_d, cudaStream_t st) {
+          const std::vector<int>& part_off, double* rho_d, double* ne_d, double* e_d, cudaStream_t st) {
     int rc;
     const int32_t ns = h->P.n_systems;
     for (int32_t q0 = 0; q0 < nq; q0 += chunk) {
@@ -850,6 +916,11 @@ int sweep(ndsi_plan* h, const double* Hd, const double* Sd, int32_t nq, int32_t 
                 return launch_accumulate(h->P, h->T, h->W, np, h->cw + static_cast<size_t>(sy) * nq + q0, Sd, rho_d,
                                          q0 > 0 ? 1 : 0, last, h->partials + part_off[sy], st, k0, cnt);
             }));
+            if (e_d)
+                NDSI_CK(timed(h->prof, "accumulate", 2.0 * np * cnt, acc_bytes, st, [&]() {
+                    return launch_accumulate(h->P, h->T, h->W, np, h->cew + static_cast<size_t>(sy) * nq + q0, Sd,
+                                             e_d, q0 > 0 ? 1 : 0, 0, nullptr, st, k0, cnt);
+                }));
         }
     }
     for (int32_t sy = 0; sy < ns; ++sy) {
@@ -1137,6 +1208,8 @@ void ndsi_plan_destroy(ndsi_plan* h) {
     if (h->T.blob) cudaFree(h->T.blob);
     if (h->cw) cudaFree(h->cw);
     if (h->zw) cudaFree(h->zw);
+    if (h->cew) cudaFree(h->cew);
+    if (h->gersh) cudaFree(h->gersh);
     if (h->partials) cudaFree(h->partials);
     if (h->stage) cudaFree(h->stage);
     if (h->graph) cudaGraphExecDestroy(h->graph);

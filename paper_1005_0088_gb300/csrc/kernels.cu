@@ -7,6 +7,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <cstring>
 
 #include "kernels.cuh"
 
@@ -538,6 +539,44 @@ cudaError_t launch_accumulate(const Plan& P, const DevTables& T, const Workspace
     k_accumulate<<<blocks, kAccThreads, 0, st>>>(T.out_map, k0, count, W.fronts, W.front_stride, np, c, S, rho,
                                                  accumulate, want_trace, partials);
     return cudaGetLastError();
+}
+
+// Order-preserving map of doubles to unsigned keys (larger double -> larger key).
+__host__ __device__ inline unsigned long long order_key(double x) {
+    unsigned long long u;
+    memcpy(&u, &x, sizeof(u));
+    return (u >> 63) ? ~u : (u | 0x8000000000000000ull);
+}
+
+__global__ void __launch_bounds__(256) k_gershgorin(const int64_t* __restrict__ rowptr,
+                                                    const int32_t* __restrict__ col, int64_t n,
+                                                    const double* __restrict__ H,
+                                                    const double* __restrict__ S,
+                                                    unsigned long long* __restrict__ out) {
+    const int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+    if (i >= n) return;
+    double h = 0.0, soff = 0.0, sdiag = 0.0;
+    for (int64_t k = rowptr[i]; k < rowptr[i + 1]; ++k) {
+        h += fabs(H[k]);
+        if (col[k] == i) sdiag = S[k];
+        else soff += fabs(S[k]);
+    }
+    atomicMax(&out[0], order_key(h));
+    atomicMax(&out[1], order_key(soff - sdiag));
+}
+
+cudaError_t launch_gershgorin(const DevTables& T, int64_t n, const double* H, const double* S,
+                              unsigned long long* out, cudaStream_t st) {
+    const unsigned blocks = static_cast<unsigned>((n + 255) / 256);
+    k_gershgorin<<<blocks, 256, 0, st>>>(T.rowptr, T.col, n, H, S, out);
+    return cudaGetLastError();
+}
+
+double gershgorin_value(unsigned long long key) {
+    const unsigned long long u = (key >> 63) ? (key & 0x7FFFFFFFFFFFFFFFull) : ~key;
+    double x;
+    memcpy(&x, &u, sizeof(x));
+    return x;
 }
 
 cudaError_t launch_reduce(const double* partials, int nblocks, double* out, cudaStream_t st) {

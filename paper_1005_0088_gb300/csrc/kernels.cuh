@@ -63,6 +63,12 @@ cudaError_t launch_accumulate(const Plan& P, const DevTables& T, const Workspace
 int accumulate_blocks(int64_t nnz);
 cudaError_t launch_reduce(const double* partials, int nblocks, double* out, cudaStream_t st);
 
+// Gershgorin data of (H, S): out[0] = order key of max_i sum_j |H_ij|, out[1] = order key of
+// max_i (sum_{j != i} |S_ij| - S_ii); keys decode with gershgorin_value.  out must be zeroed.
+cudaError_t launch_gershgorin(const DevTables& T, int64_t n, const double* H, const double* S,
+                              unsigned long long* out, cudaStream_t st);
+double gershgorin_value(unsigned long long key);
+
 // G_out[q*nnz + k] = G_q(k) for the np poles of the workspace.
 cudaError_t launch_gather_pattern(const Plan& P, const DevTables& T, const Workspace& W, int np,
                                   double2* G_out, int64_t q0, cudaStream_t st);

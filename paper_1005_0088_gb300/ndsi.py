@@ -34,6 +34,7 @@ EXPORTED_SYMBOLS = (
     "ndsi_residue_sum_static", "ndsi_find_mu", "ndsi_mu_features", "ndsi_mlp_init",
     "ndsi_mlp_forward", "ndsi_mlp_grad", "ndsi_mlp_train", "ndsi_analyze_batched",
     "ndsi_density_batched", "ndsi_graph_enable", "ndsi_graph_info", "ndsi_autotune",
+    "ndsi_density_energy",
 )
 NDSI_MLP_INPUTS = 32
 NDSI_MLP_HIDDEN = 64
@@ -101,6 +102,8 @@ def load(path: str = LIB_PATH):
     lib.ndsi_factors_destroy.restype = None
     lib.ndsi_profile_enable.argtypes = [vp, i32]
     lib.ndsi_graph_enable.argtypes = [vp, i32]
+    lib.ndsi_density_energy.argtypes = [vp, vp, vp, ctypes.c_double, ctypes.c_double, i32, vp, vp, vp, vp]
+    lib.ndsi_density_energy.restype = ctypes.c_int
     lib.ndsi_autotune.argtypes = [vp, vp, vp, ctypes.c_double, ctypes.c_double, i32,
                                   ctypes.POINTER(i32), ctypes.POINTER(i32), vp]
     lib.ndsi_autotune.restype = ctypes.c_int
@@ -268,6 +271,13 @@ def ndsi_density(plan: Plan, H, S, mu, kT, n_poles, rho_out, n_elec_out=None, st
     _check(load().ndsi_density(plan.handle, _ptr(H), _ptr(S), float(mu), float(kT), int(n_poles),
                                _ptr(rho_out), _ptr(n_elec_out), _stream(stream)))
     return rho_out
+
+
+def ndsi_density_energy(plan: Plan, H, S, mu, kT, n_poles, rho_out, e_out, n_elec_out=None, stream=None):
+    """rho and the energy density matrix (Eq. 10) on the pattern in one sweep."""
+    _check(load().ndsi_density_energy(plan.handle, _ptr(H), _ptr(S), float(mu), float(kT), int(n_poles),
+                                      _ptr(rho_out), _ptr(e_out), _ptr(n_elec_out), _stream(stream)))
+    return rho_out, e_out
 
 
 def analyze_system(system, **options) -> Plan:
