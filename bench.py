@@ -228,11 +228,16 @@ def _autotune(nd, args, plan, H, S, kT, M):
     return {"tensor_core_steps": n_split, "fp64_steps": n_fp64}
 
 
-def _measure(nd, torch, plan, H, S, rho, ne, kT, M, steps, warmup, stream, flush, by_level=False):
+def _measure(nd, torch, plan, H, S, rho, ne, kT, M, steps, warmup, stream, flush, by_level=False,
+             e=None):
     """Time `steps` density sweeps as the library runs them (one captured CUDA graph per sweep),
-    then repeat them with direct launches and per-launch CUDA events for the kernel breakdown."""
+    then repeat them with direct launches and per-launch CUDA events for the kernel breakdown.
+    With `e` (an nnz device buffer) each sweep also forms the energy density matrix."""
     def step():
-        nd.ndsi_density(plan, H, S, MU, kT, M, rho, ne, stream=stream)
+        if e is None:
+            nd.ndsi_density(plan, H, S, MU, kT, M, rho, ne, stream=stream)
+        else:
+            nd.ndsi_density_energy(plan, H, S, MU, kT, M, rho, e, ne, stream=stream)
 
     def timed_steps():
         out = []
@@ -302,8 +307,9 @@ def run_ndsi(args):
     if world > 1:
         dist.barrier()
     with ClockSampler(local) as clk:
+        e_buf = torch.zeros_like(rho) if args.energy else None
         times, prof, prof_times = _measure(nd, torch, plan, H, S, rho, ne, kT, M, args.steps,
-                                           args.warmup, stream, flush, by_level=args.by_level)
+                                           args.warmup, stream, flush, by_level=args.by_level, e=e_buf)
         graph_nodes = nd.ndsi_graph_info(plan)
     if world > 1:
         dist.barrier()
@@ -369,6 +375,15 @@ def run_ndsi(args):
             err = max(err, float(np.max(np.abs(rho_main[sel] - ref[rows[sel], t_]))))
         parity = {"max_abs_err_rho": err, "columns": cols,
                   "tolerance": 1e-10 if args.precision == "fp64" else 1e-9}
+        if e_buf is not None:
+            from oracle.dense import energy_density_columns
+            e_main = e_buf.cpu().numpy()
+            eref = energy_density_columns(system, MU, kT, M, cols)
+            ee = 0.0
+            for t_, j in enumerate(cols):
+                sel = np.nonzero(system.col == j)[0]
+                ee = max(ee, float(np.max(np.abs(e_main[sel] - eref[rows[sel], t_]))))
+            parity["max_abs_err_energy_density"] = ee
     cpu = None
     ne_gpu = float(ne.cpu()[0])
     n_elec = {"value": ne_gpu}
@@ -383,7 +398,8 @@ def run_ndsi(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64" if args.precision == "fp64" else f"bf16x{info['split_slices']}->f64",
             "data": "synthetic",
-            "config": {"workload": system.meta["label"] + f", {M} poles, {args.precision} path",
+            "config": {"workload": system.meta["label"] + f", {M} poles, {args.precision} path"
+                                   + (", rho and energy density matrix" if args.energy else ""),
                        "n": system.n, "poles": M, "kT": kT, "mu": MU, "nnz": system.nnz,
                        "precision": args.precision, "split_slices": info["split_slices"],
                        "split_bands": info["split_bands"],
@@ -590,6 +606,8 @@ def main():
                     help="launch every kernel directly instead of replaying a captured CUDA graph")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep every eligible GEMM of a split plan on the tensor cores")
+    ap.add_argument("--energy", action="store_true",
+                    help="each step also forms the energy density matrix (Eq. 10)")
     ap.add_argument("--by-level", action="store_true",
                     help="kernel breakdown of GEMM and slicing steps per tree level")
     ap.add_argument("--outer", type=int, default=0,
