@@ -11,6 +11,9 @@ evaluates it as i R G(iR) with large R, whose real part tends to S^{-1}).
 N_e = Tr(rho S) (Eq. 40) = sum over the pattern of rho_ij S_ij.
 Energy density matrix (Eq. 10): e = 2 sum_nu eps_nu f c_nu c_nu^T by definition, or from G with
 the zeroth and first moments M0 = S^{-1}, M1 = S^{-1} H S^{-1}.
+Density of states from the retarded Green function (Eq. 41): D(E) = -(2/pi) Im Tr(G(E + i eta) S),
+by dense inverses, or as the sum of Lorentzians (2/pi) eta / ((E - eps_nu)^2 + eta^2) over the
+generalised eigenvalues (Tr(G(z) S) = sum_nu 1/(z - eps_nu) since c^T S c = I).
 """
 from __future__ import annotations
 
@@ -154,3 +157,20 @@ def energy_density_columns(system, mu, kT, M, cols):
         alpha = mu + 1j * zp / beta
         e = e - (4.0 / beta) * Rp * np.real(alpha * green_columns(system, alpha, cols))
     return e
+
+
+def dos_eig(eps, E, eta):
+    """Spin-summed Lorentzian-broadened density of states at energies E (route 1)."""
+    E = np.atleast_1d(np.asarray(E, dtype=np.float64))
+    d = E[:, None] - np.asarray(eps)[None, :]
+    return (2.0 / np.pi) * np.sum(eta / (d * d + eta * eta), axis=1)
+
+
+def dos_inv(Hd, Sd, E, eta):
+    """Eq. (41) as written: -(2/pi) Im Tr(G(E + i eta) S) with G by dense LU (route 2)."""
+    E = np.atleast_1d(np.asarray(E, dtype=np.float64))
+    out = np.empty(E.size)
+    for k, e in enumerate(E):
+        G = green_dense(Hd, Sd, e + 1j * eta)
+        out[k] = -(2.0 / np.pi) * np.imag(np.trace(G @ Sd))
+    return out
