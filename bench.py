@@ -540,9 +540,11 @@ def run_batched(args, nd, torch, dist, rank, world, local, prec_code):
 
 
 def run_mu_search(args):
-    """Chemical-potential search on the workload, plain (spectral bounds) and seeded by the
-    network trained here on exact-method mu of generated systems: exact density evaluations and
-    wall time per solve.  One JSON line; not part of the default run."""
+    """Chemical-potential search on the workload three ways: a bracket spanning the spectral
+    bounds ("bounds"), no bracket (the paper's opening sequence with the retarded-Green-function
+    trial mu, "dos_start") and the bracket proposed by the network trained here on exact-method mu
+    of generated systems ("seeded"): contour sweeps and wall time per solve.  One JSON line; not
+    part of the default run."""
     import numpy as np
     import torch
     from paper_1005_0088_gb300.build import build
@@ -570,24 +572,89 @@ def run_mu_search(args):
     nd.ndsi_density(plan, H, S, MU, kT, M, rho, ne)   # warm: tables, workspace, graph
     torch.cuda.synchronize()
     out = {}
-    for mode in ("plain", "seeded"):
+    for mode in ("bounds", "dos_start", "seeded"):
         t0 = time.perf_counter()
         lo = hi = 0.0
+        if mode == "bounds":
+            lo, hi = -1e6, 1e6      # clipped to the Gershgorin bounds of the pencil
         if mode == "seeded":
             lo, hi = model.bracket(features(plan, H, S, system.n_electrons, kT))
         mu, n_e, it = nd.ndsi_find_mu(plan, H, S, kT, M, system.n_electrons, rho, mu_lo=lo, mu_hi=hi)
         torch.cuda.synchronize()
         out[mode] = {"evaluations": it, "ms": (time.perf_counter() - t0) * 1e3, "mu": mu,
                      "electron_error": n_e - system.n_electrons}
-    line = {"metric": "chemical-potential search: exact density evaluations per solve",
-            "value": out["seeded"]["evaluations"], "unit": "evaluations", "higher_is_better": False,
+    line = {"metric": "chemical-potential search: contour sweeps per solve",
+            "value": out["seeded"]["evaluations"], "unit": "sweeps", "higher_is_better": False,
             "n_gpus": 1, "data": "synthetic",
             "config": {"workload": system.meta["label"], "poles": M, "kT": kT, "precision": args.precision,
                        "n_electrons": system.n_electrons, "tolerance_electrons": 1e-8},
-            "plain": out["plain"], "seeded": out["seeded"],
+            "bounds": out["bounds"], "dos_start": out["dos_start"], "seeded": out["seeded"],
             "seed_model": {"training_systems": args.mu_train, "train_rmse_mu": model.rmse,
                            "dataset_s": t_data, "train_s": t_train,
                            "bracket_half_width": 3.0 * max(model.rmse or 0.05, 1e-3)}}
+    print(json.dumps(line))
+    return 0
+
+
+def run_eigen(args):
+    """Selected eigenstates near mu (App. B) on the workload: one factorisation at xi + i eta, the
+    block shift-invert iteration to |Hc - eps Sc| < 1e-10, and the three-step solve timed alone
+    (16 right-hand sides) against the HBM roofline of the fronts it reads.  One JSON line; not
+    part of the default run."""
+    import numpy as np
+    import torch
+    from paper_1005_0088_gb300.build import build
+    build()
+    import paper_1005_0088_gb300 as nd
+    from synth import config_system
+    torch.cuda.set_device(0)
+    system = config_system(args.config)
+    prec = {"fp64": nd.NDSI_PREC_FP64, "split": nd.NDSI_PREC_SPLIT}[args.precision]
+    plan = nd.analyze_system(system, precision=prec, split_slices=args.slices)
+    H = torch.as_tensor(system.H, device="cuda")
+    S = torch.as_tensor(system.S, device="cuda")
+    xi, n_states, block, eta = MU, 8, 12, 1e-3
+    nd.ndsi_eigenstates(plan, H, S, xi, n_states, eta=eta, block=block)          # warm
+    t0 = time.perf_counter()
+    eps, C, res, iters = nd.ndsi_eigenstates(plan, H, S, xi, n_states, eta=eta, block=block)
+    t_eig = time.perf_counter() - t0
+    # the three-step solve alone, 16 right-hand sides, against the bytes of the fronts it reads
+    f = nd.ndsi_factor_poles(plan, H, S, np.array([xi + 1j * eta]))
+    k = 16
+    Y = torch.randn(system.n, k, dtype=torch.complex128, device="cuda")
+    X = torch.zeros_like(Y)
+    for _ in range(3):
+        nd.ndsi_factors_solve(f, 0, Y, X)
+    reps = 10
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record()
+    for _ in range(reps):
+        nd.ndsi_factors_solve(f, 0, Y, X)
+    ev1.record()
+    torch.cuda.synchronize()
+    ms_solve = ev0.elapsed_time(ev1) / reps
+    info = nd.ndsi_plan_info(plan)
+    front_bytes = 16.0 * info["front_elems"]
+    groups = (k + 7) // 8
+    # forward reads A^{-1} (lower) and L_RJ, backward L_RJ again, once per group of 8 right-hand
+    # sides; counted as two passes over the whole fronts per group (an upper bound of the reads)
+    alg_bytes = groups * 2.0 * front_bytes + 4 * 16.0 * system.n * k
+    peak = _peaks().get("hbm_gbs", 6800.0)
+    line = {"metric": "selected eigenstates near mu: wall time per solve", "value": t_eig * 1e3, "unit": "ms",
+            "higher_is_better": False, "n_gpus": 1, "data": "synthetic",
+            "config": {"workload": system.meta["label"], "n": system.n, "xi": xi, "eta": eta,
+                       "n_states": n_states, "block": block, "precision": args.precision},
+            "iterations": iters, "max_residual": float(np.max(res)), "eps": [float(e) for e in eps],
+            "solve": {"rhs": k, "ms": ms_solve, "bytes_per_solve_bound": alg_bytes,
+                      "gbs": alg_bytes / ms_solve / 1e6, "peak_gbs": peak,
+                      "frac": alg_bytes / ms_solve / 1e6 / peak,
+                      "peak_source": "of measured (MEASURED_PEAKS.json hbm_gbs)"}}
+    if system.n <= 4096 and not args.no_cpu:
+        from oracle.eigen import eigenstates_near
+        Hd, Sd = system.dense()
+        eps_ref, _ = eigenstates_near(Hd, Sd, xi, n_states)
+        line["parity"] = {"max_abs_err_eps": float(np.max(np.abs(eps - eps_ref))), "oracle": "dense eigh"}
     print(json.dumps(line))
     return 0
 
@@ -624,6 +691,8 @@ def main():
                     help="skip the run of the other precision (split-vs-FP64 speedup)")
     ap.add_argument("--mu-search", action="store_true",
                     help="time the chemical-potential search, plain and seeded by the trained network")
+    ap.add_argument("--eigen", action="store_true",
+                    help="time the selected-eigenstates solver (App. B) near mu")
     ap.add_argument("--mu-train", type=int, default=2000,
                     help="generated systems the mu-search network is trained on")
     args = ap.parse_args()
@@ -631,6 +700,8 @@ def main():
         return run_reference(args)
     if args.mu_search:
         return run_mu_search(args)
+    if args.eigen:
+        return run_eigen(args)
     return run_ndsi(args)
 
 

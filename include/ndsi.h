@@ -175,6 +175,20 @@ int ndsi_factor_poles(ndsi_plan* plan, const double* H, const double* S, const d
  * Synchronises `stream`.  Errors: NDSI_ERR_SINGULAR (pivot check), NDSI_ERR_CUDA. */
 int ndsi_selinv(ndsi_factors* f, double* G_out, void* stream);
 
+/* Solve (z_p S - H) X = Y with the factors of pole p (App. B, Eqs. B8-B15, in supernodal form:
+ * forward elimination leaves first, y_R(J) -= L_RJ y_J; the diagonal step w_J = A_J^{-1} y_J;
+ * back substitution root first, x_J = w_J - L_RJ^T x_R(J)).  Valid until ndsi_selinv runs on the
+ * same factors (it overwrites them with G).
+ *   pole   - 0 <= pole < n_poles of ndsi_factor_poles.
+ *   Y      - k complex right-hand sides, interleaved double[2 * n * k], row-major by basis
+ *            index (Y[2*(i*k + c)] is Re of row i of right-hand side c), original basis order;
+ *            device or host; not modified.
+ *   X_out  - the solutions in the same layout, device or host.
+ * Synchronises the stream.  Errors: NDSI_ERR_INVALID (null pointers, k < 1, pole out of range,
+ * factors already inverted, a batched plan), NDSI_ERR_OOM, NDSI_ERR_CUDA. */
+int ndsi_factors_solve(ndsi_factors* f, int32_t pole, const double* Y, int32_t k, double* X_out,
+                       void* stream);
+
 /* Density matrix by the contour sum of Eq. 8 with M = n_poles pole pairs:
  *   rho = M0 + sum_p w_p Re G(alpha_p),  alpha_p = mu + i z_p/beta,  w_p = -4 R_p/beta,
  * with M0 = Re(iR G(iR)) (the zeroth moment, R = opt.m0_radius), and
@@ -272,20 +286,91 @@ int ndsi_profile_read(const ndsi_plan* plan, ndsi_profile_entry* out, int32_t ma
 int ndsi_residue_sum_static(const double* G, const double* c, int32_t n_points, const double* S,
                             int64_t nnz, double* rho_out, double* n_elec_out, void* stream);
 
+/* Selected eigenstates near an energy xi (App. B): the n_states pairs of H c = eps S c with the
+ * smallest |eps - xi|, by the block shift-invert iteration (B2)-(B3).  The pencil is factored once
+ * at z = xi + i eta (eta > 0 keeps every pivot block nonsingular without pivoting; the paper's
+ * real shift is the limit eta -> 0); each step forms b = (z S - H)^{-1} S c for the `block`
+ * vectors c with that factorisation (ndsi_factors_solve's three steps), solves (B3) in the real
+ * span of Re b and Im b (2 x block vectors; S-Gram directions below 1e-12 of the largest are
+ * dropped) and keeps the `block` Ritz pairs nearest xi.  The loop stops when the n_states nearest
+ * have |H c - eps S c|_2 < tol (c S-normalised).  Split precision changes only the speed of
+ * convergence: the Ritz pairs and residuals use the exact H and S.
+ *   H, S       - values on the pattern, device or host.
+ *   xi, eta    - the shift; eta > 0 (about the wanted level spacing or smaller).
+ *   n_states   - >= 1;  block - n_states..32, and <= n.
+ *   max_iter   - >= 1;  tol > 0;  seed - of the starting block (counter-based uniform [-1, 1)).
+ *   eps_out    - host double[n_states], ascending.
+ *   C_out      - device or host double[n_states * n]: state j at C_out[j*n + i], original basis
+ *                order, S-orthonormal, largest-magnitude component positive.
+ *   resid_out  - host double[n_states] or NULL;  iters_out - host or NULL.
+ * Synchronises the stream.  Errors: NDSI_ERR_INVALID (arguments, a batched plan),
+ * NDSI_ERR_TIMEOUT (not converged in max_iter; the current pairs are still written),
+ * NDSI_ERR_SINGULAR (pivot check, non-finite projections or a collapsed search space),
+ * NDSI_ERR_OOM, NDSI_ERR_CUDA. */
+int ndsi_eigenstates(ndsi_plan* plan, const double* H, const double* S, double xi, double eta,
+                     int32_t n_states, int32_t block, int32_t max_iter, double tol, uint64_t seed,
+                     double* eps_out, double* C_out, double* resid_out, int32_t* iters_out,
+                     void* stream);
+
+/* Density of states from the retarded Green function (Eq. 41):
+ *   D(E_k) = -(2/pi) Im Tr(G(E_k + i eta) S),  G(z) = (z S - H)^{-1},
+ * the spin-summed density of states broadened by a Lorentzian of half-width eta (for each
+ * generalised eigenvalue eps_nu it contributes (2/pi) eta / ((E - eps_nu)^2 + eta^2)).  One
+ * sweep of factorisation and selected inversion over the n_energies points (chunked to the
+ * workspace), then Tr(G S) = sum over the pattern of G_ij S_ij.  Single-system plans only.
+ *   H, S        - values on the pattern, device or host.
+ *   energies    - host double[n_energies], the real parts E_k.
+ *   eta         - > 0, the imaginary part shared by every point.
+ *   dos_out     - host double[n_energies], D(E_k).
+ * Synchronises the stream before returning.
+ * Errors: NDSI_ERR_INVALID (null or device energies/dos_out, n_energies < 1, eta <= 0, a
+ * non-finite energy, a batched plan), NDSI_ERR_OOM, NDSI_ERR_CUDA, and the pivot errors of
+ * ndsi_factor_poles (an energy on the real axis exactly at a singular point cannot occur for
+ * eta > 0). */
+int ndsi_dos(ndsi_plan* plan, const double* H, const double* S, const double* energies,
+             int32_t n_energies, double eta, double* dos_out, void* stream);
+
+/* Callbacks of ndsi_mu_search: DeltaN(mu) = Tr(rho(mu) S) - n_electrons into *dn, and the
+ * density of states D(E_k) = -(2/pi) Im Tr(G(E_k + i eta) S) for n energies into D.  Return 0 on
+ * success; any other value stops the search, which returns it. */
+typedef int (*ndsi_mu_eval_fn)(void* ctx, double mu, double* dn);
+typedef int (*ndsi_mu_dos_fn)(void* ctx, const double* E, int32_t n, double eta, double* D);
+
+/* The search of ndsi_find_mu over caller-supplied evaluations (host only, no GPU work): solves
+ * DeltaN(mu) = 0 (Eq. 40) for an increasing DeltaN inside the spectral bounds [elo, ehi].
+ *   With mu_lo < mu_hi the bracket is evaluated first; otherwise, when `dos` is given, one call
+ *   of it on n_grid energies evenly spanning [elo, ehi] (eta two grid spacings) builds the
+ *   density-of-states model of procedure (2) (Eqs. 41-43) and the search starts where the
+ *   model holds n_electrons; without `dos`, at the middle of the bounds.
+ *   While all evaluations have one sign it steps by the model anchored at the best point
+ *   (DeltaN_i + integral D [f((E - mu)/kT) - f((E - mu_i)/kT)] dE = 0), or by doubling steps
+ *   when that stalls.  With both signs it takes the Muller step (procedure (4), Eqs. 45-46) on the
+ *   three points of smallest |DeltaN| with both signs, else the linear step (procedure (3),
+ *   Eq. 44 with the denominator read as DeltaN_i - DeltaN_j), else the anchored model step, any
+ *   of them only strictly inside the bracket, and bisects after a step that does not halve the
+ *   smallest |DeltaN|.
+ *   mu_out, dn_out, evals_out - host; the best mu, its DeltaN, and the evaluations used (the
+ *   density-of-states call counts as one).  They are written on every return.
+ * Errors: NDSI_ERR_INVALID (elo >= ehi, kT <= 0, tol <= 0, max_iter < 1, no sign change within
+ * the bounds), NDSI_ERR_TIMEOUT (not converged in max_iter), NDSI_ERR_SINGULAR (non-finite
+ * DeltaN), or a callback's own non-zero return. */
+int ndsi_mu_search(ndsi_mu_eval_fn eval, ndsi_mu_dos_fn dos, void* ctx, double elo, double ehi,
+                   double kT, double n_electrons, int32_t n_grid, double mu_lo, double mu_hi,
+                   double tol_electrons, int32_t max_iter, double* mu_out, double* dn_out,
+                   int32_t* evals_out);
+
 /* Chemical-potential search (Sec. II.C.3): find mu with
  *   DeltaN(mu) = Tr(rho(mu) S) - n_electrons = 0      (Eq. 40)
  * to |DeltaN| < tol_electrons.  Every trial mu is one full contour evaluation (ndsi_density).
  * The bracket [mu_lo, mu_hi] (e.g. from a learned seed) is checked first and, if it does not
- * enclose the root, widened step by step towards the Gershgorin bounds of the pencil (H, S);
- * pass mu_lo >= mu_hi to start from those bounds.  Inside the bracket each step takes the
- * paper's Muller step (procedure (4), Eqs. 45-46: the positive-slope root of the quadratic
- * through the three evaluations with the smallest |DeltaN| and both signs), else the linear
- * interpolation of procedure (3) between the bracket ends (Eq. 44 with the denominator read as
- * DeltaN_i - DeltaN_j, Illinois-weighted), and bisects whenever a step would leave the
- * bracket's central 98% or two steps fail to halve it.
+ * enclose the root, widened step by step towards the Gershgorin bounds of the pencil (H, S).
+ * With mu_lo >= mu_hi the search starts from the density of states of the retarded Green
+ * function instead (procedure (2), Eqs. 41-43: ndsi_dos on n_poles + 1 energies spanning the
+ * bounds, one sweep of factorisation and selected inversion, counted as one evaluation).  The
+ * steps are those of ndsi_mu_search, each trial mu one contour evaluation.
  *   H, S            - values on the pattern, device or host.
  *   rho_out         - rho at the returned mu, device or host (double[nnz]).
- *   mu_out, n_elec_out, iters_out - host scalars (iters = contour evaluations used).
+ *   mu_out, n_elec_out, iters_out - host scalars (iters = contour sweeps used).
  * Errors: NDSI_ERR_INVALID (kT <= 0, n_poles < 1, tol <= 0, no sign change within the bounds),
  * NDSI_ERR_TIMEOUT if max_iter evaluations do not converge (the best mu is still returned),
  * and every error of ndsi_density. */

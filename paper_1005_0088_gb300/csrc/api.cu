@@ -13,6 +13,7 @@
 #include "ndsi.h"
 #include "plan.hpp"
 #include "split_gemm.cuh"
+#include "solve.cuh"
 
 namespace ndsi {
 // Event-timed launch records, resolved after the stream synchronises, keyed by kernel family
@@ -78,6 +79,10 @@ struct ndsi_plan {
     unsigned long long* gersh = nullptr;  // Gershgorin bound of (H, S) for the moment points
     int32_t cw_cap = 0;
     double* partials = nullptr;  // trace reduction scratch
+    double* dos_part = nullptr;  // per-point trace partials of the retarded-Green-function step
+    double* dos_tr = nullptr;
+    double2* dos_z = nullptr;
+    int64_t dos_cap = 0;
     double* stage = nullptr;     // staging for host H, S, rho, n_elec
     int64_t stage_cap = 0;
     std::vector<double> pole_z, pole_R;  // cached continued-fraction poles
@@ -89,6 +94,9 @@ struct ndsi_plan {
     cudaGraphExec_t graph = nullptr;
     std::vector<const void*> graph_key;
     int64_t graph_nodes = 0;
+    // tables of the triangular solves (built on first use)
+    ndsi::SolveTables ST;
+    double2* point_z = nullptr;  // the single point factored for the eigensolver
 };
 
 struct ndsi_factors {
@@ -97,6 +105,7 @@ struct ndsi_factors {
     ndsi::SplitBuffers SB;
     double2* zd = nullptr;
     int32_t np = 0;
+    bool inverted = false;  // ndsi_selinv has replaced the factors by G
 };
 
 namespace ndsi {
@@ -446,6 +455,41 @@ void setup_split(ndsi_plan* h, const ndsi_options& o) {
 }
 int sweep(ndsi_plan* h, const double* Hd, const double* Sd, int32_t nq, int32_t chunk,
           const std::vector<int>& part_off, double* rho_d, double* ne_d, double* e_d, cudaStream_t st);
+int dos_sweep(ndsi_plan* h, const double* Hd, const double* Sd, const double* E, int nE, double eta,
+              double* D, cudaStream_t st);
+
+// Callbacks of the chemical-potential search: DeltaN from one contour evaluation, and the
+// density of states from one sweep of the retarded Green function.
+struct FindMuCtx {
+    ndsi_plan* h;
+    const double *Hd, *Sd;
+    double kT;
+    int32_t n_poles;
+    double n_electrons;
+    double *rho_d, *ne_d;
+    cudaStream_t st;
+    double last_mu;
+    bool have_last;
+};
+
+int find_mu_eval(void* c, double mu, double* dn) {
+    FindMuCtx& x = *static_cast<FindMuCtx*>(c);
+    int r = density_impl(x.h, x.Hd, x.Sd, &mu, &x.kT, x.n_poles, x.rho_d, x.ne_d, x.st);
+    if (r) return r;
+    double ne = 0;
+    if (cudaMemcpy(&ne, x.ne_d, sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return fail(NDSI_ERR_CUDA, "ndsi_find_mu: readback failed");
+    x.last_mu = mu;
+    x.have_last = true;
+    *dn = ne - x.n_electrons;
+    return NDSI_OK;
+}
+
+int find_mu_dos(void* c, const double* E, int32_t n, double eta, double* D) {
+    FindMuCtx& x = *static_cast<FindMuCtx*>(c);
+    return dos_sweep(x.h, x.Hd, x.Sd, E, n, eta, D, x.st);
+}
+
 }  // namespace ndsi
 
 using namespace ndsi;
@@ -698,6 +742,7 @@ int ndsi_selinv(ndsi_factors* f, double* G_out, void* stream) {
     ndsi_plan* h = f->plan;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     int rc = run_phase(h, f->W, f->SB, 1, nullptr, nullptr, f->zd, 0, f->np, st);
+    f->inverted = true;
     if (rc) return rc;
     if (G_out) {
         const bool dev = is_device_ptr(G_out);
@@ -896,6 +941,178 @@ int density_impl(ndsi_plan* h, const double* Hd, const double* Sd, const double*
     return check_status(h, st);
 }
 
+// Device buffer that frees itself (scratch of the solve and eigensolver entry points).
+struct DevBuf {
+    void* p = nullptr;
+    ~DevBuf() {
+        if (p) cudaFree(p);
+    }
+    template <class T>
+    T* as() const {
+        return static_cast<T*>(p);
+    }
+    cudaError_t alloc(size_t bytes) { return cudaMalloc(&p, std::max<size_t>(bytes, 16)); }
+};
+
+int ensure_solve_tables(ndsi_plan* h) {
+    if (h->ST.blob) return NDSI_OK;
+    cudaError_t e = solve_tables_build(h->P, h->ST);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        solve_tables_free(h->ST);
+        return fail(e == cudaErrorMemoryAllocation ? NDSI_ERR_OOM : NDSI_ERR_CUDA,
+                    std::string("solve tables: ") + cudaGetErrorString(e));
+    }
+    return NDSI_OK;
+}
+
+// Symmetric eigendecomposition by cyclic Jacobi rotations (Golub & Van Loan, Matrix
+// Computations, Sec. 8.5): A (n x n, row-major) is overwritten; eigenvalues in w, eigenvectors as
+// the columns of V (row-major).  For the small projected problems of the eigensolver only.
+void jacobi_eig(int n, std::vector<double>& A, std::vector<double>& w, std::vector<double>& V) {
+    V.assign(static_cast<size_t>(n) * n, 0.0);
+    for (int i = 0; i < n; ++i) V[i * n + i] = 1.0;
+    for (int sweep = 0; sweep < 64; ++sweep) {
+        double off = 0.0, all = 0.0;
+        for (int p = 0; p < n; ++p)
+            for (int q = 0; q < n; ++q) {
+                all += A[p * n + q] * A[p * n + q];
+                if (p != q) off += A[p * n + q] * A[p * n + q];
+            }
+        if (off <= 1e-32 * all) break;
+        for (int p = 0; p < n - 1; ++p)
+            for (int q = p + 1; q < n; ++q) {
+                const double apq = A[p * n + q];
+                if (apq == 0.0) continue;
+                const double tau = (A[q * n + q] - A[p * n + p]) / (2.0 * apq);
+                const double t = (tau >= 0 ? 1.0 : -1.0) / (std::fabs(tau) + std::sqrt(1.0 + tau * tau));
+                const double c = 1.0 / std::sqrt(1.0 + t * t), sn = t * c;
+                for (int k = 0; k < n; ++k) {  // columns p, q of A J
+                    const double akp = A[k * n + p], akq = A[k * n + q];
+                    A[k * n + p] = c * akp - sn * akq;
+                    A[k * n + q] = sn * akp + c * akq;
+                }
+                for (int k = 0; k < n; ++k) {  // rows p, q of J^T (A J)
+                    const double apk = A[p * n + k], aqk = A[q * n + k];
+                    A[p * n + k] = c * apk - sn * aqk;
+                    A[q * n + k] = sn * apk + c * aqk;
+                }
+                for (int k = 0; k < n; ++k) {
+                    const double vkp = V[k * n + p], vkq = V[k * n + q];
+                    V[k * n + p] = c * vkp - sn * vkq;
+                    V[k * n + q] = sn * vkp + c * vkq;
+                }
+            }
+    }
+    w.resize(n);
+    for (int i = 0; i < n; ++i) w[i] = A[i * n + i];
+}
+
+// Rayleigh-Ritz of (B3) in the span of the m columns whose Gram matrices are Hs = V^T H V and
+// Ss = V^T S V (row-major m x m): columns are scaled to unit S-norm, directions with an S-Gram
+// eigenvalue below 1e-12 of the largest are dropped, and the reduced standard problem is solved.
+// Returns the Ritz values e and coefficients Y (m x e.size(), row-major) with Y^T Ss Y = I.
+void rayleigh_ritz(int m, const std::vector<double>& Hs, const std::vector<double>& Ss, std::vector<double>& e,
+                   std::vector<double>& Y) {
+    std::vector<double> d(m);
+    for (int a = 0; a < m; ++a) d[a] = Ss[a * m + a] > 0 ? 1.0 / std::sqrt(Ss[a * m + a]) : 0.0;
+    std::vector<double> Sn(static_cast<size_t>(m) * m), Hn(static_cast<size_t>(m) * m);
+    for (int a = 0; a < m; ++a)
+        for (int b = 0; b < m; ++b) {
+            Sn[a * m + b] = 0.5 * (Ss[a * m + b] + Ss[b * m + a]) * d[a] * d[b];
+            Hn[a * m + b] = 0.5 * (Hs[a * m + b] + Hs[b * m + a]) * d[a] * d[b];
+        }
+    std::vector<double> lam, Q;
+    jacobi_eig(m, Sn, lam, Q);
+    double lmax = 0.0;
+    for (double l : lam) lmax = std::max(lmax, l);
+    std::vector<int> keep;
+    for (int i = 0; i < m; ++i)
+        if (lam[i] > 1e-12 * lmax) keep.push_back(i);
+    const int r = static_cast<int>(keep.size());
+    std::vector<double> T(static_cast<size_t>(m) * r);  // m x r: Q_keep Lambda^{-1/2}
+    for (int a = 0; a < m; ++a)
+        for (int j = 0; j < r; ++j) T[a * r + j] = Q[a * m + keep[j]] / std::sqrt(lam[keep[j]]);
+    std::vector<double> HT(static_cast<size_t>(m) * r, 0.0), Ht(static_cast<size_t>(r) * r, 0.0);
+    for (int a = 0; a < m; ++a)
+        for (int j = 0; j < r; ++j) {
+            double acc = 0.0;
+            for (int b = 0; b < m; ++b) acc += Hn[a * m + b] * T[b * r + j];
+            HT[a * r + j] = acc;
+        }
+    for (int i = 0; i < r; ++i)
+        for (int j = 0; j < r; ++j) {
+            double acc = 0.0;
+            for (int a = 0; a < m; ++a) acc += T[a * r + i] * HT[a * r + j];
+            Ht[i * r + j] = acc;
+        }
+    for (int i = 0; i < r; ++i)
+        for (int j = 0; j < i; ++j) Ht[i * r + j] = Ht[j * r + i] = 0.5 * (Ht[i * r + j] + Ht[j * r + i]);
+    std::vector<double> W;
+    jacobi_eig(r, Ht, e, W);
+    Y.assign(static_cast<size_t>(m) * r, 0.0);
+    for (int a = 0; a < m; ++a)
+        for (int j = 0; j < r; ++j) {
+            double acc = 0.0;
+            for (int i = 0; i < r; ++i) acc += T[a * r + i] * W[i * r + j];
+            Y[a * r + j] = d[a] * acc;
+        }
+}
+
+// Uniform [-1, 1) numbers from a counter (splitmix64 finaliser) for the starting block.
+double counter_uniform(uint64_t seed, uint64_t i) {
+    uint64_t x = seed + 0x9E3779B97F4A7C15ull * (i + 1);
+    x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+    x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+    x ^= x >> 31;
+    return static_cast<double>(x >> 11) * (2.0 / 9007199254740992.0) - 1.0;
+}
+
+// Density of states from the retarded Green function (Eq. 41): D(E_k) = -(2/pi) Im Tr(G(E_k +
+// i eta) S) for nE energies, one batched sweep of factorisation + selected inversion (chunked to
+// the workspace) and a per-point trace on the pattern.  Host energies in, host D out.
+int dos_sweep(ndsi_plan* h, const double* Hd, const double* Sd, const double* E, int nE, double eta,
+              double* D, cudaStream_t st) {
+    std::vector<double2> z(nE);
+    for (int k = 0; k < nE; ++k) z[k] = make_double2(E[k], eta);
+    const int64_t per_pole = bytes_per_pole(h);
+    const int64_t cap = workspace_cap(h);
+    if (cap < per_pole) return fail(NDSI_ERR_OOM, "ndsi_dos: one point does not fit the workspace cap");
+    const int32_t chunk = static_cast<int32_t>(std::min<int64_t>(nE, std::max<int64_t>(1, cap / per_pole)));
+    int rc = alloc_workspace(h->W, h->P, std::max<int32_t>(chunk, h->W.np_cap));
+    if (rc) return rc;
+    if (h->P.opt.precision == NDSI_PREC_SPLIT)
+        NDSI_CK(split_alloc(h->SB, h->SP.steps, h->P.opt.split_slices, std::max<int32_t>(chunk, h->W.np_cap)));
+    const int nb = accumulate_blocks(h->P.nnz);
+    if (h->dos_cap < nE) {
+        if (h->dos_part) cudaFree(h->dos_part);
+        if (h->dos_tr) cudaFree(h->dos_tr);
+        if (h->dos_z) cudaFree(h->dos_z);
+        h->dos_part = h->dos_tr = nullptr;
+        h->dos_z = nullptr;
+        h->dos_cap = 0;
+        NDSI_CK(cudaMalloc(&h->dos_part, sizeof(double) * static_cast<size_t>(nE) * nb));
+        NDSI_CK(cudaMalloc(&h->dos_tr, sizeof(double) * (nE + 1)));
+        NDSI_CK(cudaMalloc(&h->dos_z, sizeof(double2) * nE));
+        h->dos_cap = nE;
+    }
+    NDSI_CK(cudaMemcpyAsync(h->dos_z, z.data(), sizeof(double2) * nE, cudaMemcpyHostToDevice, st));
+    for (int q0 = 0; q0 < nE; q0 += chunk) {
+        const int np = std::min(chunk, nE - q0);
+        rc = run_phase(h, h->W, h->SB, 0, Hd, Sd, h->dos_z + q0, nE, np, st);
+        if (!rc) rc = run_phase(h, h->W, h->SB, 1, Hd, Sd, h->dos_z + q0, nE, np, st);
+        if (rc) return rc;
+        NDSI_CK(launch_point_traces(h->P, h->T, h->W, np, Sd, h->dos_part, h->dos_tr + q0, st));
+    }
+    std::vector<double> tr(nE);
+    NDSI_CK(cudaMemcpyAsync(tr.data(), h->dos_tr, sizeof(double) * nE, cudaMemcpyDeviceToHost, st));
+    NDSI_CK(cudaStreamSynchronize(st));
+    rc = check_status(h, st);
+    if (rc) return rc;
+    for (int k = 0; k < nE; ++k) D[k] = (-2.0 / M_PI) * tr[k];
+    return NDSI_OK;
+}
+
 // One density sweep over all points, chunked: factor, selected inversion and residue sum per
 // chunk, then the per-system electron counts.  Only stream-ordered work: it is also the body of
 // the captured graph.
@@ -933,6 +1150,176 @@ int sweep(ndsi_plan* h, const double* Hd, const double* Sd, int32_t nq, int32_t 
 }  // namespace ndsi
 
 extern "C" {
+
+int ndsi_factors_solve(ndsi_factors* f, int32_t pole, const double* Y, int32_t k, double* X_out, void* stream) {
+    if (!f || !f->plan || !Y || !X_out || k < 1 || pole < 0 || pole >= f->np)
+        return fail(NDSI_ERR_INVALID, "ndsi_factors_solve: invalid argument");
+    if (f->inverted) return fail(NDSI_ERR_INVALID, "ndsi_factors_solve: ndsi_selinv has overwritten the factors");
+    ndsi_plan* h = f->plan;
+    if (h->P.n_systems != 1) return fail(NDSI_ERR_INVALID, "ndsi_factors_solve: batched plan");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    int rc = ensure_solve_tables(h);
+    if (rc) return rc;
+    const size_t bytes = sizeof(double2) * static_cast<size_t>(h->P.n) * k;
+    DevBuf yw, xw;
+    NDSI_CK(yw.alloc(bytes));
+    const bool x_dev = is_device_ptr(X_out);
+    if (!x_dev) NDSI_CK(xw.alloc(bytes));
+    double2* xd = x_dev ? reinterpret_cast<double2*>(X_out) : xw.as<double2>();
+    NDSI_CK(cudaMemcpyAsync(yw.p, Y, bytes, cudaMemcpyDefault, st));
+    NDSI_CK(launch_solve(h->P, h->ST, f->W.fronts + static_cast<int64_t>(pole) * f->W.front_stride, yw.as<double2>(), xd,
+                         k, st));
+    if (!x_dev) NDSI_CK(cudaMemcpyAsync(X_out, xd, bytes, cudaMemcpyDeviceToHost, st));
+    NDSI_CK(cudaStreamSynchronize(st));
+    return NDSI_OK;
+}
+
+int ndsi_eigenstates(ndsi_plan* h, const double* H, const double* S, double xi, double eta, int32_t n_states,
+                     int32_t block, int32_t max_iter, double tol, uint64_t seed, double* eps_out, double* C_out,
+                     double* resid_out, int32_t* iters_out, void* stream) {
+    if (!h || !H || !S || !eps_out || !C_out || !std::isfinite(xi) || !(eta > 0) || !std::isfinite(eta) ||
+        n_states < 1 || block < n_states || block > 32 || max_iter < 1 || !(tol > 0))
+        return fail(NDSI_ERR_INVALID, "ndsi_eigenstates: invalid argument");
+    if (h->P.n_systems != 1) return fail(NDSI_ERR_INVALID, "ndsi_eigenstates: batched plan");
+    const int64_t n = h->P.n;
+    if (block > n) return fail(NDSI_ERR_INVALID, "ndsi_eigenstates: block larger than the matrix");
+    if (is_device_ptr(eps_out) || (resid_out && is_device_ptr(resid_out)))
+        return fail(NDSI_ERR_INVALID, "ndsi_eigenstates: eps_out and resid_out are host arrays");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    int rc = upload_tables(h);
+    if (!rc) rc = ensure_solve_tables(h);
+    if (rc) return rc;
+    const double *Hd, *Sd;
+    rc = device_inputs(h, H, S, &Hd, &Sd, st);
+    if (rc) return rc;
+    // factor z S - H at z = xi + i eta (one point): A_J^{-1} and L_RJ stay in the workspace fronts
+    const int32_t np = std::max<int32_t>(1, h->W.np_cap);
+    rc = alloc_workspace(h->W, h->P, np);
+    if (rc) return rc;
+    if (h->P.opt.precision == NDSI_PREC_SPLIT) NDSI_CK(split_alloc(h->SB, h->SP.steps, h->P.opt.split_slices, np));
+    if (!h->point_z) NDSI_CK(cudaMalloc(&h->point_z, sizeof(double2)));
+    const double2 z = make_double2(xi, eta);
+    NDSI_CK(cudaMemcpyAsync(h->point_z, &z, sizeof(double2), cudaMemcpyHostToDevice, st));
+    rc = run_phase(h, h->W, h->SB, 0, Hd, Sd, h->point_z, 1, 1, st);
+    if (rc) return rc;
+    // buffers: complex right-hand sides and solutions, V = [Re B | Im B], H V, S V, the block C
+    const int mmax = 2 * block;
+    const int nb = gram_blocks(n);
+    DevBuf yb, xb, vb, hvb, svb, cb, gp, gram, yc, ec, rp;
+    NDSI_CK(yb.alloc(sizeof(double2) * n * block));
+    NDSI_CK(xb.alloc(sizeof(double2) * n * block));
+    NDSI_CK(vb.alloc(sizeof(double) * n * mmax));
+    NDSI_CK(hvb.alloc(sizeof(double) * n * mmax));
+    NDSI_CK(svb.alloc(sizeof(double) * n * mmax));
+    NDSI_CK(cb.alloc(sizeof(double) * n * block));
+    NDSI_CK(gp.alloc(sizeof(double) * nb * 2 * mmax * mmax));
+    NDSI_CK(gram.alloc(sizeof(double) * 2 * mmax * mmax));
+    NDSI_CK(yc.alloc(sizeof(double) * mmax * block));
+    NDSI_CK(ec.alloc(sizeof(double) * block));
+    NDSI_CK(rp.alloc(sizeof(double) * nb * block));
+    int m = block;
+    {
+        std::vector<double> c0(static_cast<size_t>(n) * m);
+        for (size_t i = 0; i < c0.size(); ++i) c0[i] = counter_uniform(seed, i);
+        NDSI_CK(cudaMemcpyAsync(cb.p, c0.data(), sizeof(double) * c0.size(), cudaMemcpyHostToDevice, st));
+        NDSI_CK(cudaStreamSynchronize(st));
+    }
+    std::vector<double> e, Y, res(block, 0.0), gh(2 * mmax * mmax);
+    std::vector<int> order;
+    int it = 0;
+    bool done = false;
+    while (!done && it < max_iter) {
+        ++it;
+        // (B2): b = (z S - H)^{-1} S c, the shift-invert product with the factors of z
+        NDSI_CK(launch_spmm(h->T.rowptr, h->T.col, Sd, n, cb.as<double>(), m, vb.as<double>(), m, m, st));
+        NDSI_CK(launch_real_to_complex(vb.as<double>(), n * m, yb.as<double2>(), st));
+        NDSI_CK(launch_solve(h->P, h->ST, h->W.fronts, yb.as<double2>(), xb.as<double2>(), m, st));
+        // (B3) in the real span of Re b and Im b
+        const int m2 = 2 * m;
+        NDSI_CK(launch_split_complex(xb.as<double2>(), n, m, vb.as<double>(), st));
+        NDSI_CK(launch_spmm(h->T.rowptr, h->T.col, Hd, n, vb.as<double>(), m2, hvb.as<double>(), m2, m2, st));
+        NDSI_CK(launch_spmm(h->T.rowptr, h->T.col, Sd, n, vb.as<double>(), m2, svb.as<double>(), m2, m2, st));
+        NDSI_CK(launch_gram(vb.as<double>(), hvb.as<double>(), svb.as<double>(), n, m2, gp.as<double>(), gram.as<double>(),
+                            st));
+        NDSI_CK(cudaMemcpyAsync(gh.data(), gram.p, sizeof(double) * 2 * m2 * m2, cudaMemcpyDeviceToHost, st));
+        NDSI_CK(cudaStreamSynchronize(st));
+        rc = check_status(h, st);
+        if (rc) return rc;
+        for (double v : gh)
+            if (!std::isfinite(v)) return fail(NDSI_ERR_SINGULAR, "ndsi_eigenstates: non-finite projected matrices");
+        std::vector<double> Hs(gh.begin(), gh.begin() + m2 * m2), Ss(gh.begin() + m2 * m2, gh.begin() + 2 * m2 * m2);
+        std::vector<double> ev, Yall;
+        rayleigh_ritz(m2, Hs, Ss, ev, Yall);
+        const int r = static_cast<int>(ev.size());
+        if (r < n_states) return fail(NDSI_ERR_SINGULAR, "ndsi_eigenstates: search space collapsed");
+        // keep the block's worth of Ritz pairs nearest xi
+        order.resize(r);
+        for (int i = 0; i < r; ++i) order[i] = i;
+        std::stable_sort(order.begin(), order.end(),
+                         [&](int a, int b) { return std::fabs(ev[a] - xi) < std::fabs(ev[b] - xi); });
+        const int mn = std::min(m, r);
+        e.resize(mn);
+        Y.assign(static_cast<size_t>(m2) * mn, 0.0);
+        for (int j = 0; j < mn; ++j) {
+            e[j] = ev[order[j]];
+            for (int a = 0; a < m2; ++a) Y[a * mn + j] = Yall[a * r + order[j]];
+        }
+        NDSI_CK(cudaMemcpyAsync(yc.p, Y.data(), sizeof(double) * Y.size(), cudaMemcpyHostToDevice, st));
+        NDSI_CK(cudaMemcpyAsync(ec.p, e.data(), sizeof(double) * mn, cudaMemcpyHostToDevice, st));
+        NDSI_CK(launch_ritz(vb.as<double>(), hvb.as<double>(), svb.as<double>(), n, m2, yc.as<double>(), ec.as<double>(), mn,
+                            cb.as<double>(), rp.as<double>(), st));
+        std::vector<double> part(static_cast<size_t>(nb) * mn);
+        NDSI_CK(cudaMemcpyAsync(part.data(), rp.p, sizeof(double) * part.size(), cudaMemcpyDeviceToHost, st));
+        NDSI_CK(cudaStreamSynchronize(st));
+        m = mn;
+        done = true;
+        for (int j = 0; j < m; ++j) {
+            double s2 = 0.0;
+            for (int b = 0; b < nb; ++b) s2 += part[static_cast<size_t>(b) * m + j];
+            res[j] = std::sqrt(s2);
+            if (j < n_states && !(res[j] < tol)) done = false;
+        }
+    }
+    // the n_states pairs nearest xi, ascending in energy, largest component of each made positive
+    std::vector<int> sel(n_states);
+    for (int j = 0; j < n_states; ++j) sel[j] = j;
+    std::stable_sort(sel.begin(), sel.end(), [&](int a, int b) { return e[a] < e[b]; });
+    std::vector<double> Ch(static_cast<size_t>(n) * m), out(static_cast<size_t>(n) * n_states);
+    NDSI_CK(cudaMemcpyAsync(Ch.data(), cb.p, sizeof(double) * Ch.size(), cudaMemcpyDeviceToHost, st));
+    NDSI_CK(cudaStreamSynchronize(st));
+    for (int j = 0; j < n_states; ++j) {
+        const int c = sel[j];
+        int64_t imax = 0;
+        for (int64_t i = 1; i < n; ++i)
+            if (std::fabs(Ch[i * m + c]) > std::fabs(Ch[imax * m + c])) imax = i;
+        const double sg = Ch[imax * m + c] < 0 ? -1.0 : 1.0;
+        for (int64_t i = 0; i < n; ++i) out[static_cast<size_t>(j) * n + i] = sg * Ch[i * m + c];
+        eps_out[j] = e[c];
+        if (resid_out) resid_out[j] = res[c];
+    }
+    NDSI_CK(cudaMemcpy(C_out, out.data(), sizeof(double) * out.size(), cudaMemcpyDefault));
+    if (iters_out) *iters_out = it;
+    if (!done) return fail(NDSI_ERR_TIMEOUT, "ndsi_eigenstates: not converged within max_iter (best pairs returned)");
+    return NDSI_OK;
+}
+
+int ndsi_dos(ndsi_plan* h, const double* H, const double* S, const double* energies, int32_t n_energies,
+             double eta, double* dos_out, void* stream) {
+    if (!h || !H || !S || !energies || !dos_out || n_energies < 1 || !(eta > 0) || !std::isfinite(eta))
+        return fail(NDSI_ERR_INVALID, "ndsi_dos: invalid argument");
+    if (h->P.n_systems != 1) return fail(NDSI_ERR_INVALID, "ndsi_dos: batched plan");
+    if (is_device_ptr(energies) || is_device_ptr(dos_out))
+        return fail(NDSI_ERR_INVALID, "ndsi_dos: energies and dos_out are host arrays");
+    for (int32_t k = 0; k < n_energies; ++k)
+        if (!std::isfinite(energies[k])) return fail(NDSI_ERR_INVALID, "ndsi_dos: energy not finite");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    int rc = upload_tables(h);
+    if (rc) return rc;
+    const double *Hd, *Sd;
+    rc = device_inputs(h, H, S, &Hd, &Sd, st);
+    if (rc) return rc;
+    return dos_sweep(h, Hd, Sd, energies, n_energies, eta, dos_out, st);
+}
 
 int ndsi_find_mu(ndsi_plan* h, const double* H, const double* S, double kT, int32_t n_poles,
                  double n_electrons, double mu_lo, double mu_hi, double tol_electrons, int32_t max_iter,
@@ -982,153 +1369,25 @@ int ndsi_find_mu(ndsi_plan* h, const double* H, const double* S, double kT, int3
     const bool rho_dev = is_device_ptr(rho_out);
     double* rho_d = rho_dev ? rho_out : h->stage + 2 * nnz;
     double* ne_d = h->stage + 3 * nnz;
-    int iters = 0;
-    double best_mu = 0, best_dn = 1e300;
-    auto eval = [&](double mu, double& dn) -> int {
-        int r = density_impl(h, Hd, Sd, &mu, &kT, n_poles, rho_d, ne_d, st);
-        if (r) return r;
-        double ne = 0;
-        cudaError_t e = cudaMemcpy(&ne, ne_d, sizeof(double), cudaMemcpyDeviceToHost);
-        if (e != cudaSuccess) return fail(NDSI_ERR_CUDA, "ndsi_find_mu: readback failed");
-        ++iters;
-        dn = ne - n_electrons;
-        if (std::fabs(dn) < std::fabs(best_dn)) {
-            best_dn = dn;
-            best_mu = mu;
-        }
-        return NDSI_OK;
-    };
-    double a, b, fa, fb;
-    if (mu_lo < mu_hi) {
-        a = std::max(mu_lo, elo);
-        b = std::min(mu_hi, ehi);
-        if (!(a < b)) {
-            a = elo;
-            b = ehi;
-        }
-    } else {
-        a = elo;
-        b = ehi;
+    FindMuCtx ctx{h, Hd, Sd, kT, n_poles, n_electrons, rho_d, ne_d, st, 0.0, false};
+    double mu = 0, dn = 0;
+    int32_t iters = 0;
+    std::string err;
+    rc = mu_search(find_mu_eval, find_mu_dos, &ctx, elo, ehi, kT, n_electrons, n_poles + 1, mu_lo, mu_hi,
+                   tol_electrons, max_iter, &mu, &dn, &iters, err);
+    if (rc && rc != NDSI_ERR_TIMEOUT) return err.empty() ? rc : fail(rc, "ndsi_find_mu: " + err);
+    // rho_out must hold rho(mu): evaluate once more if the last trial was another point
+    if (!ctx.have_last || ctx.last_mu != mu) {
+        double dn2 = 0;
+        const int r2 = find_mu_eval(&ctx, mu, &dn2);
+        if (r2) return r2;
     }
-    if ((rc = eval(a, fa))) return rc;
-    if (std::fabs(fa) >= tol_electrons) {
-        if ((rc = eval(b, fb))) return rc;
-    } else {
-        fb = fa;
-        b = a;
-    }
-    // widen towards the spectral bounds until the bracket encloses the root
-    double grow = std::max(b - a, 1e-3);
-    while (std::fabs(fa) >= tol_electrons && std::fabs(fb) >= tol_electrons && fa * fb > 0) {
-        if (iters >= max_iter) break;
-        if (fa > 0) {
-            if (a <= elo) return fail(NDSI_ERR_INVALID, "ndsi_find_mu: no root above the lower spectral bound");
-            b = a;
-            fb = fa;
-            a = std::max(elo, a - grow);
-            if ((rc = eval(a, fa))) return rc;
-        } else {
-            if (b >= ehi) return fail(NDSI_ERR_INVALID, "ndsi_find_mu: no root below the upper spectral bound");
-            a = b;
-            fa = fb;
-            b = std::min(ehi, b + grow);
-            if ((rc = eval(b, fb))) return rc;
-        }
-        grow *= 2;
-    }
-    // Inside the bracket: the paper's Muller step (procedure (4), Eqs. 45-46) through the three
-    // evaluated points with the smallest |DeltaN| (both signs present), else the linear
-    // interpolation of procedure (3) between the bracket ends (Illinois-weighted), else bisection.
-    std::vector<std::pair<double, double>> pts;  // (mu, DeltaN) of every evaluation in the bracket
-    pts.emplace_back(a, fa);
-    pts.emplace_back(b, fb);
-    int side = 0;
-    double ga = fa, gb = fb;
-    double width_prev = 2.0 * (b - a), width_prev2 = 4.0 * (b - a);
-    while (std::fabs(best_dn) >= tol_electrons && iters < max_iter) {
-        const double w = b - a;
-        if (w <= 1e-15 * std::max(1.0, std::fabs(a))) break;
-        double c = std::nan("");
-        if (pts.size() >= 3) {
-            std::vector<std::pair<double, double>> q(pts);
-            std::sort(q.begin(), q.end(), [](const std::pair<double, double>& x, const std::pair<double, double>& y) {
-                return std::fabs(x.second) < std::fabs(y.second);
-            });
-            std::vector<std::pair<double, double>> sel(q.begin(), q.begin() + 3);
-            bool pos = false, neg = false;
-            for (auto& t : sel) (t.second > 0 ? pos : neg) = true;
-            if (!(pos && neg)) {
-                for (size_t i = 3; i < q.size(); ++i)
-                    if ((q[i].second > 0) != pos || (q[i].second < 0) != neg) {
-                        sel[2] = q[i];
-                        break;
-                    }
-            }
-            std::sort(sel.begin(), sel.end());
-            const double m0 = sel[0].first, m1 = sel[1].first, m2 = sel[2].first;
-            const double h1 = m1 - m0, h2 = m2 - m1;
-            if (h1 > 0 && h2 > 0) {
-                const double d1 = (sel[1].second - sel[0].second) / h1;
-                const double d2 = (sel[2].second - sel[1].second) / h2;
-                const double qa = (d2 - d1) / (h1 + h2);       // DeltaN ~ qa t^2 + qb t + qc, t = mu - m2
-                const double qb = qa * h2 + d2;
-                const double qc = sel[2].second;
-                const double disc = qb * qb - 4.0 * qa * qc;
-                if (disc >= 0) {
-                    const double sq = std::sqrt(disc);
-                    double t;
-                    if (qb >= 0) t = -2.0 * qc / (qb + sq);                       // Eq. 46, b >= 0
-                    else t = (std::fabs(qa) > 0) ? (-qb + sq) / (2.0 * qa) : std::nan("");  // b < 0
-                    c = m2 + t;
-                }
-            }
-        }
-        if (!(c > a + 0.01 * w && c < b - 0.01 * w)) c = b - gb * (b - a) / (gb - ga);
-        if (!(c > a + 0.01 * w && c < b - 0.01 * w)) c = 0.5 * (a + b);
-        double fc;
-        if ((rc = eval(c, fc))) return rc;
-        pts.emplace_back(c, fc);
-        width_prev2 = width_prev;
-        width_prev = w;
-        if (fc < 0) {
-            a = c;
-            fa = ga = fc;
-            if (side == -1) gb *= 0.5;
-            side = -1;
-        } else {
-            b = c;
-            fb = gb = fc;
-            if (side == 1) ga *= 0.5;
-            side = 1;
-        }
-        if (b - a > 0.5 * width_prev2 && std::fabs(best_dn) >= tol_electrons && iters < max_iter) {
-            // two steps did not halve the bracket: bisect once
-            const double m = 0.5 * (a + b);
-            double fm;
-            if ((rc = eval(m, fm))) return rc;
-            pts.emplace_back(m, fm);
-            if (fm < 0) {
-                a = m;
-                fa = ga = fm;
-            } else {
-                b = m;
-                fb = gb = fm;
-            }
-            side = 0;
-            width_prev2 = width_prev = b - a;
-        }
-    }
-    // rho_out must hold rho(best_mu): re-evaluate if the last trial was not the best
-    double last_dn = 0;
-    if ((rc = eval(best_mu, last_dn))) return rc;
-    --iters;  // the re-evaluation is bookkeeping, not a search step
-    *mu_out = best_mu;
-    if (n_elec_out) *n_elec_out = n_electrons + best_dn;
+    *mu_out = mu;
+    if (n_elec_out) *n_elec_out = n_electrons + dn;
     if (iters_out) *iters_out = iters;
     if (!rho_dev) NDSI_CK(cudaMemcpyAsync(rho_out, rho_d, sizeof(double) * nnz, cudaMemcpyDeviceToHost, st));
     NDSI_CK(cudaStreamSynchronize(st));
-    if (std::fabs(best_dn) >= tol_electrons)
-        return fail(NDSI_ERR_TIMEOUT, "ndsi_find_mu: not converged within max_iter evaluations");
+    if (rc) return fail(rc, "ndsi_find_mu: not converged within max_iter evaluations");
     return NDSI_OK;
 }
 
@@ -1211,6 +1470,11 @@ void ndsi_plan_destroy(ndsi_plan* h) {
     if (h->cew) cudaFree(h->cew);
     if (h->gersh) cudaFree(h->gersh);
     if (h->partials) cudaFree(h->partials);
+    if (h->dos_part) cudaFree(h->dos_part);
+    if (h->dos_tr) cudaFree(h->dos_tr);
+    if (h->dos_z) cudaFree(h->dos_z);
+    if (h->point_z) cudaFree(h->point_z);
+    solve_tables_free(h->ST);
     if (h->stage) cudaFree(h->stage);
     if (h->graph) cudaGraphExecDestroy(h->graph);
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);

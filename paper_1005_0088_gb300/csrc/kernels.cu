@@ -579,6 +579,39 @@ double gershgorin_value(unsigned long long key) {
     return x;
 }
 
+__global__ void __launch_bounds__(kAccThreads) k_point_traces(const int64_t* __restrict__ out_map, int64_t nnz,
+                                                              const double2* __restrict__ F, int64_t stride,
+                                                              const double* __restrict__ S,
+                                                              double* __restrict__ partials) {
+    __shared__ double red[kAccThreads / 32];
+    const int64_t k = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+    double v = 0.0;
+    if (k < nnz) v = F[static_cast<int64_t>(blockIdx.y) * stride + out_map[k]].y * S[k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double w = threadIdx.x < kAccThreads / 32 ? red[threadIdx.x] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) w += __shfl_down_sync(0xffffffffu, w, o);
+        if (threadIdx.x == 0) partials[static_cast<int64_t>(blockIdx.y) * gridDim.x + blockIdx.x] = w;
+    }
+}
+
+cudaError_t launch_point_traces(const Plan& P, const DevTables& T, const Workspace& W, int np,
+                                const double* S, double* partials, double* out, cudaStream_t st) {
+    const int nb = accumulate_blocks(P.nnz);
+    k_point_traces<<<dim3(static_cast<unsigned>(nb), static_cast<unsigned>(np)), kAccThreads, 0, st>>>(
+        T.out_map, P.nnz, W.fronts, W.front_stride, S, partials);
+    cudaError_t e = cudaGetLastError();
+    for (int q = 0; q < np && e == cudaSuccess; ++q) {
+        k_reduce<<<1, 1024, 0, st>>>(partials + static_cast<int64_t>(q) * nb, nb, out + q);
+        e = cudaGetLastError();
+    }
+    return e;
+}
+
 cudaError_t launch_reduce(const double* partials, int nblocks, double* out, cudaStream_t st) {
     k_reduce<<<1, 1024, 0, st>>>(partials, nblocks, out);
     return cudaGetLastError();

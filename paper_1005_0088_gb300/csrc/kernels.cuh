@@ -69,6 +69,11 @@ cudaError_t launch_gershgorin(const DevTables& T, int64_t n, const double* H, co
                               unsigned long long* out, cudaStream_t st);
 double gershgorin_value(unsigned long long key);
 
+// Per point q of a chunk: out[q] = sum over the pattern of Im G_q(k) S_k = Im Tr(G(z_q) S) (the
+// density of states of Eq. 42 up to -2/pi).  partials: np x accumulate_blocks(nnz) doubles.
+cudaError_t launch_point_traces(const Plan& P, const DevTables& T, const Workspace& W, int np,
+                                const double* S, double* partials, double* out, cudaStream_t st);
+
 // G_out[q*nnz + k] = G_q(k) for the np poles of the workspace.
 cudaError_t launch_gather_pattern(const Plan& P, const DevTables& T, const Workspace& W, int np,
                                   double2* G_out, int64_t q0, cudaStream_t st);

@@ -157,6 +157,11 @@ void compute_scratch(Plan& P);
 void build_schedule(Plan& P);
 int merge_plans(std::vector<Plan>& parts, Plan& merged, std::string& err);
 
+// Chemical-potential search over caller-supplied evaluations (mu_search.cpp).
+int mu_search(ndsi_mu_eval_fn eval, ndsi_mu_dos_fn dos, void* ctx, double elo, double ehi, double kT,
+              double n_electrons, int32_t n_grid, double mu_lo, double mu_hi, double tol, int32_t max_iter,
+              double* mu_out, double* dn_out, int32_t* evals_out, std::string& err);
+
 // Continued-fraction poles (analyze.cpp).
 int cf_poles(int32_t M, double* z, double* R, std::string& err);
 

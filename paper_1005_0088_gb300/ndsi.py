@@ -34,8 +34,11 @@ EXPORTED_SYMBOLS = (
     "ndsi_residue_sum_static", "ndsi_find_mu", "ndsi_mu_features", "ndsi_mlp_init",
     "ndsi_mlp_forward", "ndsi_mlp_grad", "ndsi_mlp_train", "ndsi_analyze_batched",
     "ndsi_density_batched", "ndsi_graph_enable", "ndsi_graph_info", "ndsi_autotune",
-    "ndsi_density_energy",
+    "ndsi_density_energy", "ndsi_dos", "ndsi_factors_solve", "ndsi_eigenstates", "ndsi_mu_search",
 )
+MU_EVAL_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.c_double, ctypes.POINTER(ctypes.c_double))
+MU_DOS_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.c_int32,
+                             ctypes.c_double, ctypes.POINTER(ctypes.c_double))
 NDSI_MLP_INPUTS = 32
 NDSI_MLP_HIDDEN = 64
 NDSI_MLP_PARAMS = 6337
@@ -104,6 +107,18 @@ def load(path: str = LIB_PATH):
     lib.ndsi_graph_enable.argtypes = [vp, i32]
     lib.ndsi_density_energy.argtypes = [vp, vp, vp, ctypes.c_double, ctypes.c_double, i32, vp, vp, vp, vp]
     lib.ndsi_density_energy.restype = ctypes.c_int
+    lib.ndsi_dos.argtypes = [vp, vp, vp, vp, i32, ctypes.c_double, vp, vp]
+    lib.ndsi_dos.restype = ctypes.c_int
+    lib.ndsi_mu_search.argtypes = [MU_EVAL_FN, MU_DOS_FN, vp, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                   ctypes.c_double, i32, ctypes.c_double, ctypes.c_double, ctypes.c_double, i32,
+                                   ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                                   ctypes.POINTER(i32)]
+    lib.ndsi_mu_search.restype = ctypes.c_int
+    lib.ndsi_factors_solve.argtypes = [vp, i32, vp, i32, vp, vp]
+    lib.ndsi_factors_solve.restype = ctypes.c_int
+    lib.ndsi_eigenstates.argtypes = [vp, vp, vp, ctypes.c_double, ctypes.c_double, i32, i32, i32,
+                                     ctypes.c_double, ctypes.c_uint64, vp, vp, vp, ctypes.POINTER(i32), vp]
+    lib.ndsi_eigenstates.restype = ctypes.c_int
     lib.ndsi_autotune.argtypes = [vp, vp, vp, ctypes.c_double, ctypes.c_double, i32,
                                   ctypes.POINTER(i32), ctypes.POINTER(i32), vp]
     lib.ndsi_autotune.restype = ctypes.c_int
@@ -278,6 +293,79 @@ def ndsi_density_energy(plan: Plan, H, S, mu, kT, n_poles, rho_out, e_out, n_ele
     _check(load().ndsi_density_energy(plan.handle, _ptr(H), _ptr(S), float(mu), float(kT), int(n_poles),
                                       _ptr(rho_out), _ptr(e_out), _ptr(n_elec_out), _stream(stream)))
     return rho_out, e_out
+
+
+def ndsi_dos(plan: Plan, H, S, energies, eta, stream=None):
+    """D(E) = -(2/pi) Im Tr(G(E + i eta) S) at each energy (Eq. 41); returns a host array."""
+    E = np.ascontiguousarray(np.asarray(energies, dtype=np.float64).reshape(-1))
+    D = np.zeros_like(E)
+    _check(load().ndsi_dos(plan.handle, _ptr(H), _ptr(S), _ptr(E), int(E.size), float(eta), _ptr(D),
+                           _stream(stream)))
+    return D
+
+
+def ndsi_mu_search(delta_n, elo, ehi, kT, n_electrons, dos=None, n_grid=0, mu_lo=0.0, mu_hi=0.0,
+                   tol_electrons=1e-8, max_iter=100):
+    """(mu, DeltaN, evaluations) of the host chemical-potential search over Python callables:
+    delta_n(mu) -> float and, optionally, dos(E: ndarray, eta) -> ndarray.  Raises NdsiError
+    (with .result = (mu, DeltaN, evaluations)) when the search fails."""
+    failure = []
+
+    def ev(_ctx, mu, out):
+        try:
+            out[0] = float(delta_n(mu))
+            return 0
+        except Exception as exc:  # noqa: BLE001 - reported after the search returns
+            failure.append(exc)
+            return NDSI_ERR_INVALID
+
+    def ds(_ctx, E, n, eta, out):
+        try:
+            D = np.asarray(dos(np.ctypeslib.as_array(E, shape=(n,)).copy(), eta), dtype=np.float64)
+            for k in range(n):
+                out[k] = float(D[k])
+            return 0
+        except Exception as exc:  # noqa: BLE001
+            failure.append(exc)
+            return NDSI_ERR_INVALID
+
+    ev_c = MU_EVAL_FN(ev)
+    ds_c = MU_DOS_FN(ds) if dos is not None else ctypes.cast(None, MU_DOS_FN)
+    mu, dn, it = ctypes.c_double(), ctypes.c_double(), ctypes.c_int32()
+    rc = load().ndsi_mu_search(ev_c, ds_c, None, float(elo), float(ehi), float(kT), float(n_electrons),
+                               int(n_grid), float(mu_lo), float(mu_hi), float(tol_electrons), int(max_iter),
+                               ctypes.byref(mu), ctypes.byref(dn), ctypes.byref(it))
+    if failure:
+        raise failure[0]
+    if rc != NDSI_OK:
+        err = NdsiError(rc, load().ndsi_last_error().decode())
+        err.result = (mu.value, dn.value, it.value)
+        raise err
+    return mu.value, dn.value, it.value
+
+
+def ndsi_factors_solve(factors, pole, Y, X_out, stream=None):
+    """X = (z_p S - H)^{-1} Y with the factors of pole p; Y, X complex (n, k) or (n,), C order."""
+    k = 1 if Y.ndim == 1 else int(Y.shape[1])
+    _check(load().ndsi_factors_solve(factors.handle, int(pole), _ptr(Y), k, _ptr(X_out), _stream(stream)))
+    return X_out
+
+
+def ndsi_eigenstates(plan: Plan, H, S, xi, n_states, eta=1e-3, block=None, max_iter=200, tol=1e-10,
+                     seed=12345, C_out=None, stream=None):
+    """(eps, C, residuals, iterations): the n_states eigenpairs nearest xi (App. B).
+
+    C is (n_states, n), a host array unless a device tensor C_out is given."""
+    block = int(block if block is not None else min(32, n_states + 4))
+    eps = np.zeros(n_states)
+    res = np.zeros(n_states)
+    it = ctypes.c_int32()
+    if C_out is None:
+        C_out = np.zeros((n_states, int(ndsi_plan_info(plan)["n"])))
+    _check(load().ndsi_eigenstates(plan.handle, _ptr(H), _ptr(S), float(xi), float(eta), int(n_states), block,
+                                   int(max_iter), float(tol), int(seed), _ptr(eps), _ptr(C_out), _ptr(res),
+                                   ctypes.byref(it), _stream(stream)))
+    return eps, C_out, res, it.value
 
 
 def analyze_system(system, **options) -> Plan:
