@@ -6,7 +6,10 @@ of the ordering rules, compared bit for bit with the library's host analysis.
 Granularity is the atom (the orbitals of an atom stay together).  Two atoms are adjacent when
 H or S has a nonzero block between them.  For a domain D of N_d atoms:
  (i)   for each axis a_i (i = 0, 1, 2) number the atoms 1..N_d by (coordinate_i, atom index);
- (ii)  long-tail screening is not applied (uniform lattices need none);
+ (ii)  long-tail screening (optional, screen_degree > 0): atoms adjacent to more than
+       screen_degree atoms are taken out of the dissection and placed in the root separator
+       (read from the paper's rule that long-tail basis functions join the separator before the
+       domain is dissected; the pattern's degree stands for the tail length);
  (iii) the nucleus is the atom with the fewest adjacent atoms inside the domain, ties broken by
        the lowest ordering number (this reproduces App. A's intermediates and Fig. 1's text);
  (iv)  grow the subdomain [m_min, m_max] one atom per step, taking the end whose growth gives
@@ -20,8 +23,15 @@ H or S has a nonzero block between them.  For a domain D of N_d atoms:
        subdomain 1 = the rest.  Domains of <= leaf_atoms atoms, or without a candidate, are
        leaves.  The structured order is [subdomain 0, subdomain 1, separator] recursively;
        atoms inside a leaf or a separator are listed by ascending atom index.
+Periodic axes (cell length L > 0 along the axis): coordinates are wrapped into [0, L) for the
+ordering, and a neighbour b of atom a is seen at its image nearest a, image shift
+l = -floor((x_b - x_a)/L + 1/2) of the wrapped coordinates, with ordering number
+ord(b) + l N_d (step (i)'s numbering of the periodic cells); n_min can then be below 1 and
+n_max above N_d, and the separator is [n_min, n_max] minus subdomain 0 taken modulo N_d.
 """
 from __future__ import annotations
+
+import math
 
 import numpy as np
 
@@ -43,13 +53,18 @@ def atom_adjacency(system):
     return adj
 
 
-def _split(D, centers, adj, leaf_atoms):
+def _split(D, centers, adj, leaf_atoms, cell=(0.0, 0.0, 0.0)):
     Nd = len(D)
     if Nd <= leaf_atoms:
         return None
     best = None  # (measure, Ns, axis, m_min, m_max, n_min, n_max, order)
     for axis in range(3):
-        order = sorted(D, key=lambda a: (centers[a][axis], a))
+        L = cell[axis]
+        if L > 0:
+            x = {a: centers[a][axis] - L * math.floor(centers[a][axis] / L) for a in D}
+        else:
+            x = {a: centers[a][axis] for a in D}
+        order = sorted(D, key=lambda a: (x[a], a))
         ordn = {a: i + 1 for i, a in enumerate(order)}
         nucleus = min(D, key=lambda a: (sum(1 for b in adj[a] if b in ordn), ordn[a]))
         q = ordn[nucleus]
@@ -58,6 +73,8 @@ def _split(D, centers, adj, leaf_atoms):
             for b in adj[atom]:
                 o = ordn.get(b)
                 if o is not None:
+                    if L > 0:
+                        o += -math.floor((x[b] - x[atom]) / L + 0.5) * Nd
                     if o < lo:
                         lo = o
                     if o > hi:
@@ -105,13 +122,14 @@ def _split(D, centers, adj, leaf_atoms):
     if best is None:
         return None
     _, axis, m_min, m_max, n_min, n_max, order = best
+    in_sep = {(x - 1) % Nd for x in list(range(n_min, m_min)) + list(range(m_max + 1, n_max + 1))}
     sub0 = order[m_min - 1:m_max]
-    sep = order[n_min - 1:m_min - 1] + order[m_max:n_max]
-    sub1 = order[:n_min - 1] + order[n_max:]
+    sep = [order[i] for i in sorted(in_sep)]
+    sub1 = [order[i] for i in range(Nd) if i not in in_sep and not (m_min - 1 <= i < m_max)]
     return sorted(sub0), sorted(sub1), sorted(sep), axis
 
 
-def nested_dissection(centers, adj, leaf_atoms=20):
+def nested_dissection(centers, adj, leaf_atoms=20, cell=None, screen_degree=0):
     """Supernodal tree in postorder.
 
     Returns dict with
@@ -120,19 +138,21 @@ def nested_dissection(centers, adj, leaf_atoms=20):
       perm_atoms: atom order (concatenation of the node lists), axis: split axis (-1 for leaves).
     """
     centers = np.asarray(centers, dtype=np.float64).tolist()
+    cell = tuple(float(c) for c in (cell if cell is not None else (0.0, 0.0, 0.0)))
     nodes, children, axes = [], [], []
+    screened = [a for a in range(len(adj)) if screen_degree > 0 and len(adj[a]) > screen_degree]
 
-    def rec(D):
-        res = _split(D, centers, adj, leaf_atoms)
+    def rec(D, extra=()):
+        res = _split(D, centers, adj, leaf_atoms, cell)
         if res is None:
-            nodes.append(sorted(D))
+            nodes.append(sorted(list(D) + list(extra)))
             children.append([])
             axes.append(-1)
             return len(nodes) - 1
         sub0, sub1, sep, axis = res
         c0 = rec(sub0)
         c1 = rec(sub1)
-        nodes.append(sep)
+        nodes.append(sorted(sep + list(extra)))
         children.append([c0, c1])
         axes.append(axis)
         return len(nodes) - 1
@@ -141,7 +161,8 @@ def nested_dissection(centers, adj, leaf_atoms=20):
     old = sys.getrecursionlimit()
     sys.setrecursionlimit(max(old, 10000))
     try:
-        rec(list(range(len(adj))))
+        kept = set(screened)
+        rec([a for a in range(len(adj)) if a not in kept], screened)
     finally:
         sys.setrecursionlimit(old)
     parent = np.full(len(nodes), -1, dtype=np.int64)

@@ -1,9 +1,12 @@
-"""Seeded tight-binding Hamiltonian/overlap pairs on open 1D/2D/3D lattices.
+"""Seeded tight-binding Hamiltonian/overlap pairs on 1D/2D/3D lattices (open, or periodic
+along chosen axes).
 
 Recipe (one draw order, fixed per seed; PCG64 via numpy.random.Generator):
   * atoms on the integer grid (lattice constant a = 1), atom index = x + nx*(y + ny*z);
   * neighbour sets: 1D nearest (block tridiagonal), 2D nearest + next-nearest (8 in-plane
-    offsets), 3D cut-off 1.8a (all 26 offsets in {-1,0,1}^3); open boundaries;
+    offsets), 3D cut-off 1.8a (all 26 offsets in {-1,0,1}^3), or the square lattice's nearest
+    neighbours only ("2dnn"); open boundaries, or wrapped along the periodic axes (Gamma point:
+    one block per neighbouring pair of atoms of the cell, at least 3 atoms per periodic axis);
   * onsite block  H_aa = diag(U(-1,1)) + (G + G^T)/2, G ~ N(0, 0.1^2)  (o x o);
   * neighbour block H_ab ~ N(0, 0.1^2), H_ba = H_ab^T;
   * overlap S_aa = I, S_ab = c W_ab with W_ab ~ U(-1,1), W_ba = W_ab^T and
@@ -88,6 +91,8 @@ class System:
 def _offsets(neighbours: str):
     if neighbours == "1d":
         return [(1, 0, 0)]
+    if neighbours == "2dnn":           # square lattice, nearest neighbours only
+        return [(1, 0, 0), (0, 1, 0)]
     if neighbours == "2d":
         return [(1, 0, 0), (0, 1, 0), (1, 1, 0), (1, -1, 0)]
     if neighbours == "3d":
@@ -99,15 +104,25 @@ def _offsets(neighbours: str):
     raise ValueError(neighbours)
 
 
-def _atom_pairs(shape, neighbours):
-    """Sorted unique pairs (a, b), a < b, of neighbouring atoms on the open grid."""
+def _atom_pairs(shape, neighbours, periodic=(False, False, False)):
+    """Sorted unique pairs (a, b), a < b, of neighbouring atoms on the grid (open, or wrapped
+    along the periodic axes, which need at least 3 atoms)."""
     nx, ny, nz = shape
+    for n_ax, per in zip(shape, periodic):
+        if per and n_ax < 3:
+            raise ValueError("a periodic axis needs at least 3 atoms")
     xs, ys, zs = np.meshgrid(np.arange(nx), np.arange(ny), np.arange(nz), indexing="ij")
     xs, ys, zs = xs.ravel(), ys.ravel(), zs.ravel()
     idx = xs + nx * (ys + ny * zs)
     pa, pb = [], []
     for dx, dy, dz in _offsets(neighbours):
         x2, y2, z2 = xs + dx, ys + dy, zs + dz
+        if periodic[0]:
+            x2 = x2 % nx
+        if periodic[1]:
+            y2 = y2 % ny
+        if periodic[2]:
+            z2 = z2 % nz
         ok = (x2 >= 0) & (x2 < nx) & (y2 >= 0) & (y2 < ny) & (z2 >= 0) & (z2 < nz)
         a = idx[ok]
         b = (x2 + nx * (y2 + ny * z2))[ok]
@@ -141,14 +156,16 @@ def _assemble_csr(n_atoms, o, pa, pb, onsite_H, onsite_S, pair_H, pair_S):
 
 
 def lattice_system(shape, orbitals, neighbours, seed, onsite_range=1.0, hop_std=0.1,
-                   overlap=0.05, electrons=None) -> System:
-    """Draw one seeded (H, S) pair on an open lattice (see module docstring)."""
+                   overlap=0.05, electrons=None, periodic=(False, False, False)) -> System:
+    """Draw one seeded (H, S) pair on a lattice, open or periodic per axis (see module
+    docstring; meta["cell"] holds the periodic cell lengths, 0 for open axes)."""
     shape = tuple(int(v) for v in shape) + (1,) * (3 - len(shape))
+    periodic = tuple(bool(p) for p in periodic) + (False,) * (3 - len(periodic))
     nx, ny, nz = shape
     n_atoms = nx * ny * nz
     o = int(orbitals)
     rng = np.random.Generator(np.random.PCG64(seed))
-    pa, pb = _atom_pairs(shape, neighbours)
+    pa, pb = _atom_pairs(shape, neighbours, periodic)
     npair = pa.shape[0]
     eps = rng.uniform(-onsite_range, onsite_range, size=(n_atoms, o))
     G = rng.normal(0.0, hop_std, size=(n_atoms, o, o))
@@ -175,7 +192,8 @@ def lattice_system(shape, orbitals, neighbours, seed, onsite_range=1.0, hop_std=
     ne = float(n) / 2.0 if electrons is None else float(electrons)
     return System(n, rowptr, col, Hv, Sv, cen, aob, ne,
                   dict(shape=shape, orbitals=o, neighbours=neighbours, seed=seed,
-                       overlap_scale=c))
+                       overlap_scale=c,
+                       cell=tuple(float(n_ax) if per else 0.0 for n_ax, per in zip(shape, periodic))))
 
 
 def chain_nntb(n_atoms, a=0.0, b=-1.0, s=0.0, electrons=None) -> System:

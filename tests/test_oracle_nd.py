@@ -2,7 +2,7 @@
 import numpy as np
 import pytest
 
-from synth import chain_nntb, lattice_system, config_system
+from synth import csr_from_dense, chain_nntb, lattice_system, config_system
 from oracle.nd import atom_adjacency, nested_dissection, symbolic_structure
 from tests.conftest import golden_lines
 
@@ -120,3 +120,97 @@ def test_elimination_tree_property(name):
         if p >= 0:
             assert set(st[c]) - set(t["nodes"][p]) <= set(st[p])
     assert st[-1] == []
+
+
+def test_fig2_periodic_square_lattice():
+    # Fig. 2: s-valent NNTB square lattice, 1024 atoms per periodic cell.  The first separator
+    # consists of two lines; innermost domains hold 9 atoms; separators run over six levels
+    # (labelled 0 to 5).
+    sysm = lattice_system((32, 32, 1), 1, "2dnn", 1, periodic=(True, True, False))
+    t = nested_dissection(sysm.centers, atom_adjacency(sysm), 20, cell=sysm.meta["cell"])
+    _check_tree(sysm, t, 20)
+    root = len(t["nodes"]) - 1
+    sep = np.array(t["nodes"][root])
+    ax = t["axis"][root]
+    lines = np.unique(sysm.centers[sep, ax])
+    assert len(sep) == 64 and len(lines) == 2
+    for x in lines:
+        assert np.sum(sysm.centers[sep, ax] == x) == 32
+    leaves = [len(n) for n, ch in zip(t["nodes"], t["children"]) if not ch]
+    assert set(leaves) == {9} and len(leaves) == 64
+    parent = t["parent"]
+
+    def depth(j):
+        d = 0
+        while parent[j] >= 0:
+            j, d = parent[j], d + 1
+        return d
+
+    assert sorted({depth(j) for j, ch in enumerate(t["children"]) if ch}) == [0, 1, 2, 3, 4, 5]
+
+
+@pytest.mark.parametrize("shape,nb,periodic,shift", [
+    ((12, 1, 1), "1d", (True, False, False), 0.0),
+    ((9, 7, 1), "2d", (True, False, False), -0.5),
+    ((8, 8, 1), "2d", (True, True, False), 3.25),
+    ((5, 4, 6), "3d", (True, True, True), 0.0),
+])
+def test_periodic_trees_are_valid(shape, nb, periodic, shift):
+    # separators must cut the wrap-around couplings too; moving every atom by whole cells gives
+    # the same tree (ordering uses the wrapped coordinate, neighbours their nearest image)
+    sysm = lattice_system(shape, 2, nb, 5, periodic=periodic)
+    adj = atom_adjacency(sysm)
+    cell = np.array(sysm.meta["cell"])
+    cen = sysm.centers + shift * cell[None, :]
+    t = nested_dissection(cen, adj, 4, cell=cell)
+    _check_tree(sysm, t, 4)
+    k = np.random.default_rng(3).integers(-2, 3, size=cen.shape)
+    t2 = nested_dissection(cen + k * cell[None, :], adj, 4, cell=cell)
+    assert np.array_equal(t2["perm_atoms"], t["perm_atoms"])
+    assert np.array_equal(t2["parent"], t["parent"])
+
+
+def _long_tail_system(base, n_tail, radius, seed):
+    """The base lattice plus n_tail one-orbital atoms, each coupled to every atom within radius."""
+    rng = np.random.default_rng(seed)
+    Hd, Sd = base.dense()
+    o = base.n // base.n_atoms
+    tails = rng.uniform(0, 1, (n_tail, 3)) * (base.centers.max(0) + 1e-9)
+    n = base.n + n_tail
+    H = np.zeros((n, n))
+    S = np.zeros((n, n))
+    H[:base.n, :base.n] = Hd
+    S[:base.n, :base.n] = Sd
+    for k, c in enumerate(tails):
+        i = base.n + k
+        H[i, i], S[i, i] = rng.uniform(-1, 1), 1.0
+        near = np.nonzero(np.linalg.norm(base.centers - c, axis=1) <= radius)[0]
+        for a in near:
+            for q in range(o):
+                j = a * o + q
+                H[i, j] = H[j, i] = rng.normal(0, 0.05)
+                S[i, j] = S[j, i] = 1e-3
+    cen = np.vstack([base.centers, tails])
+    aob = np.concatenate([base.atom_of_basis, base.n_atoms + np.arange(n_tail)]).astype(np.int32)
+    return csr_from_dense(H, S, cen, aob)
+
+
+def test_screening_moves_long_tails_to_the_root():
+    base = lattice_system((10, 9, 1), 2, "2d", 8)
+    sysm = _long_tail_system(base, 3, 4.0, 2)
+    adj = atom_adjacency(sysm)
+    degs = sorted(len(a) for a in adj)
+    screen = 12                                    # lattice atoms have at most 8 + 3 neighbours
+    assert degs[-3] > screen >= max(len(adj[a]) for a in range(base.n_atoms))
+    t = nested_dissection(sysm.centers, adj, 6, screen_degree=screen)
+    _check_tree(sysm, t, 6)
+    t0 = nested_dissection(base.centers, atom_adjacency(base), 6)
+    # the kept atoms are dissected exactly as the lattice alone; the tails join the root
+    assert len(t["nodes"]) == len(t0["nodes"])
+    for a, b in zip(t["nodes"][:-1], t0["nodes"][:-1]):
+        assert a == b
+    tails = list(range(base.n_atoms, sysm.n_atoms))
+    assert t["nodes"][-1] == sorted(t0["nodes"][-1] + tails)
+    # without screening the long tails spread through the tree and the root separator grows
+    t_off = nested_dissection(sysm.centers, adj, 6)
+    _check_tree(sysm, t_off, 6)
