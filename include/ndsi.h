@@ -75,6 +75,15 @@ typedef struct {
                                     complex columns per tile) or 5 (t+u = 2..5 exact; 48 columns,
                                     about 2^7 more accurate where the tail dominates the error,
                                     about as fast); 0 (default) = 5 */
+    double cell[3];              /* periodic cell lengths along x, y, z in the units of `centers`;
+                                    0 (default) = open along that axis.  On a periodic axis the
+                                    dissection orders atoms by their coordinate wrapped into
+                                    [0, L) and sees each neighbour at its image nearest the atom
+                                    (Sec. II.C.1 step (i): ordering numbers l*N_d + q in the
+                                    periodic cells), so a separator can wrap around the cell */
+    int32_t screen_degree;       /* long-tail screening (Sec. II.C.1 step (ii)): atoms adjacent to
+                                    more than this many atoms join the root separator before the
+                                    dissection; 0 (default) = off */
 } ndsi_options;
 
 /* Summary of a plan, filled by ndsi_plan_info. */
@@ -293,8 +302,9 @@ int ndsi_residue_sum_static(const double* G, const double* c, int32_t n_points, 
  * vectors c with that factorisation (ndsi_factors_solve's three steps), solves (B3) in the real
  * span of Re b and Im b (2 x block vectors; S-Gram directions below 1e-12 of the largest are
  * dropped) and keeps the `block` Ritz pairs nearest xi.  The loop stops when the n_states nearest
- * have |H c - eps S c|_2 < tol (c S-normalised).  Split precision changes only the speed of
- * convergence: the Ritz pairs and residuals use the exact H and S.
+ * have |H c - eps S c|_2 < tol (c S-normalised).  In split precision each solve takes one step
+ * of FP64 iterative refinement (residual y - (zS - H) b with the exact H and S, solved again with
+ * the same factors), so the iteration converges to the pencil's own eigenpairs.
  *   H, S       - values on the pattern, device or host.
  *   xi, eta    - the shift; eta > 0 (about the wanted level spacing or smaller).
  *   n_states   - >= 1;  block - n_states..32, and <= n.

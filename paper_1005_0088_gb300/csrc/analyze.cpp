@@ -19,13 +19,18 @@ struct Dissector {
     const double* centers;
     const std::vector<std::vector<int32_t>>& adj;
     int32_t leaf_atoms;
+    double cell[3];               // periodic cell length per axis (0 = open)
     std::vector<int32_t> ord_of;  // atom -> ordering number in the current domain (0 = outside)
+    std::vector<double> xw;       // coordinate along the current axis, wrapped into [0, L)
     // output tree (postorder)
     std::vector<std::vector<int32_t>> nodes;
     std::vector<int32_t> child0, child1;
 
-    Dissector(int32_t n, const double* c, const std::vector<std::vector<int32_t>>& a, int32_t leaf)
-        : na(n), centers(c), adj(a), leaf_atoms(leaf), ord_of(n, 0) {}
+    Dissector(int32_t n, const double* c, const std::vector<std::vector<int32_t>>& a, int32_t leaf,
+              const double* cell_len)
+        : na(n), centers(c), adj(a), leaf_atoms(leaf), ord_of(n, 0), xw(n, 0.0) {
+        for (int k = 0; k < 3; ++k) cell[k] = cell_len[k] > 0 ? cell_len[k] : 0.0;
+    }
 
     // Best split of D (steps i, iii, iv, v).  Returns false for a leaf.
     bool split(const std::vector<int32_t>& D, std::vector<int32_t>& sub0, std::vector<int32_t>& sub1,
@@ -37,12 +42,16 @@ struct Dissector {
         int32_t b_mmin = 0, b_mmax = 0, b_nmin = 0, b_nmax = 0;
         std::vector<int32_t> best_order, order(D);
         for (int axis = 0; axis < 3; ++axis) {
-            // (i) ordering numbers along the axis: (coordinate, atom index)
+            // (i) ordering numbers along the axis: (coordinate, atom index); on a periodic axis the
+            // coordinate is wrapped into the central cell [0, L)
+            const double L = cell[axis];
+            for (int32_t a : D) {
+                const double c = centers[3 * static_cast<int64_t>(a) + axis];
+                xw[a] = L > 0 ? c - L * std::floor(c / L) : c;
+            }
             order = D;
             std::sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
-                const double ca = centers[3 * static_cast<int64_t>(a) + axis];
-                const double cb = centers[3 * static_cast<int64_t>(b) + axis];
-                if (ca != cb) return ca < cb;
+                if (xw[a] != xw[b]) return xw[a] < xw[b];
                 return a < b;
             });
             for (int32_t i = 0; i < Nd; ++i) ord_of[order[i]] = i + 1;
@@ -57,10 +66,13 @@ struct Dissector {
                     nbest = cnt;
                 }
             }
+            // ordering numbers of the neighbours; on a periodic axis the neighbour's image nearest
+            // the atom, l = -floor(dx/L + 1/2) cells away, has ordering number ord + l*Nd
             auto span = [&](int32_t atom, int32_t& lo, int32_t& hi) {
                 for (int32_t b : adj[atom]) {
-                    const int32_t o = ord_of[b];
+                    int32_t o = ord_of[b];
                     if (o > 0) {
+                        if (L > 0) o -= static_cast<int32_t>(std::floor((xw[b] - xw[atom]) / L + 0.5)) * Nd;
                         lo = std::min(lo, o);
                         hi = std::max(hi, o);
                     }
@@ -131,20 +143,28 @@ struct Dissector {
             }
         }
         if (!have) return false;
-        sub0.assign(best_order.begin() + (b_mmin - 1), best_order.begin() + b_mmax);
-        sep.assign(best_order.begin() + (b_nmin - 1), best_order.begin() + (b_mmin - 1));
-        sep.insert(sep.end(), best_order.begin() + b_mmax, best_order.begin() + b_nmax);
-        sub1.assign(best_order.begin(), best_order.begin() + (b_nmin - 1));
-        sub1.insert(sub1.end(), best_order.begin() + b_nmax, best_order.end());
+        // subdomain 0 = [m_min, m_max]; separator = [n_min, n_max] minus subdomain 0, modulo Nd
+        // (periodic axes can reach below 1 and above Nd); subdomain 1 = the rest
+        std::vector<char> role(Nd, 1);
+        for (int32_t x = b_mmin; x <= b_mmax; ++x) role[x - 1] = 0;
+        for (int32_t x = b_nmin; x <= b_nmax; ++x)
+            if (x < b_mmin || x > b_mmax) role[((x - 1) % Nd + Nd) % Nd] = 2;
+        sub0.clear();
+        sub1.clear();
+        sep.clear();
+        for (int32_t i = 0; i < Nd; ++i) (role[i] == 0 ? sub0 : role[i] == 1 ? sub1 : sep).push_back(best_order[i]);
         std::sort(sub0.begin(), sub0.end());
         std::sort(sub1.begin(), sub1.end());
         std::sort(sep.begin(), sep.end());
         return true;
     }
 
-    int32_t rec(std::vector<int32_t> D) {
+    // `extra` (the screened long-tail atoms, root only) joins the domain's separator, or the
+    // domain itself when it is a leaf
+    int32_t rec(std::vector<int32_t> D, const std::vector<int32_t>& extra = {}) {
         std::vector<int32_t> s0, s1, sp;
         if (!split(D, s0, s1, sp)) {
+            D.insert(D.end(), extra.begin(), extra.end());
             std::sort(D.begin(), D.end());
             nodes.push_back(std::move(D));
             child0.push_back(-1);
@@ -155,6 +175,8 @@ struct Dissector {
         D.shrink_to_fit();
         const int32_t c0 = rec(std::move(s0));
         const int32_t c1 = rec(std::move(s1));
+        sp.insert(sp.end(), extra.begin(), extra.end());
+        std::sort(sp.begin(), sp.end());
         nodes.push_back(std::move(sp));
         child0.push_back(c0);
         child1.push_back(c1);
@@ -266,11 +288,24 @@ int analyze(const ndsi_pattern* pat, int32_t n_atoms, const double* centers,
     }
     // ---- nested dissection
     const int32_t leaf = opt.leaf_atoms > 0 ? opt.leaf_atoms : 20;
-    Dissector dis(n_atoms, centers, adj, leaf);
+    for (int k = 0; k < 3; ++k)
+        if (!(opt.cell[k] >= 0) || !std::isfinite(opt.cell[k])) {
+            err = "ndsi_analyze: cell lengths must be finite and >= 0";
+            return NDSI_ERR_INVALID;
+        }
+    if (opt.screen_degree < 0) {
+        err = "ndsi_analyze: screen_degree must be >= 0";
+        return NDSI_ERR_INVALID;
+    }
+    Dissector dis(n_atoms, centers, adj, leaf, opt.cell);
     {
-        std::vector<int32_t> all(n_atoms);
-        std::iota(all.begin(), all.end(), 0);
-        dis.rec(std::move(all));
+        // (ii) long-tail screening: atoms adjacent to more than screen_degree atoms go to the
+        // root separator and take no part in the dissection
+        std::vector<int32_t> kept, screened;
+        for (int32_t a = 0; a < n_atoms; ++a)
+            (opt.screen_degree > 0 && static_cast<int32_t>(adj[a].size()) > opt.screen_degree ? screened : kept)
+                .push_back(a);
+        dis.rec(std::move(kept), screened);
     }
     const int32_t nn = static_cast<int32_t>(dis.nodes.size());
     P.n_nodes = nn;

@@ -506,6 +506,8 @@ void ndsi_default_options(ndsi_options* opt) {
     opt->max_workspace_bytes = 0;
     opt->outer_block = 128;
     opt->split_bands = 0;
+    opt->cell[0] = opt->cell[1] = opt->cell[2] = 0.0;
+    opt->screen_degree = 0;
 }
 
 int ndsi_poles(int32_t M, double* z_out, double* R_out) {
@@ -1205,8 +1207,12 @@ int ndsi_eigenstates(ndsi_plan* h, const double* H, const double* S, double xi, 
     // buffers: complex right-hand sides and solutions, V = [Re B | Im B], H V, S V, the block C
     const int mmax = 2 * block;
     const int nb = gram_blocks(n);
-    DevBuf yb, xb, vb, hvb, svb, cb, gp, gram, yc, ec, rp;
+    DevBuf yb, xb, rb, vb, hvb, svb, cb, gp, gram, yc, ec, rp;
+    // the split path's factors are accurate to ~1e-9 relative: one refinement step per solve
+    // restores FP64 accuracy, so the iteration converges to the pencil's own eigenpairs
+    const int refine = h->P.opt.precision == NDSI_PREC_SPLIT ? 1 : 0;
     NDSI_CK(yb.alloc(sizeof(double2) * n * block));
+    if (refine) NDSI_CK(rb.alloc(sizeof(double2) * n * block));
     NDSI_CK(xb.alloc(sizeof(double2) * n * block));
     NDSI_CK(vb.alloc(sizeof(double) * n * mmax));
     NDSI_CK(hvb.alloc(sizeof(double) * n * mmax));
@@ -1234,6 +1240,14 @@ int ndsi_eigenstates(ndsi_plan* h, const double* H, const double* S, double xi, 
         NDSI_CK(launch_spmm(h->T.rowptr, h->T.col, Sd, n, cb.as<double>(), m, vb.as<double>(), m, m, st));
         NDSI_CK(launch_real_to_complex(vb.as<double>(), n * m, yb.as<double2>(), st));
         NDSI_CK(launch_solve(h->P, h->ST, h->W.fronts, yb.as<double2>(), xb.as<double2>(), m, st));
+        for (int r = 0; r < refine; ++r) {
+            // iterative refinement in FP64: x += (zS - H)^{-1} (y - (zS - H) x)
+            NDSI_CK(launch_real_to_complex(vb.as<double>(), n * m, yb.as<double2>(), st));
+            NDSI_CK(launch_shifted_residual(h->T.rowptr, h->T.col, Hd, Sd, n, z, xb.as<double2>(), yb.as<double2>(),
+                                            rb.as<double2>(), m, st));
+            NDSI_CK(launch_solve(h->P, h->ST, h->W.fronts, rb.as<double2>(), yb.as<double2>(), m, st));
+            NDSI_CK(launch_complex_add(xb.as<double2>(), yb.as<double2>(), n * m, st));
+        }
         // (B3) in the real span of Re b and Im b
         const int m2 = 2 * m;
         NDSI_CK(launch_split_complex(xb.as<double2>(), n, m, vb.as<double>(), st));

@@ -147,6 +147,35 @@ __global__ void __launch_bounds__(256) k_real_to_complex(const double* __restric
     if (e < count) B[e] = make_double2(A[e], 0.0);
 }
 
+// One warp per row, lanes over the right-hand sides: R = Y - (z S - H) X.
+__global__ void __launch_bounds__(256) k_shifted_residual(const int64_t* __restrict__ rowptr,
+                                                          const int32_t* __restrict__ col,
+                                                          const double* __restrict__ H, const double* __restrict__ S,
+                                                          int64_t n, double2 z, const double2* __restrict__ X,
+                                                          const double2* __restrict__ Y, double2* __restrict__ R,
+                                                          int k) {
+    const int64_t i = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (i >= n) return;
+    for (int c = lane; c < k; c += 32) {
+        double2 acc = Y[i * k + c];
+        for (int64_t e = rowptr[i]; e < rowptr[i + 1]; ++e) {
+            // (z S - H)_ie = (z.x S - H) + i z.y S
+            const double2 a = make_double2(z.x * S[e] - H[e], z.y * S[e]);
+            const double2 x = X[static_cast<int64_t>(col[e]) * k + c];
+            acc.x -= a.x * x.x - a.y * x.y;
+            acc.y -= a.x * x.y + a.y * x.x;
+        }
+        R[i * k + c] = acc;
+    }
+}
+
+__global__ void __launch_bounds__(256) k_complex_add(double2* __restrict__ X, const double2* __restrict__ D,
+                                                     int64_t count) {
+    const int64_t e = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (e < count) X[e] = make_double2(X[e].x + D[e].x, X[e].y + D[e].y);
+}
+
 constexpr int kGramRows = 16;
 constexpr int kGramMax = 64;
 constexpr int kGramPairs = kGramMax * kGramMax / 256;  // pairs per thread at m = 64
@@ -361,6 +390,21 @@ cudaError_t launch_split_complex(const double2* B, int64_t n, int k, double* V, 
 cudaError_t launch_real_to_complex(const double* A, int64_t count, double2* B, cudaStream_t st) {
     if (count == 0) return cudaSuccess;
     k_real_to_complex<<<static_cast<unsigned>((count + 255) / 256), 256, 0, st>>>(A, count, B);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_shifted_residual(const int64_t* rowptr, const int32_t* col, const double* H, const double* S,
+                                    int64_t n, double2 z, const double2* X, const double2* Y, double2* R, int k,
+                                    cudaStream_t st) {
+    if (n == 0) return cudaSuccess;
+    k_shifted_residual<<<static_cast<unsigned>((n * 32 + 255) / 256), 256, 0, st>>>(rowptr, col, H, S, n, z, X, Y, R,
+                                                                                     k);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_complex_add(double2* X, const double2* D, int64_t count, cudaStream_t st) {
+    if (count == 0) return cudaSuccess;
+    k_complex_add<<<static_cast<unsigned>((count + 255) / 256), 256, 0, st>>>(X, D, count);
     return cudaGetLastError();
 }
 

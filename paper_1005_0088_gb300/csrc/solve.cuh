@@ -54,6 +54,15 @@ cudaError_t launch_solve(const Plan& P, const SolveTables& T, const double2* fro
 cudaError_t launch_spmm(const int64_t* rowptr, const int32_t* col, const double* A, int64_t n, const double* X,
                         int ldx, double* Y, int ldy, int m, cudaStream_t st);
 
+// R = Y - (z S - H) X for complex n x k blocks (row-major), H and S real on the CSR pattern: the
+// residual of one step of iterative refinement.
+cudaError_t launch_shifted_residual(const int64_t* rowptr, const int32_t* col, const double* H, const double* S,
+                                    int64_t n, double2 z, const double2* X, const double2* Y, double2* R, int k,
+                                    cudaStream_t st);
+
+// X += D for count complex values.
+cudaError_t launch_complex_add(double2* X, const double2* D, int64_t count, cudaStream_t st);
+
 // B = A + 0i for count real values.
 cudaError_t launch_real_to_complex(const double* A, int64_t count, double2* B, cudaStream_t st);
 

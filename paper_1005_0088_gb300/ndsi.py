@@ -58,7 +58,8 @@ class ndsi_options(ctypes.Structure):
     _fields_ = [("leaf_atoms", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("split_slices", ctypes.c_int32), ("block", ctypes.c_int32),
                 ("m0_radius", ctypes.c_double), ("max_workspace_bytes", ctypes.c_int64),
-                ("outer_block", ctypes.c_int32), ("split_bands", ctypes.c_int32)]
+                ("outer_block", ctypes.c_int32), ("split_bands", ctypes.c_int32),
+                ("cell", ctypes.c_double * 3), ("screen_degree", ctypes.c_int32)]
 
 
 class ndsi_plan_summary(ctypes.Structure):
@@ -368,11 +369,19 @@ def ndsi_eigenstates(plan: Plan, H, S, xi, n_states, eta=1e-3, block=None, max_i
     return eps, C_out, res, it.value
 
 
-def analyze_system(system, **options) -> Plan:
-    """ndsi_analyze on a synth.System-like object (fields n, rowptr, col, centers, atom_of_basis)."""
+def _options(options):
+    """ndsi_options from keyword values (cell as a 3-sequence)."""
     opt = ndsi_default_options()
     for k, v in options.items():
+        if k == "cell":
+            v = (ctypes.c_double * 3)(*[float(c) for c in v])
         setattr(opt, k, v)
+    return opt
+
+
+def analyze_system(system, **options) -> Plan:
+    """ndsi_analyze on a synth.System-like object (fields n, rowptr, col, centers, atom_of_basis)."""
+    opt = _options(options)
     return ndsi_analyze(system.n, system.rowptr, system.col, system.centers.shape[0],
                         system.centers, system.atom_of_basis, opt)
 
@@ -466,9 +475,7 @@ def ndsi_mlp_train(params, X, T, n, steps, lr, stream=None):
 
 def analyze_batched(systems, **options) -> Plan:
     """ndsi_analyze_batched over synth.System-like objects."""
-    opt = ndsi_default_options()
-    for k, v in options.items():
-        setattr(opt, k, v)
+    opt = _options(options)
     ns = len(systems)
     keep = []
     pats = (ndsi_pattern * ns)()

@@ -31,11 +31,12 @@ def test_poles_match_oracle(M):
     assert np.max(np.abs(R - R0) / np.abs(R0)) < 1e-11
 
 
-def _compare_structure(system, leaf):
+def _compare_structure(system, leaf, cell=None, screen_degree=0):
     nd = lib()
-    plan = nd.analyze_system(system, leaf_atoms=leaf)
+    opts = {} if cell is None else {"cell": cell}
+    plan = nd.analyze_system(system, leaf_atoms=leaf, screen_degree=screen_degree, **opts)
     adj = atom_adjacency(system)
-    tr = nested_dissection(system.centers, adj, leaf)
+    tr = nested_dissection(system.centers, adj, leaf, cell=cell, screen_degree=screen_degree)
     st = symbolic_structure(tr, adj)
     assert np.array_equal(nd.ndsi_plan_export(plan, "perm_atoms"), tr["perm_atoms"])
     assert np.array_equal(nd.ndsi_plan_export(plan, "parent"), tr["parent"])
@@ -71,6 +72,26 @@ def test_config_structure_bit_exact(name):
     (4, (13, 11, 1), 1, "2d", 5), (5, (5, 5, 5), 2, "3d", 7)])
 def test_random_structure_bit_exact(seed, shape, o, nb, leaf):
     _compare_structure(lattice_system(shape, o, nb, seed), leaf)
+
+
+@pytest.mark.parametrize("shape,o,nb,periodic,leaf", [
+    ((32, 32, 1), 1, "2dnn", (True, True, False), 20), ((12, 1, 1), 3, "1d", (True, False, False), 2),
+    ((9, 7, 1), 2, "2d", (True, False, False), 4), ((5, 4, 6), 1, "3d", (True, True, True), 5),
+    ((6, 6, 6), 2, "3d", (False, True, False), 8)])
+def test_periodic_structure_bit_exact(shape, o, nb, periodic, leaf):
+    s = lattice_system(shape, o, nb, 11, periodic=periodic)
+    _compare_structure(s, leaf, cell=s.meta["cell"])
+    # coordinates moved by -0.4 cells (wrapping differs from the unshifted lattice)
+    cell = np.array(s.meta["cell"])
+    s.centers = s.centers - 0.4 * cell[None, :]
+    _compare_structure(s, leaf, cell=s.meta["cell"])
+
+
+def test_screened_structure_bit_exact():
+    from tests.test_oracle_nd import _long_tail_system
+    s = _long_tail_system(lattice_system((10, 9, 1), 2, "2d", 8), 3, 4.0, 2)
+    _compare_structure(s, 6, screen_degree=12)
+    _compare_structure(s, 6)
 
 
 def test_shuffled_atoms_bit_exact():
@@ -123,7 +144,8 @@ def test_invalid_options_rejected():
     nd = lib()
     sysm = lattice_system((4, 4, 1), 2, "2d", 3)
     for opts in (dict(block=24), dict(outer_block=40), dict(outer_block=48, block=32),
-                 dict(precision=1, split_slices=3)):
+                 dict(precision=1, split_slices=3), dict(cell=(-1.0, 0.0, 0.0)),
+                 dict(cell=(float("nan"), 0.0, 0.0)), dict(screen_degree=-1)):
         with pytest.raises(nd.NdsiError) as ei:
             nd.analyze_system(sysm, **opts)
         assert ei.value.code == nd.ndsi.NDSI_ERR_INVALID

@@ -126,13 +126,13 @@ def test_outer_block_sizes(block, outer):
         assert np.max(np.abs(g[q] - ref)) < 1e-11 * np.max(np.abs(ref))
 
 
-def _rho_check(sysm, kT, M, leaf=20, host=False):
+def _rho_check(sysm, kT, M, leaf=20, host=False, tol=RHO_TOL, **opts):
     Hd, Sd = sysm.dense()
     eps, C = generalized_eig(Hd, Sd)
     mu = find_mu_eig(eps, kT, sysm.n_electrons, M)
     rho_ref = on_pattern(density_eig(eps, C, mu, kT, M), sysm)
-    rho, ne = _density(sysm, mu, kT, M, host=host, leaf_atoms=leaf)
-    assert np.max(np.abs(rho - rho_ref)) < RHO_TOL
+    rho, ne = _density(sysm, mu, kT, M, host=host, leaf_atoms=leaf, **opts)
+    assert np.max(np.abs(rho - rho_ref)) < tol
     assert abs(ne - electron_count_pattern(rho, sysm)) < 1e-9
     assert abs(ne - sysm.n_electrons) < 1e-8
     return rho, ne
@@ -148,6 +148,23 @@ def test_density_C1_full():
     ((200, 1, 1), 2, "1d", 9, 40)])
 def test_density_small_lattices(shape, o, nb, leaf, M):
     _rho_check(lattice_system(shape, o, nb, 123), 0.01, M, leaf)
+
+
+@pytest.mark.parametrize("shape,o,nb,periodic,leaf", [
+    ((12, 10, 1), 2, "2d", (True, True, False), 12), ((5, 4, 6), 2, "3d", (True, True, True), 8),
+    ((60, 1, 1), 3, "1d", (True, False, False), 4)])
+@pytest.mark.parametrize("precision,tol", [(0, RHO_TOL), (1, 1e-9)])
+def test_density_periodic_lattices(shape, o, nb, periodic, leaf, precision, tol):
+    # periodic cells (Sec. II.C.1 step (i)): separators wrap around the cell
+    sysm = lattice_system(shape, o, nb, 124, periodic=periodic)
+    _rho_check(sysm, 0.01, 40, leaf, tol=tol, cell=sysm.meta["cell"], precision=precision)
+
+
+def test_density_screened_long_tails():
+    # long-tail atoms in the root separator (Sec. II.C.1 step (ii))
+    from tests.test_oracle_nd import _long_tail_system
+    sysm = _long_tail_system(lattice_system((10, 9, 1), 2, "2d", 8), 3, 4.0, 2)
+    _rho_check(sysm, 0.01, 40, 6, screen_degree=12)
 
 
 def test_density_host_buffers_match_device():
