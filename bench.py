@@ -634,22 +634,31 @@ def run_eigen(args):
     ev1.record()
     torch.cuda.synchronize()
     ms_solve = ev0.elapsed_time(ev1) / reps
-    info = nd.ndsi_plan_info(plan)
-    front_bytes = 16.0 * info["front_elems"]
+    # algorithmic reads: A_J^{-1} (lower triangle) and L_RJ in the forward pass, L_RJ again in the
+    # backward pass, once per 16 right-hand sides; plus the right-hand sides and solutions
+    o = system.n // system.n_atoms
+    s_sz = np.diff(nd.ndsi_plan_export(plan, "node_atoms")).astype(np.float64) * o
+    r_sz = np.diff(nd.ndsi_plan_export(plan, "struct_ptr")).astype(np.float64) * o
     groups = (k + 7) // 8
-    # forward reads A^{-1} (lower) and L_RJ, backward L_RJ again, once per group of 8 right-hand
-    # sides; counted as two passes over the whole fronts per group (an upper bound of the reads)
-    alg_bytes = groups * 2.0 * front_bytes + 4 * 16.0 * system.n * k
+    alg_bytes = groups * 16.0 * float(np.sum(s_sz * (s_sz + 1) / 2 + 2 * r_sz * s_sz)) + 4 * 16.0 * system.n * k
+    # algorithmic flops: every complex term 8 flops, per right-hand side: A_J^{-1} y_J (s^2 terms,
+    # each stored lower element used for two), L_RJ y_J and L_RJ^T x_R (r s terms each)
+    alg_flops = 8.0 * k * float(np.sum(s_sz * s_sz + 2 * r_sz * s_sz))
     peak = _peaks().get("hbm_gbs", 6800.0)
     line = {"metric": "selected eigenstates near mu: wall time per solve", "value": t_eig * 1e3, "unit": "ms",
             "higher_is_better": False, "n_gpus": 1, "data": "synthetic",
             "config": {"workload": system.meta["label"], "n": system.n, "xi": xi, "eta": eta,
                        "n_states": n_states, "block": block, "precision": args.precision},
             "iterations": iters, "max_residual": float(np.max(res)), "eps": [float(e) for e in eps],
-            "solve": {"rhs": k, "ms": ms_solve, "bytes_per_solve_bound": alg_bytes,
-                      "gbs": alg_bytes / ms_solve / 1e6, "peak_gbs": peak,
-                      "frac": alg_bytes / ms_solve / 1e6 / peak,
-                      "peak_source": "of measured (MEASURED_PEAKS.json hbm_gbs)"}}
+            "solve": {"rhs": k, "ms": ms_solve, "algorithmic_bytes": alg_bytes,
+                      "gbs": alg_bytes / ms_solve / 1e6, "hbm_frac": alg_bytes / ms_solve / 1e6 / peak,
+                      "roofline": {"bound": "alu", "unit": "TFLOP/s", "achieved": alg_flops / ms_solve / 1e9,
+                                   "peak": 1.25, "frac": alg_flops / ms_solve / 1e9 / 1.25,
+                                   "peak_source": "nominal GB300 FP64 DFMA rate (1.25 TFLOP/s); the "
+                                                  "solve is FP64-bound (each 16-byte factor element "
+                                                  "feeds 3 real FMAs per right-hand side: the "
+                                                  "three-multiplication form executes 6 of the 8 "
+                                                  "counted flops)"}}}
     if system.n <= 4096 and not args.no_cpu:
         from oracle.eigen import eigenstates_near
         Hd, Sd = system.dense()

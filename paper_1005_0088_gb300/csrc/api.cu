@@ -106,6 +106,8 @@ struct ndsi_factors {
     double2* zd = nullptr;
     int32_t np = 0;
     bool inverted = false;  // ndsi_selinv has replaced the factors by G
+    double2* solve_buf = nullptr;  // work space of ndsi_factors_solve (two n x k blocks)
+    int64_t solve_cap = 0;         // complex elements per block
 };
 
 namespace ndsi {
@@ -1162,15 +1164,20 @@ int ndsi_factors_solve(ndsi_factors* f, int32_t pole, const double* Y, int32_t k
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     int rc = ensure_solve_tables(h);
     if (rc) return rc;
-    const size_t bytes = sizeof(double2) * static_cast<size_t>(h->P.n) * k;
-    DevBuf yw, xw;
-    NDSI_CK(yw.alloc(bytes));
+    const int64_t elems = h->P.n * static_cast<int64_t>(k);
+    const size_t bytes = sizeof(double2) * static_cast<size_t>(elems);
+    if (f->solve_cap < elems) {  // kept with the factors: repeated solves allocate nothing
+        if (f->solve_buf) cudaFree(f->solve_buf);
+        f->solve_buf = nullptr;
+        f->solve_cap = 0;
+        NDSI_CK(cudaMalloc(&f->solve_buf, 2 * bytes));
+        f->solve_cap = elems;
+    }
+    double2* yw = f->solve_buf;
     const bool x_dev = is_device_ptr(X_out);
-    if (!x_dev) NDSI_CK(xw.alloc(bytes));
-    double2* xd = x_dev ? reinterpret_cast<double2*>(X_out) : xw.as<double2>();
-    NDSI_CK(cudaMemcpyAsync(yw.p, Y, bytes, cudaMemcpyDefault, st));
-    NDSI_CK(launch_solve(h->P, h->ST, f->W.fronts + static_cast<int64_t>(pole) * f->W.front_stride, yw.as<double2>(), xd,
-                         k, st));
+    double2* xd = x_dev ? reinterpret_cast<double2*>(X_out) : f->solve_buf + f->solve_cap;
+    NDSI_CK(cudaMemcpyAsync(yw, Y, bytes, cudaMemcpyDefault, st));
+    NDSI_CK(launch_solve(h->P, h->ST, f->W.fronts + static_cast<int64_t>(pole) * f->W.front_stride, yw, xd, k, st));
     if (!x_dev) NDSI_CK(cudaMemcpyAsync(X_out, xd, bytes, cudaMemcpyDeviceToHost, st));
     NDSI_CK(cudaStreamSynchronize(st));
     return NDSI_OK;
@@ -1469,6 +1476,7 @@ void ndsi_factors_destroy(ndsi_factors* f) {
     free_workspace(f->W);
     split_free(f->SB);
     if (f->zd) cudaFree(f->zd);
+    if (f->solve_buf) cudaFree(f->solve_buf);
     delete f;
 }
 

@@ -24,95 +24,166 @@ __device__ __forceinline__ double2 cmac(double2 acc, double2 a, double2 b) {
     return acc;
 }
 
-constexpr int kFwdChunk = 32;  // columns of y_J staged in shared memory at a time
+constexpr int kT = kSolveTile;
+constexpr int kTP = kSolveTile + 1;  // padded tile row (conflict-free column reads)
 
-// One tile of kSolveFwdRows front rows of node J, kSolveRhs right-hand sides (grid.y): rows of
-// J get w = A_J^{-1} y_J (written to X), rows of R(J) subtract L_RJ y_J from Y (atomics).
-__global__ void __launch_bounds__(kSolveFwdRows) k_solve_fwd(const SolveNode* __restrict__ nodes,
-                                                            const int32_t* __restrict__ rows,
-                                                            const SolveTile* __restrict__ tiles,
-                                                            const double2* __restrict__ F, double2* Y,
-                                                            double2* __restrict__ X, int k) {
-    __shared__ double2 zs[kFwdChunk][kSolveRhs];
-    const SolveTile t = tiles[blockIdx.x];
-    const SolveNode nd = nodes[t.node];
-    const int i = t.i0 + threadIdx.x;
+constexpr int kSolveThreads = 256;
+
+// Stage a kT x kT tile of the front (column-major, rows r0.., columns c0..) into shared memory as
+// t[c][r] with asynchronous 16-byte copies (every copy of a thread in flight at once); entries
+// outside rows [0, rows) or columns [0, cols) are zero-filled.  Ends with the copies complete and
+// a block barrier.
+__device__ __forceinline__ void load_tile(double2 (*t)[kTP], const double2* __restrict__ Fn, int64_t ld, int r0,
+                                          int rows, int c0, int cols) {
+#pragma unroll
+    for (int u = 0; u < kT * kT / kSolveThreads; ++u) {
+        const int e = threadIdx.x + u * kSolveThreads;
+        const int r = e % kT, c = e / kT;
+        const bool ok = r0 + r < rows && c0 + c < cols;
+        const double2* src = ok ? Fn + (r0 + r) + static_cast<int64_t>(c0 + c) * ld : Fn;
+        const uint32_t dst = static_cast<uint32_t>(__cvta_generic_to_shared(&t[c][r]));
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(dst), "l"(src), "r"(ok ? 16 : 0)
+                     : "memory");
+    }
+}
+
+__device__ __forceinline__ void load_tile_wait() {
+    asm volatile("cp.async.wait_all;\n" ::: "memory");
+    __syncthreads();
+}
+
+// Right-hand-side values c + id of kT rows staged for the three-multiplication complex product:
+// (a + ib)(c + id) = [c(a + b) - b(c + d)] + i[c(a + b) + a(d - c)], so a dot product over a tile
+// takes three real FMAs per complex term (c, d - c and c + d stored per value).
+struct RhsTile {
+    double c[kT][kSolveRhs], dmc[kT][kSolveRhs], cpd[kT][kSolveRhs];
+};
+
+// Stage kT rows (basis indices rb[i0 + r], r < n) of a complex n x k row-major block, RHS c0..
+__device__ __forceinline__ void load_rows(RhsTile& v, const double2* X, const int32_t* rb, int i0, int n, int k,
+                                          int c0, int nc) {
+    for (int e = threadIdx.x; e < kT * kSolveRhs; e += kSolveThreads) {
+        const int r = e / kSolveRhs, c = e % kSolveRhs;
+        const double2 x = (i0 + r < n && c < nc) ? X[static_cast<int64_t>(rb[i0 + r]) * k + c0 + c]
+                                                 : make_double2(0.0, 0.0);
+        v.c[r][c] = x.x;
+        v.dmc[r][c] = x.y - x.x;
+        v.cpd[r][c] = x.x + x.y;
+    }
+}
+
+__device__ __forceinline__ void atomic_add2(double2* p, double2 v) {
+    atomicAdd(&p->x, v.x);
+    atomicAdd(&p->y, v.y);
+}
+
+constexpr int kRq = kSolveRhs / 4;  // right-hand sides per thread (four thread quarters)
+
+// Three-multiplication accumulators of kRq complex dot products.
+struct Acc3 {
+    double p1[kRq], p2[kRq], p3[kRq];
+    __device__ __forceinline__ void zero() {
+#pragma unroll
+        for (int u = 0; u < kRq; ++u) p1[u] = p2[u] = p3[u] = 0.0;
+    }
+    __device__ __forceinline__ void add(double2 a, const RhsTile& v, int row, int col0) {
+        const double ab = a.x + a.y;
+#pragma unroll
+        for (int u = 0; u < kRq; ++u) {
+            p1[u] = fma(v.c[row][col0 + u], ab, p1[u]);
+            p2[u] = fma(a.x, v.dmc[row][col0 + u], p2[u]);
+            p3[u] = fma(a.y, v.cpd[row][col0 + u], p3[u]);
+        }
+    }
+    __device__ __forceinline__ double2 get(int u, double sg) const {
+        return make_double2(sg * (p1[u] - p3[u]), sg * (p1[u] + p2[u]));
+    }
+};
+
+// Forward tile (i0, j0) of node J: front rows i0.. against y_J rows j0..  Rows of R(J) subtract
+// L_RJ y_J from Y; rows of J accumulate w = A_J^{-1} y_J into X from the lower triangle only
+// (element (i, j), i >= j, serves row i directly and, for i > j, row j transposed).
+__global__ void __launch_bounds__(kSolveThreads) k_solve_fwd(const SolveNode* __restrict__ nodes,
+                                                             const int32_t* __restrict__ rows,
+                                                             const SolveTile* __restrict__ tiles,
+                                                             const double2* __restrict__ F, double2* Y, double2* X,
+                                                             int k) {
+    extern __shared__ double2 solve_smem[];
+    auto t = reinterpret_cast<double2 (*)[kTP]>(solve_smem);
+    RhsTile& yc = *reinterpret_cast<RhsTile*>(solve_smem + kT * kTP);
+    RhsTile& yr = *(&yc + 1);
+    const SolveTile tl = tiles[blockIdx.x];
+    const SolveNode nd = nodes[tl.node];
     const int c0 = blockIdx.y * kSolveRhs;
     const int nc = min(kSolveRhs, k - c0);
     const int32_t* rb = rows + nd.row_off;
-    const double2* Fn = F + nd.front_off;
-    double2 acc[kSolveRhs];
-#pragma unroll
-    for (int c = 0; c < kSolveRhs; ++c) acc[c] = make_double2(0.0, 0.0);
-    for (int j0 = 0; j0 < nd.s; j0 += kFwdChunk) {
-        const int jn = min(kFwdChunk, nd.s - j0);
-        __syncthreads();
-        for (int e = threadIdx.x; e < kFwdChunk * kSolveRhs; e += blockDim.x) {
-            const int jj = e / kSolveRhs, cc = e % kSolveRhs;
-            zs[jj][cc] = (jj < jn && cc < nc) ? Y[static_cast<int64_t>(rb[j0 + jj]) * k + c0 + cc]
-                                              : make_double2(0.0, 0.0);
-        }
-        __syncthreads();
+    load_tile(t, F + nd.front_off, nd.f, tl.i0, nd.f, tl.j0, nd.s);
+    load_rows(yc, Y, rb, tl.j0, nd.s, k, c0, nc);
+    const bool sym = tl.i0 < nd.s;  // the tile has rows of J
+    if (sym) load_rows(yr, Y, rb, tl.i0, nd.s, k, c0, nc);
+    load_tile_wait();
+    const int q = threadIdx.x >> 6, r = threadIdx.x & (kT - 1);  // 4 quarters of kRq RHS, 64 rows
+    if (kRq * q >= nc) return;  // a whole quarter (two warps) without right-hand sides
+    // direct part: row i0 + r
+    {
+        const int i = tl.i0 + r;
         if (i < nd.f) {
-            for (int jj = 0; jj < jn; ++jj) {
-                const int j = j0 + jj;
-                // rows of R(J): L_RJ(i - s, j); rows of J: A_J^{-1}(i, j) from the lower triangle
-                const double2 a = (i >= nd.s || j <= i) ? Fn[i + static_cast<int64_t>(j) * nd.f]
-                                                        : Fn[j + static_cast<int64_t>(i) * nd.f];
+            Acc3 acc;
+            acc.zero();
+            const int jmax = i < nd.s ? min(kT, i - tl.j0 + 1) : kT;  // J rows: lower triangle only
+            for (int c = 0; c < jmax; ++c) acc.add(t[c][r], yc, c, kRq * q);
+            double2* dst = (i < nd.s ? X : Y) + static_cast<int64_t>(rb[i]) * k + c0;
+            const double sg = i < nd.s ? 1.0 : -1.0;
 #pragma unroll
-                for (int c = 0; c < kSolveRhs; ++c) acc[c] = cmac(acc[c], a, zs[jj][c]);
-            }
+            for (int u = 0; u < kRq; ++u)
+                if (kRq * q + u < nc && jmax > 0) atomic_add2(dst + kRq * q + u, acc.get(u, sg));
         }
     }
-    if (i >= nd.f) return;
-    const int64_t row = static_cast<int64_t>(rb[i]) * k + c0;
-    if (i < nd.s) {
-        for (int c = 0; c < nc; ++c) X[row + c] = acc[c];
-    } else {
-        for (int c = 0; c < nc; ++c) {
-            atomicAdd(&Y[row + c].x, -acc[c].x);
-            atomicAdd(&Y[row + c].y, -acc[c].y);
+    // transposed part (J rows only): column j0 + r gets sum over rows i > j of A(i, j) y_i
+    if (sym) {
+        const int j = tl.j0 + r;
+        if (j < nd.s) {
+            const int rmin = max(0, j - tl.i0 + 1), rmax = min(kT, nd.s - tl.i0);
+            if (rmin < rmax) {
+                Acc3 acc;
+                acc.zero();
+                for (int rr = rmin; rr < rmax; ++rr) acc.add(t[r][rr], yr, rr, kRq * q);
+                double2* dst = X + static_cast<int64_t>(rb[j]) * k + c0;
+#pragma unroll
+                for (int u = 0; u < kRq; ++u)
+                    if (kRq * q + u < nc) atomic_add2(dst + kRq * q + u, acc.get(u, 1.0));
+            }
         }
     }
 }
 
-// One warp per row i of node J: x_J(i) -= sum_t L_RJ(t, i) x_R(J)(t), lanes over t.
-__global__ void __launch_bounds__(32 * kSolveBwdRows) k_solve_bwd(const SolveNode* __restrict__ nodes,
-                                                                 const int32_t* __restrict__ rows,
-                                                                 const SolveTile* __restrict__ tiles,
-                                                                 const double2* __restrict__ F, double2* X,
-                                                                 int k) {
-    const SolveTile t = tiles[blockIdx.x];
-    const SolveNode nd = nodes[t.node];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int i = t.i0 + warp;
-    if (i >= nd.s) return;
+// Backward tile (i0, j0) of node J: x_J(j0 + c) -= sum over R rows s + i0 + t of L_RJ(t, c) x_R(t).
+__global__ void __launch_bounds__(kSolveThreads) k_solve_bwd(const SolveNode* __restrict__ nodes,
+                                                             const int32_t* __restrict__ rows,
+                                                             const SolveTile* __restrict__ tiles,
+                                                             const double2* __restrict__ F, double2* X, int k) {
+    extern __shared__ double2 solve_smem[];
+    auto t = reinterpret_cast<double2 (*)[kTP]>(solve_smem);
+    RhsTile& xr = *reinterpret_cast<RhsTile*>(solve_smem + kT * kTP);
+    const SolveTile tl = tiles[blockIdx.x];
+    const SolveNode nd = nodes[tl.node];
     const int c0 = blockIdx.y * kSolveRhs;
     const int nc = min(kSolveRhs, k - c0);
     const int32_t* rb = rows + nd.row_off;
-    const double2* Lcol = F + nd.front_off + nd.s + static_cast<int64_t>(i) * nd.f;
-    double2 acc[kSolveRhs];
+    load_tile(t, F + nd.front_off, nd.f, nd.s + tl.i0, nd.f, tl.j0, nd.s);
+    load_rows(xr, X, rb + nd.s, tl.i0, nd.r, k, c0, nc);
+    load_tile_wait();
+    const int q = threadIdx.x >> 6, c = threadIdx.x & (kT - 1);
+    const int j = tl.j0 + c;
+    if (j >= nd.s || kRq * q >= nc) return;
+    Acc3 acc;
+    acc.zero();
+    const int tmax = min(kT, nd.r - tl.i0);
+    for (int tt = 0; tt < tmax; ++tt) acc.add(t[c][tt], xr, tt, kRq * q);
+    double2* dst = X + static_cast<int64_t>(rb[j]) * k + c0;
 #pragma unroll
-    for (int c = 0; c < kSolveRhs; ++c) acc[c] = make_double2(0.0, 0.0);
-    for (int tt = lane; tt < nd.r; tt += 32) {
-        const double2 l = Lcol[tt];
-        const double2* xr = X + static_cast<int64_t>(rb[nd.s + tt]) * k + c0;
-#pragma unroll
-        for (int c = 0; c < kSolveRhs; ++c)
-            if (c < nc) acc[c] = cmac(acc[c], l, xr[c]);
-    }
-#pragma unroll
-    for (int c = 0; c < kSolveRhs; ++c) {
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            acc[c].x += __shfl_down_sync(0xffffffffu, acc[c].x, o);
-            acc[c].y += __shfl_down_sync(0xffffffffu, acc[c].y, o);
-        }
-    }
-    if (lane == 0) {
-        double2* xi = X + static_cast<int64_t>(rb[i]) * k + c0;
-        for (int c = 0; c < nc; ++c) xi[c] = make_double2(xi[c].x - acc[c].x, xi[c].y - acc[c].y);
-    }
+    for (int u = 0; u < kRq; ++u)
+        if (kRq * q + u < nc) atomic_add2(dst + kRq * q + u, acc.get(u, -1.0));
 }
 
 // One warp per row of the CSR matrix, lanes over the m columns.
@@ -316,10 +387,13 @@ cudaError_t solve_tables_build(const Plan& P, SolveTables& T) {
         T.fwd_first[L] = static_cast<int64_t>(fwd.size());
         T.bwd_first[L] = static_cast<int64_t>(bwd.size());
         for (int32_t j : P.level_nodes[L]) {
-            if (P.s[j] == 0) continue;
-            for (int32_t i0 = 0; i0 < P.f[j]; i0 += kSolveFwdRows) fwd.push_back(SolveTile{j, i0});
-            if (P.r[j] > 0)
-                for (int32_t i0 = 0; i0 < P.s[j]; i0 += kSolveBwdRows) bwd.push_back(SolveTile{j, i0});
+            const int32_t s = P.s[j], f = P.f[j], r = P.r[j];
+            if (s == 0) continue;
+            for (int32_t i0 = 0; i0 < f; i0 += kSolveTile)
+                for (int32_t j0 = 0; j0 < s; j0 += kSolveTile)
+                    if (i0 + kSolveTile > s || j0 <= i0) fwd.push_back(SolveTile{j, i0, j0, 0});
+            for (int32_t i0 = 0; i0 < r; i0 += kSolveTile)
+                for (int32_t j0 = 0; j0 < s; j0 += kSolveTile) bwd.push_back(SolveTile{j, i0, j0, 0});
         }
     }
     T.fwd_first[P.n_levels] = static_cast<int64_t>(fwd.size());
@@ -350,24 +424,34 @@ void solve_tables_free(SolveTables& T) {
     T = SolveTables{};
 }
 
+constexpr size_t kFwdSmem = sizeof(double2) * kT * kTP + 2 * sizeof(RhsTile);
+constexpr size_t kBwdSmem = sizeof(double2) * kT * kTP + sizeof(RhsTile);
+
 cudaError_t launch_solve(const Plan& P, const SolveTables& T, const double2* fronts, double2* Y, double2* X, int k,
                          cudaStream_t st) {
+    cudaError_t e;
+    if ((e = cudaFuncSetAttribute(k_solve_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  static_cast<int>(kFwdSmem))) != cudaSuccess)
+        return e;
+    if ((e = cudaFuncSetAttribute(k_solve_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  static_cast<int>(kBwdSmem))) != cudaSuccess)
+        return e;
     const unsigned gy = static_cast<unsigned>((k + kSolveRhs - 1) / kSolveRhs);
+    e = cudaMemsetAsync(X, 0, sizeof(double2) * static_cast<size_t>(P.n) * k, st);
+    if (e != cudaSuccess) return e;
     for (int32_t L = 0; L < P.n_levels; ++L) {
         const int64_t cnt = T.fwd_first[L + 1] - T.fwd_first[L];
         if (cnt == 0) continue;
-        k_solve_fwd<<<dim3(static_cast<unsigned>(cnt), gy), kSolveFwdRows, 0, st>>>(T.nodes, T.rows, T.fwd + T.fwd_first[L],
-                                                                                     fronts, Y, X, k);
-        cudaError_t e = cudaGetLastError();
-        if (e != cudaSuccess) return e;
+        k_solve_fwd<<<dim3(static_cast<unsigned>(cnt), gy), kSolveThreads, kFwdSmem, st>>>(T.nodes, T.rows, T.fwd + T.fwd_first[L], fronts,
+                                                                           Y, X, k);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     for (int32_t L = P.n_levels - 1; L >= 0; --L) {
         const int64_t cnt = T.bwd_first[L + 1] - T.bwd_first[L];
         if (cnt == 0) continue;
-        k_solve_bwd<<<dim3(static_cast<unsigned>(cnt), gy), 32 * kSolveBwdRows, 0, st>>>(
-            T.nodes, T.rows, T.bwd + T.bwd_first[L], fronts, X, k);
-        cudaError_t e = cudaGetLastError();
-        if (e != cudaSuccess) return e;
+        k_solve_bwd<<<dim3(static_cast<unsigned>(cnt), gy), kSolveThreads, kBwdSmem, st>>>(T.nodes, T.rows, T.bwd + T.bwd_first[L], fronts,
+                                                                           X, k);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     return cudaSuccess;
 }

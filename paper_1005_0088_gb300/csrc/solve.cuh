@@ -19,14 +19,14 @@ struct SolveNode {
     int32_t f, s, r, pad;
 };
 
-// A block of front rows of one node: forward tiles span kSolveFwdRows rows of the whole front,
-// backward tiles kSolveBwdRows rows of the node's own columns.
+// A kSolveTile x kSolveTile tile of one node's front: forward tiles at (front row i0, column j0)
+// of the first s columns (lower tiles only inside the J x J block), backward tiles at (row s + i0
+// of R(J), column j0).
 struct SolveTile {
-    int32_t node, i0;
+    int32_t node, i0, j0, pad;
 };
 
-constexpr int kSolveFwdRows = 128;
-constexpr int kSolveBwdRows = 8;
+constexpr int kSolveTile = 64;
 constexpr int kSolveRhs = 8;  // right-hand sides per block (grid.y covers the rest)
 
 struct SolveTables {
@@ -45,7 +45,8 @@ void solve_tables_free(SolveTables& T);
 // X = (zS - H)^{-1} Y with the factors of one point held in `fronts` (after the factor phase:
 // A_J^{-1} in the node's diagonal block, L_RJ = X_RJ A_J^{-1} below it).  Y and X are complex,
 // n x k, row-major (the k right-hand sides of a basis index are adjacent), original basis order.
-// Y is overwritten (the forward elimination works in it).
+// Y is overwritten (the forward elimination works in it).  Every tile accumulates into X and Y
+// with FP64 atomics, so the rounding order (not the result beyond it) varies from run to run.
 cudaError_t launch_solve(const Plan& P, const SolveTables& T, const double2* fronts, double2* Y, double2* X, int k,
                          cudaStream_t st);
 
