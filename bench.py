@@ -136,6 +136,52 @@ def cpu_oracle_rate(system, mu, kT, M, min_seconds=10.0, min_reps=2):
     return M * system.n / t, len(times), t, electron_count_eig(eps, mu, kT, M)
 
 
+def cpu_single_core_rate(config, mu):
+    """The oracle's route 1 on one host core (a child process with every BLAS pool at one thread):
+    poles x N per second, or None when the child fails."""
+    import subprocess
+    code = ("import time, json; from synth import config_system; "
+            "from oracle.dense import generalized_eig, density_eig, on_pattern; "
+            f"s = config_system({config!r}); Hd, Sd = s.dense(); kT, M = s.meta['kT'], s.meta['poles']; "
+            "ts = []\n"
+            "for _ in range(3):\n"
+            "    t0 = time.perf_counter(); e, C = generalized_eig(Hd, Sd); "
+            f"on_pattern(density_eig(e, C, {mu!r}, kT, M), s); ts.append(time.perf_counter() - t0)\n"
+            "print(json.dumps(M * s.n / min(ts)))")
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    try:
+        out = subprocess.run([sys.executable, "-c", code], cwd=ROOT, env=env, capture_output=True,
+                             text=True, timeout=300)
+        return float(out.stdout.strip().splitlines()[-1]) if out.returncode == 0 else None
+    except (subprocess.SubprocessError, ValueError, IndexError):
+        return None
+
+
+def cpu_sparse_lu_rate(system, mu, kT, M, max_seconds=10.0):
+    """SciPy's sparse LU (SuperLU, COLAMD ordering) of z_p S - H for as many poles as fit in about
+    max_seconds, scaled to a full sweep: a lower bound of the cost of a CPU sparse route (the
+    selected inversion is not included).  Returns (poles x N per second, poles timed, s per pole)."""
+    import numpy as np
+    import scipy.sparse
+    import scipy.sparse.linalg
+    from oracle.poles import cf_poles
+    z, _ = cf_poles(M)
+    rows = system.rows()
+    Hs = scipy.sparse.csc_matrix((system.H, (rows, system.col)), shape=(system.n, system.n))
+    Ss = scipy.sparse.csc_matrix((system.S, (rows, system.col)), shape=(system.n, system.n))
+    times = []
+    t_all = time.perf_counter()
+    for zp in z:
+        if times and time.perf_counter() - t_all > max_seconds:
+            break
+        A = ((mu + 1j * zp * kT) * Ss - Hs).tocsc()
+        t0 = time.perf_counter()
+        scipy.sparse.linalg.splu(A)
+        times.append(time.perf_counter() - t0)
+    t_pole = float(np.mean(times))
+    return M * system.n / (t_pole * (M + 1)), len(times), t_pole
+
+
 def run_reference(args):
     rank, world, _ = _env_rank()
     if rank != 0:
@@ -393,6 +439,20 @@ def run_ndsi(args):
         cpu = {"value": v, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
                "sample": f"{reps} full density evaluations of the workload by dense generalized "
                          f"eigendecomposition + {M}-pole Fermi sum ({t_rep:.2f} s each)"}
+        extra = {}
+        if system.n <= 1024:
+            v1 = cpu_single_core_rate(args.config, MU)
+            if v1 is not None:
+                extra["oracle_one_core"] = {"value": v1, "unit": UNIT, "cores": 1}
+        if system.n <= 16384:
+            vs, npl, tpl = cpu_sparse_lu_rate(system, MU, kT, M)
+            extra["scipy_sparse_lu"] = {"value": vs, "unit": UNIT, "cores": os.cpu_count(),
+                                        "sample": f"SuperLU factorisation of {npl} poles, "
+                                                  f"{tpl * 1e3:.1f} ms each, scaled to {M + 1} "
+                                                  "points; factorisation only (no selected "
+                                                  "inversion), a lower bound of a CPU sparse route"}
+        if extra:
+            cpu["other_cpu_routes"] = extra
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": ms_step,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
