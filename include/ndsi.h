@@ -390,7 +390,7 @@ int ndsi_find_mu(ndsi_plan* plan, const double* H, const double* S, double kT, i
                  int32_t* iters_out, void* stream);
 
 /* ---- Learned seed for the chemical-potential search (not in the paper; it only proposes the
- * starting bracket of ndsi_find_mu, whose bisection still decides the result). ----
+ * starting bracket of ndsi_find_mu, whose exact evaluations still decide the result). ----
  * Network: 32 inputs -> 64 tanh -> 64 tanh -> 1 output, FP32, parameters packed as
  * [W1 (64x32 row-major), b1 (64), W2 (64x64), b2 (64), W3 (64), b3 (1)]. */
 #define NDSI_MLP_INPUTS 32

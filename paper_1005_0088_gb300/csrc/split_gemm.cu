@@ -438,13 +438,20 @@ __device__ __forceinline__ void slice_pair(double x0, double x1, int E, uint32_t
 #pragma unroll
     for (int t = 0; t < S - 1; ++t) bias |= static_cast<int64_t>(128) << (8 * t);
     const int64_t g0 = fp64_scaled<S>(x0, E) + bias, g1 = fp64_scaled<S>(x1, E) + bias;
+    const uint32_t lo0 = static_cast<uint32_t>(g0), hi0 = static_cast<uint32_t>(static_cast<uint64_t>(g0) >> 32);
+    const uint32_t lo1 = static_cast<uint32_t>(g1), hi1 = static_cast<uint32_t>(static_cast<uint64_t>(g1) >> 32);
 #pragma unroll
     for (int t = 1; t < S; ++t) {
         const int k = S - 1 - t;  // byte of the biased sum holding digit t
-        const int b0 = static_cast<int>((g0 >> (8 * k)) & 0xFF), b1 = static_cast<int>((g1 >> (8 * k)) & 0xFF);
+        // one byte permute builds the FP32 bits 0x4B4000bb (= 2^23 + 2^22 + b) from byte b, and one
+        // FFMA gives (2^23 + 2^22 + b) 2^(-8t) - (2^23 + 2^22 + 128) 2^(-8t) = (b - 128) 2^(-8t):
+        // every intermediate is exact
+        const uint32_t sel = 0x7640u + static_cast<uint32_t>(k & 3);
+        const uint32_t m0 = __byte_perm(k < 4 ? lo0 : hi0, 0x4B400000u, sel);
+        const uint32_t m1 = __byte_perm(k < 4 ? lo1 : hi1, 0x4B400000u, sel);
         const float sc = __int_as_float((127 - 8 * t) << 23);
-        const float f0 = (__int_as_float(0x4B400000 + b0) - 12583040.0f) * sc;
-        const float f1 = (__int_as_float(0x4B400000 + b1) - 12583040.0f) * sc;
+        const float f0 = fmaf(__uint_as_float(m0), sc, -12583040.0f * sc);
+        const float f1 = fmaf(__uint_as_float(m1), sc, -12583040.0f * sc);
         w[t] = __byte_perm(__float_as_uint(f0), __float_as_uint(f1), 0x7632);
     }
     const int t0 = static_cast<int>(g0 >> (8 * (S - 1))), t1 = static_cast<int>(g1 >> (8 * (S - 1)));
@@ -609,6 +616,8 @@ __global__ void __launch_bounds__(256) k_slice1(const SliceArgs p) {
     const bool rows_contig = !sym && (p.isB ? p.op == OP_T : p.op == OP_N);
     const int tid = threadIdx.x;
     if (tid < 32) rowmax[tid] = -1;
+    // stage the rows with asynchronous 16-byte copies, all of a thread's copies in flight at once
+    // (rows beyond the operand are zero-filled)
     const int total = R * K;
     for (int e = tid; e < total; e += 256) {
         int rr, kk;
@@ -620,19 +629,23 @@ __global__ void __launch_bounds__(256) k_slice1(const SliceArgs p) {
             rr = e / K;
         }
         const int gr = blk.r0 + rr;
-        double2 x = make_double2(0.0, 0.0);
+        const double2* src = base;
         if (gr < nrows) {
             if (sym) {
                 const int hi = gr > kk ? gr : kk, lo = gr > kk ? kk : gr;
-                x = base[hi + static_cast<int64_t>(lo) * ld];
+                src = base + hi + static_cast<int64_t>(lo) * ld;
             } else if (rows_contig) {
-                x = base[gr + static_cast<int64_t>(kk) * ld];
+                src = base + gr + static_cast<int64_t>(kk) * ld;
             } else {
-                x = base[kk + static_cast<int64_t>(gr) * ld];
+                src = base + kk + static_cast<int64_t>(gr) * ld;
             }
         }
-        t1[rr * ldt + kk] = x;
+        const uint32_t dst = static_cast<uint32_t>(__cvta_generic_to_shared(t1 + rr * ldt + kk));
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(dst), "l"(src),
+                     "r"(gr < nrows ? 16 : 0)
+                     : "memory");
     }
+    asm volatile("cp.async.wait_all;\n" ::: "memory");
     __syncthreads();
     {
         const int tpr = 256 / R;  // threads per row
