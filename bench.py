@@ -285,28 +285,33 @@ def _measure(nd, torch, plan, H, S, rho, ne, kT, M, steps, warmup, stream, flush
         else:
             nd.ndsi_density_energy(plan, H, S, MU, kT, M, rho, e, ne, stream=stream)
 
-    def timed_steps():
-        out = []
+    def timed_steps(ahead):
+        # L2 flush, start event, sweep, end event per step, all on the launch stream; with
+        # `ahead` the steps are enqueued back to back (the host runs ahead of the GPU, so host
+        # scheduling noise does not open gaps between the events), else synchronised per step
+        events = []
+        torch.cuda.synchronize()
         for _ in range(steps):
             flush.zero_()
-            torch.cuda.synchronize()
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
             step()
             e1.record(stream)
-            torch.cuda.synchronize()
-            out.append(e0.elapsed_time(e1))
-        return out
+            events.append((e0, e1))
+            if not ahead:
+                torch.cuda.synchronize()
+        torch.cuda.synchronize()
+        return [a.elapsed_time(b) for a, b in events]
     for _ in range(max(warmup, 3)):
         step()
     torch.cuda.synchronize()
     # the timed region alone is what `ncu --profile-from-start off` records (a no-op otherwise)
     torch.cuda.profiler.start()
-    times = timed_steps()
+    times = timed_steps(True)
     torch.cuda.profiler.stop()
     nd.ndsi_profile_enable(plan, True, by_level=by_level)
-    prof_times = timed_steps()
+    prof_times = timed_steps(False)
     prof = nd.ndsi_profile_read(plan)
     nd.ndsi_profile_enable(plan, False)
     return times, prof, prof_times

@@ -94,6 +94,9 @@ struct ndsi_plan {
     cudaGraphExec_t graph = nullptr;
     std::vector<const void*> graph_key;
     int64_t graph_nodes = 0;
+    double2* pin = nullptr;         // pinned staging of the point tables (3 x pin_cap)
+    size_t pin_cap = 0;
+    cudaEvent_t pin_ev = nullptr;   // recorded after the last copies out of `pin`
     // tables of the triangular solves (built on first use)
     ndsi::SolveTables ST;
     double2* point_z = nullptr;  // the single point factored for the eigensolver
@@ -907,9 +910,28 @@ int density_impl(ndsi_plan* h, const double* Hd, const double* Sd, const double*
     for (int32_t sy = 0; sy < ns; ++sy)
         part_off[sy + 1] = part_off[sy] + accumulate_blocks(h->P.sys_nnz_first[sy + 1] - h->P.sys_nnz_first[sy]);
     if (!h->partials) NDSI_CK(cudaMalloc(&h->partials, sizeof(double) * (part_off[ns] + 1)));
-    NDSI_CK(cudaMemcpyAsync(h->zw, zq.data(), sizeof(double2) * ns * nq, cudaMemcpyHostToDevice, st));
-    NDSI_CK(cudaMemcpyAsync(h->cw, cq.data(), sizeof(double2) * ns * nq, cudaMemcpyHostToDevice, st));
-    if (e_d) NDSI_CK(cudaMemcpyAsync(h->cew, ceq.data(), sizeof(double2) * ns * nq, cudaMemcpyHostToDevice, st));
+    // the point tables go through pinned staging, so the copies are asynchronous and the host
+    // can run a sweep ahead of the GPU; the staging is rewritten only after the previous call's
+    // copies have executed
+    {
+        const size_t cnt = static_cast<size_t>(ns) * nq;
+        if (h->pin_cap < cnt) {
+            if (h->pin) cudaFreeHost(h->pin);
+            h->pin = nullptr;
+            h->pin_cap = 0;
+            NDSI_CK(cudaMallocHost(&h->pin, sizeof(double2) * 3 * cnt));
+            h->pin_cap = cnt;
+        }
+        if (!h->pin_ev) NDSI_CK(cudaEventCreateWithFlags(&h->pin_ev, cudaEventDisableTiming));
+        NDSI_CK(cudaEventSynchronize(h->pin_ev));
+        std::memcpy(h->pin, zq.data(), sizeof(double2) * cnt);
+        std::memcpy(h->pin + cnt, cq.data(), sizeof(double2) * cnt);
+        if (e_d) std::memcpy(h->pin + 2 * cnt, ceq.data(), sizeof(double2) * cnt);
+        NDSI_CK(cudaMemcpyAsync(h->zw, h->pin, sizeof(double2) * cnt, cudaMemcpyHostToDevice, st));
+        NDSI_CK(cudaMemcpyAsync(h->cw, h->pin + cnt, sizeof(double2) * cnt, cudaMemcpyHostToDevice, st));
+        if (e_d) NDSI_CK(cudaMemcpyAsync(h->cew, h->pin + 2 * cnt, sizeof(double2) * cnt, cudaMemcpyHostToDevice, st));
+        NDSI_CK(cudaEventRecord(h->pin_ev, st));
+    }
     if (h->graphs && !h->prof.on) {
         // replay the captured sweep; points and weights are read from zw / cw at run time
         const std::vector<const void*> key = {Hd, Sd, rho_d, ne_d, e_d, h->W.fronts, h->W.scr, h->SB.sliceA,
@@ -1496,6 +1518,8 @@ void ndsi_plan_destroy(ndsi_plan* h) {
     if (h->dos_tr) cudaFree(h->dos_tr);
     if (h->dos_z) cudaFree(h->dos_z);
     if (h->point_z) cudaFree(h->point_z);
+    if (h->pin) cudaFreeHost(h->pin);
+    if (h->pin_ev) cudaEventDestroy(h->pin_ev);
     solve_tables_free(h->ST);
     if (h->stage) cudaFree(h->stage);
     if (h->graph) cudaGraphExecDestroy(h->graph);
