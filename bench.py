@@ -604,6 +604,39 @@ def run_batched(args, nd, torch, dist, rank, world, local, prec_code):
     return 0
 
 
+def run_mu_search_batched(args, nd, torch):
+    """Chemical-potential search for all twelve systems of the batched workload at once
+    (ndsi_find_mu_batched: lockstep searches, one batched sweep per round, procedure (2) start):
+    batched sweeps and wall time per solve."""
+    import numpy as np
+    from synth import batched_systems
+    systems = batched_systems()
+    M = args.poles or 120
+    kT = 0.01
+    plan = nd.analyze_batched(systems, precision={"fp64": nd.NDSI_PREC_FP64, "split": nd.NDSI_PREC_SPLIT}[args.precision],
+                              split_slices=args.slices)
+    H = torch.as_tensor(np.concatenate([s.H for s in systems]), device="cuda")
+    S = torch.as_tensor(np.concatenate([s.S for s in systems]), device="cuda")
+    rho = torch.zeros(H.numel(), dtype=torch.float64, device="cuda")
+    kts = np.full(len(systems), kT)
+    ne = np.array([s.n_electrons for s in systems])
+    ne_out = torch.zeros(len(systems), dtype=torch.float64, device="cuda")
+    nd.ndsi_density_batched(plan, H, S, np.full(len(systems), MU), kts, M, rho, ne_out)   # warm
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    mu, n_e, rounds = nd.ndsi_find_mu_batched(plan, H, S, kts, M, ne, rho)
+    torch.cuda.synchronize()
+    t = time.perf_counter() - t0
+    line = {"metric": "chemical-potential search, all systems of the batched workload: batched sweeps per solve",
+            "value": rounds, "unit": "sweeps", "higher_is_better": False, "n_gpus": 1, "data": "synthetic",
+            "config": {"workload": "batched: 12 uneven systems (N 2048..32768), one plan", "poles": M, "kT": kT,
+                       "precision": args.precision, "tolerance_electrons": 1e-8},
+            "seconds": t, "mu": [float(v) for v in mu],
+            "max_electron_error": float(np.max(np.abs(n_e - ne)))}
+    print(json.dumps(line))
+    return 0
+
+
 def run_mu_search(args):
     """Chemical-potential search on the workload three ways: a bracket spanning the spectral
     bounds ("bounds"), no bracket (the paper's opening sequence with the retarded-Green-function
@@ -618,6 +651,8 @@ def run_mu_search(args):
     from paper_1005_0088_gb300.mu_seed import MuSeed, build_dataset, features
     from synth import config_system, mu_training_systems
     torch.cuda.set_device(0)
+    if args.config == "C4":
+        return run_mu_search_batched(args, nd, torch)
     t0 = time.perf_counter()
     X, T = build_dataset(mu_training_systems(args.mu_train, 1))
     t_data = time.perf_counter() - t0

@@ -369,6 +369,29 @@ int ndsi_mu_search(ndsi_mu_eval_fn eval, ndsi_mu_dos_fn dos, void* ctx, double e
                    double tol_electrons, int32_t max_iter, double* mu_out, double* dn_out,
                    int32_t* evals_out);
 
+/* Callbacks of ndsi_mu_search_batched, each answering one round for all systems at once:
+ * DeltaN_s(mu_s) for every system s into dn[s], and D_s(E_s,k) for the n energies of every system
+ * (E and D row-major n_systems x n, eta[s] per system).  active[s] = 1 marks the systems whose
+ * search asked for the round; the others' values are ignored.  Return 0 on success. */
+typedef int (*ndsi_mu_eval_batch_fn)(void* ctx, int32_t n_systems, const int32_t* active, const double* mu,
+                                     double* dn);
+typedef int (*ndsi_mu_dos_batch_fn)(void* ctx, int32_t n_systems, const int32_t* active, const double* E,
+                                    int32_t n, const double* eta, double* D);
+
+/* ndsi_mu_search for n_systems systems in lockstep (host only): every system runs its own search
+ * (per-system elo, ehi, kT, n_electrons and optional brackets mu_lo/mu_hi, NULL for none), and
+ * each round answers all pending requests of one kind with one batched callback, so a batched
+ * plan needs one sweep per round instead of one per system and step.
+ *   mu_out, dn_out, evals_out - host arrays [n_systems] (dn_out, evals_out may be NULL);
+ *   rounds_out                - host, the batched callbacks made.
+ * The search of each system runs on a worker thread; the callbacks run on the calling thread.
+ * Errors: as ndsi_mu_search, for the first failing system (its index in ndsi_last_error). */
+int ndsi_mu_search_batched(int32_t n_systems, ndsi_mu_eval_batch_fn eval, ndsi_mu_dos_batch_fn dos,
+                           void* ctx, const double* elo, const double* ehi, const double* kT,
+                           const double* n_electrons, int32_t n_grid, const double* mu_lo,
+                           const double* mu_hi, double tol_electrons, int32_t max_iter, double* mu_out,
+                           double* dn_out, int32_t* evals_out, int32_t* rounds_out);
+
 /* Chemical-potential search (Sec. II.C.3): find mu with
  *   DeltaN(mu) = Tr(rho(mu) S) - n_electrons = 0      (Eq. 40)
  * to |DeltaN| < tol_electrons.  Every trial mu is one full contour evaluation (ndsi_density).
@@ -388,6 +411,22 @@ int ndsi_find_mu(ndsi_plan* plan, const double* H, const double* S, double kT, i
                  double n_electrons, double mu_lo, double mu_hi, double tol_electrons,
                  int32_t max_iter, double* rho_out, double* mu_out, double* n_elec_out,
                  int32_t* iters_out, void* stream);
+
+/* ndsi_find_mu for every system of a batched plan at once: the searches run in lockstep
+ * (ndsi_mu_search_batched), each round one batched contour sweep (ndsi_density_batched) or one
+ * batched retarded-Green-function sweep with a grid per system, so the cost is that of the
+ * slowest system's search, not the sum.
+ *   kT, n_electrons       - host double[n_systems];
+ *   mu_lo, mu_hi          - host double[n_systems] brackets, or NULL (procedure (2) start);
+ *   rho_out               - device or host double[nnz of the batched plan], rho at mu_out;
+ *   mu_out, n_elec_out    - host double[n_systems] (n_elec_out may be NULL);
+ *   rounds_out            - host, the batched sweeps used (the density-of-states sweep counts).
+ * Errors: those of ndsi_find_mu (for the first failing system) and NDSI_ERR_INVALID for a
+ * non-positive kT or a non-finite electron count. */
+int ndsi_find_mu_batched(ndsi_plan* plan, const double* H, const double* S, const double* kT,
+                         int32_t n_poles, const double* n_electrons, const double* mu_lo,
+                         const double* mu_hi, double tol_electrons, int32_t max_iter, double* rho_out,
+                         double* mu_out, double* n_elec_out, int32_t* rounds_out, void* stream);
 
 /* ---- Learned seed for the chemical-potential search (not in the paper; it only proposes the
  * starting bracket of ndsi_find_mu, whose exact evaluations still decide the result). ----

@@ -599,17 +599,23 @@ __global__ void __launch_bounds__(kAccThreads) k_point_traces(const int64_t* __r
     }
 }
 
-cudaError_t launch_point_traces(const Plan& P, const DevTables& T, const Workspace& W, int np,
-                                const double* S, double* partials, double* out, cudaStream_t st) {
-    const int nb = accumulate_blocks(P.nnz);
+cudaError_t launch_point_traces_range(const int64_t* out_map, int64_t nnz, const double2* F, int64_t stride, int np,
+                                      const double* S, double* partials, double* out, cudaStream_t st) {
+    if (nnz <= 0 || np <= 0) return cudaSuccess;
+    const int nb = accumulate_blocks(nnz);
     k_point_traces<<<dim3(static_cast<unsigned>(nb), static_cast<unsigned>(np)), kAccThreads, 0, st>>>(
-        T.out_map, P.nnz, W.fronts, W.front_stride, S, partials);
+        out_map, nnz, F, stride, S, partials);
     cudaError_t e = cudaGetLastError();
     for (int q = 0; q < np && e == cudaSuccess; ++q) {
         k_reduce<<<1, 1024, 0, st>>>(partials + static_cast<int64_t>(q) * nb, nb, out + q);
         e = cudaGetLastError();
     }
     return e;
+}
+
+cudaError_t launch_point_traces(const Plan& P, const DevTables& T, const Workspace& W, int np, const double* S,
+                                double* partials, double* out, cudaStream_t st) {
+    return launch_point_traces_range(T.out_map, P.nnz, W.fronts, W.front_stride, np, S, partials, out, st);
 }
 
 cudaError_t launch_reduce(const double* partials, int nblocks, double* out, cudaStream_t st) {

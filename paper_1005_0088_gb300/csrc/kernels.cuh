@@ -71,6 +71,10 @@ double gershgorin_value(unsigned long long key);
 
 // Per point q of a chunk: out[q] = sum over the pattern of Im G_q(k) S_k = Im Tr(G(z_q) S) (the
 // density of states of Eq. 42 up to -2/pi).  partials: np x accumulate_blocks(nnz) doubles.
+// The same over one range of pattern entries (out_map and S offset to its first entry; F holds np
+// point slabs of `stride` complex elements): out[q] = sum_k Im F_q[out_map[k]] S[k].
+cudaError_t launch_point_traces_range(const int64_t* out_map, int64_t nnz, const double2* F, int64_t stride, int np,
+                                      const double* S, double* partials, double* out, cudaStream_t st);
 cudaError_t launch_point_traces(const Plan& P, const DevTables& T, const Workspace& W, int np,
                                 const double* S, double* partials, double* out, cudaStream_t st);
 

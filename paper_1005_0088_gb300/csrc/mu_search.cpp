@@ -17,8 +17,11 @@
 //     does not at least halve the smallest |DeltaN| is followed by one bisection.
 #include <algorithm>
 #include <cmath>
+#include <condition_variable>
 #include <limits>
+#include <mutex>
 #include <string>
+#include <thread>
 #include <utility>
 #include <vector>
 
@@ -221,6 +224,172 @@ int mu_search(ndsi_mu_eval_fn eval, ndsi_mu_dos_fn dos, void* ctx, double elo, d
     return finish(NDSI_OK);
 }
 
+// ---- many searches in lockstep ---------------------------------------------------------------
+// One worker thread per system runs mu_search; its evaluation and density-of-states requests are
+// collected by the calling thread, which answers every pending request of one kind with one
+// batched callback (one batched sweep on the GPU) and releases the workers again.  Callbacks
+// run only on the calling thread.
+namespace {
+
+struct Lockstep {
+    enum State { RUNNING, WAIT_EVAL, WAIT_DOS, DONE };
+    struct Slot {
+        State state = RUNNING;
+        double mu = 0, dn = 0, last_mu = 0;
+        const double* E = nullptr;
+        int32_t nE = 0;
+        double eta = 0;
+        double* D = nullptr;
+        int rc = NDSI_OK;
+    };
+    std::mutex m;
+    std::condition_variable cv_coord, cv_work;
+    std::vector<Slot> slots;
+    int fail_rc = NDSI_OK;  // first callback error: every later request returns it
+};
+
+struct WorkerCtx {
+    Lockstep* L;
+    int32_t sy;
+};
+
+int lockstep_eval(void* c, double mu, double* dn) {
+    WorkerCtx& w = *static_cast<WorkerCtx*>(c);
+    std::unique_lock<std::mutex> lk(w.L->m);
+    Lockstep::Slot& s = w.L->slots[w.sy];
+    s.mu = mu;
+    s.state = Lockstep::WAIT_EVAL;
+    w.L->cv_coord.notify_one();
+    w.L->cv_work.wait(lk, [&] { return s.state == Lockstep::RUNNING; });
+    *dn = s.dn;
+    return s.rc;
+}
+
+int lockstep_dos(void* c, const double* E, int32_t n, double eta, double* D) {
+    WorkerCtx& w = *static_cast<WorkerCtx*>(c);
+    std::unique_lock<std::mutex> lk(w.L->m);
+    Lockstep::Slot& s = w.L->slots[w.sy];
+    s.E = E;
+    s.nE = n;
+    s.eta = eta;
+    s.D = D;
+    s.state = Lockstep::WAIT_DOS;
+    w.L->cv_coord.notify_one();
+    w.L->cv_work.wait(lk, [&] { return s.state == Lockstep::RUNNING; });
+    return s.rc;
+}
+
+}  // namespace
+
+int mu_search_batched(int32_t ns, ndsi_mu_eval_batch_fn eval, ndsi_mu_dos_batch_fn dos, void* ctx,
+                      const double* elo, const double* ehi, const double* kT, const double* n_electrons,
+                      int32_t n_grid, const double* mu_lo, const double* mu_hi, double tol, int32_t max_iter,
+                      double* mu_out, double* dn_out, int32_t* evals_out, int32_t* rounds_out, std::string& err) {
+    if (ns < 1 || !eval || !elo || !ehi || !kT || !n_electrons || !mu_out) {
+        err = "mu search: invalid argument";
+        return NDSI_ERR_INVALID;
+    }
+    Lockstep L;
+    L.slots.resize(ns);
+    std::vector<WorkerCtx> wc(ns);
+    std::vector<int> rcs(ns, NDSI_OK);
+    std::vector<std::string> errs(ns);
+    std::vector<double> mu(ns, 0.0), dn(ns, 0.0);
+    std::vector<int32_t> ev(ns, 0);
+    std::vector<std::thread> threads;
+    threads.reserve(ns);
+    for (int32_t sy = 0; sy < ns; ++sy) {
+        wc[sy] = WorkerCtx{&L, sy};
+        threads.emplace_back([&, sy]() {
+            const double lo = mu_lo ? mu_lo[sy] : 0.0, hi = mu_hi ? mu_hi[sy] : 0.0;
+            const int rc = mu_search(lockstep_eval, dos ? lockstep_dos : nullptr, &wc[sy], elo[sy], ehi[sy], kT[sy],
+                                     n_electrons[sy], n_grid, lo, hi, tol, max_iter, &mu[sy], &dn[sy], &ev[sy],
+                                     errs[sy]);
+            std::lock_guard<std::mutex> lk(L.m);
+            rcs[sy] = rc;
+            L.slots[sy].state = Lockstep::DONE;
+            L.cv_coord.notify_one();
+        });
+    }
+    int32_t rounds = 0;
+    std::vector<double> bmu(ns), bdn(ns), etas(ns);
+    std::vector<int32_t> active(ns);
+    {
+        std::unique_lock<std::mutex> lk(L.m);
+        for (;;) {
+            L.cv_coord.wait(lk, [&] {
+                for (const auto& s : L.slots)
+                    if (s.state == Lockstep::RUNNING) return false;
+                return true;
+            });
+            bool any_dos = false, any_eval = false;
+            for (const auto& s : L.slots) {
+                any_dos |= s.state == Lockstep::WAIT_DOS;
+                any_eval |= s.state == Lockstep::WAIT_EVAL;
+            }
+            if (!any_dos && !any_eval) break;
+            int rc = L.fail_rc;
+            if (any_dos) {
+                // one batched density-of-states call; every waiting system brings its own grid
+                int32_t nE = 0;
+                for (const auto& s : L.slots)
+                    if (s.state == Lockstep::WAIT_DOS) nE = std::max(nE, s.nE);
+                std::vector<double> E(static_cast<size_t>(ns) * nE, 0.0), D(static_cast<size_t>(ns) * nE, 0.0);
+                for (int32_t sy = 0; sy < ns; ++sy) {
+                    const auto& s = L.slots[sy];
+                    active[sy] = s.state == Lockstep::WAIT_DOS;
+                    etas[sy] = active[sy] ? s.eta : 1.0;
+                    for (int32_t k = 0; k < nE; ++k)
+                        E[static_cast<size_t>(sy) * nE + k] =
+                            active[sy] ? s.E[std::min(k, s.nE - 1)] : elo[sy] + (ehi[sy] - elo[sy]) * k / std::max(1, nE - 1);
+                }
+                if (!rc) rc = dos(ctx, ns, active.data(), E.data(), nE, etas.data(), D.data());
+                ++rounds;
+                for (int32_t sy = 0; sy < ns; ++sy) {
+                    auto& s = L.slots[sy];
+                    if (s.state != Lockstep::WAIT_DOS) continue;
+                    for (int32_t k = 0; k < s.nE; ++k) s.D[k] = D[static_cast<size_t>(sy) * nE + k];
+                    s.rc = rc;
+                    s.state = Lockstep::RUNNING;
+                }
+            } else {
+                // one batched evaluation; systems without a request are evaluated at their last mu
+                for (int32_t sy = 0; sy < ns; ++sy) {
+                    const auto& s = L.slots[sy];
+                    active[sy] = s.state == Lockstep::WAIT_EVAL;
+                    bmu[sy] = active[sy] ? s.mu : s.last_mu;
+                }
+                if (!rc) rc = eval(ctx, ns, active.data(), bmu.data(), bdn.data());
+                ++rounds;
+                for (int32_t sy = 0; sy < ns; ++sy) {
+                    auto& s = L.slots[sy];
+                    if (s.state != Lockstep::WAIT_EVAL) continue;
+                    s.dn = bdn[sy];
+                    s.last_mu = s.mu;
+                    s.rc = rc;
+                    s.state = Lockstep::RUNNING;
+                }
+            }
+            if (rc && !L.fail_rc) L.fail_rc = rc;
+            L.cv_work.notify_all();
+        }
+    }
+    for (auto& t : threads) t.join();
+    int rc = NDSI_OK;
+    for (int32_t sy = 0; sy < ns; ++sy) {
+        mu_out[sy] = mu[sy];
+        if (dn_out) dn_out[sy] = dn[sy];
+        if (evals_out) evals_out[sy] = ev[sy];
+        if (rcs[sy] && (!rc || rc == NDSI_ERR_TIMEOUT)) {
+            rc = rcs[sy];
+            err = "system " + std::to_string(sy) + ": " + errs[sy];
+        }
+    }
+    if (L.fail_rc && !rc) rc = L.fail_rc;
+    if (rounds_out) *rounds_out = rounds;
+    return rc;
+}
+
 }  // namespace ndsi
 
 extern "C" int ndsi_mu_search(ndsi_mu_eval_fn eval, ndsi_mu_dos_fn dos, void* ctx, double elo, double ehi, double kT,
@@ -230,5 +399,17 @@ extern "C" int ndsi_mu_search(ndsi_mu_eval_fn eval, ndsi_mu_dos_fn dos, void* ct
     const int rc = ndsi::mu_search(eval, dos, ctx, elo, ehi, kT, n_electrons, n_grid, mu_lo, mu_hi, tol_electrons,
                                    max_iter, mu_out, dn_out, evals_out, err);
     if (rc) ndsi::set_last_error(err);
+    return rc;
+}
+
+extern "C" int ndsi_mu_search_batched(int32_t n_systems, ndsi_mu_eval_batch_fn eval, ndsi_mu_dos_batch_fn dos,
+                                      void* ctx, const double* elo, const double* ehi, const double* kT,
+                                      const double* n_electrons, int32_t n_grid, const double* mu_lo,
+                                      const double* mu_hi, double tol_electrons, int32_t max_iter, double* mu_out,
+                                      double* dn_out, int32_t* evals_out, int32_t* rounds_out) {
+    std::string err;
+    const int rc = ndsi::mu_search_batched(n_systems, eval, dos, ctx, elo, ehi, kT, n_electrons, n_grid, mu_lo, mu_hi,
+                                           tol_electrons, max_iter, mu_out, dn_out, evals_out, rounds_out, err);
+    if (rc) ndsi::set_last_error(err.empty() ? "mu search failed" : err);
     return rc;
 }

@@ -162,6 +162,12 @@ int mu_search(ndsi_mu_eval_fn eval, ndsi_mu_dos_fn dos, void* ctx, double elo, d
               double n_electrons, int32_t n_grid, double mu_lo, double mu_hi, double tol, int32_t max_iter,
               double* mu_out, double* dn_out, int32_t* evals_out, std::string& err);
 
+// The same search for several systems in lockstep, one batched callback per round.
+int mu_search_batched(int32_t ns, ndsi_mu_eval_batch_fn eval, ndsi_mu_dos_batch_fn dos, void* ctx,
+                      const double* elo, const double* ehi, const double* kT, const double* n_electrons,
+                      int32_t n_grid, const double* mu_lo, const double* mu_hi, double tol, int32_t max_iter,
+                      double* mu_out, double* dn_out, int32_t* evals_out, int32_t* rounds_out, std::string& err);
+
 // Continued-fraction poles (analyze.cpp).
 int cf_poles(int32_t M, double* z, double* R, std::string& err);
 

@@ -35,10 +35,16 @@ EXPORTED_SYMBOLS = (
     "ndsi_mlp_forward", "ndsi_mlp_grad", "ndsi_mlp_train", "ndsi_analyze_batched",
     "ndsi_density_batched", "ndsi_graph_enable", "ndsi_graph_info", "ndsi_autotune",
     "ndsi_density_energy", "ndsi_dos", "ndsi_factors_solve", "ndsi_eigenstates", "ndsi_mu_search",
+    "ndsi_mu_search_batched", "ndsi_find_mu_batched",
 )
 MU_EVAL_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.c_double, ctypes.POINTER(ctypes.c_double))
 MU_DOS_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.c_int32,
                              ctypes.c_double, ctypes.POINTER(ctypes.c_double))
+_PD = ctypes.POINTER(ctypes.c_double)
+_PI = ctypes.POINTER(ctypes.c_int32)
+MU_EVAL_BATCH_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.c_int32, _PI, _PD, _PD)
+MU_DOS_BATCH_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.c_int32, _PI, _PD, ctypes.c_int32, _PD,
+                                   _PD)
 NDSI_MLP_INPUTS = 32
 NDSI_MLP_HIDDEN = 64
 NDSI_MLP_PARAMS = 6337
@@ -115,6 +121,12 @@ def load(path: str = LIB_PATH):
                                    ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
                                    ctypes.POINTER(i32)]
     lib.ndsi_mu_search.restype = ctypes.c_int
+    lib.ndsi_mu_search_batched.argtypes = [i32, MU_EVAL_BATCH_FN, MU_DOS_BATCH_FN, vp, vp, vp, vp, vp, i32, vp, vp,
+                                           ctypes.c_double, i32, vp, vp, vp, ctypes.POINTER(i32)]
+    lib.ndsi_mu_search_batched.restype = ctypes.c_int
+    lib.ndsi_find_mu_batched.argtypes = [vp, vp, vp, vp, i32, vp, vp, vp, ctypes.c_double, i32, vp, vp, vp,
+                                         ctypes.POINTER(i32), vp]
+    lib.ndsi_find_mu_batched.restype = ctypes.c_int
     lib.ndsi_factors_solve.argtypes = [vp, i32, vp, i32, vp, vp]
     lib.ndsi_factors_solve.restype = ctypes.c_int
     lib.ndsi_eigenstates.argtypes = [vp, vp, vp, ctypes.c_double, ctypes.c_double, i32, i32, i32,
@@ -345,6 +357,58 @@ def ndsi_mu_search(delta_n, elo, ehi, kT, n_electrons, dos=None, n_grid=0, mu_lo
     return mu.value, dn.value, it.value
 
 
+def ndsi_mu_search_batched(delta_n, elo, ehi, kT, n_electrons, dos=None, n_grid=0, mu_lo=None, mu_hi=None,
+                           tol_electrons=1e-8, max_iter=100):
+    """Lockstep searches for several systems over Python callables answering whole rounds:
+    delta_n(mu: ndarray, active: ndarray) -> ndarray and, optionally,
+    dos(E: ndarray (systems x n), eta: ndarray, active) -> ndarray.  Returns
+    (mu, DeltaN, evaluations per system, rounds)."""
+    elo, ehi, kT, ne = (np.ascontiguousarray(np.asarray(v, dtype=np.float64)) for v in (elo, ehi, kT, n_electrons))
+    ns = elo.size
+    lo = None if mu_lo is None else np.ascontiguousarray(np.asarray(mu_lo, dtype=np.float64))
+    hi = None if mu_hi is None else np.ascontiguousarray(np.asarray(mu_hi, dtype=np.float64))
+    failure = []
+
+    def ev(_ctx, n, active, mu, out):
+        try:
+            d = np.asarray(delta_n(np.ctypeslib.as_array(mu, shape=(n,)).copy(),
+                                   np.ctypeslib.as_array(active, shape=(n,)).copy()), dtype=np.float64)
+            for s_ in range(n):
+                out[s_] = float(d[s_])
+            return 0
+        except Exception as exc:  # noqa: BLE001
+            failure.append(exc)
+            return NDSI_ERR_INVALID
+
+    def ds(_ctx, n, active, E, m, eta, out):
+        try:
+            D = np.asarray(dos(np.ctypeslib.as_array(E, shape=(n, m)).copy(),
+                               np.ctypeslib.as_array(eta, shape=(n,)).copy(),
+                               np.ctypeslib.as_array(active, shape=(n,)).copy()), dtype=np.float64).reshape(-1)
+            for k in range(n * m):
+                out[k] = float(D[k])
+            return 0
+        except Exception as exc:  # noqa: BLE001
+            failure.append(exc)
+            return NDSI_ERR_INVALID
+
+    ev_c = MU_EVAL_BATCH_FN(ev)
+    ds_c = MU_DOS_BATCH_FN(ds) if dos is not None else ctypes.cast(None, MU_DOS_BATCH_FN)
+    mu, dn = np.zeros(ns), np.zeros(ns)
+    evals = np.zeros(ns, dtype=np.int32)
+    rounds = ctypes.c_int32()
+    rc = load().ndsi_mu_search_batched(ns, ev_c, ds_c, None, _ptr(elo), _ptr(ehi), _ptr(kT), _ptr(ne), int(n_grid),
+                                       _ptr(lo), _ptr(hi), float(tol_electrons), int(max_iter), _ptr(mu), _ptr(dn),
+                                       _ptr(evals), ctypes.byref(rounds))
+    if failure:
+        raise failure[0]
+    if rc != NDSI_OK:
+        err = NdsiError(rc, load().ndsi_last_error().decode())
+        err.result = (mu, dn, evals, rounds.value)
+        raise err
+    return mu, dn, evals, rounds.value
+
+
 def ndsi_factors_solve(factors, pole, Y, X_out, stream=None):
     """X = (z_p S - H)^{-1} Y with the factors of pole p; Y, X complex (n, k) or (n,), C order."""
     k = 1 if Y.ndim == 1 else int(Y.shape[1])
@@ -440,6 +504,21 @@ def ndsi_find_mu(plan: Plan, H, S, kT, n_poles, n_electrons, rho_out, mu_lo=0.0,
                                int(max_iter), _ptr(rho_out), ctypes.byref(mu), ctypes.byref(ne),
                                ctypes.byref(it), _stream(stream)))
     return mu.value, ne.value, it.value
+
+
+def ndsi_find_mu_batched(plan: Plan, H, S, kT, n_poles, n_electrons, rho_out, mu_lo=None, mu_hi=None,
+                         tol_electrons=1e-8, max_iter=100, stream=None):
+    """(mu[], N_e[], rounds): Eq. 40 for every system of a batched plan, searched in lockstep."""
+    kT = np.ascontiguousarray(np.asarray(kT, dtype=np.float64))
+    ne = np.ascontiguousarray(np.asarray(n_electrons, dtype=np.float64))
+    lo = None if mu_lo is None else np.ascontiguousarray(np.asarray(mu_lo, dtype=np.float64))
+    hi = None if mu_hi is None else np.ascontiguousarray(np.asarray(mu_hi, dtype=np.float64))
+    mu, ne_out = np.zeros(kT.size), np.zeros(kT.size)
+    rounds = ctypes.c_int32()
+    _check(load().ndsi_find_mu_batched(plan.handle, _ptr(H), _ptr(S), _ptr(kT), int(n_poles), _ptr(ne), _ptr(lo),
+                                       _ptr(hi), float(tol_electrons), int(max_iter), _ptr(rho_out), _ptr(mu),
+                                       _ptr(ne_out), ctypes.byref(rounds), _stream(stream)))
+    return mu, ne_out, rounds.value
 
 
 def ndsi_mu_features(plan: Plan, H, S, n_electrons, kT, feat_out, n_vectors=16, seed=12345,

@@ -45,3 +45,40 @@ def test_batched_density_matches_single_and_oracle(precision, tol):
         ref = on_pattern(density_eig(eps, C, mus[i], kTs[i], M), sy)
         assert np.max(np.abs(r_b - ref)) < tol
         assert abs(ne[i] - electron_count_pattern(r_b, sy)) < 1e-9
+
+
+def test_find_mu_batched_lockstep():
+    # every system's mu from one lockstep search over the batched plan (Eq. 40 per system)
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from oracle.dense import generalized_eig, find_mu_eig, electron_count_eig
+    nd = lib()
+    systems = [lattice_system((8, 7, 1), 2, "2d", seed=61), lattice_system((30, 1, 1), 3, "1d", seed=62),
+               lattice_system((4, 4, 3), 2, "3d", seed=63)]
+    kT = np.array([0.01, 0.02, 0.01])
+    ne = np.array([s.n_electrons * f for s, f in zip(systems, (1.0, 0.8, 1.2))])
+    M = 40
+    plan = nd.analyze_batched(systems)
+    H = torch.as_tensor(np.concatenate([s.H for s in systems]), device="cuda")
+    S = torch.as_tensor(np.concatenate([s.S for s in systems]), device="cuda")
+    rho = torch.zeros(H.numel(), dtype=torch.float64, device="cuda")
+    mu, n_e, rounds = nd.ndsi_find_mu_batched(plan, H, S, kT, M, ne, rho)
+    singles = []
+    for i, s in enumerate(systems):
+        eps, _ = generalized_eig(*s.dense())
+        assert abs(n_e[i] - ne[i]) < 1e-8
+        assert abs(electron_count_eig(eps, mu[i], kT[i], M) - ne[i]) < 1e-7
+        p1 = nd.analyze_system(s)
+        r1 = torch.zeros(s.nnz, dtype=torch.float64, device="cuda")
+        _, _, it = nd.ndsi_find_mu(p1, torch.as_tensor(s.H, device="cuda"), torch.as_tensor(s.S, device="cuda"),
+                                   kT[i], M, ne[i], r1)
+        singles.append(it)
+    print(f"find_mu_batched: {rounds} batched sweeps; single searches {singles}")
+    assert rounds <= max(singles) + 2 and rounds < sum(singles)
+    # rho_out is the batched density at the returned chemical potentials
+    rho2 = torch.zeros_like(rho)
+    ne2 = torch.zeros(len(systems), dtype=torch.float64, device="cuda")
+    nd.ndsi_density_batched(plan, H, S, mu, kT, M, rho2, ne2)
+    torch.cuda.synchronize()
+    assert torch.equal(rho, rho2)

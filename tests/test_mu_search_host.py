@@ -87,3 +87,44 @@ def test_callback_error_stops_search():
 
     with pytest.raises(ValueError):
         nd.ndsi_mu_search(bad, -1.0, 1.0, 0.01, 1.0)
+
+
+def test_batched_lockstep_matches_single_searches():
+    # four systems searched in lockstep: every mu matches its own search, one callback per round
+    systems = [lattice_system((6, 5, 1), 2, "2d", 90 + i) for i in range(3)] + [config_system("C1")]
+    kTs = [0.01, 0.02, 0.005, 0.01]
+    probs = [_problem(s, kT, 40) for s, kT in zip(systems, kTs)]
+    nd = lib()
+    eps = [p[0] for p in probs]
+    elo = [p[1] for p in probs]
+    ehi = [p[2] for p in probs]
+    ne = [p[3] for p in probs]
+    calls = []
+
+    def delta_n(mu, active):
+        calls.append(active.copy())
+        return [float(np.sum(occupation(e, m, kT, 40))) - n for e, m, kT, n in zip(eps, mu, kTs, ne)]
+
+    def dos(E, eta, active):
+        return np.stack([dos_eig(e, E[i], eta[i]) for i, e in enumerate(eps)])
+
+    mu, dn, evals, rounds = nd.ndsi_mu_search_batched(delta_n, elo, ehi, kTs, ne, dos=dos, n_grid=41)
+    assert np.all(np.abs(dn) < 1e-8)
+    for i in range(4):
+        assert abs(mu[i] - find_mu_eig(eps[i], kTs[i], ne[i], 40)) < 1e-9
+        single = nd.ndsi_mu_search(probs[i][4], elo[i], ehi[i], kTs[i], ne[i],
+                                   dos=lambda E, eta, e=eps[i]: dos_eig(e, E, eta), n_grid=41)
+        assert abs(single[0] - mu[i]) < 1e-12 and single[2] == evals[i]
+    # rounds: the DOS round plus as many evaluation rounds as the slowest system needs
+    assert rounds == max(evals)
+    assert len(calls) == rounds - 1
+
+
+def test_batched_errors_reach_every_system():
+    nd = lib()
+
+    def bad(mu, active):
+        raise ValueError("sweep failed")
+
+    with pytest.raises(ValueError):
+        nd.ndsi_mu_search_batched(bad, [-1.0, -2.0], [1.0, 2.0], [0.01, 0.01], [1.0, 1.0])
