@@ -16,9 +16,10 @@ BUILD = os.path.join(PKG, "_build", platform.machine())
 LIB = os.path.join(PKG, "libndsi.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
-CU_SOURCES = ["kernels.cu", "api.cu", "static_scratch.cu", "split_gemm.cu", "mlp.cu", "solve.cu"]
+CU_SOURCES = ["kernels.cu", "api.cu", "api_mu.cu", "api_solve.cu", "static_scratch.cu", "split_gemm.cu", "mlp.cu",
+              "solve.cu"]
 CPP_SOURCES = ["analyze.cpp", "mu_search.cpp"]
-HEADERS = ["plan.hpp", "kernels.cuh", "split_gemm.cuh", "solve.cuh"]
+HEADERS = ["plan.hpp", "kernels.cuh", "split_gemm.cuh", "solve.cuh", "handle.hpp"]
 
 
 def _nvcc():

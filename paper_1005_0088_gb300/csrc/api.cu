@@ -1,118 +1,5 @@
 // C-ABI entry points: plan life cycle, pole-batched factor / selected inversion / density.
-#include <cuda_runtime.h>
-
-#include <algorithm>
-#include <cmath>
-#include <cstring>
-#include <memory>
-#include <new>
-#include <string>
-#include <vector>
-
-#include "kernels.cuh"
-#include "ndsi.h"
-#include "plan.hpp"
-#include "split_gemm.cuh"
-#include "solve.cuh"
-
-namespace ndsi {
-// Event-timed launch records, resolved after the stream synchronises, keyed by kernel family
-// and schedule step ("gemm_split:schur", "diaginv", ...).
-struct ProfStat {
-    int64_t launches = 0;
-    double ms = 0, flops = 0, bytes = 0, tensor_flops = 0;
-};
-struct ProfRec {
-    int key;
-    double flops, bytes, tensor_flops;
-    cudaEvent_t e0, e1;
-    int64_t launch;  // schedule launch index, or -1
-};
-struct Profiler {
-    bool on = false;
-    bool by_level = false;                  // family names carry the tree level (":L<level>")
-    int64_t cur_launch = -1;                // schedule launch being issued (run_phase)
-    std::vector<double>* per_launch = nullptr;  // when set: ms accumulated per launch index
-    std::vector<cudaEvent_t> pool;
-    size_t used = 0;
-    std::vector<ProfRec> pending;
-    std::vector<std::string> names;
-    std::vector<ProfStat> stats;
-    int key(const std::string& name) {
-        for (size_t i = 0; i < names.size(); ++i)
-            if (names[i] == name) return static_cast<int>(i);
-        names.push_back(name);
-        stats.emplace_back();
-        return static_cast<int>(names.size()) - 1;
-    }
-};
-
-// Split-precision metadata of a plan (built when opt.precision == NDSI_PREC_SPLIT).
-struct SplitPlan {
-    std::vector<SplitItem> items;
-    std::vector<SplitStep> steps;
-    std::vector<GemmTile> tiles;
-    std::vector<SliceBlock> blocks;
-    std::vector<int32_t> step_of_launch;
-    std::vector<double> tensor_flops;   // per step, one pole
-    std::vector<double> slice_bytes;    // per step, one pole: FP64 operand reads + BF16 slice writes
-    std::vector<char> use_split;        // per launch: 1 = tensor-core path (autotuner may clear)
-    SplitItem* d_items = nullptr;
-    GemmTile* d_tiles = nullptr;
-    SliceBlock* d_blocks = nullptr;
-    void* blob = nullptr;
-};
-}  // namespace ndsi
-
-struct ndsi_plan {
-    ndsi::Plan P;
-    ndsi::Profiler prof;
-    ndsi::SplitPlan SP;
-    ndsi::SplitBuffers SB;       // slice buffers of the density workspace
-    ndsi::DevTables T;
-    int device = -1;
-    // density workspace (reused across calls)
-    ndsi::Workspace W;
-    double2* cw = nullptr;       // per-chunk points and weights
-    double2* zw = nullptr;
-    double2* cew = nullptr;      // energy-density weights of the same points
-    unsigned long long* gersh = nullptr;  // Gershgorin bound of (H, S) for the moment points
-    int32_t cw_cap = 0;
-    double* partials = nullptr;  // trace reduction scratch
-    double* dos_part = nullptr;  // per-point trace partials of the retarded-Green-function step
-    double* dos_tr = nullptr;
-    double2* dos_z = nullptr;
-    int64_t dos_cap = 0;       // points (systems x energies)
-    int64_t dos_part_cap = 0;  // doubles of dos_part
-    double* stage = nullptr;     // staging for host H, S, rho, n_elec
-    int64_t stage_cap = 0;
-    std::vector<double> pole_z, pole_R;  // cached continued-fraction poles
-    int32_t pole_M = 0;
-    // CUDA graph of one density sweep (every chunk's factor, selected inversion and residue
-    // sum), captured on first use and replayed while the buffers it names stay the same
-    bool graphs = true;
-    cudaStream_t cap_stream = nullptr;
-    cudaGraphExec_t graph = nullptr;
-    std::vector<const void*> graph_key;
-    int64_t graph_nodes = 0;
-    double2* pin = nullptr;         // pinned staging of the point tables (3 x pin_cap)
-    size_t pin_cap = 0;
-    cudaEvent_t pin_ev = nullptr;   // recorded after the last copies out of `pin`
-    // tables of the triangular solves (built on first use)
-    ndsi::SolveTables ST;
-    double2* point_z = nullptr;  // the single point factored for the eigensolver
-};
-
-struct ndsi_factors {
-    ndsi_plan* plan = nullptr;
-    ndsi::Workspace W;
-    ndsi::SplitBuffers SB;
-    double2* zd = nullptr;
-    int32_t np = 0;
-    bool inverted = false;  // ndsi_selinv has replaced the factors by G
-    double2* solve_buf = nullptr;  // work space of ndsi_factors_solve (two n x k blocks)
-    int64_t solve_cap = 0;         // complex elements per block
-};
+#include "handle.hpp"
 
 namespace ndsi {
 
@@ -122,28 +9,10 @@ thread_local std::string g_last_error;
 
 void set_last_error(const std::string& msg) { g_last_error = msg; }
 
-namespace {
-
 int fail(int code, const std::string& msg) {
     set_last_error(msg);
     return code;
 }
-
-#define NDSI_CK(call)                                                                          \
-    do {                                                                                       \
-        cudaError_t e_ = (call);                                                               \
-        if (e_ != cudaSuccess) {                                                               \
-            return fail(e_ == cudaErrorMemoryAllocation ? NDSI_ERR_OOM : NDSI_ERR_CUDA,        \
-                        std::string(#call) + ": " + cudaGetErrorString(e_));                   \
-        }                                                                                      \
-    } while (0)
-
-template <class T>
-size_t bytes_of(const std::vector<T>& v) {
-    return v.size() * sizeof(T);
-}
-
-size_t align256(size_t x) { return (x + 255) & ~static_cast<size_t>(255); }
 
 // Upload every index table of the plan into one device allocation (first use only).
 int upload_tables(ndsi_plan* h) {
@@ -416,13 +285,9 @@ int64_t workspace_cap(const ndsi_plan* h) {
     return static_cast<int64_t>(0.85 * static_cast<double>(have));
 }
 
-}  // namespace
 }  // namespace ndsi
 
 namespace ndsi {
-int density_impl(ndsi_plan* h, const double* Hd, const double* Sd, const double* mu, const double* kT,
-                 int32_t n_poles, double* rho_d, double* ne_d, cudaStream_t st, double* e_d = nullptr);
-
 // Slice count of a split plan when the caller leaves it to the library: six BF16 digits (47
 // bits).  A seventh changes nothing with four accumulator bands (the tail accumulator's floor
 // dominates) and little with five.
@@ -461,107 +326,6 @@ void setup_split(ndsi_plan* h, const ndsi_options& o) {
 }
 int sweep(ndsi_plan* h, const double* Hd, const double* Sd, int32_t nq, int32_t chunk,
           const std::vector<int>& part_off, double* rho_d, double* ne_d, double* e_d, cudaStream_t st);
-int dos_sweep(ndsi_plan* h, const double* Hd, const double* Sd, const double* E, int nE, double eta,
-              double* D, cudaStream_t st);
-
-// Gershgorin bounds of the pencil (H, S) over basis rows [i0, i1) (host values on the pattern):
-// every generalised eigenvalue lies in [elo, ehi] when S is diagonally dominant there.
-void pencil_bounds(const Plan& P, const std::vector<double>& hv, const std::vector<double>& sv, int64_t i0, int64_t i1,
-                   double* elo, double* ehi) {
-    double hlo = 1e300, hhi = -1e300, slo = 1e300, shi = -1e300;
-    for (int64_t i = i0; i < i1; ++i) {
-        double hd = 0, sd = 0, hr = 0, sr = 0;
-        for (int64_t k = P.rowptr[i]; k < P.rowptr[i + 1]; ++k) {
-            if (P.col[k] == i) {
-                hd = hv[k];
-                sd = sv[k];
-            } else {
-                hr += std::fabs(hv[k]);
-                sr += std::fabs(sv[k]);
-            }
-        }
-        hlo = std::min(hlo, hd - hr);
-        hhi = std::max(hhi, hd + hr);
-        slo = std::min(slo, sd - sr);
-        shi = std::max(shi, sd + sr);
-    }
-    if (slo > 0) {
-        *elo = hlo / (hlo < 0 ? slo : shi);
-        *ehi = hhi / (hhi > 0 ? slo : shi);
-    } else {
-        *elo = hlo < 0 ? hlo * 4 : -1.0;  // S not diagonally dominant: generous guess
-        *ehi = hhi > 0 ? hhi * 4 : 1.0;
-    }
-}
-
-int dos_sweep_systems(ndsi_plan* h, const double* Hd, const double* Sd, const double* E, int nE, const double* eta,
-                      double* D, cudaStream_t st);
-
-// Callbacks of the lockstep search over the systems of a batched plan: one batched contour sweep
-// per evaluation round, one batched retarded-Green-function sweep for the density of states.
-struct FindMuBatchCtx {
-    ndsi_plan* h;
-    const double *Hd, *Sd;
-    const double* kT;
-    int32_t n_poles;
-    const double* n_electrons;
-    double *rho_d, *ne_d;
-    cudaStream_t st;
-    std::vector<double> last_mu;
-};
-
-int find_mu_eval_batch(void* c, int32_t ns, const int32_t* active, const double* mu, double* dn) {
-    (void)active;
-    FindMuBatchCtx& x = *static_cast<FindMuBatchCtx*>(c);
-    int r = density_impl(x.h, x.Hd, x.Sd, mu, x.kT, x.n_poles, x.rho_d, x.ne_d, x.st);
-    if (r) return r;
-    std::vector<double> ne(ns);
-    if (cudaMemcpy(ne.data(), x.ne_d, sizeof(double) * ns, cudaMemcpyDeviceToHost) != cudaSuccess)
-        return fail(NDSI_ERR_CUDA, "ndsi_find_mu_batched: readback failed");
-    x.last_mu.assign(mu, mu + ns);
-    for (int32_t sy = 0; sy < ns; ++sy) dn[sy] = ne[sy] - x.n_electrons[sy];
-    return NDSI_OK;
-}
-
-int find_mu_dos_batch(void* c, int32_t ns, const int32_t* active, const double* E, int32_t n, const double* eta,
-                      double* D) {
-    (void)ns;
-    (void)active;
-    FindMuBatchCtx& x = *static_cast<FindMuBatchCtx*>(c);
-    return dos_sweep_systems(x.h, x.Hd, x.Sd, E, n, eta, D, x.st);
-}
-
-// Callbacks of the chemical-potential search: DeltaN from one contour evaluation, and the
-// density of states from one sweep of the retarded Green function.
-struct FindMuCtx {
-    ndsi_plan* h;
-    const double *Hd, *Sd;
-    double kT;
-    int32_t n_poles;
-    double n_electrons;
-    double *rho_d, *ne_d;
-    cudaStream_t st;
-    double last_mu;
-    bool have_last;
-};
-
-int find_mu_eval(void* c, double mu, double* dn) {
-    FindMuCtx& x = *static_cast<FindMuCtx*>(c);
-    int r = density_impl(x.h, x.Hd, x.Sd, &mu, &x.kT, x.n_poles, x.rho_d, x.ne_d, x.st);
-    if (r) return r;
-    double ne = 0;
-    if (cudaMemcpy(&ne, x.ne_d, sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess)
-        return fail(NDSI_ERR_CUDA, "ndsi_find_mu: readback failed");
-    x.last_mu = mu;
-    x.have_last = true;
-    *dn = ne - x.n_electrons;
-    return NDSI_OK;
-}
-
-int find_mu_dos(void* c, const double* E, int32_t n, double eta, double* D) {
-    FindMuCtx& x = *static_cast<FindMuCtx*>(c);
-    return dos_sweep(x.h, x.Hd, x.Sd, E, n, eta, D, x.st);
-}
 
 }  // namespace ndsi
 
@@ -1035,198 +799,6 @@ int density_impl(ndsi_plan* h, const double* Hd, const double* Sd, const double*
     return check_status(h, st);
 }
 
-// Device buffer that frees itself (scratch of the solve and eigensolver entry points).
-struct DevBuf {
-    void* p = nullptr;
-    ~DevBuf() {
-        if (p) cudaFree(p);
-    }
-    template <class T>
-    T* as() const {
-        return static_cast<T*>(p);
-    }
-    cudaError_t alloc(size_t bytes) { return cudaMalloc(&p, std::max<size_t>(bytes, 16)); }
-};
-
-int ensure_solve_tables(ndsi_plan* h) {
-    if (h->ST.blob) return NDSI_OK;
-    cudaError_t e = solve_tables_build(h->P, h->ST);
-    if (e != cudaSuccess) {
-        cudaGetLastError();
-        solve_tables_free(h->ST);
-        return fail(e == cudaErrorMemoryAllocation ? NDSI_ERR_OOM : NDSI_ERR_CUDA,
-                    std::string("solve tables: ") + cudaGetErrorString(e));
-    }
-    return NDSI_OK;
-}
-
-// Symmetric eigendecomposition by cyclic Jacobi rotations (Golub & Van Loan, Matrix
-// Computations, Sec. 8.5): A (n x n, row-major) is overwritten; eigenvalues in w, eigenvectors as
-// the columns of V (row-major).  For the small projected problems of the eigensolver only.
-void jacobi_eig(int n, std::vector<double>& A, std::vector<double>& w, std::vector<double>& V) {
-    V.assign(static_cast<size_t>(n) * n, 0.0);
-    for (int i = 0; i < n; ++i) V[i * n + i] = 1.0;
-    for (int sweep = 0; sweep < 64; ++sweep) {
-        double off = 0.0, all = 0.0;
-        for (int p = 0; p < n; ++p)
-            for (int q = 0; q < n; ++q) {
-                all += A[p * n + q] * A[p * n + q];
-                if (p != q) off += A[p * n + q] * A[p * n + q];
-            }
-        if (off <= 1e-32 * all) break;
-        for (int p = 0; p < n - 1; ++p)
-            for (int q = p + 1; q < n; ++q) {
-                const double apq = A[p * n + q];
-                if (apq == 0.0) continue;
-                const double tau = (A[q * n + q] - A[p * n + p]) / (2.0 * apq);
-                const double t = (tau >= 0 ? 1.0 : -1.0) / (std::fabs(tau) + std::sqrt(1.0 + tau * tau));
-                const double c = 1.0 / std::sqrt(1.0 + t * t), sn = t * c;
-                for (int k = 0; k < n; ++k) {  // columns p, q of A J
-                    const double akp = A[k * n + p], akq = A[k * n + q];
-                    A[k * n + p] = c * akp - sn * akq;
-                    A[k * n + q] = sn * akp + c * akq;
-                }
-                for (int k = 0; k < n; ++k) {  // rows p, q of J^T (A J)
-                    const double apk = A[p * n + k], aqk = A[q * n + k];
-                    A[p * n + k] = c * apk - sn * aqk;
-                    A[q * n + k] = sn * apk + c * aqk;
-                }
-                for (int k = 0; k < n; ++k) {
-                    const double vkp = V[k * n + p], vkq = V[k * n + q];
-                    V[k * n + p] = c * vkp - sn * vkq;
-                    V[k * n + q] = sn * vkp + c * vkq;
-                }
-            }
-    }
-    w.resize(n);
-    for (int i = 0; i < n; ++i) w[i] = A[i * n + i];
-}
-
-// Rayleigh-Ritz of (B3) in the span of the m columns whose Gram matrices are Hs = V^T H V and
-// Ss = V^T S V (row-major m x m): columns are scaled to unit S-norm, directions with an S-Gram
-// eigenvalue below 1e-12 of the largest are dropped, and the reduced standard problem is solved.
-// Returns the Ritz values e and coefficients Y (m x e.size(), row-major) with Y^T Ss Y = I.
-void rayleigh_ritz(int m, const std::vector<double>& Hs, const std::vector<double>& Ss, std::vector<double>& e,
-                   std::vector<double>& Y) {
-    std::vector<double> d(m);
-    for (int a = 0; a < m; ++a) d[a] = Ss[a * m + a] > 0 ? 1.0 / std::sqrt(Ss[a * m + a]) : 0.0;
-    std::vector<double> Sn(static_cast<size_t>(m) * m), Hn(static_cast<size_t>(m) * m);
-    for (int a = 0; a < m; ++a)
-        for (int b = 0; b < m; ++b) {
-            Sn[a * m + b] = 0.5 * (Ss[a * m + b] + Ss[b * m + a]) * d[a] * d[b];
-            Hn[a * m + b] = 0.5 * (Hs[a * m + b] + Hs[b * m + a]) * d[a] * d[b];
-        }
-    std::vector<double> lam, Q;
-    jacobi_eig(m, Sn, lam, Q);
-    double lmax = 0.0;
-    for (double l : lam) lmax = std::max(lmax, l);
-    std::vector<int> keep;
-    for (int i = 0; i < m; ++i)
-        if (lam[i] > 1e-12 * lmax) keep.push_back(i);
-    const int r = static_cast<int>(keep.size());
-    std::vector<double> T(static_cast<size_t>(m) * r);  // m x r: Q_keep Lambda^{-1/2}
-    for (int a = 0; a < m; ++a)
-        for (int j = 0; j < r; ++j) T[a * r + j] = Q[a * m + keep[j]] / std::sqrt(lam[keep[j]]);
-    std::vector<double> HT(static_cast<size_t>(m) * r, 0.0), Ht(static_cast<size_t>(r) * r, 0.0);
-    for (int a = 0; a < m; ++a)
-        for (int j = 0; j < r; ++j) {
-            double acc = 0.0;
-            for (int b = 0; b < m; ++b) acc += Hn[a * m + b] * T[b * r + j];
-            HT[a * r + j] = acc;
-        }
-    for (int i = 0; i < r; ++i)
-        for (int j = 0; j < r; ++j) {
-            double acc = 0.0;
-            for (int a = 0; a < m; ++a) acc += T[a * r + i] * HT[a * r + j];
-            Ht[i * r + j] = acc;
-        }
-    for (int i = 0; i < r; ++i)
-        for (int j = 0; j < i; ++j) Ht[i * r + j] = Ht[j * r + i] = 0.5 * (Ht[i * r + j] + Ht[j * r + i]);
-    std::vector<double> W;
-    jacobi_eig(r, Ht, e, W);
-    Y.assign(static_cast<size_t>(m) * r, 0.0);
-    for (int a = 0; a < m; ++a)
-        for (int j = 0; j < r; ++j) {
-            double acc = 0.0;
-            for (int i = 0; i < r; ++i) acc += T[a * r + i] * W[i * r + j];
-            Y[a * r + j] = d[a] * acc;
-        }
-}
-
-// Uniform [-1, 1) numbers from a counter (splitmix64 finaliser) for the starting block.
-double counter_uniform(uint64_t seed, uint64_t i) {
-    uint64_t x = seed + 0x9E3779B97F4A7C15ull * (i + 1);
-    x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
-    x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
-    x ^= x >> 31;
-    return static_cast<double>(x >> 11) * (2.0 / 9007199254740992.0) - 1.0;
-}
-
-// Density of states from the retarded Green function (Eq. 41): D(E_k) = -(2/pi) Im Tr(G(E_k +
-// i eta) S) for nE energies, one batched sweep of factorisation + selected inversion (chunked to
-// the workspace) and a per-point trace on the pattern.  Host energies in, host D out.
-// Density of states of every system of the plan on its own grid (E and D row-major systems x nE,
-// eta per system): one sweep over the points, traces per system on its pattern range.
-int dos_sweep_systems(ndsi_plan* h, const double* Hd, const double* Sd, const double* E, int nE, const double* eta,
-                      double* D, cudaStream_t st) {
-    const int32_t ns = h->P.n_systems;
-    const int64_t npts = static_cast<int64_t>(ns) * nE;
-    std::vector<double2> z(npts);
-    for (int32_t sy = 0; sy < ns; ++sy)
-        for (int k = 0; k < nE; ++k) z[static_cast<size_t>(sy) * nE + k] = make_double2(E[static_cast<size_t>(sy) * nE + k], eta[sy]);
-    const int64_t per_pole = bytes_per_pole(h);
-    const int64_t cap = workspace_cap(h);
-    if (cap < per_pole) return fail(NDSI_ERR_OOM, "ndsi_dos: one point does not fit the workspace cap");
-    const int32_t chunk = static_cast<int32_t>(std::min<int64_t>(nE, std::max<int64_t>(1, cap / per_pole)));
-    int rc = alloc_workspace(h->W, h->P, std::max<int32_t>(chunk, h->W.np_cap));
-    if (rc) return rc;
-    if (h->P.opt.precision == NDSI_PREC_SPLIT)
-        NDSI_CK(split_alloc(h->SB, h->SP.steps, h->P.opt.split_slices, std::max<int32_t>(chunk, h->W.np_cap)));
-    // trace partials: one chunk of points times the blocks of the largest system's pattern range
-    int64_t nb = 1;
-    for (int32_t sy = 0; sy < ns; ++sy)
-        nb = std::max<int64_t>(nb, accumulate_blocks(h->P.sys_nnz_first[sy + 1] - h->P.sys_nnz_first[sy]));
-    const int64_t part_need = static_cast<int64_t>(chunk) * nb;
-    if (h->dos_cap < npts || h->dos_part_cap < part_need) {
-        if (h->dos_part) cudaFree(h->dos_part);
-        if (h->dos_tr) cudaFree(h->dos_tr);
-        if (h->dos_z) cudaFree(h->dos_z);
-        h->dos_part = h->dos_tr = nullptr;
-        h->dos_z = nullptr;
-        h->dos_cap = h->dos_part_cap = 0;
-        NDSI_CK(cudaMalloc(&h->dos_part, sizeof(double) * static_cast<size_t>(part_need)));
-        NDSI_CK(cudaMalloc(&h->dos_tr, sizeof(double) * (npts + 1)));
-        NDSI_CK(cudaMalloc(&h->dos_z, sizeof(double2) * npts));
-        h->dos_cap = npts;
-        h->dos_part_cap = part_need;
-    }
-    NDSI_CK(cudaMemcpyAsync(h->dos_z, z.data(), sizeof(double2) * npts, cudaMemcpyHostToDevice, st));
-    for (int q0 = 0; q0 < nE; q0 += chunk) {
-        const int np = std::min(chunk, nE - q0);
-        rc = run_phase(h, h->W, h->SB, 0, Hd, Sd, h->dos_z + q0, nE, np, st);
-        if (!rc) rc = run_phase(h, h->W, h->SB, 1, Hd, Sd, h->dos_z + q0, nE, np, st);
-        if (rc) return rc;
-        for (int32_t sy = 0; sy < ns; ++sy) {
-            const int64_t k0 = h->P.sys_nnz_first[sy], k1 = h->P.sys_nnz_first[sy + 1];
-            NDSI_CK(launch_point_traces_range(h->T.out_map + k0, k1 - k0, h->W.fronts, h->W.front_stride, np, Sd + k0,
-                                              h->dos_part, h->dos_tr + static_cast<int64_t>(sy) * nE + q0, st));
-        }
-    }
-    std::vector<double> tr(npts);
-    NDSI_CK(cudaMemcpyAsync(tr.data(), h->dos_tr, sizeof(double) * npts, cudaMemcpyDeviceToHost, st));
-    NDSI_CK(cudaStreamSynchronize(st));
-    rc = check_status(h, st);
-    if (rc) return rc;
-    for (int64_t k = 0; k < npts; ++k) D[k] = (-2.0 / M_PI) * tr[k];
-    return NDSI_OK;
-}
-
-// Density of states from the retarded Green function (Eq. 41) of a single-system plan.
-int dos_sweep(ndsi_plan* h, const double* Hd, const double* Sd, const double* E, int nE, double eta,
-              double* D, cudaStream_t st) {
-    return dos_sweep_systems(h, Hd, Sd, E, nE, &eta, D, st);
-}
-
 // One density sweep over all points, chunked: factor, selected inversion and residue sum per
 // chunk, then the per-system electron counts.  Only stream-ordered work: it is also the body of
 // the captured graph.
@@ -1264,295 +836,6 @@ int sweep(ndsi_plan* h, const double* Hd, const double* Sd, int32_t nq, int32_t 
 }  // namespace ndsi
 
 extern "C" {
-
-int ndsi_factors_solve(ndsi_factors* f, int32_t pole, const double* Y, int32_t k, double* X_out, void* stream) {
-    if (!f || !f->plan || !Y || !X_out || k < 1 || pole < 0 || pole >= f->np)
-        return fail(NDSI_ERR_INVALID, "ndsi_factors_solve: invalid argument");
-    if (f->inverted) return fail(NDSI_ERR_INVALID, "ndsi_factors_solve: ndsi_selinv has overwritten the factors");
-    ndsi_plan* h = f->plan;
-    if (h->P.n_systems != 1) return fail(NDSI_ERR_INVALID, "ndsi_factors_solve: batched plan");
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
-    int rc = ensure_solve_tables(h);
-    if (rc) return rc;
-    const int64_t elems = h->P.n * static_cast<int64_t>(k);
-    const size_t bytes = sizeof(double2) * static_cast<size_t>(elems);
-    if (f->solve_cap < elems) {  // kept with the factors: repeated solves allocate nothing
-        if (f->solve_buf) cudaFree(f->solve_buf);
-        f->solve_buf = nullptr;
-        f->solve_cap = 0;
-        NDSI_CK(cudaMalloc(&f->solve_buf, 2 * bytes));
-        f->solve_cap = elems;
-    }
-    double2* yw = f->solve_buf;
-    const bool x_dev = is_device_ptr(X_out);
-    double2* xd = x_dev ? reinterpret_cast<double2*>(X_out) : f->solve_buf + f->solve_cap;
-    NDSI_CK(cudaMemcpyAsync(yw, Y, bytes, cudaMemcpyDefault, st));
-    NDSI_CK(launch_solve(h->P, h->ST, f->W.fronts + static_cast<int64_t>(pole) * f->W.front_stride, yw, xd, k, st));
-    if (!x_dev) NDSI_CK(cudaMemcpyAsync(X_out, xd, bytes, cudaMemcpyDeviceToHost, st));
-    NDSI_CK(cudaStreamSynchronize(st));
-    return NDSI_OK;
-}
-
-int ndsi_eigenstates(ndsi_plan* h, const double* H, const double* S, double xi, double eta, int32_t n_states,
-                     int32_t block, int32_t max_iter, double tol, uint64_t seed, double* eps_out, double* C_out,
-                     double* resid_out, int32_t* iters_out, void* stream) {
-    if (!h || !H || !S || !eps_out || !C_out || !std::isfinite(xi) || !(eta > 0) || !std::isfinite(eta) ||
-        n_states < 1 || block < n_states || block > 32 || max_iter < 1 || !(tol > 0))
-        return fail(NDSI_ERR_INVALID, "ndsi_eigenstates: invalid argument");
-    if (h->P.n_systems != 1) return fail(NDSI_ERR_INVALID, "ndsi_eigenstates: batched plan");
-    const int64_t n = h->P.n;
-    if (block > n) return fail(NDSI_ERR_INVALID, "ndsi_eigenstates: block larger than the matrix");
-    if (is_device_ptr(eps_out) || (resid_out && is_device_ptr(resid_out)))
-        return fail(NDSI_ERR_INVALID, "ndsi_eigenstates: eps_out and resid_out are host arrays");
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
-    int rc = upload_tables(h);
-    if (!rc) rc = ensure_solve_tables(h);
-    if (rc) return rc;
-    const double *Hd, *Sd;
-    rc = device_inputs(h, H, S, &Hd, &Sd, st);
-    if (rc) return rc;
-    // factor z S - H at z = xi + i eta (one point): A_J^{-1} and L_RJ stay in the workspace fronts
-    const int32_t np = std::max<int32_t>(1, h->W.np_cap);
-    rc = alloc_workspace(h->W, h->P, np);
-    if (rc) return rc;
-    if (h->P.opt.precision == NDSI_PREC_SPLIT) NDSI_CK(split_alloc(h->SB, h->SP.steps, h->P.opt.split_slices, np));
-    if (!h->point_z) NDSI_CK(cudaMalloc(&h->point_z, sizeof(double2)));
-    const double2 z = make_double2(xi, eta);
-    NDSI_CK(cudaMemcpyAsync(h->point_z, &z, sizeof(double2), cudaMemcpyHostToDevice, st));
-    rc = run_phase(h, h->W, h->SB, 0, Hd, Sd, h->point_z, 1, 1, st);
-    if (rc) return rc;
-    // buffers: complex right-hand sides and solutions, V = [Re B | Im B], H V, S V, the block C
-    const int mmax = 2 * block;
-    const int nb = gram_blocks(n);
-    DevBuf yb, xb, rb, vb, hvb, svb, cb, gp, gram, yc, ec, rp;
-    // the split path's factors are accurate to ~1e-9 relative: one refinement step per solve
-    // restores FP64 accuracy, so the iteration converges to the pencil's own eigenpairs
-    const int refine = h->P.opt.precision == NDSI_PREC_SPLIT ? 1 : 0;
-    NDSI_CK(yb.alloc(sizeof(double2) * n * block));
-    if (refine) NDSI_CK(rb.alloc(sizeof(double2) * n * block));
-    NDSI_CK(xb.alloc(sizeof(double2) * n * block));
-    NDSI_CK(vb.alloc(sizeof(double) * n * mmax));
-    NDSI_CK(hvb.alloc(sizeof(double) * n * mmax));
-    NDSI_CK(svb.alloc(sizeof(double) * n * mmax));
-    NDSI_CK(cb.alloc(sizeof(double) * n * block));
-    NDSI_CK(gp.alloc(sizeof(double) * nb * 2 * mmax * mmax));
-    NDSI_CK(gram.alloc(sizeof(double) * 2 * mmax * mmax));
-    NDSI_CK(yc.alloc(sizeof(double) * mmax * block));
-    NDSI_CK(ec.alloc(sizeof(double) * block));
-    NDSI_CK(rp.alloc(sizeof(double) * nb * block));
-    int m = block;
-    {
-        std::vector<double> c0(static_cast<size_t>(n) * m);
-        for (size_t i = 0; i < c0.size(); ++i) c0[i] = counter_uniform(seed, i);
-        NDSI_CK(cudaMemcpyAsync(cb.p, c0.data(), sizeof(double) * c0.size(), cudaMemcpyHostToDevice, st));
-        NDSI_CK(cudaStreamSynchronize(st));
-    }
-    std::vector<double> e, Y, res(block, 0.0), gh(2 * mmax * mmax);
-    std::vector<int> order;
-    int it = 0;
-    bool done = false;
-    while (!done && it < max_iter) {
-        ++it;
-        // (B2): b = (z S - H)^{-1} S c, the shift-invert product with the factors of z
-        NDSI_CK(launch_spmm(h->T.rowptr, h->T.col, Sd, n, cb.as<double>(), m, vb.as<double>(), m, m, st));
-        NDSI_CK(launch_real_to_complex(vb.as<double>(), n * m, yb.as<double2>(), st));
-        NDSI_CK(launch_solve(h->P, h->ST, h->W.fronts, yb.as<double2>(), xb.as<double2>(), m, st));
-        for (int r = 0; r < refine; ++r) {
-            // iterative refinement in FP64: x += (zS - H)^{-1} (y - (zS - H) x)
-            NDSI_CK(launch_real_to_complex(vb.as<double>(), n * m, yb.as<double2>(), st));
-            NDSI_CK(launch_shifted_residual(h->T.rowptr, h->T.col, Hd, Sd, n, z, xb.as<double2>(), yb.as<double2>(),
-                                            rb.as<double2>(), m, st));
-            NDSI_CK(launch_solve(h->P, h->ST, h->W.fronts, rb.as<double2>(), yb.as<double2>(), m, st));
-            NDSI_CK(launch_complex_add(xb.as<double2>(), yb.as<double2>(), n * m, st));
-        }
-        // (B3) in the real span of Re b and Im b
-        const int m2 = 2 * m;
-        NDSI_CK(launch_split_complex(xb.as<double2>(), n, m, vb.as<double>(), st));
-        NDSI_CK(launch_spmm(h->T.rowptr, h->T.col, Hd, n, vb.as<double>(), m2, hvb.as<double>(), m2, m2, st));
-        NDSI_CK(launch_spmm(h->T.rowptr, h->T.col, Sd, n, vb.as<double>(), m2, svb.as<double>(), m2, m2, st));
-        NDSI_CK(launch_gram(vb.as<double>(), hvb.as<double>(), svb.as<double>(), n, m2, gp.as<double>(), gram.as<double>(),
-                            st));
-        NDSI_CK(cudaMemcpyAsync(gh.data(), gram.p, sizeof(double) * 2 * m2 * m2, cudaMemcpyDeviceToHost, st));
-        NDSI_CK(cudaStreamSynchronize(st));
-        rc = check_status(h, st);
-        if (rc) return rc;
-        for (double v : gh)
-            if (!std::isfinite(v)) return fail(NDSI_ERR_SINGULAR, "ndsi_eigenstates: non-finite projected matrices");
-        std::vector<double> Hs(gh.begin(), gh.begin() + m2 * m2), Ss(gh.begin() + m2 * m2, gh.begin() + 2 * m2 * m2);
-        std::vector<double> ev, Yall;
-        rayleigh_ritz(m2, Hs, Ss, ev, Yall);
-        const int r = static_cast<int>(ev.size());
-        if (r < n_states) return fail(NDSI_ERR_SINGULAR, "ndsi_eigenstates: search space collapsed");
-        // keep the block's worth of Ritz pairs nearest xi
-        order.resize(r);
-        for (int i = 0; i < r; ++i) order[i] = i;
-        std::stable_sort(order.begin(), order.end(),
-                         [&](int a, int b) { return std::fabs(ev[a] - xi) < std::fabs(ev[b] - xi); });
-        const int mn = std::min(m, r);
-        e.resize(mn);
-        Y.assign(static_cast<size_t>(m2) * mn, 0.0);
-        for (int j = 0; j < mn; ++j) {
-            e[j] = ev[order[j]];
-            for (int a = 0; a < m2; ++a) Y[a * mn + j] = Yall[a * r + order[j]];
-        }
-        NDSI_CK(cudaMemcpyAsync(yc.p, Y.data(), sizeof(double) * Y.size(), cudaMemcpyHostToDevice, st));
-        NDSI_CK(cudaMemcpyAsync(ec.p, e.data(), sizeof(double) * mn, cudaMemcpyHostToDevice, st));
-        NDSI_CK(launch_ritz(vb.as<double>(), hvb.as<double>(), svb.as<double>(), n, m2, yc.as<double>(), ec.as<double>(), mn,
-                            cb.as<double>(), rp.as<double>(), st));
-        std::vector<double> part(static_cast<size_t>(nb) * mn);
-        NDSI_CK(cudaMemcpyAsync(part.data(), rp.p, sizeof(double) * part.size(), cudaMemcpyDeviceToHost, st));
-        NDSI_CK(cudaStreamSynchronize(st));
-        m = mn;
-        done = true;
-        for (int j = 0; j < m; ++j) {
-            double s2 = 0.0;
-            for (int b = 0; b < nb; ++b) s2 += part[static_cast<size_t>(b) * m + j];
-            res[j] = std::sqrt(s2);
-            if (j < n_states && !(res[j] < tol)) done = false;
-        }
-    }
-    // the n_states pairs nearest xi, ascending in energy, largest component of each made positive
-    std::vector<int> sel(n_states);
-    for (int j = 0; j < n_states; ++j) sel[j] = j;
-    std::stable_sort(sel.begin(), sel.end(), [&](int a, int b) { return e[a] < e[b]; });
-    std::vector<double> Ch(static_cast<size_t>(n) * m), out(static_cast<size_t>(n) * n_states);
-    NDSI_CK(cudaMemcpyAsync(Ch.data(), cb.p, sizeof(double) * Ch.size(), cudaMemcpyDeviceToHost, st));
-    NDSI_CK(cudaStreamSynchronize(st));
-    for (int j = 0; j < n_states; ++j) {
-        const int c = sel[j];
-        int64_t imax = 0;
-        for (int64_t i = 1; i < n; ++i)
-            if (std::fabs(Ch[i * m + c]) > std::fabs(Ch[imax * m + c])) imax = i;
-        const double sg = Ch[imax * m + c] < 0 ? -1.0 : 1.0;
-        for (int64_t i = 0; i < n; ++i) out[static_cast<size_t>(j) * n + i] = sg * Ch[i * m + c];
-        eps_out[j] = e[c];
-        if (resid_out) resid_out[j] = res[c];
-    }
-    NDSI_CK(cudaMemcpy(C_out, out.data(), sizeof(double) * out.size(), cudaMemcpyDefault));
-    if (iters_out) *iters_out = it;
-    if (!done) return fail(NDSI_ERR_TIMEOUT, "ndsi_eigenstates: not converged within max_iter (best pairs returned)");
-    return NDSI_OK;
-}
-
-int ndsi_dos(ndsi_plan* h, const double* H, const double* S, const double* energies, int32_t n_energies,
-             double eta, double* dos_out, void* stream) {
-    if (!h || !H || !S || !energies || !dos_out || n_energies < 1 || !(eta > 0) || !std::isfinite(eta))
-        return fail(NDSI_ERR_INVALID, "ndsi_dos: invalid argument");
-    if (h->P.n_systems != 1) return fail(NDSI_ERR_INVALID, "ndsi_dos: batched plan");
-    if (is_device_ptr(energies) || is_device_ptr(dos_out))
-        return fail(NDSI_ERR_INVALID, "ndsi_dos: energies and dos_out are host arrays");
-    for (int32_t k = 0; k < n_energies; ++k)
-        if (!std::isfinite(energies[k])) return fail(NDSI_ERR_INVALID, "ndsi_dos: energy not finite");
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
-    int rc = upload_tables(h);
-    if (rc) return rc;
-    const double *Hd, *Sd;
-    rc = device_inputs(h, H, S, &Hd, &Sd, st);
-    if (rc) return rc;
-    return dos_sweep(h, Hd, Sd, energies, n_energies, eta, dos_out, st);
-}
-
-int ndsi_find_mu(ndsi_plan* h, const double* H, const double* S, double kT, int32_t n_poles,
-                 double n_electrons, double mu_lo, double mu_hi, double tol_electrons, int32_t max_iter,
-                 double* rho_out, double* mu_out, double* n_elec_out, int32_t* iters_out, void* stream) {
-    if (!h || !H || !S || !rho_out || !mu_out || n_poles < 1 || !(kT > 0) || !(tol_electrons > 0) ||
-        max_iter < 1 || !std::isfinite(n_electrons) || h->P.n_systems != 1)
-        return fail(NDSI_ERR_INVALID, "ndsi_find_mu: invalid argument");
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
-    int rc = upload_tables(h);
-    if (rc) return rc;
-    const int64_t nnz = h->P.nnz;
-    const double *Hd, *Sd;
-    rc = device_inputs(h, H, S, &Hd, &Sd, st);
-    if (rc) return rc;
-    // Gershgorin bounds of H and S -> bounds of the pencil's spectrum (host, O(nnz))
-    std::vector<double> hv(nnz), sv(nnz);
-    NDSI_CK(cudaMemcpyAsync(hv.data(), Hd, sizeof(double) * nnz, cudaMemcpyDeviceToHost, st));
-    NDSI_CK(cudaMemcpyAsync(sv.data(), Sd, sizeof(double) * nnz, cudaMemcpyDeviceToHost, st));
-    NDSI_CK(cudaStreamSynchronize(st));
-    double elo, ehi;
-    pencil_bounds(h->P, hv, sv, 0, h->P.n, &elo, &ehi);
-    rc = ensure_stage(h, 3 * nnz + 8);
-    if (rc) return rc;
-    const bool rho_dev = is_device_ptr(rho_out);
-    double* rho_d = rho_dev ? rho_out : h->stage + 2 * nnz;
-    double* ne_d = h->stage + 3 * nnz;
-    FindMuCtx ctx{h, Hd, Sd, kT, n_poles, n_electrons, rho_d, ne_d, st, 0.0, false};
-    double mu = 0, dn = 0;
-    int32_t iters = 0;
-    std::string err;
-    rc = mu_search(find_mu_eval, find_mu_dos, &ctx, elo, ehi, kT, n_electrons, n_poles + 1, mu_lo, mu_hi,
-                   tol_electrons, max_iter, &mu, &dn, &iters, err);
-    if (rc && rc != NDSI_ERR_TIMEOUT) return err.empty() ? rc : fail(rc, "ndsi_find_mu: " + err);
-    // rho_out must hold rho(mu): evaluate once more if the last trial was another point
-    if (!ctx.have_last || ctx.last_mu != mu) {
-        double dn2 = 0;
-        const int r2 = find_mu_eval(&ctx, mu, &dn2);
-        if (r2) return r2;
-    }
-    *mu_out = mu;
-    if (n_elec_out) *n_elec_out = n_electrons + dn;
-    if (iters_out) *iters_out = iters;
-    if (!rho_dev) NDSI_CK(cudaMemcpyAsync(rho_out, rho_d, sizeof(double) * nnz, cudaMemcpyDeviceToHost, st));
-    NDSI_CK(cudaStreamSynchronize(st));
-    if (rc) return fail(rc, "ndsi_find_mu: not converged within max_iter evaluations");
-    return NDSI_OK;
-}
-
-int ndsi_find_mu_batched(ndsi_plan* h, const double* H, const double* S, const double* kT, int32_t n_poles,
-                         const double* n_electrons, const double* mu_lo, const double* mu_hi, double tol_electrons,
-                         int32_t max_iter, double* rho_out, double* mu_out, double* n_elec_out, int32_t* rounds_out,
-                         void* stream) {
-    if (!h || !H || !S || !kT || !n_electrons || !rho_out || !mu_out || n_poles < 1 || !(tol_electrons > 0) ||
-        max_iter < 1)
-        return fail(NDSI_ERR_INVALID, "ndsi_find_mu_batched: invalid argument");
-    const int32_t ns = h->P.n_systems;
-    for (int32_t sy = 0; sy < ns; ++sy)
-        if (!(kT[sy] > 0) || !std::isfinite(n_electrons[sy]))
-            return fail(NDSI_ERR_INVALID, "ndsi_find_mu_batched: kT <= 0 or non-finite electron count");
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
-    int rc = upload_tables(h);
-    if (rc) return rc;
-    const int64_t nnz = h->P.nnz;
-    const double *Hd, *Sd;
-    rc = device_inputs(h, H, S, &Hd, &Sd, st);
-    if (rc) return rc;
-    std::vector<double> hv(nnz), sv(nnz);
-    NDSI_CK(cudaMemcpyAsync(hv.data(), Hd, sizeof(double) * nnz, cudaMemcpyDeviceToHost, st));
-    NDSI_CK(cudaMemcpyAsync(sv.data(), Sd, sizeof(double) * nnz, cudaMemcpyDeviceToHost, st));
-    NDSI_CK(cudaStreamSynchronize(st));
-    std::vector<double> elo(ns), ehi(ns);
-    for (int32_t sy = 0; sy < ns; ++sy)
-        pencil_bounds(h->P, hv, sv, h->P.sys_n_first[sy], h->P.sys_n_first[sy + 1], &elo[sy], &ehi[sy]);
-    rc = ensure_stage(h, 3 * nnz + 8 + ns);
-    if (rc) return rc;
-    const bool rho_dev = is_device_ptr(rho_out);
-    double* rho_d = rho_dev ? rho_out : h->stage + 2 * nnz;
-    double* ne_d = h->stage + 3 * nnz;
-    FindMuBatchCtx ctx{h, Hd, Sd, kT, n_poles, n_electrons, rho_d, ne_d, st, {}};
-    std::vector<double> mu(ns), dn(ns);
-    int32_t rounds = 0;
-    std::string err;
-    rc = mu_search_batched(ns, find_mu_eval_batch, find_mu_dos_batch, &ctx, elo.data(), ehi.data(), kT, n_electrons,
-                           n_poles + 1, mu_lo, mu_hi, tol_electrons, max_iter, mu.data(), dn.data(), nullptr, &rounds,
-                           err);
-    if (rc && rc != NDSI_ERR_TIMEOUT) return err.empty() ? rc : fail(rc, "ndsi_find_mu_batched: " + err);
-    // rho_out must hold rho at the returned mu of every system
-    if (ctx.last_mu != mu) {
-        std::vector<double> dn2(ns);
-        const int r2 = find_mu_eval_batch(&ctx, ns, nullptr, mu.data(), dn2.data());
-        if (r2) return r2;
-    }
-    for (int32_t sy = 0; sy < ns; ++sy) {
-        mu_out[sy] = mu[sy];
-        if (n_elec_out) n_elec_out[sy] = n_electrons[sy] + dn[sy];
-    }
-    if (rounds_out) *rounds_out = rounds;
-    if (!rho_dev) NDSI_CK(cudaMemcpyAsync(rho_out, rho_d, sizeof(double) * nnz, cudaMemcpyDeviceToHost, st));
-    NDSI_CK(cudaStreamSynchronize(st));
-    if (rc) return fail(rc, "ndsi_find_mu_batched: " + err);
-    return NDSI_OK;
-}
 
 int ndsi_mu_features(ndsi_plan* h, const double* H, const double* S, double n_electrons, double kT,
                      int32_t n_vectors, uint64_t seed, float* feat_out, void* stream) {
