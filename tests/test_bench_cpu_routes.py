@@ -1,0 +1,18 @@
+"""Host helpers of bench.py that time other CPU routes beside the oracle baseline."""
+import math
+
+import bench
+from synth import lattice_system
+
+
+def test_sparse_lu_rate_is_bounded_and_positive():
+    s = lattice_system((8, 8, 1), 2, "2d", 5)
+    v, npoles, t_pole = bench.cpu_sparse_lu_rate(s, -0.1, 0.01, 40, max_seconds=0.2)
+    assert v > 0 and 1 <= npoles <= 40 and t_pole > 0
+    # the rate is poles x N over the time of a full sweep of M + 1 points
+    assert math.isclose(v, 40 * s.n / (t_pole * 41), rel_tol=1e-12)
+
+
+def test_single_core_oracle_rate():
+    v = bench.cpu_single_core_rate("C1", -0.12)
+    assert v is not None and v > 0
