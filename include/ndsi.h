@@ -145,8 +145,10 @@ int ndsi_analyze(const ndsi_pattern* pat, int32_t n_atoms, const double* centers
  * selected inversion processes one tree level of every system and every pole at once.  Pattern
  * arrays of the batch are the systems' arrays concatenated in order.
  *   pats[i], n_atoms[i], centers[i], atom_of_basis[i] - as for ndsi_analyze, per system.
- * ndsi_density_batched, ndsi_factor_poles and ndsi_selinv accept the plan; ndsi_density,
- * ndsi_find_mu and ndsi_mu_features need a single-system plan (NDSI_ERR_INVALID otherwise). */
+ * ndsi_density_batched, ndsi_find_mu_batched, ndsi_factor_poles and ndsi_selinv accept the plan;
+ * ndsi_density, ndsi_density_energy, ndsi_dos, ndsi_find_mu, ndsi_mu_features,
+ * ndsi_factors_solve and ndsi_eigenstates need a single-system plan (NDSI_ERR_INVALID
+ * otherwise).  The options (including `cell`) apply to every system. */
 int ndsi_analyze_batched(int32_t n_systems, const ndsi_pattern* pats, const int32_t* n_atoms,
                          const double* const* centers, const int32_t* const* atom_of_basis,
                          const ndsi_options* opt, ndsi_plan** plan_out);
@@ -159,6 +161,8 @@ int ndsi_density_batched(ndsi_plan* plan, const double* H, const double* S, cons
                          const double* kT, int32_t n_poles, double* rho_out, double* n_elec_out,
                          void* stream);
 
+/* Sizes and cost figures of a plan (ndsi_plan_summary above) into the caller's *out.
+ * Errors: NDSI_ERR_INVALID for NULL arguments. */
 int ndsi_plan_info(const ndsi_plan* plan, ndsi_plan_summary* out);
 
 /* Copy one structure table of the plan (see NDSI_EXPORT_*) into host memory `out`, which must
@@ -227,6 +231,9 @@ typedef struct {
     double tensor_flops;  /* summed tensor-core flops issued (split GEMM only) */
 } ndsi_profile_entry;
 
+/* Start (enable = 1 or 2, counters cleared) or stop (0) the per-kernel timing of the plan.
+ * While it is on, density sweeps launch their kernels directly (no graph replay) so that each
+ * launch can be bracketed by events.  Errors: NDSI_ERR_INVALID for a NULL plan. */
 int ndsi_profile_enable(ndsi_plan* plan, int32_t enable);
 
 /* Autotuner for split-precision plans: times every GEMM step of one density sweep at (mu, kT,
@@ -458,6 +465,9 @@ int ndsi_mlp_grad(const float* params, const float* X, const float* T, int32_t n
 int ndsi_mlp_train(float* params, const float* X, const float* T, int32_t n, int32_t steps,
                    float lr, float* loss_out, void* stream);
 
+/* Free a plan (its device tables, workspaces, staging, captured graph) or a factors handle (its
+ * fronts of every pole).  NULL is ignored.  Destroy every factors handle of a plan before the
+ * plan; no call of the handle may be in flight on any stream. */
 void ndsi_plan_destroy(ndsi_plan* plan);
 void ndsi_factors_destroy(ndsi_factors* f);
 
