@@ -82,3 +82,31 @@ def test_find_mu_batched_lockstep():
     nd.ndsi_density_batched(plan, H, S, mu, kT, M, rho2, ne2)
     torch.cuda.synchronize()
     assert torch.equal(rho, rho2)
+
+
+def test_find_mu_batched_with_brackets_and_host_rho():
+    # brackets per system (one of them wrong, so that system widens it) and a host rho buffer
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from oracle.dense import generalized_eig, find_mu_eig, electron_count_eig
+    nd = lib()
+    systems = [lattice_system((7, 6, 1), 2, "2d", seed=64), lattice_system((24, 1, 1), 2, "1d", seed=65)]
+    kT = np.array([0.01, 0.01])
+    ne = np.array([s.n_electrons for s in systems])
+    M = 40
+    eps = [generalized_eig(*s.dense())[0] for s in systems]
+    ref = [find_mu_eig(e, k, n, M) for e, k, n in zip(eps, kT, ne)]
+    lo = np.array([ref[0] - 0.05, ref[1] + 0.2])
+    hi = np.array([ref[0] + 0.05, ref[1] + 0.3])
+    plan = nd.analyze_batched(systems)
+    H = np.concatenate([s.H for s in systems])
+    S = np.concatenate([s.S for s in systems])
+    rho = np.zeros(H.size)
+    mu, n_e, rounds = nd.ndsi_find_mu_batched(plan, H, S, kT, M, ne, rho, mu_lo=lo, mu_hi=hi)
+    assert np.all(np.abs(n_e - ne) < 1e-8)
+    for e, m, k, n in zip(eps, mu, kT, ne):
+        assert abs(electron_count_eig(e, m, k, M) - n) < 1e-7
+    rho2 = np.zeros_like(rho)
+    nd.ndsi_density_batched(plan, H, S, mu, kT, M, rho2)
+    assert np.array_equal(rho, rho2)

@@ -68,3 +68,18 @@ def test_eigenstates_errors():
     with pytest.raises(nd.NdsiError) as e:
         nd.ndsi_eigenstates(plan, H, S, 0.0, 3, max_iter=1, tol=1e-14)
     assert e.value.code == 5                                       # not converged: NDSI_ERR_TIMEOUT
+
+
+def test_eigenstates_periodic_lattice_host_inputs():
+    # periodic cell, host H and S (staged inside the call), host output
+    sysm = lattice_system((8, 9, 1), 2, "2d", seed=83, periodic=(True, True, False))
+    Hd, Sd = sysm.dense()
+    xi, n = 0.1, 4
+    eps_ref, C_ref = eigenstates_near(Hd, Sd, xi, n)
+    nd = lib()
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    plan = nd.analyze_system(sysm, cell=sysm.meta["cell"])
+    eps, C, res, it = nd.ndsi_eigenstates(plan, sysm.H.copy(), sysm.S.copy(), xi, n, block=8)
+    _check(eps, C, res, eps_ref, C_ref, Sd, 1e-11, 1e-8)

@@ -79,3 +79,16 @@ def test_energy_density_C1():
     e_ref = on_pattern(energy_density_eig(eps, C, mu, kT, M), sysm)
     rho, e, ne, _ = _run(sysm, mu, kT, M)
     assert np.max(np.abs(e - e_ref)) < 1e-10
+
+
+def test_energy_density_periodic_lattice():
+    # a periodic cell (separators wrapping around it) changes nothing in Eq. 10's evaluation
+    sysm = lattice_system((9, 8, 1), 2, "2d", 62, periodic=(True, True, False))
+    Hd, Sd = sysm.dense()
+    kT, M = 0.01, 40
+    eps, C = generalized_eig(Hd, Sd)
+    mu = find_mu_eig(eps, kT, sysm.n_electrons, M)
+    e_ref = on_pattern(energy_density_eig(eps, C, mu, kT, M), sysm)
+    rho, e, ne, rho_plain = _run(sysm, mu, kT, M, 0, cell=sysm.meta["cell"])
+    assert np.max(np.abs(e - e_ref)) < 1e-10
+    assert np.array_equal(rho, rho_plain)
