@@ -18,12 +18,6 @@ namespace ndsi {
 
 namespace {
 
-__device__ __forceinline__ double2 cmac(double2 acc, double2 a, double2 b) {
-    acc.x = fma(a.x, b.x, fma(-a.y, b.y, acc.x));
-    acc.y = fma(a.x, b.y, fma(a.y, b.x, acc.y));
-    return acc;
-}
-
 constexpr int kT = kSolveTile;
 constexpr int kTP = kSolveTile + 1;  // padded tile row (conflict-free column reads)
 

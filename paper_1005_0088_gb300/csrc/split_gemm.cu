@@ -193,18 +193,6 @@ __device__ __forceinline__ void umma_commit(uint64_t* bar) {
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
-    uint32_t r[16];
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-        : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
-}
-
 __device__ __forceinline__ void tmem_ld4(uint32_t taddr, float* v) {
     uint32_t r[4];
     asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
@@ -1122,11 +1110,9 @@ static cudaError_t run_mma(const Launch& l, int step_index, const GemmItem* item
                            const SplitBuffers& B, double2* Cbuf, int64_t sC, int np, int* status,
                            cudaStream_t st) {
     if ((l.alpha != 1.0 && l.alpha != -1.0) || (l.beta != 0.0 && l.beta != 1.0)) return cudaErrorInvalidValue;
-    GemmArgs ga{items_dev, sitems_dev, stiles_dev, step.tfirst, l.first, step.rowsA, step.rowsB,
-                step.erowsA, step.erowsB, B.expA, B.expB, Cbuf, sC, l.alpha < 0 ? 1 : 0, l.beta != 0.0 ? 1 : 0,
-                l.lower, status};
-    ga.tcount = step.tcount;
-    ga.np = np;
+    const GemmArgs ga{items_dev, sitems_dev, stiles_dev, step.tfirst, l.first, step.rowsA, step.rowsB,
+                      step.erowsA, step.erowsB, B.expA, B.expB, Cbuf, sC, l.alpha < 0 ? 1 : 0, l.beta != 0.0 ? 1 : 0,
+                      l.lower, status, step.tcount, np};
     const int64_t work = step.tcount * np;
     const unsigned grid = static_cast<unsigned>(std::max<int64_t>(1, std::min<int64_t>(work, g_num_sms)));
     if (step.nc == kSplitBNc5)
