@@ -165,6 +165,13 @@ int ndsi_density_batched(ndsi_plan* plan, const double* H, const double* S, cons
  * Errors: NDSI_ERR_INVALID for NULL arguments. */
 int ndsi_plan_info(const ndsi_plan* plan, ndsi_plan_summary* out);
 
+/* Host-only check of a plan's schedule (no GPU work): every index the kernels follow (GEMM items
+ * and tiles, copies, pivot blocks, assembly/gather tiles, scatter entries, index maps) stays in
+ * its buffer and front, and no two work items of one launch write overlapping memory or read
+ * what another item of the launch writes.  NDSI_OK, or NDSI_ERR_INVALID with the first violation
+ * in ndsi_last_error. */
+int ndsi_plan_check(const ndsi_plan* plan);
+
 /* Copy one structure table of the plan (see NDSI_EXPORT_*) into host memory `out`, which must
  * hold the documented number of elements.  Errors: NDSI_ERR_INVALID for an unknown item. */
 int ndsi_plan_export(const ndsi_plan* plan, int32_t what, void* out);

@@ -1010,6 +1010,13 @@ int ndsi_graph_info(const ndsi_plan* h, int64_t* nodes_out) {
     return NDSI_OK;
 }
 
+int ndsi_plan_check(const ndsi_plan* h) {
+    if (!h) return fail(NDSI_ERR_INVALID, "ndsi_plan_check: NULL plan");
+    std::string err;
+    const int rc = check_plan(h->P, err);
+    return rc ? fail(rc, err) : NDSI_OK;
+}
+
 const char* ndsi_last_error(void) { return g_last_error.c_str(); }
 
 }  // extern "C"

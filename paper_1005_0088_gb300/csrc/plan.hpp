@@ -157,6 +157,9 @@ void compute_scratch(Plan& P);
 void build_schedule(Plan& P);
 int merge_plans(std::vector<Plan>& parts, Plan& merged, std::string& err);
 
+// Bounds and write-overlap check of every schedule table (plan_check.cpp).
+int check_plan(const Plan& P, std::string& err);
+
 // Chemical-potential search over caller-supplied evaluations (mu_search.cpp).
 int mu_search(ndsi_mu_eval_fn eval, ndsi_mu_dos_fn dos, void* ctx, double elo, double ehi, double kT,
               double n_electrons, int32_t n_grid, double mu_lo, double mu_hi, double tol, int32_t max_iter,

@@ -35,7 +35,7 @@ EXPORTED_SYMBOLS = (
     "ndsi_mlp_forward", "ndsi_mlp_grad", "ndsi_mlp_train", "ndsi_analyze_batched",
     "ndsi_density_batched", "ndsi_graph_enable", "ndsi_graph_info", "ndsi_autotune",
     "ndsi_density_energy", "ndsi_dos", "ndsi_factors_solve", "ndsi_eigenstates", "ndsi_mu_search",
-    "ndsi_mu_search_batched", "ndsi_find_mu_batched",
+    "ndsi_mu_search_batched", "ndsi_find_mu_batched", "ndsi_plan_check",
 )
 MU_EVAL_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.c_double, ctypes.POINTER(ctypes.c_double))
 MU_DOS_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.c_int32,
@@ -127,6 +127,8 @@ def load(path: str = LIB_PATH):
     lib.ndsi_find_mu_batched.argtypes = [vp, vp, vp, vp, i32, vp, vp, vp, ctypes.c_double, i32, vp, vp, vp,
                                          ctypes.POINTER(i32), vp]
     lib.ndsi_find_mu_batched.restype = ctypes.c_int
+    lib.ndsi_plan_check.argtypes = [vp]
+    lib.ndsi_plan_check.restype = ctypes.c_int
     lib.ndsi_factors_solve.argtypes = [vp, i32, vp, i32, vp, vp]
     lib.ndsi_factors_solve.restype = ctypes.c_int
     lib.ndsi_eigenstates.argtypes = [vp, vp, vp, ctypes.c_double, ctypes.c_double, i32, i32, i32,
@@ -259,6 +261,11 @@ def ndsi_plan_info(plan: Plan) -> dict:
     s = ndsi_plan_summary()
     _check(load().ndsi_plan_info(plan.handle, ctypes.byref(s)))
     return {name: getattr(s, name) for name, _ in ndsi_plan_summary._fields_}
+
+
+def ndsi_plan_check(plan: Plan) -> None:
+    """Raise NdsiError if the plan's schedule would index out of bounds or race (host only)."""
+    _check(load().ndsi_plan_check(plan.handle))
 
 
 def ndsi_plan_export(plan: Plan, what: str) -> np.ndarray:
