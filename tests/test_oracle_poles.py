@@ -52,3 +52,30 @@ def test_pole_weights_sign():
     assert np.all(alpha.real == -0.2)
     assert np.all(alpha.imag > 0)
     assert np.all(w > 0)          # w_p = -4 R_p / beta with R_p < 0
+
+
+def test_hundred_poles_at_600_kelvin_are_exact():
+    # Sec. II.B: 100 poles at 600 K reproduce the Fermi function to double precision over the
+    # energies of a valence spectrum (here |E - mu| <= 1.5 Hartree)
+    kT = 600.0 * 3.166811563e-6            # k_B in Hartree per kelvin
+    z, R = cf_poles(100)
+    x = np.linspace(-1.5, 1.5, 40001) / kT
+    assert np.max(np.abs(fermi_from_poles(x, z, R) - fermi_exact(x))) < 1e-14
+
+
+def test_pole_count_does_not_depend_on_size():
+    # Sec. II.B: the truncation error of the M-pole expansion is set by the spectral range and kT,
+    # not by the number of states: the same M serves a chain of 40 and of 400 sites
+    from oracle.closed_form import chain_spectrum, chain_density
+    from oracle.dense import occupation
+    errs = {}
+    for N in (40, 400):
+        for M in (10, 20):
+            kw = dict(N=N, a=0.0, b=-1.0, s=0.1, mu=0.05, kT=0.01)
+            rM, _ = chain_density(occupation=lambda x, m, t, M=M: occupation(x, m, t, M), **kw)
+            rX, _ = chain_density(occupation=lambda x, m, t: occupation(x, m, t, None), **kw)
+            errs[(N, M)] = np.max(np.abs(rM - rX))
+    for M in (10, 20):
+        ratio = errs[(400, M)] / errs[(40, M)]
+        assert 0.2 < ratio < 5.0, (M, errs)
+    assert errs[(40, 20)] < errs[(40, 10)]
