@@ -18,8 +18,8 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 CU_SOURCES = ["kernels.cu", "api.cu", "api_mu.cu", "api_solve.cu", "static_scratch.cu", "split_gemm.cu", "mlp.cu",
               "solve.cu"]
-CPP_SOURCES = ["analyze.cpp", "mu_search.cpp", "plan_check.cpp"]
-HEADERS = ["plan.hpp", "kernels.cuh", "split_gemm.cuh", "solve.cuh", "handle.hpp"]
+CPP_SOURCES = ["analyze.cpp", "mu_search.cpp", "plan_check.cpp", "small_eig.cpp"]
+HEADERS = ["plan.hpp", "kernels.cuh", "split_gemm.cuh", "solve.cuh", "handle.hpp", "small_eig.hpp"]
 
 
 def _nvcc():
