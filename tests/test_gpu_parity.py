@@ -258,3 +258,13 @@ def test_density_single_pole():
     rho_ref = on_pattern(density_eig(eps, C, 0.05, 0.05, 1), sysm)
     rho, ne = _density(sysm, 0.05, 0.05, 1)
     assert np.max(np.abs(rho - rho_ref)) < RHO_TOL
+
+
+@pytest.mark.parametrize("precision", [1, 0])
+def test_density_C3_electron_count_matches_oracle(precision):
+    # Tr(rho S) (Eq. 40) of the 3D cubic workload, N = 16384, 80 poles, against the oracle's
+    # eigenvalue count stored by tests/golden/make_c3_electron_count.py
+    ref = float(golden_lines("c3_electron_count.txt")[0])
+    sysm = config_system("C3")
+    _, ne = _density(sysm, -0.12, 0.01, 80, precision=precision)
+    assert abs(ne - ref) < 1e-9, (ne, ref)
