@@ -502,6 +502,19 @@ def run_ndsi(args):
     return 0
 
 
+def _stored_batched_counts(ne, M, kT):
+    """Tr(rho S) of the batched systems against the oracle's eigenvalue counts stored by
+    tests/golden/make_c4_electron_counts.py (systems with N <= 16384, mu -0.12, kT 0.01, 120
+    poles), or None for other settings."""
+    path = os.path.join(ROOT, "tests", "golden", "c4_electron_counts.txt")
+    if M != 120 or kT != 0.01 or MU != -0.12 or not os.path.exists(path):
+        return None
+    with open(path) as fh:
+        ref = {int(l.split()[0]): float(l.split()[2]) for l in fh if l.strip() and not l.startswith("#")}
+    return {"systems": sorted(ref), "max_abs_err": max(abs(float(ne[i]) - v) for i, v in ref.items()),
+            "source": "stored (oracle eigenvalues)"}
+
+
 def run_batched(args, nd, torch, dist, rank, world, local, prec_code):
     """C4: twelve uneven systems (1D/2D/3D, N 2048..32768) in one batched plan, 120 poles."""
     import numpy as np
@@ -601,6 +614,7 @@ def run_batched(args, nd, torch, dist, rank, world, local, prec_code):
                       "ms_per_step_direct_launches": sum(prof_times) / len(prof_times)},
             "roofline": roofline, "clocks": clk.summary(),
             "n_elec": ne.cpu().numpy().tolist(),
+            "n_elec_oracle": _stored_batched_counts(ne.cpu().numpy(), M, kT),
             "parity": parity,
             "kernels": {k: {"launches": v["launches"] // args.steps, "ms_per_step": v["ms"] / args.steps}
                         for k, v in kern.items()}}

@@ -110,3 +110,26 @@ def test_find_mu_batched_with_brackets_and_host_rho():
     rho2 = np.zeros_like(rho)
     nd.ndsi_density_batched(plan, H, S, mu, kT, M, rho2)
     assert np.array_equal(rho, rho2)
+
+
+def test_batched_workload_electron_counts_match_oracle():
+    # Tr(rho S) (Eq. 40) of the batched workload's systems (split path, 120 poles) against the
+    # oracle's eigenvalue counts stored by tests/golden/make_c4_electron_counts.py
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from synth import batched_systems
+    from tests.conftest import golden_lines
+    nd = lib()
+    systems = batched_systems()
+    ref = {int(l.split()[0]): float(l.split()[2]) for l in golden_lines("c4_electron_counts.txt")}
+    plan = nd.analyze_batched(systems, precision=1)
+    H = torch.as_tensor(np.concatenate([s.H for s in systems]), device="cuda")
+    S = torch.as_tensor(np.concatenate([s.S for s in systems]), device="cuda")
+    rho = torch.zeros(H.numel(), dtype=torch.float64, device="cuda")
+    ne = torch.zeros(len(systems), dtype=torch.float64, device="cuda")
+    nd.ndsi_density_batched(plan, H, S, np.full(len(systems), -0.12), np.full(len(systems), 0.01), 120, rho, ne)
+    torch.cuda.synchronize()
+    got = ne.cpu().numpy()
+    for i, v in ref.items():
+        assert abs(got[i] - v) < 1e-9, (i, got[i], v)
