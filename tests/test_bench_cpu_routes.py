@@ -16,3 +16,24 @@ def test_sparse_lu_rate_is_bounded_and_positive():
 def test_single_core_oracle_rate():
     v = bench.cpu_single_core_rate("C1", -0.12)
     assert v is not None and v > 0
+
+
+def test_stored_oracle_counts_are_read():
+    import numpy as np
+    ref = {0: 1888.610006770609, 9: 13109.959658391954}
+    ne = np.zeros(12)
+    for i, v in ref.items():
+        ne[i] = v + 1e-10
+    out = bench._stored_batched_counts(ne, 120, 0.01)
+    assert out["systems"] == [0, 1, 2, 4, 5, 6, 8, 9]
+    assert out["max_abs_err"] > 1.0                       # the systems left at zero
+    assert bench._stored_batched_counts(ne, 80, 0.01) is None
+
+
+def test_bench_modes_parse():
+    import subprocess
+    import sys
+    out = subprocess.run([sys.executable, "bench.py", "--help"], cwd=bench.ROOT, capture_output=True, text=True)
+    assert out.returncode == 0
+    for flag in ("--impl", "--config", "--precision", "--energy", "--mu-search", "--eigen", "--no-graph"):
+        assert flag in out.stdout
