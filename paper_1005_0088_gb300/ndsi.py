@@ -205,6 +205,7 @@ def _stream(stream):
 
 
 def ndsi_default_options():
+    """The library's default ndsi_options."""
     o = ndsi_options()
     load().ndsi_default_options(ctypes.byref(o))
     return o
@@ -245,6 +246,7 @@ class Factors:
 
 
 def ndsi_analyze(n, rowptr, col, n_atoms, centers, atom_of_basis, options=None) -> Plan:
+    """ndsi_analyze: nested dissection, supernodes and schedule of one pattern (host only)."""
     rowptr = np.ascontiguousarray(rowptr, dtype=np.int64)
     col = np.ascontiguousarray(col, dtype=np.int32)
     centers = np.ascontiguousarray(centers, dtype=np.float64)
@@ -258,6 +260,7 @@ def ndsi_analyze(n, rowptr, col, n_atoms, centers, atom_of_basis, options=None) 
 
 
 def ndsi_plan_info(plan: Plan) -> dict:
+    """ndsi_plan_info as a dict of the ndsi_plan_summary fields."""
     s = ndsi_plan_summary()
     _check(load().ndsi_plan_info(plan.handle, ctypes.byref(s)))
     return {name: getattr(s, name) for name, _ in ndsi_plan_summary._fields_}
@@ -269,6 +272,8 @@ def ndsi_plan_check(plan: Plan) -> None:
 
 
 def ndsi_plan_export(plan: Plan, what: str) -> np.ndarray:
+    """One structure table of the plan (perm_atoms, perm_basis, node_atoms, parent, struct_ptr,
+    struct_atoms, schedule) as a numpy array."""
     info = ndsi_plan_info(plan)
     nn = info["n_nodes"]
     if what == "struct_atoms":
@@ -289,6 +294,7 @@ def ndsi_plan_export(plan: Plan, what: str) -> np.ndarray:
 
 
 def ndsi_factor_poles(plan: Plan, H, S, z, stream=None) -> Factors:
+    """Factor z_p S - H for every point of z (complex array); returns the factors handle."""
     z = np.ascontiguousarray(np.asarray(z, dtype=np.complex128))
     zz = np.ascontiguousarray(z.view(np.float64))
     h = ctypes.c_void_p()
@@ -298,11 +304,13 @@ def ndsi_factor_poles(plan: Plan, H, S, z, stream=None) -> Factors:
 
 
 def ndsi_selinv(factors: Factors, G_out=None, stream=None):
+    """Selected inversion of the factors; G_out (n_poles x nnz x 2 doubles) or None."""
     _check(load().ndsi_selinv(factors.handle, _ptr(G_out), _stream(stream)))
     return G_out
 
 
 def ndsi_density(plan: Plan, H, S, mu, kT, n_poles, rho_out, n_elec_out=None, stream=None):
+    """rho on the pattern and Tr(rho S) at (mu, kT) with n_poles poles (Eq. 8, Eq. 40)."""
     _check(load().ndsi_density(plan.handle, _ptr(H), _ptr(S), float(mu), float(kT), int(n_poles),
                                _ptr(rho_out), _ptr(n_elec_out), _stream(stream)))
     return rho_out
@@ -479,6 +487,7 @@ def ndsi_graph_info(plan: Plan) -> int:
 
 
 def ndsi_profile_enable(plan: Plan, enable=True, by_level: bool = False):
+    """Per-kernel timing on (by_level splits GEMM and slicing families by tree level) or off."""
     _check(load().ndsi_profile_enable(plan.handle, (2 if by_level else 1) if enable else 0))
 
 
@@ -530,22 +539,26 @@ def ndsi_find_mu_batched(plan: Plan, H, S, kT, n_poles, n_electrons, rho_out, mu
 
 def ndsi_mu_features(plan: Plan, H, S, n_electrons, kT, feat_out, n_vectors=16, seed=12345,
                      stream=None):
+    """The 32 spectral-moment features of (H, S) for the chemical-potential seed network."""
     _check(load().ndsi_mu_features(plan.handle, _ptr(H), _ptr(S), float(n_electrons), float(kT),
                                    int(n_vectors), int(seed), _ptr(feat_out), _stream(stream)))
     return feat_out
 
 
 def ndsi_mlp_init(params, seed=0, stream=None):
+    """Glorot-uniform initial parameters of the seed network (device float array)."""
     _check(load().ndsi_mlp_init(_ptr(params), int(seed), _stream(stream)))
     return params
 
 
 def ndsi_mlp_forward(params, X, n, Y, stream=None):
+    """Network outputs Y[s] for the rows of X (device arrays)."""
     _check(load().ndsi_mlp_forward(_ptr(params), _ptr(X), int(n), _ptr(Y), _stream(stream)))
     return Y
 
 
 def ndsi_mlp_grad(params, X, T, n, grad, loss=None, stream=None):
+    """Gradient of the mean squared error over the n rows (and the loss, if given)."""
     _check(load().ndsi_mlp_grad(_ptr(params), _ptr(X), _ptr(T), int(n), _ptr(grad), _ptr(loss),
                                 _stream(stream)))
     return grad
@@ -585,6 +598,7 @@ def analyze_batched(systems, **options) -> Plan:
 
 
 def ndsi_density_batched(plan: Plan, H, S, mu, kT, n_poles, rho_out, n_elec_out=None, stream=None):
+    """rho and Tr(rho S) of every system of a batched plan at its own mu and kT."""
     mu = np.ascontiguousarray(mu, dtype=np.float64)
     kT = np.ascontiguousarray(kT, dtype=np.float64)
     _check(load().ndsi_density_batched(plan.handle, _ptr(H), _ptr(S), _ptr(mu), _ptr(kT),
