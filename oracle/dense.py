@@ -66,6 +66,18 @@ def density_inv(Hd, Sd, mu, kT, M):
     return rho
 
 
+def density_inv_terms(Hd, Sd, mu, kT, M):
+    """The M + 1 terms of Eq. (8) one by one (tiny inputs): [S^{-1}, w_1 Re G(alpha_1), ...,
+    w_M Re G(alpha_M)]; their sum is `density_inv`.  Poles are independent (Sec. III.D), so any
+    partition of these terms among processes sums to the same rho."""
+    beta = 1.0 / kT
+    z, R = cf_poles(M)
+    terms = [np.linalg.inv(Sd)]
+    for zp, Rp in zip(z, R):
+        terms.append((-4.0 * Rp / beta) * np.real(green_dense(Hd, Sd, mu + 1j * zp / beta)))
+    return terms
+
+
 def energy_density_eig(eps, C, mu, kT, M=None):
     """Energy density matrix by definition: e = sum_nu eps_nu 2 f(beta(eps_nu - mu)) c c^T."""
     w = np.asarray(eps) * occupation(eps, mu, kT, M)
