@@ -47,6 +47,14 @@ def _max_over_ranks(x, dist, world, device):
     return float(t.item())
 
 
+def _sum_over_ranks(buf, dist, world):
+    """In-place sum of a tensor over all ranks: the one exchange of the pole-sharded sweep (each
+    rank holds its share of Eq. 8's sum; rho and Tr(rho S) are the totals)."""
+    if world > 1:
+        dist.all_reduce(buf, op=dist.ReduceOp.SUM)
+    return buf
+
+
 def _job_value(units_per_rank, world, ms_per_step):
     """Whole-job throughput: every replica processes units_per_rank per step."""
     return world * units_per_rank / (ms_per_step * 1e-3)

@@ -222,6 +222,29 @@ int ndsi_factors_solve(ndsi_factors* f, int32_t pole, const double* Y, int32_t k
 int ndsi_density(ndsi_plan* plan, const double* H, const double* S, double mu, double kT,
                  int32_t n_poles, double* rho_out, double* n_elec_out, void* stream);
 
+/* One rank's share of the contour sum of Eq. 8 when the poles are divided among processes
+ * (Sec. III.D: the poles are independent, and the only exchange is the sum of the results):
+ *   rho_part   = [M0 if with_m0] + sum_{pole_begin <= p < pole_end} w_p Re G(alpha_p),
+ *   n_elec_part = Tr(rho_part S) = sum_k rho_part_k S_k,
+ * with the poles, weights and M0 of ndsi_density for the same n_poles, mu and kT.  When the
+ * ranges of all ranks partition [0, n_poles) and exactly one rank sets with_m0, the sums over
+ * ranks of rho_part and n_elec_part are ndsi_density's rho and Tr(rho S) (equal up to the order
+ * of the floating-point additions).  An empty share (pole_begin == pole_end, with_m0 = 0) writes
+ * zeros.  Arguments, outputs and synchronisation as ndsi_density; single-system plans only.
+ * Errors: NDSI_ERR_INVALID (0 <= pole_begin <= pole_end <= n_poles violated, a batched plan, or
+ * as ndsi_density), otherwise as ndsi_density. */
+int ndsi_density_poles(ndsi_plan* plan, const double* H, const double* S, double mu, double kT,
+                       int32_t n_poles, int32_t pole_begin, int32_t pole_end, int32_t with_m0,
+                       double* rho_out, double* n_elec_out, void* stream);
+
+/* The pole range of `rank` among `world` processes for ndsi_density_poles: contiguous ranges
+ * [floor(r M / W), floor((r + 1) M / W)), whose sizes differ by at most one, and with_m0 set on
+ * the first rank holding the smallest number of poles (rank 0 when all are equal), so that every
+ * rank sums about the same number of points.  Host only.  Errors: NDSI_ERR_INVALID (M < 1,
+ * world < 1, rank outside [0, world), NULL outputs). */
+int ndsi_pole_shard(int32_t n_poles, int32_t rank, int32_t world, int32_t* pole_begin,
+                    int32_t* pole_end, int32_t* with_m0);
+
 /* Per-kernel timing.  While enabled, every launch made for this plan by ndsi_factor_poles,
  * ndsi_selinv and ndsi_density is bracketed by CUDA events on its stream; durations, launch
  * counts and the algorithmic flops and bytes of the launches accumulate per kernel family.

@@ -601,10 +601,8 @@ int ndsi_selinv(ndsi_factors* f, double* G_out, void* stream) {
     return check_status(h, st);
 }
 
-int ndsi_density(ndsi_plan* h, const double* H, const double* S, double mu, double kT, int32_t n_poles,
-                 double* rho_out, double* n_elec_out, void* stream) {
-    if (!h || !H || !S || !rho_out || n_poles < 1 || !(kT > 0) || !std::isfinite(mu))
-        return fail(NDSI_ERR_INVALID, "ndsi_density: invalid argument");
+static int density_entry(ndsi_plan* h, const double* H, const double* S, double mu, double kT, int32_t n_poles,
+                         const PoleRange* range, double* rho_out, double* n_elec_out, void* stream) {
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     int rc = upload_tables(h);
     if (rc) return rc;
@@ -618,11 +616,52 @@ int ndsi_density(ndsi_plan* h, const double* H, const double* S, double mu, doub
     double* rho_d = rho_dev ? rho_out : h->stage + 2 * h->P.nnz;
     double* ne_d = ne_dev ? n_elec_out : h->stage + 3 * h->P.nnz;
     if (h->P.n_systems != 1) return fail(NDSI_ERR_INVALID, "ndsi_density: batched plan, use ndsi_density_batched");
-    rc = density_impl(h, Hd, Sd, &mu, &kT, n_poles, rho_d, ne_d, st);
+    rc = density_impl(h, Hd, Sd, &mu, &kT, n_poles, rho_d, ne_d, st, nullptr, range);
     if (rc) return rc;
     if (!rho_dev) NDSI_CK(cudaMemcpyAsync(rho_out, rho_d, sizeof(double) * h->P.nnz, cudaMemcpyDeviceToHost, st));
     if (n_elec_out && !ne_dev) NDSI_CK(cudaMemcpyAsync(n_elec_out, ne_d, sizeof(double), cudaMemcpyDeviceToHost, st));
     NDSI_CK(cudaStreamSynchronize(st));
+    return NDSI_OK;
+}
+
+int ndsi_density(ndsi_plan* h, const double* H, const double* S, double mu, double kT, int32_t n_poles,
+                 double* rho_out, double* n_elec_out, void* stream) {
+    if (!h || !H || !S || !rho_out || n_poles < 1 || !(kT > 0) || !std::isfinite(mu))
+        return fail(NDSI_ERR_INVALID, "ndsi_density: invalid argument");
+    return density_entry(h, H, S, mu, kT, n_poles, nullptr, rho_out, n_elec_out, stream);
+}
+
+int ndsi_density_poles(ndsi_plan* h, const double* H, const double* S, double mu, double kT, int32_t n_poles,
+                       int32_t pole_begin, int32_t pole_end, int32_t with_m0, double* rho_out,
+                       double* n_elec_out, void* stream) {
+    if (!h || !H || !S || !rho_out || n_poles < 1 || !(kT > 0) || !std::isfinite(mu) || pole_begin < 0 ||
+        pole_end > n_poles || pole_begin > pole_end)
+        return fail(NDSI_ERR_INVALID, "ndsi_density_poles: invalid argument");
+    PoleRange r;
+    r.begin = pole_begin;
+    r.end = pole_end;
+    r.m0 = with_m0 != 0;
+    return density_entry(h, H, S, mu, kT, n_poles, &r, rho_out, n_elec_out, stream);
+}
+
+int ndsi_pole_shard(int32_t n_poles, int32_t rank, int32_t world, int32_t* pole_begin, int32_t* pole_end,
+                    int32_t* with_m0) {
+    if (n_poles < 1 || world < 1 || rank < 0 || rank >= world || !pole_begin || !pole_end || !with_m0)
+        return fail(NDSI_ERR_INVALID, "ndsi_pole_shard: invalid argument");
+    // contiguous ranges whose sizes differ by at most one: rank r takes [r M / W, (r + 1) M / W);
+    // the first rank of the smaller size (the first rank when all are equal) also takes M0
+    auto lo = [&](int32_t r) { return static_cast<int32_t>((static_cast<int64_t>(r) * n_poles) / world); };
+    int32_t m0_rank = 0, min_cnt = n_poles + 1;
+    for (int32_t r = 0; r < world; ++r) {
+        const int32_t cnt = lo(r + 1) - lo(r);
+        if (cnt < min_cnt) {
+            min_cnt = cnt;
+            m0_rank = r;
+        }
+    }
+    *pole_begin = lo(rank);
+    *pole_end = lo(rank + 1);
+    *with_m0 = rank == m0_rank ? 1 : 0;
     return NDSI_OK;
 }
 
@@ -660,10 +699,22 @@ namespace ndsi {
 // rho(mu) and Tr(rho S) of every system of the plan (mu[s], kT[s]) for device inputs and
 // outputs (ne_d[s] per system); synchronises the stream.
 int density_impl(ndsi_plan* h, const double* Hd, const double* Sd, const double* mu, const double* kT,
-                 int32_t n_poles, double* rho_d, double* ne_d, cudaStream_t st, double* e_d) {
+                 int32_t n_poles, double* rho_d, double* ne_d, cudaStream_t st, double* e_d,
+                 const PoleRange* range) {
     int rc;
     const int32_t ns = h->P.n_systems;
     if (e_d && ns != 1) return fail(NDSI_ERR_INVALID, "energy density: single-system plans only");
+    const int32_t pb = range ? range->begin : 0;
+    const int32_t pe = range ? range->end : n_poles;
+    const bool with_m0 = range ? range->m0 : true;
+    if (range && (ns != 1 || e_d || pb < 0 || pe > n_poles || pb > pe))
+        return fail(NDSI_ERR_INVALID, "density: bad pole range");
+    if (pe - pb + (with_m0 ? 1 : 0) == 0) {
+        // an empty share of the sum: rho = 0, Tr(rho S) = 0
+        NDSI_CK(cudaMemsetAsync(rho_d, 0, sizeof(double) * h->P.nnz, st));
+        NDSI_CK(cudaMemsetAsync(ne_d, 0, sizeof(double), st));
+        return check_status(h, st);
+    }
     // Energy density matrix (Eq. 10): the same points with weights -4 R_p alpha_p kT, kappa on the
     // M0 point, and the first moment M1 from three more points z = Re, -Re, i Re with
     // M1 = (Re^2 / 4) [G(Re) + G(-Re) - 2 Re G(i Re)] (the four points Re i^k annihilate every
@@ -690,7 +741,9 @@ int density_impl(ndsi_plan* h, const double* Hd, const double* Sd, const double*
         if (rc) return fail(rc, err);
         h->pole_M = n_poles;
     }
-    const int32_t nq = n_poles + 1 + (e_d ? 3 : 0);
+    // points of this call: poles pb..pe-1, then M0 (when summed), then the three moment points
+    const int32_t npl = pe - pb;
+    const int32_t nq = npl + (with_m0 ? 1 : 0) + (e_d ? 3 : 0);
     std::vector<double2> zq(static_cast<size_t>(ns) * nq), cq(static_cast<size_t>(ns) * nq),
         ceq(static_cast<size_t>(ns) * nq, make_double2(0.0, 0.0));
     const double R = h->P.opt.m0_radius;
@@ -699,23 +752,27 @@ int density_impl(ndsi_plan* h, const double* Hd, const double* Sd, const double*
         double2* c = cq.data() + static_cast<size_t>(sy) * nq;
         double2* ce = ceq.data() + static_cast<size_t>(sy) * nq;
         double kappa = 0.0;
-        for (int32_t p = 0; p < n_poles; ++p) {
-            z[p] = make_double2(mu[sy], h->pole_z[p] * kT[sy]);
-            c[p] = make_double2(-4.0 * h->pole_R[p] * kT[sy], 0.0);
+        for (int32_t p = 0; p < n_poles; ++p) kappa += 4.0 * kT[sy] * h->pole_R[p];
+        for (int32_t p = pb; p < pe; ++p) {
+            const int32_t q = p - pb;
+            z[q] = make_double2(mu[sy], h->pole_z[p] * kT[sy]);
+            c[q] = make_double2(-4.0 * h->pole_R[p] * kT[sy], 0.0);
             // -4 R_p kT alpha_p: Re(ce G) = -4 R_p kT Re(alpha_p G)
-            ce[p] = make_double2(-4.0 * h->pole_R[p] * kT[sy] * mu[sy], -4.0 * h->pole_R[p] * kT[sy] * z[p].y);
-            kappa += 4.0 * kT[sy] * h->pole_R[p];
+            ce[q] = make_double2(-4.0 * h->pole_R[p] * kT[sy] * mu[sy], -4.0 * h->pole_R[p] * kT[sy] * z[q].y);
         }
-        z[n_poles] = make_double2(0.0, R);
-        c[n_poles] = make_double2(0.0, R);
-        ce[n_poles] = make_double2(0.0, kappa * R);  // kappa M0, M0 = Re(i R G(i R))
+        if (with_m0) {
+            z[npl] = make_double2(0.0, R);
+            c[npl] = make_double2(0.0, R);
+            ce[npl] = make_double2(0.0, kappa * R);  // kappa M0, M0 = Re(i R G(i R))
+        }
         if (e_d) {
-            z[n_poles + 1] = make_double2(Re, 0.0);
-            z[n_poles + 2] = make_double2(-Re, 0.0);
-            z[n_poles + 3] = make_double2(0.0, Re);
-            c[n_poles + 1] = c[n_poles + 2] = c[n_poles + 3] = make_double2(0.0, 0.0);
-            ce[n_poles + 1] = ce[n_poles + 2] = make_double2(0.25 * Re * Re, 0.0);
-            ce[n_poles + 3] = make_double2(-0.5 * Re * Re, 0.0);
+            const int32_t q = npl + 1;
+            z[q] = make_double2(Re, 0.0);
+            z[q + 1] = make_double2(-Re, 0.0);
+            z[q + 2] = make_double2(0.0, Re);
+            c[q] = c[q + 1] = c[q + 2] = make_double2(0.0, 0.0);
+            ce[q] = ce[q + 1] = make_double2(0.25 * Re * Re, 0.0);
+            ce[q + 2] = make_double2(-0.5 * Re * Re, 0.0);
         }
     }
     // chunk the points to the workspace cap

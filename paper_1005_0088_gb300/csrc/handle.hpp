@@ -155,9 +155,17 @@ int check_status(ndsi_plan* h, cudaStream_t st);
 // per system).
 int run_phase(ndsi_plan* h, const Workspace& W, const SplitBuffers& SB, int phase, const double* H,
               const double* S, const double2* z, int64_t zstride, int np, cudaStream_t st);
-// rho (and e) and the per-system electron counts at per-system mu and kT (Eq. 8).
+// Subset of the contour points of Eq. 8 a call sums: the poles begin <= p < end and, when m0 is
+// set, the zeroth-moment point (all of them by default).
+struct PoleRange {
+    int32_t begin = 0, end = -1;
+    bool m0 = true;
+};
+// rho (and e) and the per-system electron counts at per-system mu and kT (Eq. 8); with a pole
+// range only that part of the sum (single-system plans, no energy density).
 int density_impl(ndsi_plan* h, const double* Hd, const double* Sd, const double* mu, const double* kT,
-                 int32_t n_poles, double* rho_d, double* ne_d, cudaStream_t st, double* e_d = nullptr);
+                 int32_t n_poles, double* rho_d, double* ne_d, cudaStream_t st, double* e_d = nullptr,
+                 const PoleRange* range = nullptr);
 // Density of states (Eq. 41) of every system on its own grid, and of a single-system plan.
 int dos_sweep_systems(ndsi_plan* h, const double* Hd, const double* Sd, const double* E, int nE, const double* eta,
                       double* D, cudaStream_t st);

@@ -35,7 +35,8 @@ EXPORTED_SYMBOLS = (
     "ndsi_mlp_forward", "ndsi_mlp_grad", "ndsi_mlp_train", "ndsi_analyze_batched",
     "ndsi_density_batched", "ndsi_graph_enable", "ndsi_graph_info", "ndsi_autotune",
     "ndsi_density_energy", "ndsi_dos", "ndsi_factors_solve", "ndsi_eigenstates", "ndsi_mu_search",
-    "ndsi_mu_search_batched", "ndsi_find_mu_batched", "ndsi_plan_check",
+    "ndsi_mu_search_batched", "ndsi_find_mu_batched", "ndsi_plan_check", "ndsi_density_poles",
+    "ndsi_pole_shard",
 )
 MU_EVAL_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.c_double, ctypes.POINTER(ctypes.c_double))
 MU_DOS_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.c_int32,
@@ -106,6 +107,10 @@ def load(path: str = LIB_PATH):
     lib.ndsi_factor_poles.argtypes = [vp, vp, vp, vp, i32, ctypes.POINTER(vp), vp]
     lib.ndsi_selinv.argtypes = [vp, vp, vp]
     lib.ndsi_density.argtypes = [vp, vp, vp, dbl, dbl, i32, vp, vp, vp]
+    lib.ndsi_density_poles.argtypes = [vp, vp, vp, dbl, dbl, i32, i32, i32, i32, vp, vp, vp]
+    lib.ndsi_density_poles.restype = ctypes.c_int
+    lib.ndsi_pole_shard.argtypes = [i32, i32, i32, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32)]
+    lib.ndsi_pole_shard.restype = ctypes.c_int
     lib.ndsi_plan_destroy.argtypes = [vp]
     lib.ndsi_plan_destroy.restype = None
     lib.ndsi_factors_destroy.argtypes = [vp]
@@ -314,6 +319,24 @@ def ndsi_density(plan: Plan, H, S, mu, kT, n_poles, rho_out, n_elec_out=None, st
     _check(load().ndsi_density(plan.handle, _ptr(H), _ptr(S), float(mu), float(kT), int(n_poles),
                                _ptr(rho_out), _ptr(n_elec_out), _stream(stream)))
     return rho_out
+
+
+def ndsi_density_poles(plan: Plan, H, S, mu, kT, n_poles, pole_begin, pole_end, with_m0, rho_out,
+                       n_elec_out=None, stream=None):
+    """One rank's share of Eq. 8: M0 (if with_m0) plus the poles pole_begin <= p < pole_end of an
+    n_poles expansion, and its Tr(rho_part S)."""
+    _check(load().ndsi_density_poles(plan.handle, _ptr(H), _ptr(S), float(mu), float(kT), int(n_poles),
+                                     int(pole_begin), int(pole_end), int(bool(with_m0)), _ptr(rho_out),
+                                     _ptr(n_elec_out), _stream(stream)))
+    return rho_out
+
+
+def ndsi_pole_shard(n_poles, rank, world):
+    """(pole_begin, pole_end, with_m0) of `rank` among `world` processes (host only)."""
+    b, e, m = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+    _check(load().ndsi_pole_shard(int(n_poles), int(rank), int(world), ctypes.byref(b), ctypes.byref(e),
+                                  ctypes.byref(m)))
+    return b.value, e.value, bool(m.value)
 
 
 def ndsi_density_energy(plan: Plan, H, S, mu, kT, n_poles, rho_out, e_out, n_elec_out=None, stream=None):
