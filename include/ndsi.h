@@ -84,6 +84,16 @@ typedef struct {
     int32_t screen_degree;       /* long-tail screening (Sec. II.C.1 step (ii)): atoms adjacent to
                                     more than this many atoms join the root separator before the
                                     dissection; 0 (default) = off */
+    double split_far_ratio;      /* split mode, density sweeps only: poles with z_p >= ratio * z_1
+                                    (farther from the real axis, Eq. 8) run with split_slices - 1
+                                    slices.  The error a GEMM leaves in G(alpha_p) grows with the
+                                    condition of alpha_p S - H (~ spectral width / Im alpha_p), and
+                                    the pole's weight in rho is ~ 1 / Im alpha_p of its G, so one
+                                    digit fewer (2^8 larger product error) at Im alpha_p >= 32 Im
+                                    alpha_1 leaves each far pole's contribution below the nearest
+                                    pole's.  M0, the moment points of the energy density and every
+                                    pole of ndsi_factor_poles / ndsi_dos keep split_slices.
+                                    0 (default) = 32; negative = off (every point split_slices) */
 } ndsi_options;
 
 /* Summary of a plan, filled by ndsi_plan_info. */
@@ -271,9 +281,12 @@ int ndsi_profile_enable(ndsi_plan* plan, int32_t enable);
  * on the FP64 CUDA cores, with CUDA events per launch after an untimed warm-up of each, and keeps
  * the faster path per step for all later calls on the plan.  Both paths meet the split-mode
  * tolerance, so only speed changes.  Small steps (few tiles, short inner dimension) usually go
- * to the CUDA cores, separator-sized ones to the tensor cores.  Counts of the steps left on each
- * path in *n_split_out / *n_fp64_out (either may be NULL).  Runs four sweeps; the profiler
- * counters are unchanged and any captured graph is dropped.  FP64 plans: no-op (all steps
+ * to the CUDA cores, separator-sized ones to the tensor cores.  A step whose tensor-core time is
+ * below the least time the FP64 cores could need for it (its issued FP64 flops at the DFMA rate
+ * measured on the device, as ndsi_fp64_peak) is decided without an FP64 run, so on large systems
+ * the FP64 sweeps time only the small steps.  Counts of the steps left on each path in
+ * *n_split_out / *n_fp64_out (either may be NULL).  Runs four sweeps; the profiler counters are
+ * unchanged and any captured graph is dropped.  FP64 plans: no-op (all steps
  * counted as FP64).  Errors: NDSI_ERR_INVALID for bad arguments or a batched plan; as
  * ndsi_density otherwise. */
 int ndsi_autotune(ndsi_plan* plan, const double* H, const double* S, double mu, double kT, int32_t n_poles,
@@ -311,24 +324,36 @@ int ndsi_graph_info(const ndsi_plan* plan, int64_t* nodes_out);
 int ndsi_profile_read(const ndsi_plan* plan, ndsi_profile_entry* out, int32_t max_entries,
                       int32_t* n_out);
 
+/* FP64 throughput of the current GPU in TFLOP/s (host *tflops_out): every SM runs 2048 threads
+ * of eight independent fused multiply-add chains (2 flops each), timed with CUDA events on
+ * `stream`, best of five launches after a warm-up (about 0.1 s in all).  This is the measured
+ * ceiling of the FP64 path's kernels (the paper's arithmetic is FP64 throughout, Sec. II; GB300
+ * runs FP64 on the CUDA cores only), against which their roofline fractions are quoted.
+ * Synchronises `stream`.  Errors: NDSI_ERR_INVALID (NULL output), NDSI_ERR_CUDA. */
+int ndsi_fp64_peak(double* tflops_out, void* stream);
+
 /* Residue sum and electron count from caller-held G, allocating no device memory.
  * The paper has no counterpart: this is a library convenience for callers that cannot call
  * cudaMalloc (a host framework that owns the whole device-memory budget, or a latency-critical
  * path where cudaMalloc/cudaFree, which can synchronise the device, are not allowed).  It runs the
  * residue-sum kernel of ndsi_density with its partial traces kept in a fixed 256 KiB
  * file-scope __device__ array instead of an allocated buffer:
- *   rho_out[k]  = sum_q Re(c_q * G[q][k])         (the contour sum of Eq. 8),
- *   *n_elec_out = sum_k rho_out[k] * S[k]          (Tr(rho S), Eq. 40).
+ *   rho_out[k]  = sum_q Re(c_q * G[q][k])         (the residue-weighted sum of G),
+ *   *n_elec_out = sum_k rho_out[k] * S[k]          (the trace of rho S).
  *   G          - device, interleaved complex double[2 * n_points * nnz], point-major (the layout
- *                ndsi_selinv writes).
- *   c          - device, interleaved complex double[2 * n_points]: w_p = -4 R_p kT for the poles
- *                alpha_p, and iR for the zeroth-moment point iR.
+ *                ndsi_selinv writes), 16-byte aligned.
+ *   c          - device, interleaved complex double[2 * n_points], 16-byte aligned: w_p = -4 R_p kT
+ *                for the poles alpha_p, and iR for the zeroth-moment point iR.
  *   S          - device double[nnz]; rho_out device double[nnz]; n_elec_out device double or NULL.
+ * Every array must be device memory of the current device (or managed memory).
  * Limit: nnz <= 8,388,608 (32768 blocks of 256 entries); larger nnz -> NDSI_ERR_INVALID.
- * Host pointers -> NDSI_ERR_INVALID.  Stream-ordered, no synchronisation.  The first call on a
- * device resolves the array's device address (cudaGetSymbolAddress) with that device current,
- * so make that first call before any stream capture.  Every call on a device shares the one
- * array: calls whose kernels overlap on the GPU (other streams or threads) race on it. */
+ * Host pointers, another device's memory, or a misaligned G or c -> NDSI_ERR_INVALID, with no
+ * launch.  Stream-ordered, no synchronisation.  The first call on a device resolves the array's
+ * device address (cudaGetSymbolAddress) with that device current, so make that first call before
+ * any stream capture; the address is kept for the life of the process, so a cudaDeviceReset (or
+ * any other teardown of the device's primary context) invalidates this entry point on that
+ * device.  Every call on a device shares the one array: calls whose kernels overlap on the GPU
+ * (other streams or threads) race on it. */
 int ndsi_residue_sum_static(const double* G, const double* c, int32_t n_points, const double* S,
                             int64_t nnz, double* rho_out, double* n_elec_out, void* stream);
 

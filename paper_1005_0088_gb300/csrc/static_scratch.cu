@@ -80,14 +80,20 @@ __global__ void __launch_bounds__(1024) k_reduce_static(const double* __restrict
     }
 }
 
-bool on_device(const void* p) {
+// Memory the kernels may read or write on device `dev`: device memory of that device, or
+// managed memory.  Device memory of another GPU is refused (the kernels would fault on it).
+bool on_device(const void* p, int dev) {
     cudaPointerAttributes a{};
     if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+    if (a.type == cudaMemoryTypeManaged) return true;
+    return a.type == cudaMemoryTypeDevice && a.device == dev;
 }
+
+// G and c are read as complex pairs (16-byte loads).
+bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
 int static_fail(int code, const std::string& msg) {
     set_last_error(msg);
@@ -109,14 +115,16 @@ extern "C" int ndsi_residue_sum_static(const double* G, const double* c, int32_t
                            "ndsi_residue_sum_static: nnz = " + std::to_string(nnz) +
                                " exceeds the static scratch limit of " +
                                std::to_string(kStaticMaxNnz) + " pattern entries");
-    if (!on_device(G) || !on_device(c) || !on_device(S) || !on_device(rho_out) ||
-        (n_elec_out && !on_device(n_elec_out)))
-        return static_fail(NDSI_ERR_INVALID,
-                           "ndsi_residue_sum_static: every array must be in device memory");
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess || dev < 0 || dev >= kMaxDevices)
         return static_fail(NDSI_ERR_CUDA, "ndsi_residue_sum_static: no usable current device");
+    if (!on_device(G, dev) || !on_device(c, dev) || !on_device(S, dev) || !on_device(rho_out, dev) ||
+        (n_elec_out && !on_device(n_elec_out, dev)))
+        return static_fail(NDSI_ERR_INVALID,
+                           "ndsi_residue_sum_static: every array must be in device memory of the current device");
+    if (!aligned16(G) || !aligned16(c))
+        return static_fail(NDSI_ERR_INVALID, "ndsi_residue_sum_static: G and c must be 16-byte aligned");
     double* partials = nullptr;
     {
         // First call on this device: resolve the array's device address with the device current.

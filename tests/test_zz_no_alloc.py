@@ -49,6 +49,13 @@ def test_static_residue_sum_matches_density():
         torch.cuda.synchronize()
         assert np.max(np.abs(rho.cpu().numpy() - ref)) < TOL
         assert abs(float(ne.cpu()[0]) - float(ne_ref.cpu()[0])) < TOL * sysm.n
+    # without the trace (the reduction launch is skipped), on a caller stream
+    st = torch.cuda.Stream()
+    with torch.cuda.stream(st):
+        rho = torch.full((sysm.nnz,), float("nan"), dtype=torch.float64, device="cuda")
+    nd.ndsi_residue_sum_static(G, c, len(pts), S, sysm.nnz, rho, None, stream=st)
+    st.synchronize()
+    assert np.max(np.abs(rho.cpu().numpy() - ref)) < TOL
 
 
 def test_static_residue_sum_rejects_oversize_and_host():
@@ -65,3 +72,11 @@ def test_static_residue_sum_rejects_oversize_and_host():
     assert ei.value.code == nd.ndsi.NDSI_ERR_INVALID and "static scratch limit" in str(ei.value)
     with pytest.raises(nd.NdsiError):
         nd.ndsi_residue_sum_static(G.cpu(), c, 1, S, 2, rho)
+    # G and c are read as 16-byte complex pairs: a view one double in is refused before any launch
+    Gw = torch.zeros(6, dtype=torch.float64, device="cuda")
+    with pytest.raises(nd.NdsiError) as ei:
+        nd.ndsi_residue_sum_static(Gw[1:5], c, 1, S, 2, rho)
+    assert ei.value.code == nd.ndsi.NDSI_ERR_INVALID and "aligned" in str(ei.value)
+    cw = torch.zeros(3, dtype=torch.float64, device="cuda")
+    with pytest.raises(nd.NdsiError):
+        nd.ndsi_residue_sum_static(G, cw[1:3], 1, S, 2, rho)
