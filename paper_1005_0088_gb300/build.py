@@ -17,7 +17,7 @@ LIB = os.path.join(PKG, "libndsi.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 CU_SOURCES = ["kernels.cu", "api.cu", "api_mu.cu", "api_solve.cu", "static_scratch.cu", "split_gemm.cu", "mlp.cu",
-              "solve.cu"]
+              "solve.cu", "peak.cu"]
 CPP_SOURCES = ["analyze.cpp", "mu_search.cpp", "plan_check.cpp", "small_eig.cpp"]
 HEADERS = ["plan.hpp", "kernels.cuh", "split_gemm.cuh", "solve.cuh", "handle.hpp", "small_eig.hpp"]
 

@@ -83,6 +83,23 @@ bool is_device_ptr(const void* p) {
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+// Device memory of a GPU other than the current one: the kernels cannot use it (and staging
+// it as host memory would be wrong too), so the entry points refuse it.
+bool foreign_device_ptr(const void* p) {
+    if (!p) return false;
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice && a.device != dev;
+}
+
 int alloc_workspace(Workspace& W, const Plan& P, int32_t np) {
     if (W.np_cap >= np && W.fronts) return NDSI_OK;
     if (W.fronts) cudaFree(W.fronts);
@@ -170,9 +187,13 @@ void prof_resolve(Profiler& pf) {
 }
 
 int run_phase(ndsi_plan* h, const Workspace& W, const SplitBuffers& SB, int phase, const double* H,
-              const double* S, const double2* z, int64_t zstride, int np, cudaStream_t st) {
+              const double* S, const double2* z, int64_t zstride, int np, cudaStream_t st, int slices) {
     const Plan& P = h->P;
     const bool split = P.opt.precision == NDSI_PREC_SPLIT;
+    // digits per operand of this batch of points (the slice buffers keep the layout of
+    // opt.split_slices; a smaller count fills and reads only the leading digits)
+    const int ns = slices > 0 ? slices : P.opt.split_slices;
+    const double pair_frac = split ? static_cast<double>(ns * (ns + 1)) / (P.opt.split_slices * (P.opt.split_slices + 1)) : 1.0;
     for (size_t li = 0; li < P.launches.size(); ++li) {
         const Launch& l = P.launches[li];
         if (l.phase != phase) continue;
@@ -186,19 +207,18 @@ int run_phase(ndsi_plan* h, const Workspace& W, const SplitBuffers& SB, int phas
             const std::string tg = std::string(tag_name(l.tag)) +
                                    (h->prof.by_level ? ":L" + std::to_string(l.level) : std::string());
             e = timed(h->prof, "slice:" + tg, 0.0, h->SP.slice_bytes[si] * np, st, [&]() {
-                return split_slice_step(l, h->T.gemm_items, h->SP.d_items, h->SP.d_blocks, step, SB,
-                                        P.opt.split_slices, bufs[l.bufA], strides[l.bufA], bufs[l.bufB],
-                                        strides[l.bufB], np, st);
+                return split_slice_step(l, h->T.gemm_items, h->SP.d_items, h->SP.d_blocks, step, SB, ns,
+                                        bufs[l.bufA], strides[l.bufA], bufs[l.bufB], strides[l.bufB], np, st);
             });
             if (e == cudaSuccess)
                 e = timed(
                     h->prof, "gemm_split:" + tg, l.flops * np, l.bytes * np, st,
                     [&]() {
-                        return split_mma_step(l, si, h->T.gemm_items, h->SP.d_items, h->SP.d_tiles, step, SB,
-                                              P.opt.split_slices, const_cast<double2*>(bufs[l.bufC]),
-                                              strides[l.bufC], np, h->T.status, st);
+                        return split_mma_step(l, si, h->T.gemm_items, h->SP.d_items, h->SP.d_tiles, step, SB, ns,
+                                              const_cast<double2*>(bufs[l.bufC]), strides[l.bufC], np,
+                                              h->T.status, st);
                     },
-                    h->SP.tensor_flops[si] * np);
+                    h->SP.tensor_flops[si] * np * pair_frac);
         } else {
             e = timed(h->prof,
                       family_of(l) + (h->prof.by_level && l.kind == L_GEMM ? ":L" + std::to_string(l.level) : std::string()),
@@ -240,6 +260,8 @@ int ensure_stage(ndsi_plan* h, int64_t doubles) {
 int device_inputs(ndsi_plan* h, const double* H, const double* S, const double** Hd,
                   const double** Sd, cudaStream_t st) {
     const int64_t nnz = h->P.nnz;
+    if (foreign_device_ptr(H) || foreign_device_ptr(S))
+        return fail(NDSI_ERR_INVALID, "H or S is device memory of another GPU");
     const bool hd = is_device_ptr(H), sd = is_device_ptr(S);
     if (!hd || !sd) {
         int rc = ensure_stage(h, 3 * nnz + 8);
@@ -324,7 +346,7 @@ void setup_split(ndsi_plan* h, const ndsi_options& o) {
         S.step_of_launch[li] = k++;
     }
 }
-int sweep(ndsi_plan* h, const double* Hd, const double* Sd, int32_t nq, int32_t chunk,
+int sweep(ndsi_plan* h, const double* Hd, const double* Sd, int32_t nq, int32_t n_near, int32_t chunk,
           const std::vector<int>& part_off, double* rho_d, double* ne_d, double* e_d, cudaStream_t st);
 
 }  // namespace ndsi
@@ -345,6 +367,7 @@ void ndsi_default_options(ndsi_options* opt) {
     opt->split_bands = 0;
     opt->cell[0] = opt->cell[1] = opt->cell[2] = 0.0;
     opt->screen_degree = 0;
+    opt->split_far_ratio = 0.0;
 }
 
 int ndsi_poles(int32_t M, double* z_out, double* R_out) {
@@ -392,8 +415,14 @@ int ndsi_analyze(const ndsi_pattern* pat, int32_t n_atoms, const double* centers
         }
         if (o.split_slices == 0) o.split_slices = auto_slices(h->P);
         if (o.split_bands == 0) o.split_bands = auto_bands(h->P);
+        if (!std::isfinite(o.split_far_ratio) || (o.split_far_ratio > 0 && o.split_far_ratio < 1)) {
+            delete h;
+            return fail(NDSI_ERR_INVALID, "ndsi_analyze: split_far_ratio must be 0, negative or >= 1");
+        }
+        if (o.split_far_ratio == 0) o.split_far_ratio = kSplitFarRatio;
         h->P.opt.split_slices = o.split_slices;
         h->P.opt.split_bands = o.split_bands;
+        h->P.opt.split_far_ratio = o.split_far_ratio;
         setup_split(h, o);
     }
     *plan_out = h;
@@ -434,8 +463,14 @@ int ndsi_analyze_batched(int32_t n_systems, const ndsi_pattern* pats, const int3
             }
             if (o.split_slices == 0) o.split_slices = auto_slices(h->P);
             if (o.split_bands == 0) o.split_bands = auto_bands(h->P);
+            if (!std::isfinite(o.split_far_ratio) || (o.split_far_ratio > 0 && o.split_far_ratio < 1)) {
+                delete h;
+                return fail(NDSI_ERR_INVALID, "ndsi_analyze_batched: split_far_ratio must be 0, negative or >= 1");
+            }
+            if (o.split_far_ratio == 0) o.split_far_ratio = kSplitFarRatio;
             h->P.opt.split_slices = o.split_slices;
             h->P.opt.split_bands = o.split_bands;
+            h->P.opt.split_far_ratio = o.split_far_ratio;
             setup_split(h, o);
         }
         *plan_out = h;
@@ -452,6 +487,8 @@ int ndsi_density_batched(ndsi_plan* h, const double* H, const double* S, const d
     const int32_t ns = h->P.n_systems;
     for (int32_t i = 0; i < ns; ++i)
         if (!(kT[i] > 0) || !std::isfinite(mu[i])) return fail(NDSI_ERR_INVALID, "ndsi_density_batched: bad mu/kT");
+    if (foreign_device_ptr(rho_out) || foreign_device_ptr(n_elec_out))
+        return fail(NDSI_ERR_INVALID, "ndsi_density_batched: an output is device memory of another GPU");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     int rc = upload_tables(h);
     if (rc) return rc;
@@ -603,6 +640,8 @@ int ndsi_selinv(ndsi_factors* f, double* G_out, void* stream) {
 
 static int density_entry(ndsi_plan* h, const double* H, const double* S, double mu, double kT, int32_t n_poles,
                          const PoleRange* range, double* rho_out, double* n_elec_out, void* stream) {
+    if (foreign_device_ptr(rho_out) || foreign_device_ptr(n_elec_out))
+        return fail(NDSI_ERR_INVALID, "ndsi_density: an output is device memory of another GPU");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     int rc = upload_tables(h);
     if (rc) return rc;
@@ -670,6 +709,8 @@ int ndsi_density_energy(ndsi_plan* h, const double* H, const double* S, double m
     if (!h || !H || !S || !rho_out || !e_out || n_poles < 1 || !(kT > 0) || !std::isfinite(mu))
         return fail(NDSI_ERR_INVALID, "ndsi_density_energy: invalid argument");
     if (h->P.n_systems != 1) return fail(NDSI_ERR_INVALID, "ndsi_density_energy: batched plan");
+    if (foreign_device_ptr(rho_out) || foreign_device_ptr(e_out) || foreign_device_ptr(n_elec_out))
+        return fail(NDSI_ERR_INVALID, "ndsi_density_energy: an output is device memory of another GPU");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     int rc = upload_tables(h);
     if (rc) return rc;
@@ -741,9 +782,17 @@ int density_impl(ndsi_plan* h, const double* Hd, const double* Sd, const double*
         if (rc) return fail(rc, err);
         h->pole_M = n_poles;
     }
-    // points of this call: poles pb..pe-1, then M0 (when summed), then the three moment points
-    const int32_t npl = pe - pb;
-    const int32_t nq = npl + (with_m0 ? 1 : 0) + (e_d ? 3 : 0);
+    // Points of this call, in two groups: first those that need every slice of a split plan
+    // (poles pb..pf-1 near the real axis, M0, the three moment points), then the far poles pf..pe-1,
+    // which a split plan runs with one slice fewer (ndsi_options.split_far_ratio; pf = pe when the
+    // plan is FP64, the option is off or no slice can be dropped).
+    int32_t pf = pe;
+    if (h->P.opt.precision == NDSI_PREC_SPLIT && h->P.opt.split_far_ratio > 0 && h->P.opt.split_slices > 4) {
+        pf = pb;
+        while (pf < pe && h->pole_z[pf] < h->P.opt.split_far_ratio * h->pole_z[0]) ++pf;
+    }
+    const int32_t n_near = (pf - pb) + (with_m0 ? 1 : 0) + (e_d ? 3 : 0);
+    const int32_t nq = n_near + (pe - pf);
     std::vector<double2> zq(static_cast<size_t>(ns) * nq), cq(static_cast<size_t>(ns) * nq),
         ceq(static_cast<size_t>(ns) * nq, make_double2(0.0, 0.0));
     const double R = h->P.opt.m0_radius;
@@ -753,27 +802,30 @@ int density_impl(ndsi_plan* h, const double* Hd, const double* Sd, const double*
         double2* ce = ceq.data() + static_cast<size_t>(sy) * nq;
         double kappa = 0.0;
         for (int32_t p = 0; p < n_poles; ++p) kappa += 4.0 * kT[sy] * h->pole_R[p];
-        for (int32_t p = pb; p < pe; ++p) {
-            const int32_t q = p - pb;
+        auto put_pole = [&](int32_t q, int32_t p) {
             z[q] = make_double2(mu[sy], h->pole_z[p] * kT[sy]);
             c[q] = make_double2(-4.0 * h->pole_R[p] * kT[sy], 0.0);
             // -4 R_p kT alpha_p: Re(ce G) = -4 R_p kT Re(alpha_p G)
             ce[q] = make_double2(-4.0 * h->pole_R[p] * kT[sy] * mu[sy], -4.0 * h->pole_R[p] * kT[sy] * z[q].y);
-        }
+        };
+        int32_t q = 0;
+        for (int32_t p = pb; p < pf; ++p) put_pole(q++, p);
         if (with_m0) {
-            z[npl] = make_double2(0.0, R);
-            c[npl] = make_double2(0.0, R);
-            ce[npl] = make_double2(0.0, kappa * R);  // kappa M0, M0 = Re(i R G(i R))
+            z[q] = make_double2(0.0, R);
+            c[q] = make_double2(0.0, R);
+            ce[q] = make_double2(0.0, kappa * R);  // kappa M0, M0 = Re(i R G(i R))
+            ++q;
         }
         if (e_d) {
-            const int32_t q = npl + 1;
             z[q] = make_double2(Re, 0.0);
             z[q + 1] = make_double2(-Re, 0.0);
             z[q + 2] = make_double2(0.0, Re);
             c[q] = c[q + 1] = c[q + 2] = make_double2(0.0, 0.0);
             ce[q] = ce[q + 1] = make_double2(0.25 * Re * Re, 0.0);
             ce[q + 2] = make_double2(-0.5 * Re * Re, 0.0);
+            q += 3;
         }
+        for (int32_t p = pf; p < pe; ++p) put_pole(q++, p);
     }
     // chunk the points to the workspace cap
     const int64_t per_pole = bytes_per_pole(h);
@@ -826,13 +878,14 @@ int density_impl(ndsi_plan* h, const double* Hd, const double* Sd, const double*
         const std::vector<const void*> key = {Hd, Sd, rho_d, ne_d, e_d, h->W.fronts, h->W.scr, h->SB.sliceA,
                                               h->SB.sliceB, h->cw, h->zw, h->cew, h->partials,
                                               reinterpret_cast<const void*>(static_cast<intptr_t>(nq)),
-                                              reinterpret_cast<const void*>(static_cast<intptr_t>(chunk))};
+                                              reinterpret_cast<const void*>(static_cast<intptr_t>(chunk)),
+                                              reinterpret_cast<const void*>(static_cast<intptr_t>(n_near))};
         if (!h->graph || h->graph_key != key) {
             if (h->graph) cudaGraphExecDestroy(h->graph);
             h->graph = nullptr;
             if (!h->cap_stream) NDSI_CK(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
             NDSI_CK(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
-            rc = sweep(h, Hd, Sd, nq, chunk, part_off, rho_d, ne_d, e_d, h->cap_stream);
+            rc = sweep(h, Hd, Sd, nq, n_near, chunk, part_off, rho_d, ne_d, e_d, h->cap_stream);
             cudaGraph_t g = nullptr;
             const cudaError_t ec = cudaStreamEndCapture(h->cap_stream, &g);
             if (rc || ec != cudaSuccess) {
@@ -851,22 +904,25 @@ int density_impl(ndsi_plan* h, const double* Hd, const double* Sd, const double*
         NDSI_CK(cudaGraphLaunch(h->graph, st));
         return check_status(h, st);
     }
-    rc = sweep(h, Hd, Sd, nq, chunk, part_off, rho_d, ne_d, e_d, st);
+    rc = sweep(h, Hd, Sd, nq, n_near, chunk, part_off, rho_d, ne_d, e_d, st);
     if (rc) return rc;
     return check_status(h, st);
 }
 
 // One density sweep over all points, chunked: factor, selected inversion and residue sum per
-// chunk, then the per-system electron counts.  Only stream-ordered work: it is also the body of
-// the captured graph.
-int sweep(ndsi_plan* h, const double* Hd, const double* Sd, int32_t nq, int32_t chunk,
+// chunk, then the per-system electron counts.  Points [0, n_near) run with the plan's slice
+// count, the far poles [n_near, nq) of a split plan with one slice fewer; no chunk spans both.
+// Only stream-ordered work: it is also the body of the captured graph.
+int sweep(ndsi_plan* h, const double* Hd, const double* Sd, int32_t nq, int32_t n_near, int32_t chunk,
           const std::vector<int>& part_off, double* rho_d, double* ne_d, double* e_d, cudaStream_t st) {
     int rc;
     const int32_t ns = h->P.n_systems;
-    for (int32_t q0 = 0; q0 < nq; q0 += chunk) {
-        const int32_t np = std::min(chunk, nq - q0);
-        rc = run_phase(h, h->W, h->SB, 0, Hd, Sd, h->zw + q0, nq, np, st);
-        if (!rc) rc = run_phase(h, h->W, h->SB, 1, Hd, Sd, h->zw + q0, nq, np, st);
+    for (int32_t q0 = 0; q0 < nq;) {
+        const bool far = q0 >= n_near;
+        const int32_t np = std::min(chunk, (far ? nq : n_near) - q0);
+        const int slices = far ? h->P.opt.split_slices - 1 : 0;
+        rc = run_phase(h, h->W, h->SB, 0, Hd, Sd, h->zw + q0, nq, np, st, slices);
+        if (!rc) rc = run_phase(h, h->W, h->SB, 1, Hd, Sd, h->zw + q0, nq, np, st, slices);
         if (rc) return rc;
         const int last = q0 + np >= nq;
         for (int32_t sy = 0; sy < ns; ++sy) {
@@ -882,6 +938,7 @@ int sweep(ndsi_plan* h, const double* Hd, const double* Sd, int32_t nq, int32_t 
                                              e_d, q0 > 0 ? 1 : 0, 0, nullptr, st, k0, cnt);
                 }));
         }
+        q0 += np;
     }
     for (int32_t sy = 0; sy < ns; ++sy) {
         const int nblk = part_off[sy + 1] - part_off[sy];
@@ -1020,20 +1077,41 @@ int ndsi_autotune(ndsi_plan* h, const double* H, const double* S, double mu, dou
     // with every eligible GEMM on the FP64 CUDA cores (each after an untimed warm-up sweep); each
     // launch then keeps the faster of the two.  Both choices meet the split tolerance, so the
     // result only changes speed.  The profiler's own counters are left as they were.
+    // A step whose tensor-core time is already below the least time the FP64 path could take
+    // (its issued FP64 flops, 3 of every 4 counted, at the measured DFMA rate) is decided without
+    // running it on the FP64 cores: only the other steps are timed there, so the FP64 passes cost
+    // about as much as tensor-core ones on large systems.
+    double peak = 0.0;
+    rc = fp64_rate(st, &peak);
+    if (rc) return rc;
     Profiler saved = h->prof;
     h->prof.pending.clear();
     h->prof.used = 0;
     h->prof.on = true;
     std::vector<double> t_split(nl, 0.0), t_fp64(nl, 0.0);
-    for (int pass = 0; pass < 4 && !rc; ++pass) {
-        const bool on_tensor = (pass % 2) == 0;
-        std::fill(h->SP.use_split.begin(), h->SP.use_split.end(), on_tensor ? 1 : 0);
-        h->prof.per_launch = pass < 2 ? nullptr : (on_tensor ? &t_split : &t_fp64);
+    std::vector<char> decided(nl, 0);
+    for (int pass = 0; pass < 2 && !rc; ++pass) {
+        std::fill(h->SP.use_split.begin(), h->SP.use_split.end(), 1);
+        h->prof.per_launch = pass == 0 ? nullptr : &t_split;
+        rc = density_impl(h, Hd, Sd, &mu, &kT, n_poles, rho_d, ne_d, st);
+    }
+    const double points = static_cast<double>(n_poles) + 1.0;
+    for (size_t li = 0; li < nl && !rc; ++li) {
+        const Launch& l = h->P.launches[li];
+        if (!split_eligible(l)) continue;
+        const double fp64_min_ms = 0.75 * l.flops * points / (peak * 1e12) * 1e3;
+        decided[li] = t_split[li] <= fp64_min_ms ? 1 : 0;
+    }
+    for (int pass = 0; pass < 2 && !rc; ++pass) {
+        for (size_t li = 0; li < nl; ++li) h->SP.use_split[li] = decided[li];
+        h->prof.per_launch = pass == 0 ? nullptr : &t_fp64;
         rc = density_impl(h, Hd, Sd, &mu, &kT, n_poles, rho_d, ne_d, st);
     }
     h->prof.per_launch = nullptr;
     for (size_t li = 0; li < nl; ++li)
-        h->SP.use_split[li] = !rc && split_eligible(h->P.launches[li]) ? (t_split[li] <= t_fp64[li] ? 1 : 0) : 1;
+        h->SP.use_split[li] = !rc && split_eligible(h->P.launches[li])
+                                  ? (decided[li] || t_split[li] <= t_fp64[li] ? 1 : 0)
+                                  : 1;
     saved.pool = h->prof.pool;  // events created meanwhile stay owned by the plan
     h->prof = saved;
     h->prof.pending.clear();

@@ -142,6 +142,7 @@ inline size_t align256(size_t x) { return (x + 255) & ~static_cast<size_t>(255);
 // Plan tables and workspaces.
 int upload_tables(ndsi_plan* h);
 bool is_device_ptr(const void* p);
+bool foreign_device_ptr(const void* p);
 int alloc_workspace(Workspace& W, const Plan& P, int32_t np);
 void free_workspace(Workspace& W);
 int64_t bytes_per_pole(const ndsi_plan* h);
@@ -154,7 +155,7 @@ int check_status(ndsi_plan* h, cudaStream_t st);
 // Every launch of one phase (0 factor, 1 selected inversion) for np points of z (stride zstride
 // per system).
 int run_phase(ndsi_plan* h, const Workspace& W, const SplitBuffers& SB, int phase, const double* H,
-              const double* S, const double2* z, int64_t zstride, int np, cudaStream_t st);
+              const double* S, const double2* z, int64_t zstride, int np, cudaStream_t st, int slices = 0);
 // Subset of the contour points of Eq. 8 a call sums: the poles begin <= p < end and, when m0 is
 // set, the zeroth-moment point (all of them by default).
 struct PoleRange {
@@ -171,6 +172,9 @@ int dos_sweep_systems(ndsi_plan* h, const double* Hd, const double* Sd, const do
                       double* D, cudaStream_t st);
 int dos_sweep(ndsi_plan* h, const double* Hd, const double* Sd, const double* E, int nE, double eta, double* D,
               cudaStream_t st);
+
+// Measured FP64 (DFMA) throughput of the current device in TFLOP/s (peak.cu).
+int fp64_rate(cudaStream_t st, double* tflops_out);
 
 // Device buffer that frees itself (scratch of the solve and eigensolver entry points).
 struct DevBuf {

@@ -26,6 +26,9 @@ constexpr int kSplitChunkKB = NDSI_SPLIT_CHUNK_KB;
 constexpr int kSplitChunkKB = 8;   // stages per exact chunk (256 stacked-K elements)
 #endif
 constexpr int kSplitMaxSlices = 7;
+// Default of ndsi_options.split_far_ratio: density-sweep poles with z_p >= 32 z_1 use one slice
+// fewer (32^2 ~ 2^10 covers the 2^8 larger product error of the shorter expansion).
+constexpr double kSplitFarRatio = 32.0;
 
 // Where an item's slices and exponents live inside one pole's block of the step buffers.
 struct SplitItem {

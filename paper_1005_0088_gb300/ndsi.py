@@ -36,7 +36,7 @@ EXPORTED_SYMBOLS = (
     "ndsi_density_batched", "ndsi_graph_enable", "ndsi_graph_info", "ndsi_autotune",
     "ndsi_density_energy", "ndsi_dos", "ndsi_factors_solve", "ndsi_eigenstates", "ndsi_mu_search",
     "ndsi_mu_search_batched", "ndsi_find_mu_batched", "ndsi_plan_check", "ndsi_density_poles",
-    "ndsi_pole_shard",
+    "ndsi_pole_shard", "ndsi_fp64_peak",
 )
 MU_EVAL_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.c_double, ctypes.POINTER(ctypes.c_double))
 MU_DOS_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.c_int32,
@@ -66,7 +66,8 @@ class ndsi_options(ctypes.Structure):
                 ("split_slices", ctypes.c_int32), ("block", ctypes.c_int32),
                 ("m0_radius", ctypes.c_double), ("max_workspace_bytes", ctypes.c_int64),
                 ("outer_block", ctypes.c_int32), ("split_bands", ctypes.c_int32),
-                ("cell", ctypes.c_double * 3), ("screen_degree", ctypes.c_int32)]
+                ("cell", ctypes.c_double * 3), ("screen_degree", ctypes.c_int32),
+                ("split_far_ratio", ctypes.c_double)]
 
 
 class ndsi_plan_summary(ctypes.Structure):
@@ -111,6 +112,8 @@ def load(path: str = LIB_PATH):
     lib.ndsi_density_poles.restype = ctypes.c_int
     lib.ndsi_pole_shard.argtypes = [i32, i32, i32, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32)]
     lib.ndsi_pole_shard.restype = ctypes.c_int
+    lib.ndsi_fp64_peak.argtypes = [ctypes.POINTER(dbl), vp]
+    lib.ndsi_fp64_peak.restype = ctypes.c_int
     lib.ndsi_plan_destroy.argtypes = [vp]
     lib.ndsi_plan_destroy.restype = None
     lib.ndsi_factors_destroy.argtypes = [vp]
@@ -337,6 +340,13 @@ def ndsi_pole_shard(n_poles, rank, world):
     _check(load().ndsi_pole_shard(int(n_poles), int(rank), int(world), ctypes.byref(b), ctypes.byref(e),
                                   ctypes.byref(m)))
     return b.value, e.value, bool(m.value)
+
+
+def ndsi_fp64_peak(stream=None):
+    """Measured FP64 (DFMA) throughput of the current GPU in TFLOP/s."""
+    out = ctypes.c_double()
+    _check(load().ndsi_fp64_peak(ctypes.byref(out), _stream(stream)))
+    return out.value
 
 
 def ndsi_density_energy(plan: Plan, H, S, mu, kT, n_poles, rho_out, e_out, n_elec_out=None, stream=None):
