@@ -736,10 +736,11 @@ __global__ void __launch_bounds__(kThreads, 1)
     uint64_t* full = bars;            // [2]
     uint64_t* empty = bars + 2;       // [2]
     uint64_t* chunk_full = bars + 4;
-    uint64_t* tmem_free = bars + 5;
     uint64_t* mma_done = bars + 6;
     uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(bars + 8);
     volatile int* abort = reinterpret_cast<volatile int*>(bars + 9);
+    uint64_t* tmem_free = bars + 10;  // [BANDS]: band b of the last chunk has been read out
+    static_assert(BANDS <= 6, "band barriers overlap the exponent tables");
     int* sm_ea = reinterpret_cast<int*>(bars + 16);  // [128] exponents of the current tile's rows
     int* sm_eb = sm_ea + 128;                         // [64] exponents of its complex columns
 
@@ -756,7 +757,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         mbar_init(&empty[0], 1);
         mbar_init(&empty[1], 1);
         mbar_init(chunk_full, 1);
-        mbar_init(tmem_free, kEpiWarps);
+#pragma unroll
+        for (int b = 0; b < BANDS; ++b) mbar_init(&tmem_free[b], kEpiWarps);
         mbar_init(mma_done, 1);
         *abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -820,12 +822,19 @@ __global__ void __launch_bounds__(kThreads, 1)
                     }
                     tc_fence_after();
                     const bool first_in_chunk = (kb % kSplitChunkKB) == 0;
-                    if (first_in_chunk && c > 0) {
-                        if (!mbar_wait(tmem_free, static_cast<uint32_t>((c - 1) & 1), abort)) {
-                            ok = false;
-                            break;
-                        }
+                    // The first K-block of a chunk overwrites the accumulators: each band waits
+                    // until the epilogue has read that band of the previous chunk (the bands are
+                    // released one by one, in the order they are issued here).
+                    const bool wait_bands = first_in_chunk && c > 0;
+                    auto band_free = [&](int band) {
+                        if (!wait_bands) return true;
+                        if (!mbar_wait(&tmem_free[band], static_cast<uint32_t>((c - 1) & 1), abort)) return false;
                         tc_fence_after();
+                        return true;
+                    };
+                    if (!band_free(BANDS - 1)) {
+                        ok = false;
+                        break;
                     }
                     // Descriptors of this stage's slice tiles: the start-address field is the low
                     // 14 bits (address >> 4), so tile t and K16 half ks are compile-time offsets
@@ -852,6 +861,10 @@ __global__ void __launch_bounds__(kThreads, 1)
                     // exact bands 0..BANDS-2: t+u = 2 .. BANDS (1-based), one scale each
 #pragma unroll
                     for (int band = 0; band < BANDS - 1; ++band) {
+                        if (!band_free(band)) {
+                            ok = false;
+                            break;
+                        }
 #pragma unroll
                         for (int t = 0; t < S; ++t) {
                             const int u = band - t;
@@ -864,6 +877,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                             }
                         }
                     }
+                    if (!ok) break;
                     umma_commit(&empty[stage]);
                     if ((kb % kSplitChunkKB) == kSplitChunkKB - 1 || kb == nkb - 1) {
                         umma_commit(chunk_full);
@@ -925,31 +939,27 @@ __global__ void __launch_bounds__(kThreads, 1)
                     break;
                 }
                 tc_fence_after();
+                // bands in the MMA warp's issue order (tail first): each band's values are loaded
+                // into registers and the band is released before the float-float additions, so
+                // the next chunk's MMAs into it can start while the other bands are read
 #pragma unroll
-                for (int band = 0; band < BANDS; ++band) {
+                for (int bi = 0; bi < BANDS; ++bi) {
+                    const int band = bi == 0 ? BANDS - 1 : bi - 1;
+                    float v[2 * CW];
 #pragma unroll
                     for (int part = 0; part < 2; ++part) {  // Re columns, then the matching Im columns
                         const uint32_t base = tmem + (static_cast<uint32_t>(32 * q) << 16) + band * NB +
                                               part * NC + cg * CW;
 #pragma unroll
-                        for (int j0 = 0; j0 + 8 <= CW; j0 += 8) {
-                            float v[8];
-                            tmem_ld8(base + j0, v);
-#pragma unroll
-                            for (int i = 0; i < 8; ++i) ff_add(hi[part * CW + j0 + i], lo[part * CW + j0 + i], v[i]);
-                        }
-                        if (CW % 8) {
-                            float v[4];
-                            tmem_ld4(base + (CW / 8) * 8, v);
-#pragma unroll
-                            for (int i = 0; i < 4; ++i)
-                                ff_add(hi[part * CW + (CW / 8) * 8 + i], lo[part * CW + (CW / 8) * 8 + i], v[i]);
-                        }
+                        for (int j0 = 0; j0 + 8 <= CW; j0 += 8) tmem_ld8(base + j0, v + part * CW + j0);
+                        if (CW % 8) tmem_ld4(base + (CW / 8) * 8, v + part * CW + (CW / 8) * 8);
                     }
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&tmem_free[band]);
+#pragma unroll
+                    for (int j = 0; j < 2 * CW; ++j) ff_add(hi[j], lo[j], v[j]);
                 }
-                tc_fence_before();
-                __syncwarp();
-                if (lane == 0) mbar_arrive(tmem_free);
             }
             if (!ok || *abort) break;
             // C = alpha * 2^e (hi + lo) + beta * C for this thread's row and 16 complex columns:
