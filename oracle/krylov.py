@@ -71,11 +71,12 @@ def krylov_threads() -> int:
     return int(_load().krylov_threads())
 
 
-def solve_columns(system, alphas, gammas, cols, tol=1e-13, max_iter=200000):
+def solve_columns(system, alphas, gammas, cols, tol=1e-13, max_iter=200000, require_converged=True):
     """x_t = (alphas[t] S - gammas[t] H)^{-1} e_{cols[t]} for every t.
 
     Returns (X complex [n_tasks, n], iterations int64 [n_tasks], true relative residuals
-    [n_tasks]).  Raises if a solve misses `tol` within max_iter iterations."""
+    [n_tasks]).  Raises if a solve misses `tol` within max_iter iterations, unless
+    require_converged is False (then the iterates reached are returned as they are)."""
     lib = _load()
     alphas = np.ascontiguousarray(np.asarray(alphas, dtype=np.complex128))
     gammas = np.ascontiguousarray(np.asarray(gammas, dtype=np.float64))
@@ -96,7 +97,7 @@ def solve_columns(system, alphas, gammas, cols, tol=1e-13, max_iter=200000):
                             ptr(res))
     if rc < 0:
         raise ValueError("krylov_columns: invalid arguments or out of memory")
-    if rc > 0:
+    if rc > 0 and require_converged:
         raise RuntimeError(f"krylov_columns: {rc} solves missed the residual target {tol:g} "
                            f"(worst {res.max():.3e})")
     return X, iters, res
