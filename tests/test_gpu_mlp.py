@@ -39,6 +39,20 @@ def test_mlp_forward_and_gradient_match_oracle():
     assert np.max(np.abs(Y.cpu().numpy() - y_ref)) < 1e-5 * max(1.0, np.max(np.abs(y_ref)))
     g = G.cpu().numpy().astype(np.float64)
     assert np.linalg.norm(g - g_ref) < 1e-5 * np.linalg.norm(g_ref)
+    # element by element: each gradient entry is a sum over the samples, so its FP32 rounding
+    # scales with the sum of the per-sample magnitudes (a small entry that is a cancellation of
+    # large per-sample terms may differ by more than 1e-5 of itself, but not of that sum)
+    scale = np.zeros_like(g_ref)
+    for s_ in range(n):
+        scale += np.abs(omlp.grad(theta, X[s_:s_ + 1].astype(np.float64), T[s_:s_ + 1].astype(np.float64))) / n
+    bad = np.abs(g - g_ref) > 1e-5 * (np.abs(g_ref) + scale) + 1e-12
+    assert not bad.any(), (np.nonzero(bad)[0][:10], g[bad][:5], g_ref[bad][:5])
+    # every block of the parameter vector (including b3 and the W3 row) is exercised
+    off = 0
+    for name, shape in omlp.SIZES:
+        k = int(np.prod(shape))
+        assert np.max(np.abs(g_ref[off:off + k])) > 0, name
+        off += k
     assert abs(float(L.cpu()[0]) - omlp.loss(theta, X, T)) < 1e-5 * omlp.loss(theta, X, T)
 
 
