@@ -2,21 +2,26 @@
 """Benchmark: poles x N per second of the selected-inversion density path on one GB300.
 
 Step = one density evaluation rho(mu) (assembly, factor, selected inversion and the residue sum
-for every pole of the workload), inputs resident in HBM.  Default workload: the 2D square sheet
-of 32 x 32 atoms x 4 orbitals (N = 4096), 80 poles, kT = 0.01 Ha, FP64 path.
+for every pole of the workload), inputs resident in HBM.  Default workload: the 3D metallic
+lattice of 24^3 atoms x 8 orbitals (N = 110592), kT = 0.002 Ha, 160 poles, on the split-precision
+path (the largest configuration that fits one GPU); beside it the plain FP64 path is timed on a
+stated subset of the poles (every pole costs the same), which gives the split-vs-FP64 speed-up.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ndsi|reference] [--config C2]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ndsi|reference] [--config C5]
 
-Under torchrun every rank runs its own replica of the workload (weak scaling, no data-path
-collective); the max step time over ranks is reported.  `--impl reference` times the CPU
-oracle (dense generalized eigendecomposition + the same pole-truncated Fermi function) on the
-same workload, on rank 0 only.
+Under torchrun the poles are divided among the ranks (ndsi_pole_shard: contiguous ranges, M0 on
+one rank); every rank computes its share of Eq. 8 (ndsi_density_poles) and one sum all-reduce
+over NCCL of rho and Tr(rho S) completes the step, so N GPUs share one density evaluation
+(strong scaling); the max step time over ranks is reported.  `--impl reference` times the CPU
+oracle on the same workload, on rank 0 only: the dense generalized eigendecomposition with the
+same pole-truncated Fermi function for N <= 8192, else the oracle's Krylov column solves.
 """
 from __future__ import annotations
 
 import argparse
 import json
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -28,8 +33,8 @@ sys.path.insert(0, ROOT)
 
 METRIC = "poles x N per second (selected inversion); split-prec vs FP64 speedup at 1e-9"
 UNIT = "poles*N/s"
-FP64_PEAK_TFLOPS = 1.25   # nominal GB300 FP64 (DFMA) rate from the hardware table
 MU = -0.12
+DENSE_ORACLE_MAX_N = 8192     # larger systems: the oracle's Krylov column route
 
 
 def _env_rank():
@@ -38,7 +43,7 @@ def _env_rank():
 
 
 def _max_over_ranks(x, dist, world, device):
-    """Largest value of x over all ranks (the slowest replica sets the job's time)."""
+    """Largest value of x over all ranks (the slowest rank sets the job's time)."""
     if world <= 1:
         return float(x)
     import torch
@@ -56,7 +61,7 @@ def _sum_over_ranks(buf, dist, world):
 
 
 def _job_value(units_per_rank, world, ms_per_step):
-    """Whole-job throughput: every replica processes units_per_rank per step."""
+    """Whole-job throughput when every rank processes units_per_rank per step (replicas)."""
     return world * units_per_rank / (ms_per_step * 1e-3)
 
 
@@ -126,6 +131,41 @@ class ClockSampler:
                 "sm_max_mhz": mx or None, "reasons": sorted(reasons), "samples": len(sms)}
 
 
+# ------------------------------------------------------------------- stored oracle values ---
+
+def stored_columns(name, mu, kT, M):
+    """Oracle columns of rho stored by tests/golden/make_rho_columns.py for a workload:
+    {"values": {pattern index: rho}, "columns", "bound", "iterations_per_column", "leaf_atoms"},
+    or None when no file matches these settings."""
+    path = os.path.join(ROOT, "tests", "golden", f"rho_columns_{name}.txt")
+    if not os.path.exists(path):
+        return None
+    out = {"values": {}}
+    with open(path) as fh:
+        for ln in fh:
+            if ln.startswith("#"):
+                m = re.search(r"mu = ([-\d.eE+]+), kT = ([-\d.eE+]+), (\d+) poles, leaf_atoms (\d+)", ln)
+                if m:
+                    out.update(mu=float(m.group(1)), kT=float(m.group(2)), M=int(m.group(3)),
+                               leaf_atoms=int(m.group(4)))
+                m = re.search(r"# columns: (.*)", ln)
+                if m:
+                    out["columns"] = [int(c) for c in m.group(1).split()]
+                m = re.search(r"a posteriori\): ([\d.eE+-]+);.* (\d+) iterations", ln)
+                if m:
+                    out["bound"] = float(m.group(1))
+                    out["iterations"] = int(m.group(2))
+                continue
+            k, v = ln.split()
+            out["values"][int(k)] = float(v)
+    if out.get("mu") != mu or out.get("kT") != kT or out.get("M") != M:
+        return None
+    out["iterations_per_column"] = out["iterations"] / len(out["columns"])
+    return out
+
+
+# ------------------------------------------------------------------------ CPU baselines ---
+
 def cpu_oracle_rate(system, mu, kT, M, min_seconds=10.0, min_reps=2):
     """Time the oracle's route 1 (dense eigendecomposition + truncated Fermi sum on the pattern);
     also returns the oracle's Tr(rho S) (Eq. 40)."""
@@ -144,25 +184,47 @@ def cpu_oracle_rate(system, mu, kT, M, min_seconds=10.0, min_reps=2):
     return M * system.n / t, len(times), t, electron_count_eig(eps, mu, kT, M)
 
 
-def cpu_single_core_rate(config, mu):
-    """The oracle's route 1 on one host core (a child process with every BLAS pool at one thread):
-    poles x N per second, or None when the child fails."""
-    import subprocess
-    code = ("import time, json; from synth import config_system; "
-            "from oracle.dense import generalized_eig, density_eig, on_pattern; "
-            f"s = config_system({config!r}); Hd, Sd = s.dense(); kT, M = s.meta['kT'], s.meta['poles']; "
-            "ts = []\n"
-            "for _ in range(3):\n"
-            "    t0 = time.perf_counter(); e, C = generalized_eig(Hd, Sd); "
-            f"on_pattern(density_eig(e, C, {mu!r}, kT, M), s); ts.append(time.perf_counter() - t0)\n"
-            "print(json.dumps(M * s.n / min(ts)))")
-    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
-    try:
-        out = subprocess.run([sys.executable, "-c", code], cwd=ROOT, env=env, capture_output=True,
-                             text=True, timeout=300)
-        return float(out.stdout.strip().splitlines()[-1]) if out.returncode == 0 else None
-    except (subprocess.SubprocessError, ValueError, IndexError):
-        return None
+def krylov_slice(system, mu, kT, M, column, iters_per_task):
+    """One bounded sample of the oracle's Krylov column route: the M + 1 solves of one column of
+    rho (Eq. 8), each advanced by at most iters_per_task COCG iterations.  Returns (iterations
+    done, seconds)."""
+    import numpy as np
+    from oracle.krylov import solve_columns
+    from oracle.poles import cf_poles
+    z, _ = cf_poles(M)
+    alphas = np.concatenate([mu + 1j * z * kT, [1.0 + 0.0j]])
+    gammas = np.concatenate([np.ones(M), [0.0]])
+    t0 = time.perf_counter()
+    _, it, _ = solve_columns(system, alphas, gammas, np.full(M + 1, column), max_iter=iters_per_task,
+                             require_converged=False)
+    return int(it.sum()), time.perf_counter() - t0
+
+
+def krylov_iterations_per_column(system, mu, kT, M, stored):
+    """COCG iterations one column of rho needs (the stored oracle run's count when there is one,
+    else one column solved to convergence now)."""
+    if stored is not None:
+        return stored["iterations_per_column"], "stored oracle run (tests/golden)"
+    from oracle.krylov import density_columns_krylov
+    _, info = density_columns_krylov(system, mu, kT, M, [system.n // 2])
+    return float(info["iterations"]), "one column solved to convergence"
+
+
+def cpu_krylov_rate(system, mu, kT, M, stored, seconds=12.0, iters_per_task=12):
+    """Throughput of the oracle's Krylov route from bounded samples: the COCG iteration rate of
+    time-sliced column solves, divided by the iterations a full column needs (N columns make the
+    whole rho): poles x N / s = M x rate / iterations_per_column."""
+    from oracle.krylov import krylov_threads
+    per_col, src = krylov_iterations_per_column(system, mu, kT, M, stored)
+    done, t, reps = 0, 0.0, 0
+    while t < seconds or reps < 1:
+        d, dt = krylov_slice(system, mu, kT, M, (7919 * (reps + 1)) % system.n, iters_per_task)
+        done, t, reps = done + d, t + dt, reps + 1
+    rate = done / t
+    sample = (f"{reps} time slices of the oracle's Krylov column solves (all {M + 1} points of a "
+              f"column, {iters_per_task} COCG iterations each; {done} iterations in {t:.1f} s), scaled "
+              f"by the {per_col:.0f} iterations a column of rho needs ({src}) and N = {system.n} columns")
+    return M * rate / per_col, sample, krylov_threads()
 
 
 def cpu_sparse_lu_rate(system, mu, kT, M, max_seconds=10.0):
@@ -194,39 +256,70 @@ def run_reference(args):
     rank, world, _ = _env_rank()
     if rank != 0:
         return 0
-    from synth import config_system
-    from oracle.dense import generalized_eig, density_eig, on_pattern
-    system = config_system(args.config)
-    kT, M = system.meta["kT"], system.meta["poles"]
-    Hd, Sd = system.dense()
-    def step():
-        eps, C = generalized_eig(Hd, Sd)
-        on_pattern(density_eig(eps, C, MU, kT, M), system)
+    from synth import config_system, batched_systems
+    if args.config == "C4":
+        systems = [s for s in batched_systems() if s.n <= DENSE_ORACLE_MAX_N]
+        M, kT, label = args.poles or 120, 0.01, "batched: 120 poles x 12 uneven systems (N 2048..32768)"
+        n_total = sum(s.n for s in batched_systems())
+    else:
+        system = config_system(args.config)
+        systems = [system]
+        kT, M = system.meta["kT"], args.poles or system.meta["poles"]
+        label, n_total = system.meta["label"], system.n
+    cores = os.cpu_count()
+    if all(s.n <= DENSE_ORACLE_MAX_N for s in systems):
+        from oracle.dense import generalized_eig, density_eig, on_pattern
+        dense = [s.dense() for s in systems]
+
+        def step():
+            t0 = time.perf_counter()
+            for s, (Hd, Sd) in zip(systems, dense):
+                eps, C = generalized_eig(Hd, Sd)
+                on_pattern(density_eig(eps, C, MU, kT, M), s)
+            return M * sum(s.n for s in systems) / (time.perf_counter() - t0)
+        kind = "oracle (dense generalized eigendecomposition + pole-truncated Fermi sum)"
+        sample = (f"per step one full density evaluation of {len(systems)} system(s) "
+                  f"(N = {', '.join(str(s.n) for s in systems)}) by the oracle's route 1")
+        if args.config == "C4":
+            sample += "; the batched systems with N <= 8192 stand for the whole batch"
+    else:
+        from oracle.krylov import krylov_threads
+        system = systems[0]
+        stored = stored_columns(args.config, MU, kT, M)
+        per_col, src = krylov_iterations_per_column(system, MU, kT, M, stored)
+        counter = [0]
+
+        def step():
+            counter[0] += 1
+            d, dt = krylov_slice(system, MU, kT, M, (7919 * counter[0]) % system.n, 12)
+            return M * (d / dt) / per_col
+        cores = krylov_threads()
+        kind = "oracle (Krylov column solves of Eq. 8)"
+        sample = (f"per step one time slice of the oracle's Krylov solves of a column of rho (all {M + 1} "
+                  f"points, 12 COCG iterations each), scaled by the {per_col:.0f} iterations a column "
+                  f"needs ({src}) and N = {system.n} columns")
     for _ in range(args.warmup):
         step()
-    times = []
+    rates = []
     for _ in range(args.steps):
-        t0 = time.perf_counter()
-        step()
-        times.append(time.perf_counter() - t0)
-    t = sum(times) / len(times)
-    value = M * system.n / t
-    cores = os.cpu_count()
-    sample = (f"one full density evaluation of {args.config} per step by the oracle's dense "
-              f"generalized eigendecomposition (N={system.n}) and the {M}-pole Fermi sum")
+        rates.append(step())
+    # mean time per unit of work over the steps (harmonic mean of the rates)
+    value = len(rates) / sum(1.0 / r for r in rates)
+    ms = 1e3 * M * n_total / value
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": 1e3 * t, "higher_is_better": True, "scaling": "weak",
+            "ms_per_step": ms, "higher_is_better": True, "scaling": "strong",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": system.meta["label"], "n": system.n, "poles": M, "kT": kT,
-                       "mu": MU},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "config": {"workload": label, "n": n_total, "poles": M, "kT": kT, "mu": MU},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": kind,
                              "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
 
+
+# --------------------------------------------------------------------------- GPU side ---
 
 def _kernel_totals(prof):
     """Aggregate per-step profiler entries ("gemm_split:schur") into kernels ("gemm_split")."""
@@ -242,28 +335,31 @@ def _kernel_totals(prof):
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum, averaged over the kernel's
 # launches in one timed sweep) from an ncu capture of the same build and workload with default
 # options.  Entries are removed whenever the kernel changes.
-TRAFFIC_PER_LAUNCH = {("C2", "fp64", "gemm_f64"): 55.06e6}
+TRAFFIC_PER_LAUNCH = {}
 
 
-def _roofline(prof, steps, peaks, traffic_key=None):
+def _roofline(prof, steps, peaks, fp64_peak, traffic_key=None):
     kern = _kernel_totals(prof)
     dname, d = max(kern.items(), key=lambda kv: kv[1]["ms"])
     total = sum(v["ms"] for v in kern.values())
     if dname == "gemm_split":
-        peak = peaks.get("bf16_tflops_sustained", 1738.1)
+        peak = peaks.get("bf16_tflops_sustained", 1729.1)
         achieved = d["tensor_flops"] / (d["ms"] * 1e-3) / 1e12
         r = {"bound": "tensor", "unit": "TFLOP/s", "peak": peak,
              "peak_source": "of measured (MEASURED_PEAKS.json bf16_tflops_sustained; the kernel runs "
                             "inside a long step)",
              "fp64_equivalent_tflops": d["flops"] / (d["ms"] * 1e-3) / 1e12}
     elif dname in ("gemm_f64", "diaginv"):
-        peak = FP64_PEAK_TFLOPS
+        peak = fp64_peak
         achieved = d["flops"] / (d["ms"] * 1e-3) / 1e12
         r = {"bound": "alu", "unit": "TFLOP/s", "peak": peak,
-             "peak_source": "nominal GB300 FP64 DFMA rate from the hardware table (1.25 TFLOP/s); "
-                            "a DFMA loop measured 1.01 TFLOP/s"}
+             "peak_source": "of measured (ndsi_fp64_peak in this run: DFMA chains on every SM); "
+                            "achieved counts 8 flops per complex multiply-add"}
+        if dname == "gemm_f64":
+            # the three-multiplication complex product issues 6 of the 8 counted flops
+            r["frac_issued"] = 0.75 * achieved / peak
     else:
-        peak = peaks.get("hbm_gbs", 6800.0)
+        peak = peaks.get("hbm_gbs", 6792.7)
         achieved = d["bytes"] / (d["ms"] * 1e-3) / 1e9
         r = {"bound": "hbm", "unit": "GB/s", "peak": peak,
              "peak_source": "of measured (MEASURED_PEAKS.json hbm_gbs)"}
@@ -274,55 +370,157 @@ def _roofline(prof, steps, peaks, traffic_key=None):
     return r, kern
 
 
-def _autotune(nd, args, plan, H, S, kT, M):
-    """Per-step tensor-core / FP64 choice of a split plan, made once before any timing."""
+def _plan_options(args):
+    """Plan options given on the command line (unset ones keep the library defaults)."""
+    kw = dict(split_slices=args.slices, outer_block=args.outer, block=args.block, split_bands=args.bands,
+              leaf_atoms=args.leaf, split_far_ratio=args.far_ratio)
+    return {k: v for k, v in kw.items() if v}
+
+
+def _autotune(nd, args, plan, H, S, kT, M, n):
+    """Per-step tensor-core / FP64 choice of a split plan, made once before any timing: on every
+    pole of small systems, on ten poles (one workspace chunk) of large ones."""
     if args.no_autotune:
         return None
-    n_split, n_fp64 = nd.ndsi_autotune(plan, H, S, MU, kT, M)
-    return {"tensor_core_steps": n_split, "fp64_steps": n_fp64}
+    m = M if n <= 20000 else min(M, 10)
+    n_split, n_fp64 = nd.ndsi_autotune(plan, H, S, MU, kT, m)
+    return {"tensor_core_steps": n_split, "fp64_steps": n_fp64, "poles_timed": m}
 
 
-def _measure(nd, torch, plan, H, S, rho, ne, kT, M, steps, warmup, stream, flush, by_level=False,
-             e=None):
+def _timed_steps(torch, step, stream, flush, steps, ahead):
+    """L2 flush, start event, step, end event per step on the launch stream; with `ahead` the
+    steps are enqueued back to back, else synchronised one by one.  Returns ms per step."""
+    events = []
+    torch.cuda.synchronize()
+    for _ in range(steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step()
+        e1.record(stream)
+        events.append((e0, e1))
+        if not ahead:
+            torch.cuda.synchronize()
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in events]
+
+
+def _measure(nd, torch, plan, step, steps, warmup, stream, flush, prof_steps, by_level=False):
     """Time `steps` density sweeps as the library runs them (one captured CUDA graph per sweep),
-    then repeat them with direct launches and per-launch CUDA events for the kernel breakdown.
-    With `e` (an nnz device buffer) each sweep also forms the energy density matrix."""
-    def step():
-        if e is None:
-            nd.ndsi_density(plan, H, S, MU, kT, M, rho, ne, stream=stream)
-        else:
-            nd.ndsi_density_energy(plan, H, S, MU, kT, M, rho, e, ne, stream=stream)
-
-    def timed_steps(ahead):
-        # L2 flush, start event, sweep, end event per step, all on the launch stream; with
-        # `ahead` the steps are enqueued back to back (the host runs ahead of the GPU, so host
-        # scheduling noise does not open gaps between the events), else synchronised per step
-        events = []
-        torch.cuda.synchronize()
-        for _ in range(steps):
-            flush.zero_()
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            step()
-            e1.record(stream)
-            events.append((e0, e1))
-            if not ahead:
-                torch.cuda.synchronize()
-        torch.cuda.synchronize()
-        return [a.elapsed_time(b) for a, b in events]
+    then repeat `prof_steps` of them with direct launches and per-launch CUDA events for the
+    kernel breakdown."""
     for _ in range(max(warmup, 3)):
         step()
     torch.cuda.synchronize()
     # the timed region alone is what `ncu --profile-from-start off` records (a no-op otherwise)
     torch.cuda.profiler.start()
-    times = timed_steps(True)
+    times = _timed_steps(torch, step, stream, flush, steps, True)
     torch.cuda.profiler.stop()
     nd.ndsi_profile_enable(plan, True, by_level=by_level)
-    prof_times = timed_steps(False)
+    prof_times = _timed_steps(torch, step, stream, flush, prof_steps, False)
     prof = nd.ndsi_profile_read(plan)
     nd.ndsi_profile_enable(plan, False)
     return times, prof, prof_times
+
+
+def _parity(args, system, rho, kT, M, stored, e_buf=None):
+    """max |rho - oracle| on sampled columns: the stored oracle columns of the workload when
+    present, else the oracle's column route run now (SuperLU solves per pole)."""
+    import numpy as np
+    if stored is not None:
+        idx = np.fromiter(stored["values"].keys(), dtype=np.int64)
+        ref = np.fromiter(stored["values"].values(), dtype=np.float64)
+        err = float(np.max(np.abs(rho[idx] - ref)))
+        return {"max_abs_err_rho": err, "columns": stored["columns"], "entries": int(idx.size),
+                "oracle": "stored Krylov columns of Eq. 8 (tests/golden, oracle-only script)",
+                "oracle_error_bound": stored["bound"],
+                "tolerance": 1e-10 if args.precision == "fp64" else 1e-9}
+    if system.n > 20000:
+        return {"skipped": "no stored oracle columns for these settings (the column route takes "
+                           "hours at this size; tests/golden/make_rho_columns.py stores them)"}
+    from oracle.dense import density_columns
+    rng = np.random.default_rng(11)
+    cols = sorted(rng.choice(system.n, 3, replace=False).tolist())
+    ref = density_columns(system, MU, kT, M, cols)
+    rows = system.rows()
+    err = 0.0
+    for t_, j in enumerate(cols):
+        sel = np.nonzero(system.col == j)[0]
+        err = max(err, float(np.max(np.abs(rho[sel] - ref[rows[sel], t_]))))
+    out = {"max_abs_err_rho": err, "columns": cols, "oracle": "SuperLU columns of Eq. 8, run now",
+           "tolerance": 1e-10 if args.precision == "fp64" else 1e-9}
+    if e_buf is not None:
+        from oracle.dense import energy_density_columns
+        eref = energy_density_columns(system, MU, kT, M, cols)
+        ee = 0.0
+        for t_, j in enumerate(cols):
+            sel = np.nonzero(system.col == j)[0]
+            ee = max(ee, float(np.max(np.abs(e_buf[sel] - eref[rows[sel], t_]))))
+        out["max_abs_err_energy_density"] = ee
+    return out
+
+
+def _release(torch):
+    """Drop unreferenced plans (their device workspaces) before the next plan is sized."""
+    import gc
+    gc.collect()
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+
+
+def _other_leg(nd, torch, args, system, H, S, kT, M, stream, flush, prec_code, fp64_peak, ms_main,
+               rho_main, ne_main):
+    """The other precision on the same workload.  Every pole costs the same, so a large system's
+    FP64 path is timed on a stated subset of the poles and compared per contour point; the two
+    paths' rho are compared on that subset's expansion.  One plan (and its workspace) is alive at
+    a time, so each gets the device memory the headline plan had."""
+    import numpy as np
+    _release(torch)
+    oprec = "split" if args.precision == "fp64" else "fp64"
+    Mo = M if system.n <= 20000 else min(M, args.fp64_poles or 8)
+    kw = _plan_options(args)
+    plan2 = nd.analyze_system(system, precision=prec_code[oprec], **kw)
+    tune2 = _autotune(nd, args, plan2, H, S, kT, M, system.n) if oprec == "split" else None
+    rho2 = torch.zeros(system.nnz, dtype=torch.float64, device=H.device)
+    ne2 = torch.zeros(1, dtype=torch.float64, device=H.device)
+
+    def step2():
+        nd.ndsi_density(plan2, H, S, MU, kT, Mo, rho2, ne2, stream=stream)
+    w2, k2 = (max(args.warmup, 3), args.steps) if Mo == M else (1, min(args.steps, 2))
+    t2, prof2, _ = _measure(nd, torch, plan2, step2, k2, w2, stream, flush, 1)
+    ms2 = sum(t2) / len(t2)
+    rl2, kk2 = _roofline(prof2, 1, _peaks(), fp64_peak)
+    per_point_main = ms_main / (M + 1)
+    per_point_other = ms2 / (Mo + 1)
+    split_pp, fp64_pp = ((per_point_other, per_point_main) if oprec == "split" else
+                         (per_point_main, per_point_other))
+    out = {"precision": oprec, "poles": Mo, "ms_per_step": ms2, "steps": k2, "warmup": w2,
+           "ms_per_point": per_point_other, "value": Mo * system.n / (ms2 * 1e-3),
+           "split_speedup_vs_fp64": fp64_pp / split_pp, "autotune": tune2, "roofline": rl2,
+           "kernels": {k: {"launches": v["launches"], "ms_per_step": v["ms"]} for k, v in kk2.items()}}
+    rho2_h = rho2.cpu().numpy()
+    ne2_h = float(ne2.cpu()[0])
+    del plan2, step2
+    _release(torch)
+    if Mo == M:
+        out["max_abs_rho_diff_vs_headline"] = float(np.max(np.abs(rho2_h - rho_main)))
+        out["abs_n_elec_diff_vs_headline"] = abs(ne2_h - ne_main)
+    else:
+        # both precisions on the subset's expansion (Mo poles)
+        plan_main = nd.analyze_system(system, precision=prec_code[args.precision], **kw)
+        rho3 = torch.zeros_like(rho2)
+        ne3 = torch.zeros_like(ne2)
+        nd.ndsi_density(plan_main, H, S, MU, kT, Mo, rho3, ne3, stream=stream)
+        torch.cuda.synchronize()
+        out["max_abs_rho_diff_same_poles"] = float(np.max(np.abs(rho2_h - rho3.cpu().numpy())))
+        out["fp64_ms_per_step_full_poles_estimate"] = (fp64_pp * (M + 1))
+        out["note"] = (f"the FP64 path is timed on the first {Mo} poles (+ M0): every pole of one "
+                       "system costs the same, so the speed-up is the ratio of the two paths' time "
+                       "per contour point")
+        del plan_main
+        _release(torch)
+    return out, (fp64_pp * (M + 1))
 
 
 def run_ndsi(args):
@@ -349,160 +547,157 @@ def run_ndsi(args):
     kT, M = system.meta["kT"], system.meta["poles"]
     if args.poles:
         M = args.poles
-    plan = nd.analyze_system(system, precision=prec_code[args.precision], split_slices=args.slices,
-                             outer_block=args.outer, block=args.block, split_bands=args.bands)
+    stored = stored_columns(args.config, MU, kT, M)
+    plan = nd.analyze_system(system, precision=prec_code[args.precision], **_plan_options(args))
     info = nd.ndsi_plan_info(plan)
     dev = torch.device("cuda", local)
+    fp64_peak = nd.ndsi_fp64_peak()
     H = torch.as_tensor(system.H, device=dev)
     S = torch.as_tensor(system.S, device=dev)
-    tune = _autotune(nd, args, plan, H, S, kT, M)
+    tune = _autotune(nd, args, plan, H, S, kT, M, system.n)
     if args.no_graph:
         nd.ndsi_graph_enable(plan, False)
-    rho = torch.zeros(system.nnz, dtype=torch.float64, device=dev)
-    ne = torch.zeros(1, dtype=torch.float64, device=dev)
+    nnz = system.nnz
+    out = torch.zeros(nnz + 1, dtype=torch.float64, device=dev)    # rho, then Tr(rho S)
+    rho, ne = out[:nnz], out[nnz:]
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > L2
     stream = torch.cuda.current_stream()
+    pb, pe, m0 = nd.ndsi_pole_shard(M, rank, world)
+    e_buf = torch.zeros_like(rho) if args.energy else None
+
+    def step():
+        if world == 1:
+            if e_buf is None:
+                nd.ndsi_density(plan, H, S, MU, kT, M, rho, ne, stream=stream)
+            else:
+                nd.ndsi_density_energy(plan, H, S, MU, kT, M, rho, e_buf, ne, stream=stream)
+        else:
+            nd.ndsi_density_poles(plan, H, S, MU, kT, M, pb, pe, m0, rho, ne, stream=stream)
+            _sum_over_ranks(out, dist, world)
 
     if world > 1:
         dist.barrier()
     with ClockSampler(local) as clk:
-        e_buf = torch.zeros_like(rho) if args.energy else None
-        times, prof, prof_times = _measure(nd, torch, plan, H, S, rho, ne, kT, M, args.steps,
-                                           args.warmup, stream, flush, by_level=args.by_level, e=e_buf)
+        times, prof, prof_times = _measure(nd, torch, plan, step, args.steps, args.warmup, stream, flush,
+                                           min(args.steps, 2), by_level=args.by_level)
         graph_nodes = nd.ndsi_graph_info(plan)
     if world > 1:
         dist.barrier()
     total_ms = _max_over_ranks(sum(times), dist, world, dev)
     ms_step = total_ms / args.steps
-    value = _job_value(M * system.n, world, ms_step)
+    value = M * system.n / (ms_step * 1e-3)       # one density evaluation per step, all ranks
     rho_main = rho.cpu().numpy()
+    ne_main = float(ne.cpu()[0])
     # end to end through the public API with pinned host buffers (copies inside the call)
     Hh = torch.as_tensor(system.H).pin_memory()
     Sh = torch.as_tensor(system.S).pin_memory()
-    rho_h = torch.zeros(system.nnz, dtype=torch.float64).pin_memory()
-    ne_h = torch.zeros(1, dtype=torch.float64).pin_memory()
-    nd.ndsi_density(plan, Hh, Sh, MU, kT, M, rho_h, ne_h, stream=stream)
+    out_h = torch.zeros(nnz + 1, dtype=torch.float64).pin_memory()
+    rho_h, ne_h = out_h[:nnz], out_h[nnz:]
+
+    def e2e_step():
+        if world == 1:
+            nd.ndsi_density(plan, Hh, Sh, MU, kT, M, rho_h, ne_h, stream=stream)
+        else:
+            nd.ndsi_density_poles(plan, Hh, Sh, MU, kT, M, pb, pe, m0, rho, ne, stream=stream)
+            _sum_over_ranks(out, dist, world)
+            out_h.copy_(out)
+    e2e_step()
+    e2e_steps = min(args.steps, 3)
     e2e_times = []
-    for _ in range(args.steps):
+    for _ in range(e2e_steps):
         flush.zero_()
         torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
         t0 = time.perf_counter()
-        nd.ndsi_density(plan, Hh, Sh, MU, kT, M, rho_h, ne_h, stream=stream)
+        e2e_step()
+        torch.cuda.synchronize()
         e2e_times.append(time.perf_counter() - t0)
     e2e_s = _max_over_ranks(sum(e2e_times) / len(e2e_times), dist, world, dev)
+    sys.stderr.write(json.dumps({"progress": "headline timed", "ms_per_step": ms_step,
+                                 "e2e_s": e2e_s, "step_ms": times}) + "\n")
     # the other precision on the same workload: split-vs-FP64 speedup and rho difference
-    other = None
+    other, fp64_ms_full = None, None
+    del plan, step, e2e_step              # the headline plan's workspace goes back to the device
     if not args.no_other and rank == 0:
-        oprec = "split" if args.precision == "fp64" else "fp64"
-        plan2 = nd.analyze_system(system, precision=prec_code[oprec], split_slices=args.slices,
-                                  outer_block=args.outer, block=args.block, split_bands=args.bands)
-        tune2 = _autotune(nd, args, plan2, H, S, kT, M)
-        rho2 = torch.zeros_like(rho)
-        ne2 = torch.zeros_like(ne)
-        t2, prof2, _ = _measure(nd, torch, plan2, H, S, rho2, ne2, kT, M, args.steps, args.warmup,
-                                stream, flush)
-        ms2 = sum(t2) / len(t2)
-        ms_split, ms_fp64 = (ms2, ms_step) if oprec == "split" else (ms_step, ms2)
-        rl2, k2 = _roofline(prof2, args.steps, _peaks())
-        other = {"precision": oprec, "ms_per_step": ms2, "value": M * system.n / (ms2 * 1e-3),
-                 "split_speedup_vs_fp64": ms_fp64 / ms_split, "autotune": tune2,
-                 "abs_n_elec_diff_vs_headline": abs(float(ne2.cpu()[0]) - float(ne.cpu()[0])),
-                 "max_abs_rho_diff_vs_headline": float(np.max(np.abs(rho2.cpu().numpy() - rho_main))),
-                 "roofline": rl2,
-                 "kernels": {k: {"launches": v["launches"] // args.steps, "ms_per_step": v["ms"] / args.steps}
-                             for k, v in k2.items()}}
-        del plan2
+        other, fp64_ms_full = _other_leg(nd, torch, args, system, H, S, kT, M, stream, flush, prec_code,
+                                         fp64_peak, ms_step * world if world > 1 else ms_step, rho_main,
+                                         ne_main)
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
         return 0
-    default_opts = not (args.poles or args.outer or args.block or args.slices or args.bands)
-    roofline, kern = _roofline(prof, args.steps, _peaks(),
+    default_opts = not (args.poles or args.outer or args.block or args.slices or args.bands or args.leaf
+                        or args.far_ratio)
+    roofline, kern = _roofline(prof, len(prof_times), _peaks(), fp64_peak,
                                (args.config, args.precision) if default_opts else None)
     launches = sum(v["launches"] for v in kern.values())
-    # parity spot check outside the timed region: sampled columns from the oracle
-    parity = None
-    if not args.no_parity:
-        from oracle.dense import density_columns
-        rng = np.random.default_rng(11)
-        cols = sorted(rng.choice(system.n, 3, replace=False).tolist())
-        ref = density_columns(system, MU, kT, M, cols)
-        rows = system.rows()
-        err = 0.0
-        for t_, j in enumerate(cols):
-            sel = np.nonzero(system.col == j)[0]
-            err = max(err, float(np.max(np.abs(rho_main[sel] - ref[rows[sel], t_]))))
-        parity = {"max_abs_err_rho": err, "columns": cols,
-                  "tolerance": 1e-10 if args.precision == "fp64" else 1e-9}
-        if e_buf is not None:
-            from oracle.dense import energy_density_columns
-            e_main = e_buf.cpu().numpy()
-            eref = energy_density_columns(system, MU, kT, M, cols)
-            ee = 0.0
-            for t_, j in enumerate(cols):
-                sel = np.nonzero(system.col == j)[0]
-                ee = max(ee, float(np.max(np.abs(e_main[sel] - eref[rows[sel], t_]))))
-            parity["max_abs_err_energy_density"] = ee
+    parity = None if args.no_parity else _parity(args, system, rho_main, kT, M, stored,
+                                                 e_buf.cpu().numpy() if e_buf is not None else None)
     cpu = None
-    ne_gpu = float(ne.cpu()[0])
-    n_elec = {"value": ne_gpu}
+    n_elec = {"value": ne_main}
     golden = os.path.join(ROOT, "tests", "golden", "c3_electron_count.txt")
     if args.config == "C3" and M == 80 and os.path.exists(golden):
         # the oracle's count for this workload (eigenvalues by LAPACK, stored by
         # tests/golden/make_c3_electron_count.py): too slow to recompute inside the bench
         with open(golden) as fh:
             ne_ref = float([ln for ln in fh if ln.strip() and not ln.startswith("#")][0])
-        n_elec.update(oracle=ne_ref, abs_err=abs(ne_gpu - ne_ref), oracle_source="stored (oracle eigenvalues)")
+        n_elec.update(oracle=ne_ref, abs_err=abs(ne_main - ne_ref), oracle_source="stored (oracle eigenvalues)")
     if world == 1 and not args.no_cpu:
-        v, reps, t_rep, ne_oracle = cpu_oracle_rate(system, MU, kT, M)
-        n_elec.update(oracle=ne_oracle, abs_err=abs(ne_gpu - ne_oracle))
-        cpu = {"value": v, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
-               "sample": f"{reps} full density evaluations of the workload by dense generalized "
-                         f"eigendecomposition + {M}-pole Fermi sum ({t_rep:.2f} s each)"}
-        extra = {}
-        if system.n <= 1024:
-            v1 = cpu_single_core_rate(args.config, MU)
-            if v1 is not None:
-                extra["oracle_one_core"] = {"value": v1, "unit": UNIT, "cores": 1}
-        if system.n <= 16384:
+        if system.n <= DENSE_ORACLE_MAX_N:
+            v, reps, t_rep, ne_oracle = cpu_oracle_rate(system, MU, kT, M)
+            n_elec.update(oracle=ne_oracle, abs_err=abs(ne_main - ne_oracle))
+            cpu = {"value": v, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                   "sample": f"{reps} full density evaluations of the workload by dense generalized "
+                             f"eigendecomposition + {M}-pole Fermi sum ({t_rep:.2f} s each)"}
+        elif stored is not None or system.n <= 20000:
+            v, sample, threads = cpu_krylov_rate(system, MU, kT, M, stored)
+            cpu = {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample}
+        if cpu is not None and system.n <= 16384:
             vs, npl, tpl = cpu_sparse_lu_rate(system, MU, kT, M)
-            extra["scipy_sparse_lu"] = {"value": vs, "unit": UNIT, "cores": os.cpu_count(),
-                                        "sample": f"SuperLU factorisation of {npl} poles, "
-                                                  f"{tpl * 1e3:.1f} ms each, scaled to {M + 1} "
-                                                  "points; factorisation only (no selected "
-                                                  "inversion), a lower bound of a CPU sparse route"}
-        if extra:
-            cpu["other_cpu_routes"] = extra
+            cpu["other_cpu_routes"] = {
+                "scipy_sparse_lu": {"value": vs, "unit": UNIT, "cores": os.cpu_count(),
+                                    "sample": f"SuperLU factorisation of {npl} poles, {tpl * 1e3:.1f} ms "
+                                              f"each, scaled to {M + 1} points; factorisation only (no "
+                                              "selected inversion), a lower bound of a CPU sparse route"}}
+    speedup = other["split_speedup_vs_fp64"] if other else None
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": ms_step,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "higher_is_better": True, "scaling": "strong", "vs_baseline": None,
             "dtype": "f64" if args.precision == "fp64" else f"bf16x{info['split_slices']}->f64",
             "data": "synthetic",
+            "split_speedup_vs_fp64": speedup,
+            "fp64_ms_per_step": (ms_step if args.precision == "fp64" else fp64_ms_full),
+            "max_abs_err_rho_vs_oracle": parity.get("max_abs_err_rho") if parity else None,
             "config": {"workload": system.meta["label"] + f", {M} poles, {args.precision} path"
                                    + (", rho and energy density matrix" if args.energy else ""),
-                       "n": system.n, "poles": M, "kT": kT, "mu": MU, "nnz": system.nnz,
+                       "n": system.n, "poles": M, "kT": kT, "mu": MU, "nnz": nnz,
                        "precision": args.precision, "split_slices": info["split_slices"],
                        "split_bands": info["split_bands"],
-                       "l2": "flushed (256 MB write) before every timed step",
-                       "flops_per_pole": info["flops_per_pole"], "parallelism": f"replicas x{world}"},
-            "e2e": {"value": world * M * system.n / e2e_s, "unit": UNIT,
-                    "h2d_bytes_per_step": 2 * 8 * system.nnz,
-                    "d2h_bytes_per_step": 8 * system.nnz + 8},
-            "gpu_launches": launches,
+                       "l2": "flushed (256 MB write) before every timed step; inputs and fronts "
+                             "are far larger than L2",
+                       "flops_per_pole": info["flops_per_pole"],
+                       "parallelism": "one GPU" if world == 1 else f"pole-sharded x{world} (sum all-reduce of rho)"},
+            "e2e": {"value": M * system.n / e2e_s, "unit": UNIT, "steps": e2e_steps,
+                    "h2d_bytes_per_step": 2 * 8 * nnz,
+                    "d2h_bytes_per_step": 8 * nnz + 8},
+            "gpu_launches": launches // len(prof_times) * args.steps,
             "step_ms": [round(t, 4) for t in times],
-            "autotune": tune,
+            "autotune": tune, "fp64_peak_tflops_measured": fp64_peak,
             "graph": {"kernel_nodes": graph_nodes,
                       "ms_per_step_direct_launches": sum(prof_times) / len(prof_times),
                       "note": "timed steps replay one captured CUDA graph per sweep; the kernel "
-                              "breakdown and roofline come from the same steps repeated with direct "
-                              "launches bracketed by CUDA events on the launch stream"},
+                              "breakdown and roofline come from steps repeated with direct launches "
+                              "bracketed by CUDA events on the launch stream"},
             "roofline": roofline, "clocks": clk.summary(), "cpu_baseline": cpu,
             "parity": parity, "n_elec": n_elec, "other_precision": other,
-            "kernels": {k: {"launches": v["launches"] // args.steps, "ms_per_step": v["ms"] / args.steps,
+            "kernels": {k: {"launches": v["launches"] // len(prof_times),
+                            "ms_per_step": v["ms"] / len(prof_times),
                             "gbs": v["bytes"] / max(v["ms"], 1e-9) / 1e6,
                             "tflops": v["flops"] / max(v["ms"], 1e-9) / 1e9}
                         for k, v in kern.items()},
-            "steps_detail": {k: {"launches": v["launches"] // args.steps, "ms_per_step": v["ms"] / args.steps}
+            "steps_detail": {k: {"launches": v["launches"] // len(prof_times),
+                                 "ms_per_step": v["ms"] / len(prof_times)}
                              for k, v in prof.items()}}
     print(json.dumps(line))
     if world > 1:
@@ -530,8 +725,7 @@ def run_batched(args, nd, torch, dist, rank, world, local, prec_code):
     systems = batched_systems()
     M = args.poles or 120
     kT = 0.01
-    plan = nd.analyze_batched(systems, precision=prec_code[args.precision], split_slices=args.slices,
-                              outer_block=args.outer, block=args.block, split_bands=args.bands)
+    plan = nd.analyze_batched(systems, precision=prec_code[args.precision], **_plan_options(args))
     info = nd.ndsi_plan_info(plan)
     dev = torch.device("cuda", local)
     H = torch.as_tensor(np.concatenate([s.H for s in systems]), device=dev)
@@ -604,7 +798,7 @@ def run_batched(args, nd, torch, dist, rank, world, local, prec_code):
             checked.append({"system": i, "n": sy.n, "columns": cols})
         parity = {"max_abs_err_rho": err, "checked": checked,
                   "tolerance": 1e-10 if args.precision == "fp64" else 1e-9}
-    roofline, kern = _roofline(prof, args.steps, _peaks())
+    roofline, kern = _roofline(prof, args.steps, _peaks(), nd.ndsi_fp64_peak())
     line = {"metric": METRIC, "value": _job_value(M * ntot, world, ms), "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -803,8 +997,8 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ndsi", choices=["ndsi", "reference"])
-    ap.add_argument("--config", default="C2", choices=["C1", "C2", "C3", "C4", "C5"])
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "split"])
+    ap.add_argument("--config", default="C5", choices=["C1", "C2", "C3", "C4", "C5"])
+    ap.add_argument("--precision", default="split", choices=["fp64", "split"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-parity", action="store_true", help="skip the sampled-column check")
     ap.add_argument("--no-graph", action="store_true",
@@ -825,6 +1019,13 @@ def main():
                     help="BF16 slices per operand of the split path (4-7; 0: the library's choice)")
     ap.add_argument("--poles", type=int, default=0,
                     help="override the workload's pole count (small profiling runs only)")
+    ap.add_argument("--fp64-poles", type=int, default=0,
+                    help="poles of the FP64 comparison leg on systems above N = 20000 (0: 8)")
+    ap.add_argument("--leaf", type=int, default=0,
+                    help="innermost-domain size of the dissection in atoms (0: library default)")
+    ap.add_argument("--far-ratio", type=float, default=0.0,
+                    help="split plans: poles with z_p >= ratio z_1 use one slice fewer (0: library "
+                         "default, negative: off)")
     ap.add_argument("--no-other", action="store_true",
                     help="skip the run of the other precision (split-vs-FP64 speedup)")
     ap.add_argument("--mu-search", action="store_true",

@@ -1,8 +1,9 @@
-"""Host-side multi-process path of bench.py on CPU (gloo, world size 2).
+"""Host-side multi-process timing helpers of bench.py on CPU (gloo, world size 2).
 
-With N GPUs bench.py runs N independent replicas of the workload (the poles and systems of one
-replica never need another's data), times each, takes the slowest replica's time and reports
-the whole-job throughput.  These are the two host steps exercised here, with two gloo ranks.
+With N GPUs every rank times its own steps and the slowest rank's time sets the job's time
+(the max over ranks); replicated workloads (the batched configuration) count every rank's work
+in the whole-job throughput.  These two host steps are exercised here with two gloo ranks; the
+pole-sharded exchange is in test_pole_shard_ranks.py.
 """
 import os
 import socket
