@@ -14,4 +14,5 @@ from .lattice import (  # noqa: F401
     batched_systems,
     csr_from_dense,
     mu_training_systems,
+    c5_family_systems,
 )

@@ -259,6 +259,23 @@ def batched_systems(count=None):
     return out
 
 
+def c5_family_systems(count, seed):
+    """Small seeded systems of the 3D metallic workload's recipe (3D cubic lattice, cut-off 1.8a,
+    8 orbitals per atom, onsite U(-1,1), hopping N(0, 0.1^2), overlap 0.05) for the
+    chemical-potential seed: cubes and boxes of 4 to 7 atoms per side (N 512..2744), kT drawn in
+    [0.0015, 0.003] Ha and the filling in [0.2, 0.3] electrons per orbital (the workload has 0.25).
+    Returns (System, kT) pairs."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = []
+    for _ in range(count):
+        shape = tuple(int(v) for v in rng.integers(4, 8, size=3))
+        n = int(np.prod(shape)) * 8
+        filling = float(rng.uniform(0.2, 0.3))
+        sysm = lattice_system(shape, 8, "3d", int(rng.integers(1 << 30)), electrons=round(n * filling))
+        out.append((sysm, float(rng.uniform(0.0015, 0.003))))
+    return out
+
+
 def mu_training_systems(count, seed):
     """Small seeded systems with varied recipe parameters for the chemical-potential seed.
 
