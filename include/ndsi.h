@@ -70,11 +70,11 @@ typedef struct {
                                     panel, trailing update and inverse assembly outside it are the
                                     GEMMs that split mode moves to the tensor cores; a multiple of
                                     `block` (0 = default 128) */
-    int32_t split_bands;         /* TMEM accumulator bands of the split GEMM: 4 (slice products with
-                                    t+u = 2, 3, 4 exact, the rest in one tail accumulator; 64
-                                    complex columns per tile) or 5 (t+u = 2..5 exact; 48 columns,
-                                    about 2^7 more accurate where the tail dominates the error,
-                                    about as fast); 0 (default) = 5 */
+    int32_t split_bands;         /* TMEM accumulators of the split GEMM: 0 (default) = one per
+                                    slice-product scale t+u (every scale exact; 40 complex columns
+                                    per tile, 32 with seven slices); 4 (t+u = 2, 3, 4 exact, the
+                                    rest in one tail accumulator whose low bits the tensor core
+                                    drops; 64 columns) or 5 (t+u = 2..5 exact; 48 columns) */
     double cell[3];              /* periodic cell lengths along x, y, z in the units of `centers`;
                                     0 (default) = open along that axis.  On a periodic axis the
                                     dissection orders atoms by their coordinate wrapped into
@@ -110,7 +110,8 @@ typedef struct {
     int32_t n_launches;        /* schedule launches per pole batch (factor + selected inversion) */
     int32_t n_systems;         /* systems in the plan (1 unless built by ndsi_analyze_batched) */
     int32_t split_slices;      /* slices per operand of a split plan (0 for an FP64 plan) */
-    int32_t split_bands;       /* accumulator bands of a split plan (0 for an FP64 plan) */
+    int32_t split_bands;       /* accumulators of a split plan (the slice count when there is one
+                                  per scale; 0 for an FP64 plan) */
 } ndsi_plan_summary;
 
 /* Items for ndsi_plan_export. */

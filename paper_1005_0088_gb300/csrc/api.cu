@@ -315,13 +315,13 @@ namespace ndsi {
 // dominates) and little with five.
 int auto_slices(const Plan&) { return 6; }
 
-// Accumulator bands when the caller leaves it to the library.  With four bands the tail
-// accumulator mixes products 2^8 and 2^16 apart and the tensor core drops the low bits of the
-// smaller ones (a floor near 2^-38 of the result, whatever the slice count); five bands keep
-// t+u = 5 exact and move the floor to ~2^-43.  On the 3D metallic lattice (largest front 7016,
-// kT = 0.002) rho moved from 2.0e-9 to 4.0e-11 of the FP64 path for 6% more time; on the 2D
-// sheet the narrower tiles were faster (less padding), on the 3D cubic lattice 2% slower.
-int auto_bands(const Plan&) { return 5; }
+// Accumulators when the caller leaves it to the library: one per slice-product scale (reported as
+// 0 in the options, S in ndsi_plan_info).  The tail variants (4 or 5) mix the smallest scales in
+// one accumulator, where the tensor core drops the low bits of the smaller products (a floor near
+// 2^-38 or 2^-43 of the result); one accumulator per scale has no such floor, and because each A
+// digit's products are one wide MMA the operand tiles are read from shared memory once per digit,
+// which is what limited the tail variants' tensor throughput at N = 96.
+int auto_bands(const Plan&) { return 0; }
 
 // Split-precision metadata of a plan: tensor-core steps, their tile lists and cost figures.
 void setup_split(ndsi_plan* h, const ndsi_options& o) {
@@ -525,7 +525,9 @@ int ndsi_plan_info(const ndsi_plan* h, ndsi_plan_summary* out) {
     out->n_launches = static_cast<int32_t>(P.launches.size());
     out->n_systems = P.n_systems;
     out->split_slices = P.opt.precision == NDSI_PREC_SPLIT ? P.opt.split_slices : 0;
-    out->split_bands = P.opt.precision == NDSI_PREC_SPLIT ? P.opt.split_bands : 0;
+    out->split_bands = P.opt.precision == NDSI_PREC_SPLIT
+                           ? (P.opt.split_bands != 0 ? P.opt.split_bands : P.opt.split_slices)
+                           : 0;
     return NDSI_OK;
 }
 

@@ -10,25 +10,31 @@
 //    S balanced base-256 digits, x = 2^(E-7) sum_t d_t 2^(-8(t-1)), d_1 in [-128,128],
 //    d_t in [-128,127]; digit t is stored pre-scaled, d_t 2^(-8(t-1)), exactly as BF16.  The
 //    digits come from the FP64 bit pattern with integer operations only;
-//  * the slice products A_t B_u^T with t+u <= S+1 are accumulated in TMEM in BANDS bands: each
-//    t+u = 2 .. BANDS in its own accumulator, where every partial sum over a 256-element K chunk
-//    is an integer of at most 2^24 times a power of two and so exact in FP32; the remaining
-//    products share a tail accumulator.  Every band is read out after every chunk into a
-//    per-element float-float (hi, lo) sum.  When products of different scales meet in one
-//    accumulator the tensor core drops the low bits of the smaller ones, so the tail must hold
-//    only products well below the result's last digit: BANDS = 5 (NC = 48, 5 x 96 TMEM columns)
-//    gives a floor near 2^-43 of the result, BANDS = 4 (NC = 64, 4 x 128 columns) near 2^-38;
+//  * the slice products A_t B_u^T with t+u <= S+1 are accumulated in TMEM, by default one
+//    accumulator per scale t+u (S of them, 2NC columns each): the B digits of a stage are
+//    consecutive rows of one K-major block, so A_t times [B_1; ...; B_{S+1-t}] is one wide MMA (or
+//    two, N <= 256) whose output columns fall into the accumulators of t+1 .. S+1 - each operand
+//    tile is read from shared memory once per digit instead of once per product, which keeps
+//    the tensor pipe fed at N = 2NC = 80.  Within an accumulator every partial sum over a
+//    256-element K chunk has at most four products per K for the leading four scales, so it is
+//    an integer of at most 2^24 times a power of two and exact in FP32 (the lower scales, 2^-32
+//    and below, may round at 2^-24 of themselves).  Every accumulator is read out after every
+//    chunk into a per-element float-float (hi, lo) sum.  The optional tail variants keep t+u = 2
+//    .. BANDS in their own accumulators and the rest in a shared tail, where the tensor core
+//    drops the low bits of the smaller products: BANDS = 5 (NC = 48) gives a floor near 2^-43 of
+//    the result, BANDS = 4 (NC = 64) near 2^-38;
 //  * the epilogue scales by 2^(E_m + F_n - 14) and forms C = alpha*(hi+lo)*scale + beta*C.
-// Pipeline (persistent, one CTA per SM): warp 0 issues TMA loads (2 stages of S A tiles 128x32 and
-// S B tiles 2NCx32, BF16, 64-byte swizzle), one thread of warp 1 issues the MMAs (M=128, N=2NC,
-// K=16), warps 2-17 read TMEM and convert and store finished tiles while the next tile's MMAs
-// run.  Every mbarrier wait is bounded: on time-out the kernel flags NDSI timeout status, drains
+// Pipeline (persistent, one CTA per SM): warp 0 issues TMA loads (2 to 4 stages, as many as fit
+// shared memory, of S A tiles 128x32 and S B tiles 2NCx32, BF16, 64-byte swizzle), one thread of
+// warp 1 issues the MMAs (M=128, K=16), warps 2-17 read TMEM and convert and store finished tiles
+// while the next tile's MMAs run.  Every mbarrier wait is bounded: on time-out the kernel flags NDSI timeout status, drains
 // what it issued and frees its TMEM.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <type_traits>
 #include <cstdint>
 
 #include "kernels.cuh"
@@ -39,7 +45,7 @@ namespace ndsi {
 void build_split_schedule(const Plan& P, int slices, int bands, std::vector<SplitItem>& items,
                           std::vector<SplitStep>& steps, std::vector<GemmTile>& tiles,
                           std::vector<SliceBlock>& blocks) {
-    const int32_t nc = bands == 5 ? kSplitBNc5 : kSplitBNc;
+    const int32_t nc = split_nc(slices, bands);
     items.assign(P.gemm_items.size(), SplitItem{});
     steps.clear();
     tiles.clear();
@@ -201,6 +207,13 @@ __device__ __forceinline__ void tmem_ld4(uint32_t taddr, float* v) {
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
     for (int i = 0; i < 4; ++i) v[i] = __uint_as_float(r[i]);
+}
+__device__ __forceinline__ void tmem_ld2(uint32_t taddr, float* v) {
+    uint32_t r[2];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x2.b32 {%0,%1}, [%2];" : "=r"(r[0]), "=r"(r[1]) : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+    v[0] = __uint_as_float(r[0]);
+    v[1] = __uint_as_float(r[1]);
 }
 __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float* v) {
     uint32_t r[8];
@@ -713,34 +726,71 @@ template <int NC>
 __host__ __device__ constexpr int tile_bytes_b() { return 2 * NC * kSplitKB * 2; }  // 2NC rows x 64 bytes
 template <int S, int NC>
 __host__ __device__ constexpr int stage_bytes() { return S * (kTileBytes + tile_bytes_b<NC>()); }
+// barriers (128 B), the tile's row / column exponents (768 B) and up to 1 KB lost to aligning the
+// tiles to 1024 bytes
+constexpr int kSplitSmemExtra = 128 + 768 + 1024;
+// Pipeline depth: as many stages (2..4) as fit the 227 KB of shared memory a CTA may use.
+template <int S, int NC>
+__host__ __device__ constexpr int split_stages() {
+    return (227 * 1024 - kSplitSmemExtra) / stage_bytes<S, NC>() >= 4
+               ? 4
+               : ((227 * 1024 - kSplitSmemExtra) / stage_bytes<S, NC>() >= 3 ? 3 : 2);
+}
 template <int S, int NC>
 __host__ __device__ constexpr int split_smem_bytes() {
-    // pipeline tiles, then barriers (128 B) and the tile's row / column exponents (768 B), plus
-    // up to 1 KB lost to aligning the tiles to 1024 bytes
-    return 2 * stage_bytes<S, NC>() + 128 + 768 + 1024;
+    return split_stages<S, NC>() * stage_bytes<S, NC>() + kSplitSmemExtra;
+}
+// Per-scale mode: one accumulator per t+u (any tile width other than the two tail variants).
+template <int NC>
+__host__ __device__ constexpr bool split_exact_mode() { return NC != kSplitBNc && NC != kSplitBNc5; }
+
+// The MMAs of one A digit t in per-scale mode: A_t times the stage's B digits 0 .. S-1-t, which
+// are consecutive rows of one K-major block, land in accumulator columns t*NB .. S*NB, i.e. the
+// product with B_u in the accumulator of scale t+u.  Issued in pieces of at most 256 rows.
+template <int S, int NB, int T, int R0>
+__device__ __forceinline__ void issue_digit(uint32_t tmem, uint64_t da, uint64_t db0, int ks, uint32_t acc) {
+    constexpr int rows = (S - T) * NB;
+    if constexpr (R0 < rows) {
+        constexpr int n = rows - R0 < 256 ? rows - R0 : 256;
+        const uint64_t db = db0 + static_cast<uint64_t>((R0 * 64 + ks * 32) >> 4);
+        umma_bf16(tmem + T * NB + R0, da, db, idesc_bf16(n), acc);
+        issue_digit<S, NB, T, R0 + 256>(tmem, da, db0, ks, acc);
+    }
+}
+template <int S, int NB, int KT, int T>
+__device__ __forceinline__ void issue_digits(uint32_t tmem, uint64_t da0, uint64_t db0, int ks, uint32_t fresh) {
+    if constexpr (T < S) {
+        const uint64_t da = da0 + static_cast<uint64_t>((T * KT + ks * 32) >> 4);
+        // the first digit writes every accumulator: it starts the chunk's sums on its first K16
+        issue_digit<S, NB, T, 0>(tmem, da, db0, ks, (T == 0 && ks == 0) ? fresh : 1u);
+        issue_digits<S, NB, KT, T + 1>(tmem, da0, db0, ks, fresh);
+    }
 }
 
 template <int S, int NC>
 __global__ void __launch_bounds__(kThreads, 1)
     k_gemm_split(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const GemmArgs p) {
-    constexpr int BANDS = NC == kSplitBNc ? 4 : 5;  // TMEM accumulators: BANDS x 2NC columns <= 512
+    constexpr bool EXACT = split_exact_mode<NC>();
+    // TMEM accumulators: one per scale (EXACT), else four or five with a tail; BANDS x 2NC <= 512
+    constexpr int BANDS = EXACT ? S : (NC == kSplitBNc ? 4 : 5);
     constexpr int NB = 2 * NC;                       // accumulator columns per band (Re | Im)
     constexpr int CW = NC / 4;                       // complex columns per epilogue warp
     constexpr int kTileB = tile_bytes_b<NC>();
     constexpr int kStage = stage_bytes<S, NC>();
+    constexpr int STAGES = split_stages<S, NC>();
     constexpr uint32_t kId = idesc_bf16(NB);
     static_assert(BANDS * NB <= 512, "accumulators exceed TMEM");
+    static_assert(CW % 2 == 0, "epilogue column groups read TMEM in pairs of columns");
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + 2 * kStage);
-    uint64_t* full = bars;            // [2]
-    uint64_t* empty = bars + 2;       // [2]
-    uint64_t* chunk_full = bars + 4;
-    uint64_t* mma_done = bars + 6;
-    uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(bars + 8);
-    volatile int* abort = reinterpret_cast<volatile int*>(bars + 9);
-    uint64_t* tmem_free = bars + 10;  // [BANDS]: band b of the last chunk has been read out
-    static_assert(BANDS <= 6, "band barriers overlap the exponent tables");
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + STAGES * kStage);
+    uint64_t* full = bars;                 // [STAGES]
+    uint64_t* empty = bars + 4;            // [STAGES]
+    uint64_t* chunk_full = bars + 8;
+    uint64_t* tmem_free = bars + 9;
+    uint64_t* mma_done = bars + 10;
+    uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(bars + 11);
+    volatile int* abort = reinterpret_cast<volatile int*>(bars + 12);
     int* sm_ea = reinterpret_cast<int*>(bars + 16);  // [128] exponents of the current tile's rows
     int* sm_eb = sm_ea + 128;                         // [64] exponents of its complex columns
 
@@ -752,13 +802,13 @@ __global__ void __launch_bounds__(kThreads, 1)
     auto nkb_of = [&](const GemmTile& t) { return 2 * p.sitems[p.ifirst + t.item].Kpad / kSplitKB; };
 
     if (threadIdx.x == 0) {
-        mbar_init(&full[0], 1);
-        mbar_init(&full[1], 1);
-        mbar_init(&empty[0], 1);
-        mbar_init(&empty[1], 1);
-        mbar_init(chunk_full, 1);
 #pragma unroll
-        for (int b = 0; b < BANDS; ++b) mbar_init(&tmem_free[b], kEpiWarps);
+        for (int st = 0; st < STAGES; ++st) {
+            mbar_init(&full[st], 1);
+            mbar_init(&empty[st], 1);
+        }
+        mbar_init(chunk_full, 1);
+        mbar_init(tmem_free, kEpiWarps);
         mbar_init(mma_done, 1);
         *abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -772,7 +822,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 
     if (warp == 0) {
         if (lane == 0) {
-            // producer: one ring of two stages across all of this CTA's tiles
+            // producer: one ring of STAGES stages across all of this CTA's tiles
             int64_t g = 0;      // K-blocks issued so far (all tiles)
             int64_t armed = 0;
             for (int64_t w = blockIdx.x; w < n_work && !*abort; w += gridDim.x) {
@@ -784,8 +834,9 @@ __global__ void __launch_bounds__(kThreads, 1)
                 const int yB0 = static_cast<int>(pole * p.rowsB + si.rowB + (tile.n0 / NC) * NB);
                 bool ok = true;
                 for (int kb = 0; kb < nkb; ++kb, ++g) {
-                    const int stage = static_cast<int>(g & 1);
-                    if (g >= 2 && !mbar_wait(&empty[stage], static_cast<uint32_t>(((g >> 1) - 1) & 1), abort)) {
+                    const int stage = static_cast<int>(g % STAGES);
+                    if (g >= STAGES &&
+                        !mbar_wait(&empty[stage], static_cast<uint32_t>(((g / STAGES) - 1) & 1), abort)) {
                         ok = false;
                         break;
                     }
@@ -801,9 +852,9 @@ __global__ void __launch_bounds__(kThreads, 1)
                 if (!ok) break;
             }
             if (*abort) {
-                // drain: wait for the last (up to two) armed stages' copies to land
-                for (int64_t k = armed > 2 ? armed - 2 : 0; k < armed; ++k)
-                    mbar_wait_drain(&full[k & 1], static_cast<uint32_t>((k >> 1) & 1));
+                // drain: wait for the last (up to STAGES) armed stages' copies to land
+                for (int64_t k = armed > STAGES ? armed - STAGES : 0; k < armed; ++k)
+                    mbar_wait_drain(&full[k % STAGES], static_cast<uint32_t>((k / STAGES) & 1));
             }
         }
     } else if (warp == 1) {
@@ -815,69 +866,62 @@ __global__ void __launch_bounds__(kThreads, 1)
             for (int64_t w = blockIdx.x; w < n_work && ok; w += gridDim.x) {
                 const int nkb = nkb_of(tile_of(w));
                 for (int kb = 0; kb < nkb; ++kb, ++g) {
-                    const int stage = static_cast<int>(g & 1);
-                    if (!mbar_wait(&full[stage], static_cast<uint32_t>((g >> 1) & 1), abort)) {
+                    const int stage = static_cast<int>(g % STAGES);
+                    if (!mbar_wait(&full[stage], static_cast<uint32_t>((g / STAGES) & 1), abort)) {
                         ok = false;
                         break;
                     }
                     tc_fence_after();
                     const bool first_in_chunk = (kb % kSplitChunkKB) == 0;
-                    // The first K-block of a chunk overwrites the accumulators: each band waits
-                    // until the epilogue has read that band of the previous chunk (the bands are
-                    // released one by one, in the order they are issued here).
-                    const bool wait_bands = first_in_chunk && c > 0;
-                    auto band_free = [&](int band) {
-                        if (!wait_bands) return true;
-                        if (!mbar_wait(&tmem_free[band], static_cast<uint32_t>((c - 1) & 1), abort)) return false;
-                        tc_fence_after();
-                        return true;
-                    };
-                    if (!band_free(BANDS - 1)) {
-                        ok = false;
-                        break;
-                    }
-                    // Descriptors of this stage's slice tiles: the start-address field is the low
-                    // 14 bits (address >> 4), so tile t and K16 half ks are compile-time offsets
-                    // from the stage's first tile.  The pair loops unroll completely (S is a
-                    // template parameter), leaving one 64-bit add and one tcgen05.mma per product.
-                    const uint64_t da0 = sdesc_sw64(smem_u32(a_tile(stage, 0)));
-                    const uint64_t db0 = sdesc_sw64(smem_u32(b_tile(stage, 0)));
-                    const uint32_t fresh = first_in_chunk ? 0u : 1u;
-                    // tail band BANDS-1: slice pairs with t+u >= BANDS+1 (1-based), read out per chunk
-                    // like the others
-#pragma unroll
-                    for (int t = 0; t < S; ++t)
-#pragma unroll
-                        for (int u = 0; u < S; ++u) {
-                            if (t + u > S - 1 || t + u < BANDS - 1) continue;
-                            const bool lead = (t + u == BANDS - 1) && t == 0;  // first tail product of a K-block
-#pragma unroll
-                            for (int ks = 0; ks < 2; ++ks) {
-                                const uint64_t da = da0 + static_cast<uint64_t>((t * kTileBytes + ks * 32) >> 4);
-                                const uint64_t db = db0 + static_cast<uint64_t>((u * kTileB + ks * 32) >> 4);
-                                umma_bf16(tmem + (BANDS - 1) * NB, da, db, kId, (lead && ks == 0) ? fresh : 1u);
-                            }
-                        }
-                    // exact bands 0..BANDS-2: t+u = 2 .. BANDS (1-based), one scale each
-#pragma unroll
-                    for (int band = 0; band < BANDS - 1; ++band) {
-                        if (!band_free(band)) {
+                    if (first_in_chunk && c > 0) {
+                        if (!mbar_wait(tmem_free, static_cast<uint32_t>((c - 1) & 1), abort)) {
                             ok = false;
                             break;
                         }
+                        tc_fence_after();
+                    }
+                    // Descriptors of this stage's slice tiles: the start-address field is the low
+                    // 14 bits (address >> 4), so tile t and K16 half ks are compile-time offsets
+                    // from the stage's first tile.  The loops unroll completely (S is a template
+                    // parameter), leaving one 64-bit add and one tcgen05.mma per instruction.
+                    const uint64_t da0 = sdesc_sw64(smem_u32(a_tile(stage, 0)));
+                    const uint64_t db0 = sdesc_sw64(smem_u32(b_tile(stage, 0)));
+                    const uint32_t fresh = first_in_chunk ? 0u : 1u;
+                    if constexpr (EXACT) {
 #pragma unroll
-                        for (int t = 0; t < S; ++t) {
-                            const int u = band - t;
-                            if (u < 0 || u >= S) continue;
+                        for (int ks = 0; ks < 2; ++ks) issue_digits<S, NB, kTileBytes, 0>(tmem, da0, db0, ks, fresh);
+                    } else {
+                        // tail band BANDS-1: slice pairs with t+u >= BANDS+1 (1-based), read out per
+                        // chunk like the others
 #pragma unroll
-                            for (int ks = 0; ks < 2; ++ks) {
-                                const uint64_t da = da0 + static_cast<uint64_t>((t * kTileBytes + ks * 32) >> 4);
-                                const uint64_t db = db0 + static_cast<uint64_t>((u * kTileB + ks * 32) >> 4);
-                                umma_bf16(tmem + band * NB, da, db, kId, (t == 0 && ks == 0) ? fresh : 1u);
+                        for (int t = 0; t < S; ++t)
+#pragma unroll
+                            for (int u = 0; u < S; ++u) {
+                                if (t + u > S - 1 || t + u < BANDS - 1) continue;
+                                const bool lead = (t + u == BANDS - 1) && t == 0;  // first tail product of a K-block
+#pragma unroll
+                                for (int ks = 0; ks < 2; ++ks) {
+                                    const uint64_t da = da0 + static_cast<uint64_t>((t * kTileBytes + ks * 32) >> 4);
+                                    const uint64_t db = db0 + static_cast<uint64_t>((u * kTileB + ks * 32) >> 4);
+                                    umma_bf16(tmem + (BANDS - 1) * NB, da, db, kId, (lead && ks == 0) ? fresh : 1u);
+                                }
+                            }
+                        // exact bands 0..BANDS-2: t+u = 2 .. BANDS (1-based), one scale each
+#pragma unroll
+                        for (int band = 0; band < BANDS - 1; ++band) {
+#pragma unroll
+                            for (int t = 0; t < S; ++t) {
+                                const int u = band - t;
+                                if (u < 0 || u >= S) continue;
+#pragma unroll
+                                for (int ks = 0; ks < 2; ++ks) {
+                                    const uint64_t da = da0 + static_cast<uint64_t>((t * kTileBytes + ks * 32) >> 4);
+                                    const uint64_t db = db0 + static_cast<uint64_t>((u * kTileB + ks * 32) >> 4);
+                                    umma_bf16(tmem + band * NB, da, db, kId, (t == 0 && ks == 0) ? fresh : 1u);
+                                }
                             }
                         }
                     }
-                    if (!ok) break;
                     umma_commit(&empty[stage]);
                     if ((kb % kSplitChunkKB) == kSplitChunkKB - 1 || kb == nkb - 1) {
                         umma_commit(chunk_full);
@@ -889,9 +933,9 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
     } else {
         // epilogue: warp quarter q reads TMEM lanes 32q..32q+31 (tile rows); column group cg the
-        // complex columns 16cg..16cg+15, i.e. accumulator columns 16cg.. (Re) and 64+16cg.. (Im),
-        // so that every thread holds whole complex elements.  After a tile's last chunk TMEM is
-        // released at once and the conversion to FP64 and the store run from registers while
+        // complex columns cg*CW .. cg*CW+CW-1, i.e. accumulator columns cg*CW.. (Re) and NC+cg*CW..
+        // (Im), so that every thread holds whole complex elements.  After a tile's last chunk TMEM
+        // is released at once and the conversion to FP64 and the store run from registers while
         // the MMAs of the next tile proceed.
         const int q = warp & 3;
         const int cg = (warp - 2) >> 2;
@@ -939,30 +983,41 @@ __global__ void __launch_bounds__(kThreads, 1)
                     break;
                 }
                 tc_fence_after();
-                // bands in the MMA warp's issue order (tail first): each band's values are loaded
-                // into registers and the band is released before the float-float additions, so
-                // the next chunk's MMAs into it can start while the other bands are read
 #pragma unroll
-                for (int bi = 0; bi < BANDS; ++bi) {
-                    const int band = bi == 0 ? BANDS - 1 : bi - 1;
-                    float v[2 * CW];
+                for (int band = 0; band < BANDS; ++band) {
 #pragma unroll
                     for (int part = 0; part < 2; ++part) {  // Re columns, then the matching Im columns
                         const uint32_t base = tmem + (static_cast<uint32_t>(32 * q) << 16) + band * NB +
                                               part * NC + cg * CW;
 #pragma unroll
-                        for (int j0 = 0; j0 + 8 <= CW; j0 += 8) tmem_ld8(base + j0, v + part * CW + j0);
-                        if (CW % 8) tmem_ld4(base + (CW / 8) * 8, v + part * CW + (CW / 8) * 8);
-                    }
-                    tc_fence_before();
-                    __syncwarp();
-                    if (lane == 0) mbar_arrive(&tmem_free[band]);
+                        for (int j0 = 0; j0 + 8 <= CW; j0 += 8) {
+                            float v[8];
+                            tmem_ld8(base + j0, v);
 #pragma unroll
-                    for (int j = 0; j < 2 * CW; ++j) ff_add(hi[j], lo[j], v[j]);
+                            for (int i = 0; i < 8; ++i) ff_add(hi[part * CW + j0 + i], lo[part * CW + j0 + i], v[i]);
+                        }
+                        if (CW % 8 >= 4) {
+                            float v[4];
+                            tmem_ld4(base + (CW / 8) * 8, v);
+#pragma unroll
+                            for (int i = 0; i < 4; ++i)
+                                ff_add(hi[part * CW + (CW / 8) * 8 + i], lo[part * CW + (CW / 8) * 8 + i], v[i]);
+                        }
+                        if (CW % 4 == 2) {
+                            float v[2];
+                            tmem_ld2(base + (CW / 4) * 4, v);
+#pragma unroll
+                            for (int i = 0; i < 2; ++i)
+                                ff_add(hi[part * CW + (CW / 4) * 4 + i], lo[part * CW + (CW / 4) * 4 + i], v[i]);
+                        }
+                    }
                 }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(tmem_free);
             }
             if (!ok || *abort) break;
-            // C = alpha * 2^e (hi + lo) + beta * C for this thread's row and 16 complex columns:
+            // C = alpha * 2^e (hi + lo) + beta * C for this thread's row and CW complex columns:
             // alpha is +-1 and beta 0 or 1 (checked at launch), the sign goes onto the integer
             // result and beta = 1 costs the only FP64 instructions.  A warp stores one column's
             // 32 consecutive rows (512 contiguous bytes) per instruction.
@@ -1004,13 +1059,18 @@ __global__ void __launch_bounds__(kThreads, 1)
 PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
 int g_num_sms = 148;  // multiprocessors of the current device (persistent grid size)
 
+template <int S, int NC>
+cudaError_t set_gemm_attr() {
+    return cudaFuncSetAttribute(k_gemm_split<S, NC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                split_smem_bytes<S, NC>());
+}
 template <int S>
 cudaError_t set_attrs() {
-    cudaError_t e = cudaFuncSetAttribute(k_gemm_split<S, kSplitBNc>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         split_smem_bytes<S, kSplitBNc>());
-    if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(k_gemm_split<S, kSplitBNc5>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             split_smem_bytes<S, kSplitBNc5>());
+    cudaError_t e = set_gemm_attr<S, kSplitBNc>();
+    if (e == cudaSuccess) e = set_gemm_attr<S, kSplitBNc5>();
+    if (e == cudaSuccess) e = set_gemm_attr<S, kSplitBNcX7>();
+    if constexpr (S <= 6)
+        if (e == cudaSuccess) e = set_gemm_attr<S, kSplitBNcX>();
     if (e != cudaSuccess) return e;
     return cudaFuncSetAttribute(k_slice1<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSplitSlice1SmemWide);
 }
@@ -1125,13 +1185,20 @@ static cudaError_t run_mma(const Launch& l, int step_index, const GemmItem* item
                       l.lower, status, step.tcount, np};
     const int64_t work = step.tcount * np;
     const unsigned grid = static_cast<unsigned>(std::max<int64_t>(1, std::min<int64_t>(work, g_num_sms)));
-    if (step.nc == kSplitBNc5)
-        k_gemm_split<S, kSplitBNc5><<<grid, kThreads, split_smem_bytes<S, kSplitBNc5>(), st>>>(B.tmA[step_index],
-                                                                                             B.tmB[step_index], ga);
-    else
-        k_gemm_split<S, kSplitBNc><<<grid, kThreads, split_smem_bytes<S, kSplitBNc>(), st>>>(B.tmA[step_index],
-                                                                                           B.tmB[step_index], ga);
-    return cudaGetLastError();
+    auto go = [&](auto nc_const) {
+        constexpr int NC = decltype(nc_const)::value;
+        k_gemm_split<S, NC><<<grid, kThreads, split_smem_bytes<S, NC>(), st>>>(B.tmA[step_index], B.tmB[step_index], ga);
+        return cudaGetLastError();
+    };
+    switch (step.nc) {
+        case kSplitBNc: return go(std::integral_constant<int, kSplitBNc>{});
+        case kSplitBNc5: return go(std::integral_constant<int, kSplitBNc5>{});
+        case kSplitBNcX7: return go(std::integral_constant<int, kSplitBNcX7>{});
+        case kSplitBNcX:
+            if constexpr (S <= 6) return go(std::integral_constant<int, kSplitBNcX>{});
+            return cudaErrorInvalidValue;
+        default: return cudaErrorInvalidValue;
+    }
 }
 
 cudaError_t split_slice_step(const Launch& l, const GemmItem* items_dev, const SplitItem* sitems_dev,

@@ -10,12 +10,20 @@
 
 namespace ndsi {
 
-// Tile of the split GEMM: 128 output rows x NC complex output columns, NC = 64 with four TMEM
-// accumulator bands (slice products t+u = 2, 3, 4 exact, the rest in a tail band) or NC = 48 with
-// five (t+u = 2..5 exact, the rest in the tail; 5 x 96 TMEM columns), the accurate variant.
+// Tile of the split GEMM: 128 output rows x NC complex output columns.  Default: one TMEM
+// accumulator per slice-product scale t+u (S of them, S x 2NC <= 512 columns: NC = 40 for up to
+// six slices, 32 for seven), filled by one wide MMA per A digit.  Optional: NC = 64 with four
+// accumulators (t+u = 2, 3, 4 exact, the rest in a tail) or NC = 48 with five (t+u = 2..5 exact).
 constexpr int kSplitBM = 128;
 constexpr int kSplitBNc = 64;      // complex columns per tile, four-band variant
 constexpr int kSplitBNc5 = 48;     // complex columns per tile, five-band variant
+constexpr int kSplitBNcX = 40;     // complex columns per tile, one accumulator per scale (S <= 6)
+constexpr int kSplitBNcX7 = 32;    // the same for seven slices
+// Complex columns per tile of a plan: bands 4 or 5 select the tail variants, 0 one accumulator
+// per scale.
+constexpr int split_nc(int slices, int bands) {
+    return bands == 4 ? kSplitBNc : bands == 5 ? kSplitBNc5 : (slices >= 7 ? kSplitBNcX7 : kSplitBNcX);
+}
 constexpr int kSplitSliceRows = 32;  // operand rows per slicing block (two-pass slicer)
 constexpr int kSplitSlice1Smem = 72 * 1024;       // one-pass slicer budget, 4..32 rows per block
 constexpr int kSplitSlice1SmemWide = 200 * 1024;  // budget for very long rows, 1 or 2 rows per block
@@ -42,7 +50,7 @@ struct SplitItem {
 struct SplitStep {
     int64_t rowsA, rowsB, erowsA, erowsB;  // per pole
     int32_t Kcols;                         // row length of the slice buffers (2*max Kpad)
-    int32_t nc;                            // complex columns per output tile (64 or 48)
+    int32_t nc;                            // complex columns per output tile (64, 48, 40 or 32)
     int32_t slice_rows;                    // operand rows per slicing block
     int32_t slice_ldt;                     // one-pass slicing: shared-memory row stride (0: two passes)
     int32_t pad;

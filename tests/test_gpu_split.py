@@ -77,12 +77,12 @@ def test_split_density_lattices(shape, o, nb, leaf, M):
 def test_split_error_falls_with_slices():
     sysm = lattice_system((10, 10, 1), 3, "2d", 99)
     errs = {}
-    for S in (4, 5, 6):
+    for S in (4, 5, 6, 7):
         rho, ne, ref = _rho_split(sysm, 0.01, 30, slices=S)
         errs[S] = np.max(np.abs(rho - ref))
     print("split rho err by slices", errs)
     assert errs[4] > errs[6]
-    assert errs[6] < RHO_TOL_SPLIT
+    assert errs[6] < RHO_TOL_SPLIT and errs[7] < RHO_TOL_SPLIT
 
 
 def test_split_matches_fp64_path_C2():
@@ -121,27 +121,31 @@ def test_autotune_keeps_accuracy():
     assert np.max(np.abs(rho.cpu().numpy() - ref)) < RHO_TOL_SPLIT
 
 
-def test_five_band_accumulation_is_more_accurate():
-    # Five TMEM bands keep slice products with t+u = 5 exact; four leave them in the tail
-    # accumulator, where the tensor core drops low bits of the smaller products.  Five is markedly
-    # closer to the dense inverse.
+def test_accumulators_per_scale_are_most_accurate():
+    # One accumulator per slice-product scale (the default, bands = 0) keeps every scale exact;
+    # five bands keep t+u = 2..5 exact and mix the rest in a tail; four leave t+u = 5 in the tail
+    # too, where the tensor core drops low bits of the smaller products.
     nd = lib()
     sysm = lattice_system((6, 6, 5), 3, "3d", 5)
     Hd, Sd = sysm.dense()
     Z = [-0.2 + 0.004j, 0.3 + 0.02j]
+    refs = [on_pattern(green_dense(Hd, Sd, z), sysm) for z in Z]
     errs = {}
-    for bands in (4, 5):
+    for bands in (0, 4, 5):
         g = _selinv(sysm, Z, leaf_atoms=12, precision=nd.NDSI_PREC_SPLIT, split_bands=bands)
-        errs[bands] = max(np.max(np.abs(g[q] - on_pattern(green_dense(Hd, Sd, z), sysm))) /
-                          np.max(np.abs(on_pattern(green_dense(Hd, Sd, z), sysm))) for q, z in enumerate(Z))
-    print(f"split G rel err: 4 bands {errs[4]:.2e}, 5 bands {errs[5]:.2e}")
+        errs[bands] = max(np.max(np.abs(g[q] - refs[q])) / np.max(np.abs(refs[q])) for q in range(len(Z)))
+    print(f"split G rel err: per scale {errs[0]:.2e}, 4 bands {errs[4]:.2e}, 5 bands {errs[5]:.2e}")
     # Im z = 0.004 is closer to the real axis than any pole of the configs (pi kT >= 0.0063):
-    # four bands lose ~4e-9 here, five stay well inside the tolerance
-    assert errs[5] < 1e-9
+    # four bands lose ~4e-9 here, five and one per scale stay well inside the tolerance
+    assert errs[5] < 1e-9 and errs[0] < 1e-9
     assert errs[5] < errs[4] / 4
+    assert errs[0] <= 2 * errs[5]
+    plan = nd.analyze_system(sysm, leaf_atoms=12, precision=nd.NDSI_PREC_SPLIT)
+    info = nd.ndsi_plan_info(plan)
+    assert info["split_bands"] == info["split_slices"] == 6
 
 
-@pytest.mark.parametrize("bands", [4, 5])
+@pytest.mark.parametrize("bands", [0, 4, 5])
 def test_split_density_bands(bands):
     rho, ne, ref = _rho_split_bands(lattice_system((6, 6, 6), 2, "3d", 123), 0.01, 40, bands)
     assert np.max(np.abs(rho - ref)) < RHO_TOL_SPLIT
