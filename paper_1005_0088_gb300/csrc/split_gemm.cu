@@ -72,11 +72,30 @@ void build_split_schedule(const Plan& P, int slices, int bands, std::vector<Spli
             st.erowsA += s.Mpad;
             st.erowsB += s.Npad;
             kmax = std::max(kmax, s.Kpad);
-            for (int32_t m0 = 0; m0 < g.M; m0 += kSplitBM)
-                for (int32_t n0 = 0; n0 < g.N; n0 += nc) {
-                    if (l.lower && n0 > m0 + kSplitBM - 1) continue;
-                    tiles.push_back(GemmTile{static_cast<int32_t>(i), m0, n0, 0});
-                }
+            // Tile order: the CTAs running at one time take consecutive tiles, so whichever
+            // operand is larger is walked in the outer loop and read from HBM once, while the
+            // other is re-read from L2 - in groups of tiles whose slices fit a share of L2.
+            // (m-major order over a wide B streamed all of B once per 128-row block.)
+            const int32_t mt = (g.M + kSplitBM - 1) / kSplitBM, nt = (g.N + nc - 1) / nc;
+            const double a_tile = static_cast<double>(slices) * 2.0 * s.Kpad * 2.0 * kSplitBM;
+            const double b_tile = static_cast<double>(slices) * 2.0 * s.Kpad * 2.0 * 2.0 * nc;
+            const bool b_outer = b_tile * nt >= a_tile * mt;
+            auto push = [&](int32_t mi, int32_t ni) {
+                const int32_t m0 = mi * kSplitBM, n0 = ni * nc;
+                if (l.lower && n0 > m0 + kSplitBM - 1) return;
+                tiles.push_back(GemmTile{static_cast<int32_t>(i), m0, n0, 0});
+            };
+            if (b_outer) {
+                const int32_t gm = std::max<int32_t>(1, static_cast<int32_t>(kSplitL2Share / a_tile));
+                for (int32_t m1 = 0; m1 < mt; m1 += gm)
+                    for (int32_t ni = 0; ni < nt; ++ni)
+                        for (int32_t mi = m1; mi < std::min(mt, m1 + gm); ++mi) push(mi, ni);
+            } else {
+                const int32_t gn = std::max<int32_t>(1, static_cast<int32_t>(kSplitL2Share / b_tile));
+                for (int32_t n1 = 0; n1 < nt; n1 += gn)
+                    for (int32_t mi = 0; mi < mt; ++mi)
+                        for (int32_t ni = n1; ni < std::min(nt, n1 + gn); ++ni) push(mi, ni);
+            }
         }
         st.tcount = static_cast<int64_t>(tiles.size()) - st.tfirst;
         // slicing: one pass over the operand when a block of rows x K fits the shared-memory
@@ -225,14 +244,17 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float* v) {
     for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-// Shared-memory matrix descriptor: K-major tile of 8-row x 64-byte swizzle atoms stacked along M
-// (stride 512 bytes), descriptor version 1, 64-byte swizzle.
-__device__ __forceinline__ uint64_t sdesc_sw64(uint32_t saddr) {
+// Bytes of one K-major tile row (the stage's K in BF16) and the matching swizzle.
+constexpr int kRowBytes = kSplitKB * 2;
+constexpr int kK16Steps = kSplitKB / 16;  // K16 MMA steps per stage
+// Shared-memory matrix descriptor: K-major tile of 8-row x kRowBytes swizzle atoms stacked along M
+// (stride 8 rows), descriptor version 1, 32-byte (layout 6) or 64-byte (layout 4) swizzle.
+__device__ __forceinline__ uint64_t sdesc_sw(uint32_t saddr) {
     uint64_t d = static_cast<uint64_t>((saddr >> 4) & 0x3FFFu);
     d |= static_cast<uint64_t>(1) << 16;
-    d |= static_cast<uint64_t>(512 >> 4) << 32;
+    d |= static_cast<uint64_t>((8 * kRowBytes) >> 4) << 32;
     d |= static_cast<uint64_t>(1) << 46;
-    d |= static_cast<uint64_t>(4) << 61;
+    d |= static_cast<uint64_t>(kRowBytes == 32 ? 6 : 4) << 61;
     return d;
 }
 // Instruction descriptor: D = F32, A = B = BF16, both K-major, M = 128, N = n (multiple of 16).
@@ -718,23 +740,26 @@ struct GemmArgs {
     int np;                // poles
 };
 
-constexpr int kTileBytes = kSplitBM * kSplitKB * 2;  // 128 rows x 64 bytes
+constexpr int kTileBytes = kSplitBM * kRowBytes;  // 128 rows x kRowBytes
 constexpr int kThreads = 576;
 constexpr int kEpiWarps = 16;
 
 template <int NC>
-__host__ __device__ constexpr int tile_bytes_b() { return 2 * NC * kSplitKB * 2; }  // 2NC rows x 64 bytes
+__host__ __device__ constexpr int tile_bytes_b() { return 2 * NC * kRowBytes; }  // 2NC rows x kRowBytes
 template <int S, int NC>
 __host__ __device__ constexpr int stage_bytes() { return S * (kTileBytes + tile_bytes_b<NC>()); }
-// barriers (128 B), the tile's row / column exponents (768 B) and up to 1 KB lost to aligning the
+// barriers (256 B), the tile's row / column exponents (768 B) and up to 1 KB lost to aligning the
 // tiles to 1024 bytes
-constexpr int kSplitSmemExtra = 128 + 768 + 1024;
+constexpr int kSplitSmemExtra = 256 + 768 + 1024;
+constexpr int kSplitMaxStages = 6;
 // Pipeline depth: as many stages (2..4) as fit the 227 KB of shared memory a CTA may use.
 template <int S, int NC>
 __host__ __device__ constexpr int split_stages() {
-    return (227 * 1024 - kSplitSmemExtra) / stage_bytes<S, NC>() >= 4
-               ? 4
-               : ((227 * 1024 - kSplitSmemExtra) / stage_bytes<S, NC>() >= 3 ? 3 : 2);
+    return (227 * 1024 - kSplitSmemExtra) / stage_bytes<S, NC>() >= kSplitMaxStages
+               ? kSplitMaxStages
+               : ((227 * 1024 - kSplitSmemExtra) / stage_bytes<S, NC>() < 2
+                      ? 2
+                      : (227 * 1024 - kSplitSmemExtra) / stage_bytes<S, NC>());
 }
 template <int S, int NC>
 __host__ __device__ constexpr int split_smem_bytes() {
@@ -752,7 +777,7 @@ __device__ __forceinline__ void issue_digit(uint32_t tmem, uint64_t da, uint64_t
     constexpr int rows = (S - T) * NB;
     if constexpr (R0 < rows) {
         constexpr int n = rows - R0 < 256 ? rows - R0 : 256;
-        const uint64_t db = db0 + static_cast<uint64_t>((R0 * 64 + ks * 32) >> 4);
+        const uint64_t db = db0 + static_cast<uint64_t>((R0 * kRowBytes + ks * 32) >> 4);
         umma_bf16(tmem + T * NB + R0, da, db, idesc_bf16(n), acc);
         issue_digit<S, NB, T, R0 + 256>(tmem, da, db0, ks, acc);
     }
@@ -785,13 +810,14 @@ __global__ void __launch_bounds__(kThreads, 1)
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem + STAGES * kStage);
     uint64_t* full = bars;                 // [STAGES]
-    uint64_t* empty = bars + 4;            // [STAGES]
-    uint64_t* chunk_full = bars + 8;
-    uint64_t* tmem_free = bars + 9;
-    uint64_t* mma_done = bars + 10;
-    uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(bars + 11);
-    volatile int* abort = reinterpret_cast<volatile int*>(bars + 12);
-    int* sm_ea = reinterpret_cast<int*>(bars + 16);  // [128] exponents of the current tile's rows
+    uint64_t* empty = bars + kSplitMaxStages;  // [STAGES]
+    uint64_t* chunk_full = bars + 2 * kSplitMaxStages;
+    uint64_t* tmem_free = chunk_full + 1;
+    uint64_t* mma_done = chunk_full + 2;
+    uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(chunk_full + 3);
+    volatile int* abort = reinterpret_cast<volatile int*>(chunk_full + 4);
+    static_assert(2 * kSplitMaxStages + 5 <= 32, "barriers overflow their 256 bytes");
+    int* sm_ea = reinterpret_cast<int*>(bars + 32);  // [128] exponents of the current tile's rows
     int* sm_eb = sm_ea + 128;                         // [64] exponents of its complex columns
 
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
@@ -884,12 +910,12 @@ __global__ void __launch_bounds__(kThreads, 1)
                     // 14 bits (address >> 4), so tile t and K16 half ks are compile-time offsets
                     // from the stage's first tile.  The loops unroll completely (S is a template
                     // parameter), leaving one 64-bit add and one tcgen05.mma per instruction.
-                    const uint64_t da0 = sdesc_sw64(smem_u32(a_tile(stage, 0)));
-                    const uint64_t db0 = sdesc_sw64(smem_u32(b_tile(stage, 0)));
+                    const uint64_t da0 = sdesc_sw(smem_u32(a_tile(stage, 0)));
+                    const uint64_t db0 = sdesc_sw(smem_u32(b_tile(stage, 0)));
                     const uint32_t fresh = first_in_chunk ? 0u : 1u;
                     if constexpr (EXACT) {
 #pragma unroll
-                        for (int ks = 0; ks < 2; ++ks) issue_digits<S, NB, kTileBytes, 0>(tmem, da0, db0, ks, fresh);
+                        for (int ks = 0; ks < kK16Steps; ++ks) issue_digits<S, NB, kTileBytes, 0>(tmem, da0, db0, ks, fresh);
                     } else {
                         // tail band BANDS-1: slice pairs with t+u >= BANDS+1 (1-based), read out per
                         // chunk like the others
@@ -900,7 +926,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                                 if (t + u > S - 1 || t + u < BANDS - 1) continue;
                                 const bool lead = (t + u == BANDS - 1) && t == 0;  // first tail product of a K-block
 #pragma unroll
-                                for (int ks = 0; ks < 2; ++ks) {
+                                for (int ks = 0; ks < kK16Steps; ++ks) {
                                     const uint64_t da = da0 + static_cast<uint64_t>((t * kTileBytes + ks * 32) >> 4);
                                     const uint64_t db = db0 + static_cast<uint64_t>((u * kTileB + ks * 32) >> 4);
                                     umma_bf16(tmem + (BANDS - 1) * NB, da, db, kId, (lead && ks == 0) ? fresh : 1u);
@@ -914,7 +940,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                                 const int u = band - t;
                                 if (u < 0 || u >= S) continue;
 #pragma unroll
-                                for (int ks = 0; ks < 2; ++ks) {
+                                for (int ks = 0; ks < kK16Steps; ++ks) {
                                     const uint64_t da = da0 + static_cast<uint64_t>((t * kTileBytes + ks * 32) >> 4);
                                     const uint64_t db = db0 + static_cast<uint64_t>((u * kTileB + ks * 32) >> 4);
                                     umma_bf16(tmem + band * NB, da, db, kId, (t == 0 && ks == 0) ? fresh : 1u);
@@ -1112,7 +1138,8 @@ static cudaError_t encode(CUtensorMap* map, void* base, int64_t cols, int64_t ro
     cuuint32_t box[2] = {static_cast<cuuint32_t>(kSplitKB), static_cast<cuuint32_t>(box_rows)};
     cuuint32_t estr[2] = {1, 1};
     CUresult r = g_encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, base, dims, strides, box, estr,
-                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE,
+                          kRowBytes == 32 ? CU_TENSOR_MAP_SWIZZLE_32B : CU_TENSOR_MAP_SWIZZLE_64B,
                           CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }

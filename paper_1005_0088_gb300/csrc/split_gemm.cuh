@@ -27,13 +27,20 @@ constexpr int split_nc(int slices, int bands) {
 constexpr int kSplitSliceRows = 32;  // operand rows per slicing block (two-pass slicer)
 constexpr int kSplitSlice1Smem = 72 * 1024;       // one-pass slicer budget, 4..32 rows per block
 constexpr int kSplitSlice1SmemWide = 200 * 1024;  // budget for very long rows, 1 or 2 rows per block
-constexpr int kSplitKB = 32;       // K per pipeline stage (64-byte rows, 64B swizzle)
-#ifdef NDSI_SPLIT_CHUNK_KB
-constexpr int kSplitChunkKB = NDSI_SPLIT_CHUNK_KB;
+// Stacked K per pipeline stage: 32 BF16 (64-byte rows, 64-byte swizzle, two K16 MMA steps per
+// digit).  16 (32-byte rows, 32-byte swizzle) fits five stages at six slices instead of two, but
+// its half-size row requests loaded L1 and L2 far more and the 3D metallic sweep ran 9% slower.
+#ifdef NDSI_SPLIT_KB
+constexpr int kSplitKB = NDSI_SPLIT_KB;
 #else
-constexpr int kSplitChunkKB = 8;   // stages per exact chunk (256 stacked-K elements)
+constexpr int kSplitKB = 32;
 #endif
+static_assert(kSplitKB == 16 || kSplitKB == 32, "stage K must be 16 or 32");
+constexpr int kSplitChunkKB = 256 / kSplitKB;   // stages per exact chunk (256 stacked-K elements)
 constexpr int kSplitMaxSlices = 7;
+// Bytes of one operand's slices a tile group may keep in L2 while the other operand streams
+// (a third of GB300's 126 MB L2).
+constexpr double kSplitL2Share = 40.0 * 1024 * 1024;
 // Default of ndsi_options.split_far_ratio: density-sweep poles with z_p >= 32 z_1 use one slice
 // fewer (32^2 ~ 2^10 covers the 2^8 larger product error of the shorter expansion).
 constexpr double kSplitFarRatio = 32.0;
@@ -43,7 +50,7 @@ struct SplitItem {
     int64_t rowA, rowB;     // first slice row of the item (A: S*Mpad rows, B: S*2*Npad rows)
     int64_t erowA, erowB;   // first exponent of the item
     int32_t Mpad, Npad;     // Mpad multiple of 128 rows, Npad multiple of nc complex columns
-    int32_t Kpad, pad;      // multiple of 32 (complex K); stacked K is 2*Kpad
+    int32_t Kpad, pad;      // multiple of kSplitKB (complex K); stacked K is 2*Kpad
 };
 
 // Per GEMM launch: sizes of one pole's block in the step buffers, and the split tile range.
