@@ -172,6 +172,16 @@ int ndsi_density_batched(ndsi_plan* plan, const double* H, const double* S, cons
                          const double* kT, int32_t n_poles, double* rho_out, double* n_elec_out,
                          void* stream);
 
+/* One rank's share of ndsi_density_batched when the poles are divided among processes (the
+ * (pole, system) pairs of the batch, split by pole): for every system of the plan, M0 if with_m0
+ * plus the poles pole_begin <= p < pole_end of an n_poles expansion, and each system's
+ * Tr(rho_part S) in n_elec_out[i].  Summed over ranks whose ranges partition [0, n_poles) with one
+ * with_m0, the shares give ndsi_density_batched's results (ndsi_pole_shard picks the ranges).
+ * Arguments, outputs and errors as ndsi_density_batched, plus NDSI_ERR_INVALID for a bad range. */
+int ndsi_density_batched_poles(ndsi_plan* plan, const double* H, const double* S, const double* mu,
+                               const double* kT, int32_t n_poles, int32_t pole_begin, int32_t pole_end,
+                               int32_t with_m0, double* rho_out, double* n_elec_out, void* stream);
+
 /* Sizes and cost figures of a plan (ndsi_plan_summary above) into the caller's *out.
  * Errors: NDSI_ERR_INVALID for NULL arguments. */
 int ndsi_plan_info(const ndsi_plan* plan, ndsi_plan_summary* out);
@@ -241,7 +251,8 @@ int ndsi_density(ndsi_plan* plan, const double* H, const double* S, double mu, d
  * ranges of all ranks partition [0, n_poles) and exactly one rank sets with_m0, the sums over
  * ranks of rho_part and n_elec_part are ndsi_density's rho and Tr(rho S) (equal up to the order
  * of the floating-point additions).  An empty share (pole_begin == pole_end, with_m0 = 0) writes
- * zeros.  Arguments, outputs and synchronisation as ndsi_density; single-system plans only.
+ * zeros.  Arguments, outputs and synchronisation as ndsi_density; single-system plans only
+ * (ndsi_density_batched_poles is the batched form).
  * Errors: NDSI_ERR_INVALID (0 <= pole_begin <= pole_end <= n_poles violated, a batched plan, or
  * as ndsi_density), otherwise as ndsi_density. */
 int ndsi_density_poles(ndsi_plan* plan, const double* H, const double* S, double mu, double kT,

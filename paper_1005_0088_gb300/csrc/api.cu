@@ -480,8 +480,9 @@ int ndsi_analyze_batched(int32_t n_systems, const ndsi_pattern* pats, const int3
     return NDSI_OK;
 }
 
-int ndsi_density_batched(ndsi_plan* h, const double* H, const double* S, const double* mu, const double* kT,
-                         int32_t n_poles, double* rho_out, double* n_elec_out, void* stream) {
+static int density_batched_entry(ndsi_plan* h, const double* H, const double* S, const double* mu,
+                                 const double* kT, int32_t n_poles, const PoleRange* range, double* rho_out,
+                                 double* n_elec_out, void* stream) {
     if (!h || !H || !S || !mu || !kT || !rho_out || n_poles < 1)
         return fail(NDSI_ERR_INVALID, "ndsi_density_batched: invalid argument");
     const int32_t ns = h->P.n_systems;
@@ -502,12 +503,29 @@ int ndsi_density_batched(ndsi_plan* h, const double* H, const double* S, const d
     double* rho_d = rho_dev ? rho_out : h->stage + 2 * h->P.nnz;
     double* ne_d = ne_dev ? n_elec_out : h->stage + 3 * h->P.nnz;
     std::vector<double> muv(mu, mu + ns), ktv(kT, kT + ns);
-    rc = density_impl(h, Hd, Sd, muv.data(), ktv.data(), n_poles, rho_d, ne_d, st);
+    rc = density_impl(h, Hd, Sd, muv.data(), ktv.data(), n_poles, rho_d, ne_d, st, nullptr, range);
     if (rc) return rc;
     if (!rho_dev) NDSI_CK(cudaMemcpyAsync(rho_out, rho_d, sizeof(double) * h->P.nnz, cudaMemcpyDeviceToHost, st));
     if (n_elec_out && !ne_dev) NDSI_CK(cudaMemcpyAsync(n_elec_out, ne_d, sizeof(double) * ns, cudaMemcpyDeviceToHost, st));
     NDSI_CK(cudaStreamSynchronize(st));
     return NDSI_OK;
+}
+
+int ndsi_density_batched(ndsi_plan* h, const double* H, const double* S, const double* mu, const double* kT,
+                         int32_t n_poles, double* rho_out, double* n_elec_out, void* stream) {
+    return density_batched_entry(h, H, S, mu, kT, n_poles, nullptr, rho_out, n_elec_out, stream);
+}
+
+int ndsi_density_batched_poles(ndsi_plan* h, const double* H, const double* S, const double* mu,
+                               const double* kT, int32_t n_poles, int32_t pole_begin, int32_t pole_end,
+                               int32_t with_m0, double* rho_out, double* n_elec_out, void* stream) {
+    if (pole_begin < 0 || pole_end > n_poles || pole_begin > pole_end)
+        return fail(NDSI_ERR_INVALID, "ndsi_density_batched_poles: bad pole range");
+    PoleRange r;
+    r.begin = pole_begin;
+    r.end = pole_end;
+    r.m0 = with_m0 != 0;
+    return density_batched_entry(h, H, S, mu, kT, n_poles, &r, rho_out, n_elec_out, stream);
 }
 
 int ndsi_plan_info(const ndsi_plan* h, ndsi_plan_summary* out) {
@@ -750,12 +768,12 @@ int density_impl(ndsi_plan* h, const double* Hd, const double* Sd, const double*
     const int32_t pb = range ? range->begin : 0;
     const int32_t pe = range ? range->end : n_poles;
     const bool with_m0 = range ? range->m0 : true;
-    if (range && (ns != 1 || e_d || pb < 0 || pe > n_poles || pb > pe))
+    if (range && (e_d || pb < 0 || pe > n_poles || pb > pe))
         return fail(NDSI_ERR_INVALID, "density: bad pole range");
     if (pe - pb + (with_m0 ? 1 : 0) == 0) {
-        // an empty share of the sum: rho = 0, Tr(rho S) = 0
+        // an empty share of the sum: rho = 0, Tr(rho S) = 0 for every system
         NDSI_CK(cudaMemsetAsync(rho_d, 0, sizeof(double) * h->P.nnz, st));
-        NDSI_CK(cudaMemsetAsync(ne_d, 0, sizeof(double), st));
+        NDSI_CK(cudaMemsetAsync(ne_d, 0, sizeof(double) * ns, st));
         return check_status(h, st);
     }
     // Energy density matrix (Eq. 10): the same points with weights -4 R_p alpha_p kT, kappa on the

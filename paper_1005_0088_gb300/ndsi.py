@@ -36,7 +36,7 @@ EXPORTED_SYMBOLS = (
     "ndsi_density_batched", "ndsi_graph_enable", "ndsi_graph_info", "ndsi_autotune",
     "ndsi_density_energy", "ndsi_dos", "ndsi_factors_solve", "ndsi_eigenstates", "ndsi_mu_search",
     "ndsi_mu_search_batched", "ndsi_find_mu_batched", "ndsi_plan_check", "ndsi_density_poles",
-    "ndsi_pole_shard", "ndsi_fp64_peak",
+    "ndsi_pole_shard", "ndsi_fp64_peak", "ndsi_density_batched_poles",
 )
 MU_EVAL_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.c_double, ctypes.POINTER(ctypes.c_double))
 MU_DOS_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.c_int32,
@@ -112,6 +112,8 @@ def load(path: str = LIB_PATH):
     lib.ndsi_density_poles.restype = ctypes.c_int
     lib.ndsi_pole_shard.argtypes = [i32, i32, i32, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32)]
     lib.ndsi_pole_shard.restype = ctypes.c_int
+    lib.ndsi_density_batched_poles.argtypes = [vp, vp, vp, vp, vp, i32, i32, i32, i32, vp, vp, vp]
+    lib.ndsi_density_batched_poles.restype = ctypes.c_int
     lib.ndsi_fp64_peak.argtypes = [ctypes.POINTER(dbl), vp]
     lib.ndsi_fp64_peak.restype = ctypes.c_int
     lib.ndsi_plan_destroy.argtypes = [vp]
@@ -637,4 +639,16 @@ def ndsi_density_batched(plan: Plan, H, S, mu, kT, n_poles, rho_out, n_elec_out=
     _check(load().ndsi_density_batched(plan.handle, _ptr(H), _ptr(S), _ptr(mu), _ptr(kT),
                                        int(n_poles), _ptr(rho_out), _ptr(n_elec_out),
                                        _stream(stream)))
+    return rho_out
+
+
+def ndsi_density_batched_poles(plan: Plan, H, S, mu, kT, n_poles, pole_begin, pole_end, with_m0, rho_out,
+                               n_elec_out=None, stream=None):
+    """One rank's share (poles pole_begin..pole_end-1, M0 if with_m0) of ndsi_density_batched."""
+    mu = np.ascontiguousarray(mu, dtype=np.float64)
+    kT = np.ascontiguousarray(kT, dtype=np.float64)
+    _check(load().ndsi_density_batched_poles(plan.handle, _ptr(H), _ptr(S), _ptr(mu), _ptr(kT),
+                                             int(n_poles), int(pole_begin), int(pole_end),
+                                             int(bool(with_m0)), _ptr(rho_out), _ptr(n_elec_out),
+                                             _stream(stream)))
     return rho_out

@@ -2,7 +2,8 @@
 FP64 throughput probe.
 
 * ndsi_density_poles: the shares ndsi_pole_shard assigns to 1, 2, 3 and 5 ranks sum to
-  ndsi_density's rho and Tr(rho S) (FP64 and split plans); an empty share writes zeros.
+  ndsi_density's rho and Tr(rho S) (FP64 and split plans); an empty share writes zeros; the
+  batched form sums to ndsi_density_batched for every system.
 * split_far_ratio: with the relaxation (default) and without it the density stays within the
   split tolerance of the oracle; it changes nothing on FP64 plans and nothing in ndsi_selinv.
 * ndsi_fp64_peak: a plausible DFMA rate.
@@ -57,6 +58,34 @@ def test_pole_shares_sum_to_density(precision):
     assert np.all(part == 0.0) and pne[0] == 0.0
     with pytest.raises(nd.NdsiError):
         nd.ndsi_density_poles(plan, H, S, mu, kT, M, 5, 41, True, rho, ne)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_batched_pole_shares_sum_to_batched_density(precision):
+    torch = _torch()
+    nd = lib()
+    systems = [lattice_system((9, 1, 1), 3, "1d", 701), lattice_system((5, 4, 1), 2, "2d", 702),
+               lattice_system((4, 3, 3), 2, "3d", 703)]
+    plan = nd.analyze_batched(systems, precision=precision)
+    H = torch.as_tensor(np.concatenate([s.H for s in systems]), device="cuda")
+    S = torch.as_tensor(np.concatenate([s.S for s in systems]), device="cuda")
+    nnz = int(H.shape[0])
+    mus, kts, M = np.array([-0.1, 0.0, 0.05]), np.array([0.01, 0.02, 0.015]), 30
+    rho = torch.zeros(nnz, dtype=torch.float64, device="cuda")
+    ne = torch.zeros(3, dtype=torch.float64, device="cuda")
+    nd.ndsi_density_batched(plan, H, S, mus, kts, M, rho, ne)
+    ref, ne_ref = rho.cpu().numpy(), ne.cpu().numpy()
+    for world in (2, 4):
+        tot, tot_ne = np.zeros(nnz), np.zeros(3)
+        for r in range(world):
+            b, e, m0 = nd.ndsi_pole_shard(M, r, world)
+            part = torch.full((nnz,), float("nan"), dtype=torch.float64, device="cuda")
+            pne = torch.full((3,), float("nan"), dtype=torch.float64, device="cuda")
+            nd.ndsi_density_batched_poles(plan, H, S, mus, kts, M, b, e, m0, part, pne)
+            tot += part.cpu().numpy()
+            tot_ne += pne.cpu().numpy()
+        assert np.max(np.abs(tot - ref)) < 1e-13, world
+        assert np.max(np.abs(tot_ne - ne_ref)) < 1e-10, world
 
 
 def test_far_pole_relaxation_keeps_split_tolerance():
