@@ -108,7 +108,7 @@ class ClockSampler:
         self.fh.close()
 
     def summary(self):
-        sms, mx, reasons = [], 0.0, set()
+        sms, mx, reasons, watts = [], 0.0, set(), []
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         try:
             rows = [ln.split(",") for ln in open(self.path) if ln.strip()]
@@ -121,6 +121,7 @@ class ClockSampler:
             try:
                 sms.append(float(r[1]))
                 mx = max(mx, float(r[2]))
+                watts.append(float(r[3]))
             except ValueError:
                 continue
             for name, v in zip(names, r[5:9]):
@@ -128,7 +129,10 @@ class ClockSampler:
                     reasons.add(name)
         os.unlink(self.path)
         return {"sm_mhz": statistics.median(sms) if sms else None,
-                "sm_max_mhz": mx or None, "reasons": sorted(reasons), "samples": len(sms)}
+                "sm_min_mhz": min(sms) if sms else None,
+                "sm_max_mhz": mx or None, "reasons": sorted(reasons), "samples": len(sms),
+                "power_w_median": statistics.median(watts) if watts else None,
+                "power_w_max": max(watts) if watts else None}
 
 
 # ------------------------------------------------------------------- stored oracle values ---
