@@ -393,7 +393,11 @@ def _autotune(nd, args, plan, H, S, kT, M, n):
         return None
     m = M if n <= 20000 else min(M, 10)
     n_split, n_fp64 = nd.ndsi_autotune(plan, H, S, MU, kT, m)
-    return {"tensor_core_steps": n_split, "fp64_steps": n_fp64, "poles_timed": m}
+    shapes = nd.ndsi_plan_export(plan, "tile_shapes")
+    widths = {int(w): int((shapes == w).sum()) for w in sorted(set(shapes.tolist())) if w > 0}
+    return {"tensor_core_steps": n_split, "fp64_steps": n_fp64, "poles_timed": m,
+            "tensor_steps_by_tile_columns": widths,
+            "launches_per_pole_batch": int(nd.ndsi_plan_info(plan)["n_launches"])}
 
 
 def _timed_steps(torch, step, stream, flush, steps, ahead):

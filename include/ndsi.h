@@ -125,6 +125,11 @@ typedef struct {
 #define NDSI_EXPORT_SCHEDULE     8  /* int32[4*n_launches]: (kind, level, step tag, items) per launch
                                        of one pole batch, in issue order; n_launches from
                                        ndsi_plan_info.n_launches */
+#define NDSI_EXPORT_TILE_SHAPES  9  /* int32[n_launches]: per launch of the schedule, -1 (not a GEMM),
+                                       0 (a GEMM on the FP64 CUDA cores) or the complex columns per
+                                       128-row tile of its tensor-core kernel (40 one accumulator per
+                                       slice scale, 48 five bands, 64 four bands, 32 seven slices),
+                                       as the split options and ndsi_autotune left them */
 
 /* Fill *opt with the defaults listed above. */
 void ndsi_default_options(ndsi_options* opt);
@@ -296,8 +301,12 @@ int ndsi_profile_enable(ndsi_plan* plan, int32_t enable);
  * to the CUDA cores, separator-sized ones to the tensor cores.  A step whose tensor-core time is
  * below the least time the FP64 cores could need for it (its issued FP64 flops at the DFMA rate
  * measured on the device, as ndsi_fp64_peak) is decided without an FP64 run, so on large systems
- * the FP64 sweeps time only the small steps.  Counts of the steps left on each path in
- * *n_split_out / *n_fp64_out (either may be NULL).  Runs four sweeps; the profiler counters are
+ * the FP64 sweeps time only the small steps.  A plan with the default accumulators (one per
+ * slice scale) then times every tensor-core step once more with five accumulator bands (48
+ * complex columns per tile instead of 40, within the same tolerance) and keeps the faster tile per
+ * step (NDSI_EXPORT_TILE_SHAPES lists the result); factors made before the call can no longer be
+ * inverted by ndsi_selinv.  Counts of the steps left on each path in
+ * *n_split_out / *n_fp64_out (either may be NULL).  Runs four to six sweeps; the profiler counters are
  * unchanged and any captured graph is dropped.  FP64 plans: no-op (all steps
  * counted as FP64).  Errors: NDSI_ERR_INVALID for bad arguments or a batched plan; as
  * ndsi_density otherwise. */

@@ -15,6 +15,8 @@ int fail(int code, const std::string& msg) {
 }
 
 // Upload every index table of the plan into one device allocation (first use only).
+static int upload_split(ndsi_plan* h);
+
 int upload_tables(ndsi_plan* h) {
     if (h->T.blob) return NDSI_OK;
     Plan& P = h->P;
@@ -57,17 +59,8 @@ int upload_tables(ndsi_plan* h) {
     NDSI_CK(cudaMemset(T.status, 0, sizeof(int) * 4));
     NDSI_CK(kernels_init());
     if (P.opt.precision == NDSI_PREC_SPLIT) {
-        SplitPlan& S = h->SP;
-        const size_t bi = align256(std::max<size_t>(bytes_of(S.items), 16));
-        const size_t bt = align256(std::max<size_t>(bytes_of(S.tiles), 16));
-        const size_t bb = align256(std::max<size_t>(bytes_of(S.blocks), 16));
-        NDSI_CK(cudaMalloc(&S.blob, bi + bt + bb));
-        S.d_items = reinterpret_cast<SplitItem*>(S.blob);
-        S.d_tiles = reinterpret_cast<GemmTile*>(static_cast<char*>(S.blob) + bi);
-        S.d_blocks = reinterpret_cast<SliceBlock*>(static_cast<char*>(S.blob) + bi + bt);
-        if (!S.items.empty()) NDSI_CK(cudaMemcpy(S.d_items, S.items.data(), bytes_of(S.items), cudaMemcpyHostToDevice));
-        if (!S.tiles.empty()) NDSI_CK(cudaMemcpy(S.d_tiles, S.tiles.data(), bytes_of(S.tiles), cudaMemcpyHostToDevice));
-        if (!S.blocks.empty()) NDSI_CK(cudaMemcpy(S.d_blocks, S.blocks.data(), bytes_of(S.blocks), cudaMemcpyHostToDevice));
+        int rc = upload_split(h);
+        if (rc) return rc;
         NDSI_CK(split_init());
     }
     return NDSI_OK;
@@ -324,17 +317,19 @@ int auto_slices(const Plan&) { return 6; }
 int auto_bands(const Plan&) { return 0; }
 
 // Split-precision metadata of a plan: tensor-core steps, their tile lists and cost figures.
-void setup_split(ndsi_plan* h, const ndsi_options& o) {
+static void build_split_metadata(ndsi_plan* h) {
     SplitPlan& S = h->SP;
-    build_split_schedule(h->P, o.split_slices, o.split_bands, S.items, S.steps, S.tiles, S.blocks);
+    const int slices = h->P.opt.split_slices;
+    build_split_schedule(h->P, slices, S.bands, S.items, S.steps, S.tiles, S.blocks);
     S.step_of_launch.assign(h->P.launches.size(), -1);
-    S.use_split.assign(h->P.launches.size(), 1);
+    S.tensor_flops.clear();
+    S.slice_bytes.clear();
     int k = 0;
     for (size_t li = 0; li < h->P.launches.size(); ++li) {
         const Launch& l = h->P.launches[li];
         if (!split_eligible(l)) continue;
         const SplitStep& st = S.steps[k];
-        S.tensor_flops.push_back(split_executed_flops(h->P, st, S.items, S.tiles, l, o.split_slices));
+        S.tensor_flops.push_back(split_executed_flops(h->P, st, S.items, S.tiles, l, slices));
         double sb = 0;
         for (int64_t i = 0; i < l.count; ++i) {
             const GemmItem& g = h->P.gemm_items[l.first + i];
@@ -345,6 +340,44 @@ void setup_split(ndsi_plan* h, const ndsi_options& o) {
         S.slice_bytes.push_back(sb);
         S.step_of_launch[li] = k++;
     }
+    ++S.generation;
+}
+
+void setup_split(ndsi_plan* h, const ndsi_options& o) {
+    SplitPlan& S = h->SP;
+    S.bands.assign(h->P.launches.size(), static_cast<int8_t>(o.split_bands));
+    S.use_split.assign(h->P.launches.size(), 1);
+    build_split_metadata(h);
+}
+
+static int upload_split(ndsi_plan* h) {
+    SplitPlan& S = h->SP;
+    if (S.blob) cudaFree(S.blob);
+    S.blob = nullptr;
+    const size_t bi = align256(std::max<size_t>(bytes_of(S.items), 16));
+    const size_t bt = align256(std::max<size_t>(bytes_of(S.tiles), 16));
+    const size_t bb = align256(std::max<size_t>(bytes_of(S.blocks), 16));
+    NDSI_CK(cudaMalloc(&S.blob, bi + bt + bb));
+    S.d_items = reinterpret_cast<SplitItem*>(S.blob);
+    S.d_tiles = reinterpret_cast<GemmTile*>(static_cast<char*>(S.blob) + bi);
+    S.d_blocks = reinterpret_cast<SliceBlock*>(static_cast<char*>(S.blob) + bi + bt);
+    if (!S.items.empty()) NDSI_CK(cudaMemcpy(S.d_items, S.items.data(), bytes_of(S.items), cudaMemcpyHostToDevice));
+    if (!S.tiles.empty()) NDSI_CK(cudaMemcpy(S.d_tiles, S.tiles.data(), bytes_of(S.tiles), cudaMemcpyHostToDevice));
+    if (!S.blocks.empty()) NDSI_CK(cudaMemcpy(S.d_blocks, S.blocks.data(), bytes_of(S.blocks), cudaMemcpyHostToDevice));
+    return NDSI_OK;
+}
+
+int rebuild_split(ndsi_plan* h) {
+    NDSI_CK(cudaDeviceSynchronize());   // no launch of the old schedule may still read its tables
+    build_split_metadata(h);
+    split_free(h->SB);
+    if (h->graph) {
+        cudaGraphExecDestroy(h->graph);
+        h->graph = nullptr;
+        h->graph_key.clear();
+        h->graph_nodes = 0;
+    }
+    return h->T.blob ? upload_split(h) : NDSI_OK;
 }
 int sweep(ndsi_plan* h, const double* Hd, const double* Sd, int32_t nq, int32_t n_near, int32_t chunk,
           const std::vector<int>& part_off, double* rho_d, double* ne_d, double* e_d, cudaStream_t st);
@@ -552,7 +585,8 @@ int ndsi_plan_info(const ndsi_plan* h, ndsi_plan_summary* out) {
 int ndsi_plan_export(const ndsi_plan* h, int32_t what, void* out) {
     if (!h || !out) return fail(NDSI_ERR_INVALID, "ndsi_plan_export: NULL argument");
     const Plan& P = h->P;
-    if (P.n_systems != 1 && what != NDSI_EXPORT_SCHEDULE && what != NDSI_EXPORT_LEVEL && what != NDSI_EXPORT_PARENT)
+    if (P.n_systems != 1 && what != NDSI_EXPORT_SCHEDULE && what != NDSI_EXPORT_LEVEL && what != NDSI_EXPORT_PARENT &&
+        what != NDSI_EXPORT_TILE_SHAPES)
         return fail(NDSI_ERR_INVALID, "ndsi_plan_export: ordering tables are per system; not available for a batch");
     switch (what) {
         case NDSI_EXPORT_PERM_ATOMS: std::memcpy(out, P.perm_atoms.data(), bytes_of(P.perm_atoms)); break;
@@ -571,6 +605,21 @@ int ndsi_plan_export(const ndsi_plan* h, int32_t what, void* out) {
                 o[4 * i + 1] = P.launches[i].level;
                 o[4 * i + 2] = P.launches[i].tag;
                 o[4 * i + 3] = static_cast<int32_t>(P.launches[i].count);
+            }
+            break;
+        }
+        case NDSI_EXPORT_TILE_SHAPES: {
+            int32_t* o = static_cast<int32_t*>(out);
+            const bool split = P.opt.precision == NDSI_PREC_SPLIT;
+            for (size_t i = 0; i < P.launches.size(); ++i) {
+                const Launch& l = P.launches[i];
+                if (l.kind != L_GEMM) {
+                    o[i] = -1;
+                } else if (!split || !split_eligible(l) || !h->SP.use_split[i]) {
+                    o[i] = 0;
+                } else {
+                    o[i] = h->SP.steps[h->SP.step_of_launch[i]].nc;
+                }
             }
             break;
         }
@@ -594,6 +643,7 @@ int ndsi_factor_poles(ndsi_plan* h, const double* H, const double* S, const doub
     if (!f) return fail(NDSI_ERR_OOM, "ndsi_factor_poles: out of host memory");
     f->plan = h;
     f->np = n_poles;
+    f->split_gen = h->SP.generation;
     rc = alloc_workspace(f->W, h->P, n_poles);
     if (rc) {
         free_workspace(f->W);
@@ -636,6 +686,8 @@ int ndsi_factor_poles(ndsi_plan* h, const double* H, const double* S, const doub
 int ndsi_selinv(ndsi_factors* f, double* G_out, void* stream) {
     if (!f || !f->plan) return fail(NDSI_ERR_INVALID, "ndsi_selinv: NULL factors");
     ndsi_plan* h = f->plan;
+    if (f->split_gen != h->SP.generation)
+        return fail(NDSI_ERR_INVALID, "ndsi_selinv: the plan's split schedule was retuned after these factors were made");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     int rc = run_phase(h, f->W, f->SB, 1, nullptr, nullptr, f->zd, 0, f->np, st);
     f->inverted = true;
@@ -1132,6 +1184,29 @@ int ndsi_autotune(ndsi_plan* h, const double* H, const double* S, double mu, dou
         h->SP.use_split[li] = !rc && split_eligible(h->P.launches[li])
                                   ? (decided[li] || t_split[li] <= t_fp64[li] ? 1 : 0)
                                   : 1;
+    // Tile shape of each tensor-core step: one accumulator per scale (40 complex columns per
+    // tile, the plan default) or five accumulator bands (48 columns, a floor near 2^-43 of the
+    // result, well inside the split tolerance).  The wider tile carries more multiply-adds per
+    // operand byte; which one is faster depends on the step's shapes, so each step keeps the
+    // faster of the two timings.  Plans built with a fixed band count keep it.
+    bool per_scale = true;
+    for (size_t li = 0; li < nl; ++li)
+        if (split_eligible(h->P.launches[li]) && h->SP.bands[li] != 0) per_scale = false;
+    if (!rc && per_scale) {
+        std::vector<double> t_b5(nl, 0.0);
+        for (size_t li = 0; li < nl; ++li)
+            if (split_eligible(h->P.launches[li]) && h->SP.use_split[li]) h->SP.bands[li] = 5;
+        rc = rebuild_split(h);
+        for (int pass = 0; pass < 2 && !rc; ++pass) {
+            h->prof.per_launch = pass == 0 ? nullptr : &t_b5;
+            rc = density_impl(h, Hd, Sd, &mu, &kT, n_poles, rho_d, ne_d, st);
+        }
+        h->prof.per_launch = nullptr;
+        for (size_t li = 0; li < nl; ++li)
+            h->SP.bands[li] = (!rc && h->SP.bands[li] == 5 && t_b5[li] < t_split[li]) ? 5 : 0;
+        const int rc2 = rebuild_split(h);
+        if (!rc) rc = rc2;
+    }
     saved.pool = h->prof.pool;  // events created meanwhile stay owned by the plan
     h->prof = saved;
     h->prof.pending.clear();

@@ -61,6 +61,8 @@ struct SplitPlan {
     std::vector<double> tensor_flops;   // per step, one pole
     std::vector<double> slice_bytes;    // per step, one pole: FP64 operand reads + BF16 slice writes
     std::vector<char> use_split;        // per launch: 1 = tensor-core path (autotuner may clear)
+    std::vector<int8_t> bands;          // per launch: accumulator layout (0 per scale, 4 or 5 bands)
+    int64_t generation = 0;             // bumped whenever the schedule is rebuilt
     SplitItem* d_items = nullptr;
     GemmTile* d_tiles = nullptr;
     SliceBlock* d_blocks = nullptr;
@@ -114,6 +116,7 @@ struct ndsi_factors {
     double2* zd = nullptr;
     int32_t np = 0;
     bool inverted = false;  // ndsi_selinv has replaced the factors by G
+    int64_t split_gen = 0;  // split schedule generation the factors were made with
     double2* solve_buf = nullptr;  // work space of ndsi_factors_solve (two n x k blocks)
     int64_t solve_cap = 0;         // complex elements per block
 };
@@ -172,6 +175,10 @@ int dos_sweep_systems(ndsi_plan* h, const double* Hd, const double* Sd, const do
                       double* D, cudaStream_t st);
 int dos_sweep(ndsi_plan* h, const double* Hd, const double* Sd, const double* E, int nE, double eta, double* D,
               cudaStream_t st);
+
+// (Re)build the split schedule of a plan from SplitPlan::bands; when its tables are on the device
+// they are uploaded again and the slice buffers (whose tensor maps follow the schedule) dropped.
+int rebuild_split(ndsi_plan* h);
 
 // Measured FP64 (DFMA) throughput of the current device in TFLOP/s (peak.cu).
 int fp64_rate(cudaStream_t st, double* tflops_out);

@@ -34,6 +34,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <type_traits>
 #include <cstdint>
 
@@ -42,16 +43,17 @@
 
 namespace ndsi {
 
-void build_split_schedule(const Plan& P, int slices, int bands, std::vector<SplitItem>& items,
-                          std::vector<SplitStep>& steps, std::vector<GemmTile>& tiles,
-                          std::vector<SliceBlock>& blocks) {
-    const int32_t nc = split_nc(slices, bands);
+void build_split_schedule(const Plan& P, int slices, const std::vector<int8_t>& bands,
+                          std::vector<SplitItem>& items, std::vector<SplitStep>& steps,
+                          std::vector<GemmTile>& tiles, std::vector<SliceBlock>& blocks) {
     items.assign(P.gemm_items.size(), SplitItem{});
     steps.clear();
     tiles.clear();
     blocks.clear();
-    for (const Launch& l : P.launches) {
+    for (size_t li = 0; li < P.launches.size(); ++li) {
+        const Launch& l = P.launches[li];
         if (!split_eligible(l)) continue;
+        const int32_t nc = split_nc(slices, bands[li]);
         SplitStep st{};
         st.nc = nc;
         int32_t kmax = 0;
@@ -72,29 +74,52 @@ void build_split_schedule(const Plan& P, int slices, int bands, std::vector<Spli
             st.erowsA += s.Mpad;
             st.erowsB += s.Npad;
             kmax = std::max(kmax, s.Kpad);
-            // Tile order: the CTAs running at one time take consecutive tiles, so whichever
-            // operand is larger is walked in the outer loop and read from HBM once, while the
-            // other is re-read from L2 - in groups of tiles whose slices fit a share of L2.
-            // (m-major order over a wide B streamed all of B once per 128-row block.)
+            // Tile order.  The persistent CTAs take consecutive tiles, about kSplitConcurrentTiles
+            // at a time, and move through K at about the same pace, so a K-block of an operand tile
+            // that several running CTAs share is read from HBM once and from L2 by the others.
+            // Tiles are ordered in groups of g row tiles (column tiles) swept across all column
+            // (row) tiles; the group keeps its operand in L2 for the whole sweep when it fits a
+            // share of L2, and otherwise shares it only among the tiles running together.  The
+            // group size and direction with the fewest estimated DRAM bytes win: a wide operand
+            // streamed once per 128-row block (row-block order) read a 4000-wide L_RJ 9x over.
             const int32_t mt = (g.M + kSplitBM - 1) / kSplitBM, nt = (g.N + nc - 1) / nc;
             const double a_tile = static_cast<double>(slices) * 2.0 * s.Kpad * 2.0 * kSplitBM;
             const double b_tile = static_cast<double>(slices) * 2.0 * s.Kpad * 2.0 * 2.0 * nc;
-            const bool b_outer = b_tile * nt >= a_tile * mt;
+            // DRAM bytes of the order "groups of gp tiles along P swept across all q of Q"
+            auto traffic = [&](int32_t gp, int32_t np_, int32_t nq, double p_tile, double q_tile) {
+                const double groups = std::ceil(static_cast<double>(np_) / gp);
+                const double q_bytes = q_tile * nq * groups;      // each q tile once per group
+                double p_reads = 1.0;                             // the group's p tiles...
+                if (gp * p_tile > kSplitL2Share) {                // ...unless they leave L2
+                    const double together = std::max(1.0, static_cast<double>(kSplitConcurrentTiles) / gp);
+                    p_reads = std::ceil(nq / together);
+                }
+                return q_bytes + p_tile * np_ * p_reads;
+            };
+            int32_t best_g = 1;
+            bool rows_grouped = true;
+            double best = -1.0;
+            for (int32_t gsz = 1; gsz <= mt; ++gsz) {
+                const double t = traffic(gsz, mt, nt, a_tile, b_tile);
+                if (best < 0 || t < best) { best = t; best_g = gsz; rows_grouped = true; }
+            }
+            for (int32_t gsz = 1; gsz <= nt; ++gsz) {
+                const double t = traffic(gsz, nt, mt, b_tile, a_tile);
+                if (t < best) { best = t; best_g = gsz; rows_grouped = false; }
+            }
             auto push = [&](int32_t mi, int32_t ni) {
                 const int32_t m0 = mi * kSplitBM, n0 = ni * nc;
                 if (l.lower && n0 > m0 + kSplitBM - 1) return;
                 tiles.push_back(GemmTile{static_cast<int32_t>(i), m0, n0, 0});
             };
-            if (b_outer) {
-                const int32_t gm = std::max<int32_t>(1, static_cast<int32_t>(kSplitL2Share / a_tile));
-                for (int32_t m1 = 0; m1 < mt; m1 += gm)
+            if (rows_grouped) {
+                for (int32_t m1 = 0; m1 < mt; m1 += best_g)
                     for (int32_t ni = 0; ni < nt; ++ni)
-                        for (int32_t mi = m1; mi < std::min(mt, m1 + gm); ++mi) push(mi, ni);
+                        for (int32_t mi = m1; mi < std::min(mt, m1 + best_g); ++mi) push(mi, ni);
             } else {
-                const int32_t gn = std::max<int32_t>(1, static_cast<int32_t>(kSplitL2Share / b_tile));
-                for (int32_t n1 = 0; n1 < nt; n1 += gn)
+                for (int32_t n1 = 0; n1 < nt; n1 += best_g)
                     for (int32_t mi = 0; mi < mt; ++mi)
-                        for (int32_t ni = n1; ni < std::min(nt, n1 + gn); ++ni) push(mi, ni);
+                        for (int32_t ni = n1; ni < std::min(nt, n1 + best_g); ++ni) push(mi, ni);
             }
         }
         st.tcount = static_cast<int64_t>(tiles.size()) - st.tfirst;

@@ -39,8 +39,10 @@ static_assert(kSplitKB == 16 || kSplitKB == 32, "stage K must be 16 or 32");
 constexpr int kSplitChunkKB = 256 / kSplitKB;   // stages per exact chunk (256 stacked-K elements)
 constexpr int kSplitMaxSlices = 7;
 // Bytes of one operand's slices a tile group may keep in L2 while the other operand streams
-// (a third of GB300's 126 MB L2).
+// (a third of GB300's 126 MB L2), and the tiles the persistent GEMM runs at one time (one CTA on
+// each of GB300's 152 SMs).
 constexpr double kSplitL2Share = 40.0 * 1024 * 1024;
+constexpr int kSplitConcurrentTiles = 152;
 // Default of ndsi_options.split_far_ratio: density-sweep poles with z_p >= 32 z_1 use one slice
 // fewer (32^2 ~ 2^10 covers the 2^8 larger product error of the shorter expansion).
 constexpr double kSplitFarRatio = 32.0;
@@ -72,9 +74,10 @@ struct SliceBlock {
 };
 
 // Build the split metadata of every GEMM launch (called by the analysis in split mode).
-void build_split_schedule(const Plan& P, int slices, int bands, std::vector<SplitItem>& items,
-                          std::vector<SplitStep>& steps, std::vector<GemmTile>& tiles,
-                          std::vector<SliceBlock>& blocks);
+// bands[li]: accumulator layout of launch li (0 one per scale, 4 or 5 with a tail).
+void build_split_schedule(const Plan& P, int slices, const std::vector<int8_t>& bands,
+                          std::vector<SplitItem>& items, std::vector<SplitStep>& steps,
+                          std::vector<GemmTile>& tiles, std::vector<SliceBlock>& blocks);
 
 struct SplitBuffers {
     uint16_t* sliceA = nullptr;   // bf16 bit patterns

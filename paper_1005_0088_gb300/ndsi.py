@@ -24,7 +24,7 @@ NDSI_ERR_UNSUPPORTED = 6
 NDSI_PREC_FP64 = 0
 NDSI_PREC_SPLIT = 1
 EXPORT = dict(perm_atoms=1, perm_basis=2, node_atoms=3, parent=4, struct_ptr=5, struct_atoms=6,
-              level=7, schedule=8)
+              level=7, schedule=8, tile_shapes=9)
 
 # Every function declared in include/ndsi.h.
 EXPORTED_SYMBOLS = (
@@ -283,7 +283,7 @@ def ndsi_plan_check(plan: Plan) -> None:
 
 def ndsi_plan_export(plan: Plan, what: str) -> np.ndarray:
     """One structure table of the plan (perm_atoms, perm_basis, node_atoms, parent, struct_ptr,
-    struct_atoms, schedule) as a numpy array."""
+    struct_atoms, schedule, tile_shapes) as a numpy array."""
     info = ndsi_plan_info(plan)
     nn = info["n_nodes"]
     if what == "struct_atoms":
@@ -294,7 +294,7 @@ def ndsi_plan_export(plan: Plan, what: str) -> np.ndarray:
     sizes = dict(perm_atoms=(info["n_atoms"], np.int32), perm_basis=(info["n"], np.int32),
                  node_atoms=(nn + 1, np.int32), parent=(nn, np.int32),
                  struct_ptr=(nn + 1, np.int64), level=(nn, np.int32),
-                 schedule=(4 * info["n_launches"], np.int32))
+                 schedule=(4 * info["n_launches"], np.int32), tile_shapes=(info["n_launches"], np.int32))
     cnt, dt = sizes[what]
     out = np.zeros(cnt, dtype=dt)
     _check(load().ndsi_plan_export(plan.handle, EXPORT[what], _ptr(out)))

@@ -109,9 +109,18 @@ def test_autotune_keeps_accuracy():
     plan = nd.analyze_system(sysm, precision=nd.NDSI_PREC_SPLIT)
     H = torch.as_tensor(sysm.H, device="cuda")
     S = torch.as_tensor(sysm.S, device="cuda")
+    f_old = nd.ndsi_factor_poles(plan, H, S, np.array([mu + 0.05j]))
     n_split, n_fp64 = nd.ndsi_autotune(plan, H, S, mu, kT, M)
     sched = nd.ndsi_plan_export(plan, "schedule")
     assert n_split + n_fp64 == sum(1 for k, l, t, c in sched if k == 3 and t not in (3, 4, 6, 7))
+    # every tensor-core step keeps one of the two tile shapes it was timed with
+    shapes = nd.ndsi_plan_export(plan, "tile_shapes")
+    assert set(shapes[shapes > 0].tolist()) <= {40, 48}
+    assert int((shapes > 0).sum()) == n_split
+    assert all(shapes[i] == -1 for i, (k, l, t, c) in enumerate(sched) if k != 3)
+    # factors made before the retuning are refused by the selected inversion
+    with pytest.raises(nd.NdsiError):
+        nd.ndsi_selinv(f_old, None)
     rho = torch.zeros(sysm.nnz, dtype=torch.float64, device="cuda")
     ne = torch.zeros(1, dtype=torch.float64, device="cuda")
     for _ in range(2):
