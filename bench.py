@@ -500,7 +500,7 @@ def _other_leg(nd, torch, args, system, H, S, kT, M, stream, flush, prec_code, f
 
     def step2():
         nd.ndsi_density(plan2, H, S, MU, kT, Mo, rho2, ne2, stream=stream)
-    w2, k2 = (max(args.warmup, 3), args.steps) if Mo == M else (1, min(args.steps, 2))
+    w2, k2 = (max(args.warmup, 3), args.steps) if Mo == M else (1, 1)
     t2, prof2, _ = _measure(nd, torch, plan2, step2, k2, w2, stream, flush, 1)
     ms2 = sum(t2) / len(t2)
     rl2, kk2 = _roofline(prof2, 1, _peaks(), fp64_peak)

@@ -505,7 +505,10 @@ cudaError_t launch_step(const Plan& P, const DevTables& T, const Launch& l, cons
             return cudaErrorInvalidValue;
         }
         case L_COPY: {
-            dim3 grid(static_cast<unsigned>(l.count), static_cast<unsigned>(np), 8);
+            // column slices per item: launches of few items (the upper tree levels) would
+            // otherwise leave most SMs idle
+            const unsigned zc = l.count * np < 4 * 152 ? 32u : 8u;
+            dim3 grid(static_cast<unsigned>(l.count), static_cast<unsigned>(np), zc);
             k_copy<<<grid, 256, 0, st>>>(T.copy_items, l.first, W.scr, W.scr_stride, W.fronts, W.front_stride,
                                          l.alpha);
             return cudaGetLastError();
