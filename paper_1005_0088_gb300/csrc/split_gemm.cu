@@ -243,30 +243,34 @@ __device__ __forceinline__ void umma_commit(uint64_t* bar) {
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
-__device__ __forceinline__ void tmem_ld4(uint32_t taddr, float* v) {
-    uint32_t r[4];
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
-                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
-                 : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int i = 0; i < 4; ++i) v[i] = __uint_as_float(r[i]);
-}
-__device__ __forceinline__ void tmem_ld2(uint32_t taddr, float* v) {
-    uint32_t r[2];
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x2.b32 {%0,%1}, [%2];" : "=r"(r[0]), "=r"(r[1]) : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-    v[0] = __uint_as_float(r[0]);
-    v[1] = __uint_as_float(r[1]);
-}
-__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float* v) {
-    uint32_t r[8];
+// TMEM loads without the wait: the registers are valid only after tmem_wait_ld, which names them
+// as outputs so that no use of them is scheduled before it.
+__device__ __forceinline__ void tmem_ld8_async(uint32_t taddr, uint32_t* r) {
     asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
                  : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
                  : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_ld4_async(uint32_t taddr, uint32_t* r) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_ld2_async(uint32_t taddr, uint32_t* r) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x2.b32 {%0,%1}, [%2];" : "=r"(r[0]), "=r"(r[1]) : "r"(taddr));
+}
+// W consecutive accumulator columns (W even) of this warp's 32 lanes into r[0, W)
+template <int W>
+__device__ __forceinline__ void tmem_ld_cols_async(uint32_t taddr, uint32_t* r) {
+#pragma unroll
+    for (int j0 = 0; j0 + 8 <= W; j0 += 8) tmem_ld8_async(taddr + j0, r + j0);
+    if constexpr (W % 8 >= 4) tmem_ld4_async(taddr + (W / 8) * 8, r + (W / 8) * 8);
+    if constexpr (W % 4 == 2) tmem_ld2_async(taddr + (W / 4) * 4, r + (W / 4) * 4);
+}
+template <int N>
+__device__ __forceinline__ void tmem_wait_ld(uint32_t* r) {
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-    for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
+    for (int i = 0; i < N; ++i) asm volatile("" : "+r"(r[i]));
 }
 
 // Bytes of one K-major tile row (the stage's K in BF16) and the matching swizzle.
@@ -768,6 +772,10 @@ struct GemmArgs {
 constexpr int kTileBytes = kSplitBM * kRowBytes;  // 128 rows x kRowBytes
 constexpr int kThreads = 576;
 constexpr int kEpiWarps = 16;
+// Epilogue TMEM read-out with two band buffers (register budget: 2 x 2CW values beside the 4CW
+// float-float sums)
+template <int CW>
+constexpr bool kEpiDoubleBuffer = CW <= 12;
 
 template <int NC>
 __host__ __device__ constexpr int tile_bytes_b() { return 2 * NC * kRowBytes; }  // 2NC rows x kRowBytes
@@ -1034,38 +1042,56 @@ __global__ void __launch_bounds__(kThreads, 1)
                     break;
                 }
                 tc_fence_after();
+                // A band's Re and Im columns are requested together and awaited once; with two
+                // buffers the next band's loads are in flight while this band's sums run.  TMEM goes
+                // back to the MMA warp as soon as the last band is in registers.
+                auto load_band = [&](int band, uint32_t* r) {
 #pragma unroll
-                for (int band = 0; band < BANDS; ++band) {
+                    for (int part = 0; part < 2; ++part)  // Re columns, then the matching Im columns
+                        tmem_ld_cols_async<CW>(tmem + (static_cast<uint32_t>(32 * q) << 16) + band * NB +
+                                                   part * NC + cg * CW,
+                                               r + part * CW);
+                };
+                auto release = [&]() {
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(tmem_free);
+                };
+                auto sum_band = [&](const uint32_t* r) {
 #pragma unroll
-                    for (int part = 0; part < 2; ++part) {  // Re columns, then the matching Im columns
-                        const uint32_t base = tmem + (static_cast<uint32_t>(32 * q) << 16) + band * NB +
-                                              part * NC + cg * CW;
+                    for (int i = 0; i < 2 * CW; ++i) ff_add(hi[i], lo[i], __uint_as_float(r[i]));
+                };
+                (void)load_band;
+                (void)sum_band;
+                if constexpr (kEpiDoubleBuffer<CW>) {
+                    uint32_t r[2][2 * CW];
+                    load_band(0, r[0]);
+                    tmem_wait_ld<2 * CW>(r[0]);
 #pragma unroll
-                        for (int j0 = 0; j0 + 8 <= CW; j0 += 8) {
-                            float v[8];
-                            tmem_ld8(base + j0, v);
-#pragma unroll
-                            for (int i = 0; i < 8; ++i) ff_add(hi[part * CW + j0 + i], lo[part * CW + j0 + i], v[i]);
-                        }
-                        if (CW % 8 >= 4) {
-                            float v[4];
-                            tmem_ld4(base + (CW / 8) * 8, v);
-#pragma unroll
-                            for (int i = 0; i < 4; ++i)
-                                ff_add(hi[part * CW + (CW / 8) * 8 + i], lo[part * CW + (CW / 8) * 8 + i], v[i]);
-                        }
-                        if (CW % 4 == 2) {
-                            float v[2];
-                            tmem_ld2(base + (CW / 4) * 4, v);
-#pragma unroll
-                            for (int i = 0; i < 2; ++i)
-                                ff_add(hi[part * CW + (CW / 4) * 4 + i], lo[part * CW + (CW / 4) * 4 + i], v[i]);
-                        }
+                    for (int band = 0; band < BANDS; ++band) {
+                        if (band + 1 < BANDS) load_band(band + 1, r[(band + 1) & 1]);
+                        sum_band(r[band & 1]);
+                        if (band + 1 < BANDS) tmem_wait_ld<2 * CW>(r[(band + 1) & 1]);
+                        if (band + 1 == BANDS - 1) release();
                     }
+                    if constexpr (BANDS == 1) release();
+                } else {
+                    // wide column groups: one part (Re or Im columns) at a time
+#pragma unroll
+                    for (int band = 0; band < BANDS; ++band)
+#pragma unroll
+                        for (int part = 0; part < 2; ++part) {
+                            uint32_t r[CW];
+                            tmem_ld_cols_async<CW>(tmem + (static_cast<uint32_t>(32 * q) << 16) + band * NB +
+                                                       part * NC + cg * CW,
+                                                   r);
+                            tmem_wait_ld<CW>(r);
+                            if (band == BANDS - 1 && part == 1) release();
+#pragma unroll
+                            for (int i = 0; i < CW; ++i)
+                                ff_add(hi[part * CW + i], lo[part * CW + i], __uint_as_float(r[i]));
+                        }
                 }
-                tc_fence_before();
-                __syncwarp();
-                if (lane == 0) mbar_arrive(tmem_free);
             }
             if (!ok || *abort) break;
             // C = alpha * 2^e (hi + lo) + beta * C for this thread's row and CW complex columns:
