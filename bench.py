@@ -1044,7 +1044,9 @@ def run_eigen(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=None,
+                    help="timed steps (default 10; 2 for the 3D metallic lattice, ~25 s a sweep, so "
+                         "that the timed region stays near a minute)")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ndsi", choices=["ndsi", "reference"])
     ap.add_argument("--config", default="C5", choices=["C1", "C2", "C3", "C4", "C5"])
@@ -1091,6 +1093,8 @@ def main():
                     help="training systems: small varied lattices, or the 3D metallic recipe's "
                          "family (default: c5 for --config C5)")
     args = ap.parse_args()
+    if args.steps is None:
+        args.steps = 2 if args.config == "C5" and not (args.poles or args.lattice) else 10
     if args.impl == "reference":
         return run_reference(args)
     if args.mu_search:

@@ -233,6 +233,7 @@ int check_status(ndsi_plan* h, cudaStream_t st) {
     if (hs[0] != 0) {
         NDSI_CK(cudaMemsetAsync(h->T.status, 0, sizeof(int) * 4, st));
         NDSI_CK(cudaStreamSynchronize(st));
+        if (hs[0] & kStatusBadItem) return fail(NDSI_ERR_INVALID, "internal: a diagonal block wider than its kernel");
         if (hs[0] & kStatusSingular) return fail(NDSI_ERR_SINGULAR, "singular or non-finite pivot block");
         return fail(NDSI_ERR_TIMEOUT, "bounded device wait gave up");
     }

@@ -23,33 +23,45 @@ __device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_doub
 // ---------------------------------------------------------------------------------------------
 // Front assembly: F_J = sum over children c of U_c (extend-add through the inverse relative
 // index maps), written for the lower triangle of every front of a level.  Zero where no child
-// contributes; the original entries are added afterwards by k_scatter.
+// contributes; the original entries are added afterwards by k_scatter.  One CTA per 32 x 32 tile
+// (lanes = rows, 8 warps x 4 columns): the tile's column indices into each child are staged in
+// shared memory first, so a thread's four column loads are independent and in flight together.
 __global__ void __launch_bounds__(256) k_assemble(const NodeDev* __restrict__ nodes,
                                                   const NodeTile* __restrict__ tiles, int64_t first,
                                                   const int32_t* __restrict__ inv_map,
                                                   double2* __restrict__ F, int64_t stride) {
+    static_assert(kNodeTile == 32, "one lane per tile row, 8 warps x 4 columns");
+    constexpr int kCols = kNodeTile / 8;
     const NodeTile t = tiles[first + blockIdx.x];
     const NodeDev nd = nodes[t.node];
     double2* Fp = F + static_cast<int64_t>(blockIdx.y) * stride;
     __shared__ NodeDev ch[2];
-    if (threadIdx.x < nd.nchild && threadIdx.y == 0) ch[threadIdx.x] = nodes[nd.child[threadIdx.x]];
+    __shared__ int ibs[2][kNodeTile];
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    if (tx < nd.nchild && ty == 0) ch[tx] = nodes[nd.child[tx]];
+    if (ty < nd.nchild) ibs[ty][tx] = t.j0 + tx < nd.f ? inv_map[nd.inv_off[ty] + t.j0 + tx] : -1;
     __syncthreads();
-    const int a = t.i0 + threadIdx.x;
+    const int a = t.i0 + tx;
     if (a >= nd.f) return;
-    int ia[2];
-    for (int c = 0; c < nd.nchild; ++c) ia[c] = inv_map[nd.inv_off[c] + a];
-    for (int q = threadIdx.y; q < kNodeTile; q += blockDim.y) {
-        const int b = t.j0 + q;
-        if (b > a || b >= nd.f) continue;
-        double2 v = make_double2(0.0, 0.0);
-        for (int c = 0; c < nd.nchild; ++c) {
-            const int ib = inv_map[nd.inv_off[c] + b];
-            if (ia[c] >= 0 && ib >= 0) {
-                const NodeDev& cd = ch[c];
-                v = cadd(v, Fp[cd.front_off + (cd.s + ia[c]) + static_cast<int64_t>(cd.s + ib) * cd.f]);
-            }
+    double2 v[kCols];
+#pragma unroll
+    for (int u = 0; u < kCols; ++u) v[u] = make_double2(0.0, 0.0);
+    for (int c = 0; c < nd.nchild; ++c) {
+        const int ia = inv_map[nd.inv_off[c] + a];
+        if (ia < 0) continue;
+        const NodeDev& cd = ch[c];
+        const double2* U = Fp + cd.front_off + cd.s + ia + static_cast<int64_t>(cd.s) * cd.f;
+#pragma unroll
+        for (int u = 0; u < kCols; ++u) {
+            const int q = ty + 8 * u;
+            const int ib = ibs[c][q];
+            if (ib >= 0 && t.j0 + q <= a) v[u] = cadd(v[u], U[static_cast<int64_t>(ib) * cd.f]);
         }
-        Fp[nd.front_off + a + static_cast<int64_t>(b) * nd.f] = v;
+    }
+#pragma unroll
+    for (int u = 0; u < kCols; ++u) {
+        const int b = t.j0 + ty + 8 * u;
+        if (b <= a && b < nd.f) Fp[nd.front_off + a + static_cast<int64_t>(b) * nd.f] = v[u];
     }
 }
 
@@ -91,6 +103,10 @@ __global__ void __launch_bounds__(256) k_diaginv(const DiagItem* __restrict__ it
     double2* A = F + static_cast<int64_t>(blockIdx.y) * stride + d.off;
     const int nb = d.nb, ld = d.ld;
     const int tid = threadIdx.x;
+    if (nb > NB) {
+        if (tid == 0) atomicOr(status, kStatusBadItem);
+        return;
+    }
     for (int e = tid; e < nb * nb; e += blockDim.x) {
         const int i = e % nb, j = e / nb;
         a[i][j] = i >= j ? A[i + static_cast<int64_t>(j) * ld] : A[j + static_cast<int64_t>(i) * ld];
@@ -158,6 +174,10 @@ __global__ void __launch_bounds__(32) k_diaginv_sweep(const DiagItem* __restrict
     const DiagItem d = items[first + blockIdx.x];
     double2* A = F + static_cast<int64_t>(blockIdx.y) * stride + d.off;
     const int nb = d.nb, ld = d.ld;
+    if (nb > N) {
+        if (lane == 0) atomicOr(status, kStatusBadItem);
+        return;
+    }
     const int c = lane % VC, vbase = (lane / VC) * SLOTS;
     int rc[SLOTS];  // row | column << 8 of each slot (32 = unused slot)
     double2 a[SLOTS];
@@ -348,11 +368,17 @@ __global__ void __launch_bounds__(256) k_copy(const CopyItem* __restrict__ items
     const CopyItem c = items[first + blockIdx.x];
     const double2* S = src + static_cast<int64_t>(blockIdx.y) * s_src + c.src_off;
     double2* D = dst + static_cast<int64_t>(blockIdx.y) * s_dst + c.dst_off;
-    for (int j = blockIdx.z; j < c.cols; j += gridDim.z) {
-        for (int i = threadIdx.x; i < c.rows; i += blockDim.x) {
-            const double2 v = S[i + static_cast<int64_t>(j) * c.lds];
-            D[i + static_cast<int64_t>(j) * c.ldd] = make_double2(scale * v.x, scale * v.y);
-        }
+    // the block's rows x cols elements (column-major, < 2^31) in gridDim.z contiguous ranges, so
+    // that short columns still occupy every thread
+    const uint32_t rows = static_cast<uint32_t>(c.rows);
+    const uint32_t total = rows * static_cast<uint32_t>(c.cols);
+    const uint32_t per = (total + gridDim.z - 1) / gridDim.z;
+    const uint32_t e0 = blockIdx.z * per, e1 = min(total, e0 + per);
+#pragma unroll 4
+    for (uint32_t e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+        const uint32_t j = e / rows, i = e - j * rows;
+        const double2 v = S[i + static_cast<int64_t>(j) * c.lds];
+        D[i + static_cast<int64_t>(j) * c.ldd] = make_double2(scale * v.x, scale * v.y);
     }
 }
 

@@ -10,6 +10,7 @@ namespace ndsi {
 // Error bits latched in the device status word.
 constexpr int kStatusSingular = 1;
 constexpr int kStatusTimeout = 2;
+constexpr int kStatusBadItem = 4;  // a schedule item outside what its kernel handles (skipped)
 
 struct DevTables {
     NodeDev* nodes = nullptr;

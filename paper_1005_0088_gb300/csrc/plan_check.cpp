@@ -187,6 +187,8 @@ struct Checker {
             } else if (l.kind == L_COPY) {
                 for (int64_t i = l.first; i < l.first + l.count; ++i) {
                     const CopyItem& c = P.copy_items[i];
+                    if (static_cast<int64_t>(c.rows) * c.cols >= (int64_t{1} << 31))
+                        return fail("copy block of 2^31 or more elements (" + tag + ")");
                     Region S, D;
                     if (!region(BUF_SCR, c.src_off, c.lds, c.rows, c.cols, S, "copy source") ||
                         !region(BUF_FRONT, c.dst_off, c.ldd, c.rows, c.cols, D, "copy destination"))
@@ -196,10 +198,13 @@ struct Checker {
                 Writes W;
                 if (!build_writes(writes, W, tag)) return false;
             } else if (l.kind == L_DIAGINV) {
+                // widest block the launch's kernel inverts: warp sweeps of 16 or 32, else the
+                // shared-memory kernel of 64
+                const int32_t cap = P.block <= 32 ? (l.tile == 16 ? 16 : 32) : 64;
                 for (int64_t i = l.first; i < l.first + l.count; ++i) {
                     const DiagItem& d = P.diag_items[i];
                     Region D;
-                    if (d.nb <= 0 || d.nb > 64 || !region(BUF_FRONT, d.off, d.ld, d.nb, d.nb, D, "pivot block"))
+                    if (d.nb <= 0 || d.nb > cap || !region(BUF_FRONT, d.off, d.ld, d.nb, d.nb, D, "pivot block"))
                         return fail("pivot block out of range (" + tag + ")");
                     writes.push_back(D);
                 }

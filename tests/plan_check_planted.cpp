@@ -1,6 +1,7 @@
 // Planted mistakes for the schedule check: a plan built by the host analysis passes, and each
 // corruption below (an index out of its buffer, two items writing the same block, an index map
-// entry outside the parent front, a tile outside its item) is reported.  Prints one line per
+// entry outside the parent front, a tile outside its item, a diagonal block wider than its
+// kernel) is reported.  Prints one line per
 // case; exits non-zero if a corruption goes unnoticed or the clean plan fails.
 #include <algorithm>
 #include <cstdio>
@@ -101,6 +102,18 @@ int main() {
         expect("GEMM tile outside its item", false);
         P.gemm_tiles[0].m0 = keep;
     }
+    // 5. a diagonal block wider than the kernel its launch selects
+    planted = false;
+    for (const ndsi::Launch& l : P.launches) {
+        if (l.kind != ndsi::L_DIAGINV || planted) continue;
+        ndsi::DiagItem& d = P.diag_items[l.first];
+        const int32_t keep = d.nb;
+        d.nb = l.tile + 1;
+        expect("diagonal block wider than its kernel", false);
+        d.nb = keep;
+        planted = true;
+    }
+    if (!planted) ++bad;
     expect("clean plan at the end", true);
     return bad ? 1 : 0;
 }

@@ -20,7 +20,8 @@ def test_batched_plan_passes():
 
 
 @pytest.mark.parametrize("opts", [dict(block=32), dict(block=64, outer_block=256), dict(outer_block=64),
-                                  dict(leaf_atoms=3), dict(leaf_atoms=60, block=32, outer_block=96)])
+                                  dict(leaf_atoms=3), dict(leaf_atoms=60, block=32, outer_block=96),
+                                  dict(block=64, outer_block=128), dict(outer_block=32, leaf_atoms=40)])
 @pytest.mark.parametrize("shape,o,nb", [((9, 8, 1), 4, "2d"), ((5, 5, 5), 3, "3d"), ((120, 1, 1), 2, "1d")])
 def test_option_variants_pass(opts, shape, o, nb):
     nd = lib()

@@ -21,4 +21,4 @@ def test_planted_schedule_mistakes_are_reported(tmp_path):
     out = subprocess.run([exe], capture_output=True, text=True)
     print(out.stdout)
     assert out.returncode == 0, out.stdout
-    assert out.stdout.count("rejected") == 4
+    assert out.stdout.count("rejected") == 5
