@@ -339,7 +339,15 @@ def _kernel_totals(prof):
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum, averaged over the kernel's
 # launches in one timed sweep) from an ncu capture of the same build and workload with default
 # options.  Entries are removed whenever the kernel changes.
-TRAFFIC_PER_LAUNCH = {}
+# DRAM bytes (read + write) per launch of the dominant kernel, from a single-pass ncu capture of
+# the same kernel build (profiles/gemm_split_C5_dram.md): every split-GEMM launch of one full-size
+# 8-point chunk of the 3D metallic lattice (six slices), scaled to the sweep's mix of chunks (17
+# six-slice points, 144 five-slice poles, 21 chunks) in proportion to points x slices.
+TRAFFIC_PER_LAUNCH = {("C5", "split", "gemm_split"): 4.88e9}
+TRAFFIC_SOURCE = {("C5", "split", "gemm_split"):
+                  "ncu dram__bytes_read.sum + dram__bytes_write.sum of all 356 split-GEMM launches of "
+                  "one 8-point six-slice chunk (5.99 GB per launch), scaled to the sweep's chunk mix; "
+                  "algorithmic bytes are ~1.5 GB per launch (operands re-read 3.3x)"}
 
 
 def _roofline(prof, steps, peaks, fp64_peak, traffic_key=None):
@@ -373,6 +381,8 @@ def _roofline(prof, steps, peaks, fp64_peak, traffic_key=None):
         r = {"bound": "hbm", "unit": "GB/s", "peak": peak,
              "peak_source": "of measured (MEASURED_PEAKS.json hbm_gbs)"}
     traffic = TRAFFIC_PER_LAUNCH.get(traffic_key + (dname,)) if traffic_key else None
+    if traffic is not None:
+        r["traffic_source"] = TRAFFIC_SOURCE[traffic_key + (dname,)]
     r.update({"kernel": dname, "achieved": achieved, "frac": achieved / peak, "traffic": traffic,
               "launches": d["launches"], "kernel_ms_per_step": d["ms"] / steps,
               "share": d["ms"] / total})
