@@ -343,11 +343,11 @@ def _kernel_totals(prof):
 # the same kernel build (profiles/gemm_split_C5_dram.md): every split-GEMM launch of one full-size
 # 8-point chunk of the 3D metallic lattice (six slices), scaled to the sweep's mix of chunks (17
 # six-slice points, 144 five-slice poles, 21 chunks) in proportion to points x slices.
-TRAFFIC_PER_LAUNCH = {("C5", "split", "gemm_split"): 4.88e9}
+TRAFFIC_PER_LAUNCH = {("C5", "split", "gemm_split"): 3.52e9}
 TRAFFIC_SOURCE = {("C5", "split", "gemm_split"):
                   "ncu dram__bytes_read.sum + dram__bytes_write.sum of all 356 split-GEMM launches of "
-                  "one 8-point six-slice chunk (5.99 GB per launch), scaled to the sweep's chunk mix; "
-                  "algorithmic bytes are ~1.5 GB per launch (operands re-read 3.3x)"}
+                  "one 8-point six-slice chunk (4.31 GB per launch), scaled to the sweep's chunk mix; "
+                  "algorithmic bytes are ~1.5 GB per launch (operands re-read 2.4x)"}
 
 
 def _roofline(prof, steps, peaks, fp64_peak, traffic_key=None):

@@ -772,6 +772,19 @@ struct GemmArgs {
 constexpr int kTileBytes = kSplitBM * kRowBytes;  // 128 rows x kRowBytes
 constexpr int kThreads = 576;
 constexpr int kEpiWarps = 16;
+constexpr int kTileQueue = 4;  // tiles claimed ahead of the epilogue
+
+// OR of a predicate over the epilogue threads (named barrier 1), so that they all take the same
+// branch.
+__device__ __forceinline__ bool epi_any(bool v) {
+    uint32_t r;
+    asm volatile(
+        "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.or.pred q, 1, %2, p;\n selp.u32 %0, 1, 0, q;\n}"
+        : "=r"(r)
+        : "r"(static_cast<uint32_t>(v)), "n"(kEpiWarps * 32)
+        : "memory");
+    return r != 0;
+}
 // Epilogue TMEM read-out with two band buffers (register budget: 2 x 2CW values beside the 4CW
 // float-float sums)
 template <int CW>
@@ -849,14 +862,24 @@ __global__ void __launch_bounds__(kThreads, 1)
     uint64_t* mma_done = chunk_full + 2;
     uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(chunk_full + 3);
     volatile int* abort = reinterpret_cast<volatile int*>(chunk_full + 4);
-    static_assert(2 * kSplitMaxStages + 5 <= 32, "barriers overflow their 256 bytes");
+    // tile queue: the producer claims tiles and hands them to the MMA thread and the epilogue
+    uint64_t* tq_full = chunk_full + 5;    // [kTileQueue] tile written (producer arrives)
+    uint64_t* tq_empty = tq_full + kTileQueue;  // [kTileQueue] read by the MMA thread and the epilogue
+    volatile int64_t* tq = reinterpret_cast<volatile int64_t*>(tq_empty + kTileQueue);  // [kTileQueue]
+    volatile int64_t* epi_w = tq + kTileQueue;  // the epilogue's current tile, broadcast
+    static_assert(2 * kSplitMaxStages + 5 + 3 * kTileQueue + 1 <= 32, "barriers overflow their 256 bytes");
     int* sm_ea = reinterpret_cast<int*>(bars + 32);  // [128] exponents of the current tile's rows
     int* sm_eb = sm_ea + 128;                         // [64] exponents of its complex columns
 
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-    // Persistent: CTA b takes work items b, b + gridDim.x, ... (work = pole * tcount + tile), so
-    // the CTAs running at the same time share the A and B slices of one pole in L2.
+    // Persistent with dynamic tiles: CTA b starts with work item b and then claims the next
+    // unstarted item from a counter (work = pole * tcount + tile), so tiles start in list order
+    // whatever the durations of the tiles before them.  The tiles that share an operand tile are
+    // adjacent in the list, hence start together and read each K-block of it from L2 within a
+    // short window; a fixed round-robin assignment drifted apart on launches whose items have
+    // different K and re-read shared operand tiles from DRAM.
     const int64_t n_work = p.tcount * p.np;
+    int* claim = p.status + 2;  // [0] items claimed beyond the first wave, [1] CTAs finished
     auto tile_of = [&](int64_t w) { return p.tiles[p.tfirst + w % p.tcount]; };
     auto nkb_of = [&](const GemmTile& t) { return 2 * p.sitems[p.ifirst + t.item].Kpad / kSplitKB; };
 
@@ -869,6 +892,11 @@ __global__ void __launch_bounds__(kThreads, 1)
         mbar_init(chunk_full, 1);
         mbar_init(tmem_free, kEpiWarps);
         mbar_init(mma_done, 1);
+#pragma unroll
+        for (int i = 0; i < kTileQueue; ++i) {
+            mbar_init(&tq_full[i], 1);
+            mbar_init(&tq_empty[i], 2);
+        }
         *abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -884,7 +912,16 @@ __global__ void __launch_bounds__(kThreads, 1)
             // producer: one ring of STAGES stages across all of this CTA's tiles
             int64_t g = 0;      // K-blocks issued so far (all tiles)
             int64_t armed = 0;
-            for (int64_t w = blockIdx.x; w < n_work && !*abort; w += gridDim.x) {
+            for (int64_t jt = 0;; ++jt) {
+                const int slot = static_cast<int>(jt % kTileQueue);
+                if (jt >= kTileQueue &&
+                    !mbar_wait(&tq_empty[slot], static_cast<uint32_t>(((jt / kTileQueue) - 1) & 1), abort))
+                    break;
+                int64_t w = jt == 0 ? static_cast<int64_t>(blockIdx.x) : gridDim.x + static_cast<int64_t>(atomicAdd(claim, 1));
+                if (w >= n_work || *abort) w = -1;
+                tq[slot] = w;
+                mbar_arrive(&tq_full[slot]);
+                if (w < 0) break;
                 const GemmTile tile = tile_of(w);
                 const int64_t pole = w / p.tcount;
                 const SplitItem si = p.sitems[p.ifirst + tile.item];
@@ -922,7 +959,12 @@ __global__ void __launch_bounds__(kThreads, 1)
             // has read chunk c - 1 out of TMEM (which may belong to the previous tile)
             int64_t g = 0, c = 0;
             bool ok = true;
-            for (int64_t w = blockIdx.x; w < n_work && ok; w += gridDim.x) {
+            for (int64_t jt = 0; ok; ++jt) {
+                const int slot = static_cast<int>(jt % kTileQueue);
+                if (!mbar_wait(&tq_full[slot], static_cast<uint32_t>((jt / kTileQueue) & 1), abort)) break;
+                const int64_t w = tq[slot];
+                mbar_arrive(&tq_empty[slot]);
+                if (w < 0) break;
                 const int nkb = nkb_of(tile_of(w));
                 for (int kb = 0; kb < nkb; ++kb, ++g) {
                     const int stage = static_cast<int>(g % STAGES);
@@ -1001,16 +1043,29 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int et = threadIdx.x - 64;
         const bool neg_alpha = p.neg_alpha != 0, add_c = p.add_c != 0;
         int64_t c = 0;  // chunks consumed (all tiles)
-        bool ok = true;
-        for (int64_t w = blockIdx.x; w < n_work && ok; w += gridDim.x) {
+        for (int64_t jt = 0;; ++jt) {
+            // one thread takes the next tile from the queue and broadcasts it, so every epilogue
+            // thread leaves the loop at the same tile (no thread waits at a barrier alone)
+            if (et == 0) {
+                const int slot = static_cast<int>(jt % kTileQueue);
+                int64_t wv = -1;
+                if (mbar_wait(&tq_full[slot], static_cast<uint32_t>((jt / kTileQueue) & 1), abort)) {
+                    wv = tq[slot];
+                    mbar_arrive(&tq_empty[slot]);
+                }
+                *epi_w = wv;
+            }
+            // also: this tile's scale exponents may now be written (the previous tile's are no
+            // longer read)
+            asm volatile("bar.sync 1, %0;" ::"n"(kEpiWarps * 32) : "memory");
+            const int64_t w = *epi_w;
+            if (w < 0) break;
             const GemmTile tile = tile_of(w);
             const int64_t pole = w / p.tcount;
             const GemmItem it = p.items[p.ifirst + tile.item];
             const SplitItem si = p.sitems[p.ifirst + tile.item];
             const int nchunks = (nkb_of(tile) + kSplitChunkKB - 1) / kSplitChunkKB;
             double2* Cp = p.C + pole * p.sC + it.c_off;
-            // this tile's scale exponents (the previous tile's are no longer read)
-            asm volatile("bar.sync 1, %0;" ::"n"(kEpiWarps * 32) : "memory");
             if (et < 128) {
                 const int m = tile.m0 + et;
                 sm_ea[et] = m < it.M ? p.expA[pole * p.erowsA + si.erowA + m] : 0;
@@ -1030,6 +1085,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 }
             }
             asm volatile("bar.sync 1, %0;" ::"n"(kEpiWarps * 32) : "memory");
+            bool ok = true;
             float hi[2 * CW], lo[2 * CW];  // [0, CW): Re, [CW, 2CW): Im of this warp's columns
 #pragma unroll
             for (int j = 0; j < 2 * CW; ++j) {
@@ -1093,7 +1149,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                         }
                 }
             }
-            if (!ok || *abort) break;
+            if (epi_any(!ok || *abort)) break;  // the same decision in every epilogue thread
             // C = alpha * 2^e (hi + lo) + beta * C for this thread's row and CW complex columns:
             // alpha is +-1 and beta 0 or 1 (checked at launch), the sign goes onto the integer
             // result and beta = 1 costs the only FP64 instructions.  A warp stores one column's
@@ -1130,7 +1186,16 @@ __global__ void __launch_bounds__(kThreads, 1)
         tc_fence_after();
         tmem_dealloc(tmem, 512);
     }
-    if (threadIdx.x == 0 && *abort) atomicOr(p.status, kStatusTimeout);
+    if (threadIdx.x == 0) {
+        if (*abort) atomicOr(p.status, kStatusTimeout);
+        // the last CTA to finish resets the claim counters for the next launch (every CTA has
+        // claimed its last item before it gets here)
+        __threadfence();
+        if (atomicAdd(claim + 1, 1) == static_cast<int>(gridDim.x) - 1) {
+            atomicExch(claim, 0);
+            atomicExch(claim + 1, 0);
+        }
+    }
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
