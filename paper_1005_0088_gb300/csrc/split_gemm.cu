@@ -24,11 +24,12 @@
 //    drops the low bits of the smaller products: BANDS = 5 (NC = 48) gives a floor near 2^-43 of
 //    the result, BANDS = 4 (NC = 64) near 2^-38;
 //  * the epilogue scales by 2^(E_m + F_n - 14) and forms C = alpha*(hi+lo)*scale + beta*C.
-// Pipeline (persistent, one CTA per SM): warp 0 issues TMA loads (2 to 4 stages, as many as fit
-// shared memory, of S A tiles 128x32 and S B tiles 2NCx32, BF16, 64-byte swizzle), one thread of
-// warp 1 issues the MMAs (M=128, K=16), warps 2-17 read TMEM and convert and store finished tiles
-// while the next tile's MMAs run.  Every mbarrier wait is bounded: on time-out the kernel flags NDSI timeout status, drains
-// what it issued and frees its TMEM.
+// Pipeline (persistent, one CTA per SM, tiles claimed from a counter in list order and handed on
+// through a small shared-memory queue): warp 0 claims tiles and issues TMA loads (2 to 6 stages,
+// as many as fit shared memory, of S A tiles 128x32 and S B tiles 2NCx32, BF16, 64-byte
+// swizzle), one thread of warp 1 issues the MMAs (M=128, K=16), warps 2-17 read TMEM and convert
+// and store finished tiles while the next tile's MMAs run.  Every mbarrier wait is bounded: on
+// time-out the kernel flags NDSI timeout status, drains what it issued and frees its TMEM.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_runtime.h>
@@ -798,7 +799,7 @@ __host__ __device__ constexpr int stage_bytes() { return S * (kTileBytes + tile_
 // tiles to 1024 bytes
 constexpr int kSplitSmemExtra = 256 + 768 + 1024;
 constexpr int kSplitMaxStages = 6;
-// Pipeline depth: as many stages (2..4) as fit the 227 KB of shared memory a CTA may use.
+// Pipeline depth: as many stages (2..6) as fit the 227 KB of shared memory a CTA may use.
 template <int S, int NC>
 __host__ __device__ constexpr int split_stages() {
     return (227 * 1024 - kSplitSmemExtra) / stage_bytes<S, NC>() >= kSplitMaxStages
