@@ -263,13 +263,16 @@ def run_reference(args):
     from synth import config_system, batched_systems
     if args.config == "C4":
         systems = [s for s in batched_systems() if s.n <= DENSE_ORACLE_MAX_N]
-        M, kT, label = args.poles or 120, 0.01, "batched: 120 poles x 12 uneven systems (N 2048..32768)"
-        n_total = sum(s.n for s in batched_systems())
+        allsys = batched_systems()
+        M, kT = args.poles or 120, 0.01
+        label = (f"batched: {M} poles x {len(allsys)} uneven systems "
+                 f"(N {min(s.n for s in allsys)}..{max(s.n for s in allsys)})")
+        n_total = sum(s.n for s in allsys)
     else:
         system = config_system(args.config)
         systems = [system]
         kT, M = system.meta["kT"], args.poles or system.meta["poles"]
-        label, n_total = system.meta["label"], system.n
+        label, n_total = system.meta["label"] + f", {M} poles", system.n
     cores = os.cpu_count()
     if all(s.n <= DENSE_ORACLE_MAX_N for s in systems):
         from oracle.dense import generalized_eig, density_eig, on_pattern
@@ -703,7 +706,7 @@ def run_ndsi(args):
             "split_speedup_vs_fp64": speedup,
             "fp64_ms_per_step": (ms_step if args.precision == "fp64" else fp64_ms_full),
             "max_abs_err_rho_vs_oracle": parity.get("max_abs_err_rho") if parity else None,
-            "config": {"workload": system.meta["label"] + f", {M} poles, {args.precision} path"
+            "config": {"workload": system.meta["label"] + f", {M} poles"
                                    + (", rho and energy density matrix" if args.energy else ""),
                        "n": system.n, "poles": M, "kT": kT, "mu": MU, "nnz": nnz,
                        "precision": args.precision, "split_slices": info["split_slices"],
@@ -856,8 +859,8 @@ def run_batched(args, nd, torch, dist, rank, world, local, prec_code):
             "higher_is_better": True, "scaling": "strong", "vs_baseline": None,
             "dtype": "f64" if args.precision == "fp64" else f"bf16x{info['split_slices']}->f64", "data": "synthetic",
             "config": {"workload": f"batched: {M} poles x {len(systems)} uneven systems "
-                                   f"(N {min(s.n for s in systems)}..{max(s.n for s in systems)}), "
-                                   f"{args.precision} path, one launch per tree level",
+                                   f"(N {min(s.n for s in systems)}..{max(s.n for s in systems)})",
+                       "schedule": "one plan, one launch per tree level and step",
                        "n_total": ntot, "poles": M, "kT": kT, "nnz": nnz, "precision": args.precision,
                        "flops_per_pole": info["flops_per_pole"], "n_levels": info["n_levels"],
                        "l2": "flushed (256 MB write) before every timed step"},
