@@ -339,13 +339,12 @@ def _kernel_totals(prof):
     return out
 
 
-# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum, averaged over the kernel's
-# launches in one timed sweep) from an ncu capture of the same build and workload with default
-# options.  Entries are removed whenever the kernel changes.
-# DRAM bytes (read + write) per launch of the dominant kernel, from a single-pass ncu capture of
-# the same kernel build (profiles/gemm_split_C5_dram.md): every split-GEMM launch of one full-size
-# 8-point chunk of the 3D metallic lattice (six slices), scaled to the sweep's mix of chunks (17
-# six-slice points, 144 five-slice poles, 21 chunks) in proportion to points x slices.
+# DRAM bytes per launch of the dominant kernel (dram__bytes_read.sum + dram__bytes_write.sum,
+# averaged over its launches in one sweep) for a workload with default options, from a single-pass
+# ncu capture of the same kernel build; an entry is removed whenever the kernel changes.  The 3D
+# metallic lattice's entry: every split-GEMM launch of one full-size 8-point chunk (six slices),
+# scaled to the sweep's mix of chunks (17 six-slice points, 144 five-slice poles, 21 chunks) in
+# proportion to points x slices.
 TRAFFIC_PER_LAUNCH = {("C5", "split", "gemm_split"): 3.52e9}
 TRAFFIC_SOURCE = {("C5", "split", "gemm_split"):
                   "ncu dram__bytes_read.sum + dram__bytes_write.sum of all 356 split-GEMM launches of "

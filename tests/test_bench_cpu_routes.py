@@ -54,3 +54,42 @@ def test_bench_modes_parse():
     for flag in ("--impl", "--config", "--precision", "--energy", "--mu-search", "--eigen", "--no-graph",
                  "--fp64-poles", "--far-ratio", "--leaf"):
         assert flag in out.stdout
+
+
+def _fake_profile():
+    # two schedule steps of the split GEMM and one slicing step, one sweep
+    return {"gemm_split:schur": dict(launches=3, ms=30.0, flops=6e12, bytes=3e9, tensor_flops=4e13),
+            "gemm_split:sel_t": dict(launches=2, ms=20.0, flops=4e12, bytes=2e9, tensor_flops=2e13),
+            "slice:sel_t": dict(launches=2, ms=5.0, flops=0.0, bytes=2e10, tensor_flops=0.0)}
+
+
+def test_roofline_of_the_dominant_kernel():
+    peaks = {"bf16_tflops_sustained": 1700.0, "hbm_gbs": 6800.0}
+    r, kern = bench._roofline(_fake_profile(), 1, peaks, 1.25)
+    assert r["kernel"] == "gemm_split" and r["bound"] == "tensor" and r["launches"] == 5
+    assert math.isclose(r["achieved"], 6e13 / 0.05 / 1e12) and math.isclose(r["frac"], r["achieved"] / 1700.0)
+    assert math.isclose(r["share"], 50.0 / 55.0)
+    assert kern["slice"]["launches"] == 2
+    # no DRAM figure without a capture of that workload and kernel; the 3D metallic default has one
+    assert r["traffic"] is None and "traffic_source" not in r
+    r5, _ = bench._roofline(_fake_profile(), 1, peaks, 1.25, ("C5", "split"))
+    assert r5["traffic"] == bench.TRAFFIC_PER_LAUNCH[("C5", "split", "gemm_split")]
+    assert "ncu" in r5["traffic_source"]
+    r2, _ = bench._roofline(_fake_profile(), 1, peaks, 1.25, ("C2", "split"))
+    assert r2["traffic"] is None
+
+
+def test_reference_arm_names_the_workload_like_the_gpu_arm():
+    # the driver pairs the two arms by config.workload: both name the lattice and the pole count
+    import subprocess
+    import sys
+    import json
+    out = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--config", "C1", "--steps", "1",
+                          "--warmup", "0"], cwd=bench.ROOT, capture_output=True, text=True, timeout=600)
+    assert out.returncode == 0, out.stderr[-2000:]
+    line = json.loads(out.stdout.strip().splitlines()[-1])
+    from synth import config_system
+    s = config_system("C1")
+    assert line["impl"] == "reference"
+    assert line["config"]["workload"] == s.meta["label"] + f", {s.meta['poles']} poles"
+    assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["cpu_baseline"]["value"] == line["value"]
