@@ -105,3 +105,39 @@ def test_sampled_columns_match_dense():
     Z = 0.3 + 0.2j
     g = green_columns(sysm, Z, cols)
     assert np.max(np.abs(g - green_dense(Hd, Sd, Z)[:, cols])) < 1e-12
+
+
+@pytest.mark.parametrize("M", [8, 40, 160])
+def test_particle_hole_symmetry_at_half_filling(M):
+    # A bipartite lattice (nearest-neighbour square lattice, zero on-site energy, S = I) has a
+    # spectrum symmetric about 0, and the pole-truncated Fermi function of Eq. 7 keeps
+    # f_M(x) + f_M(-x) = 1 (the continued fraction of tanh is odd).  So at mu = 0 and any M:
+    # rho = I - tanh_M(H / 2kT) with tanh_M odd in H, i.e. every diagonal element is exactly 1
+    # (spin factor 2 x 1/2) and rho vanishes between distinct sites of the same sublattice (odd
+    # powers of H connect opposite sublattices only).  Both routes: eigendecomposition (Eq. 5)
+    # and the contour sum of dense inverses with the M0 term (Eq. 8).
+    nx, ny = 6, 5
+    n = nx * ny
+    H = np.zeros((n, n))
+    for y in range(ny):
+        for x in range(nx):
+            i = x + nx * y
+            if x + 1 < nx:
+                H[i, i + 1] = H[i + 1, i] = -1.0
+            if y + 1 < ny:
+                H[i, i + nx] = H[i + nx, i] = -0.7
+    S = np.eye(n)
+    kT = 0.05
+    eps, C = generalized_eig(H, S)
+    parity = np.array([(i % nx + i // nx) % 2 for i in range(n)])
+    same = (parity[:, None] == parity[None, :]) & ~np.eye(n, dtype=bool)
+    for rho in (density_eig(eps, C, 0.0, kT, M), density_inv(H, S, 0.0, kT, M)):
+        assert np.max(np.abs(np.diag(rho) - 1.0)) < 1e-12
+        assert np.max(np.abs(rho[same])) < 1e-12
+        assert abs(np.trace(rho @ S) - n) < 1e-10                 # half filling: N_e = N
+    # away from mu = 0 the symmetry maps mu -> -mu: rho(mu) + P rho(-mu) P = 2 I with
+    # P = diag(+-1) on the sublattices (P H P = -H)
+    P = np.diag(np.where(parity == 0, 1.0, -1.0))
+    r1 = density_inv(H, S, 0.13, kT, M)
+    r2 = density_inv(H, S, -0.13, kT, M)
+    assert np.max(np.abs(r1 + P @ r2 @ P - 2.0 * np.eye(n))) < 1e-11
