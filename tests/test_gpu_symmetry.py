@@ -1,4 +1,4 @@
-"""GPU density against an exact symmetry, no oracle involved.
+"""GPU density and selected inverse against exact symmetries, no oracle involved.
 
 A bipartite system (S = I, hopping only between neighbouring sites of opposite sublattices, no
 on-site terms) has P H P = -H with P = +-1 on the two sublattices, and the pole-truncated Fermi
@@ -56,3 +56,36 @@ def test_density_particle_hole_symmetry(precision, tol):
     assert np.max(np.abs(rp[diag] + rm[diag] - 2.0)) < tol
     assert np.max(np.abs(rp[~diag] - rm[~diag])) < tol
     assert np.max(np.abs(rp[~diag])) > 1e-3                 # the off-diagonal entries are not trivially zero
+
+
+@pytest.mark.parametrize("precision,tol", [(0, 1e-11), (1, 1e-9)])
+def test_green_at_conjugate_points_is_conjugate(precision, tol):
+    # real H and S: (z* S - H)^{-1} = conj((z S - H)^{-1}) on every selected element
+    from synth import lattice_system
+    from tests.test_gpu_parity import _selinv
+    s = lattice_system((7, 6, 5), 2, "3d", 43)
+    Z = np.array([-0.3 + 0.04j, 0.8 + 1.7j])
+    g = _selinv(s, np.concatenate([Z, np.conj(Z)]), precision=precision, leaf_atoms=12)
+    for q in range(len(Z)):
+        scale = np.max(np.abs(g[q]))
+        assert np.max(np.abs(g[len(Z) + q] - np.conj(g[q]))) < tol * scale
+
+
+@pytest.mark.parametrize("precision,tol", [(0, 1e-10), (1, 1e-9)])
+def test_density_is_invariant_under_affine_energy_change(precision, tol):
+    # rho depends on the pencil only through (eps - mu) / kT: H -> a H + b S, mu -> a mu + b,
+    # kT -> a kT leaves every element of rho unchanged (the points alpha_p = mu + i z_p kT, the
+    # weights -4 R_p kT and M0 all follow)
+    from synth import lattice_system
+    s = lattice_system((7, 6, 5), 2, "3d", 44)
+    a, b = 2.5, 0.3
+    mu, kT, M = -0.12, 0.01, 80
+    r1, n1 = _density(s, mu, kT, M, precision=precision, leaf_atoms=12)
+    H0 = s.H.copy()
+    s.H = a * H0 + b * s.S
+    try:
+        r2, n2 = _density(s, a * mu + b, a * kT, M, precision=precision, leaf_atoms=12)
+    finally:
+        s.H = H0
+    assert np.max(np.abs(r2 - r1)) < tol
+    assert abs(n2 - n1) < tol * s.n
