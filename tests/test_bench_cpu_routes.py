@@ -93,3 +93,19 @@ def test_reference_arm_names_the_workload_like_the_gpu_arm():
     assert line["impl"] == "reference"
     assert line["config"]["workload"] == s.meta["label"] + f", {s.meta['poles']} poles"
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["cpu_baseline"]["value"] == line["value"]
+
+
+def test_roofline_of_fp64_and_memory_bound_sweeps():
+    peaks = {"bf16_tflops_sustained": 1700.0, "hbm_gbs": 6800.0}
+    # FP64 path: the GEMM counts 8 flops per complex multiply-add, executes 6 (three-multiplication
+    # product); achieved is the executed rate against the measured DFMA peak
+    prof = {"gemm_f64:schur": dict(launches=4, ms=40.0, flops=4e10, bytes=1e9, tensor_flops=0.0),
+            "assemble": dict(launches=1, ms=2.0, flops=0.0, bytes=5e9, tensor_flops=0.0)}
+    r, _ = bench._roofline(prof, 1, peaks, 1.25)
+    assert r["bound"] == "alu" and r["kernel"] == "gemm_f64" and r["peak"] == 1.25
+    assert math.isclose(r["achieved_8flop_count"], 1.0) and math.isclose(r["achieved"], 0.75)
+    assert math.isclose(r["frac"], 0.6)
+    # an element-wise kernel on top: bytes over time against the measured copy bandwidth
+    prof = {"assemble": dict(launches=2, ms=10.0, flops=0.0, bytes=5e10, tensor_flops=0.0)}
+    r, _ = bench._roofline(prof, 1, peaks, 1.25)
+    assert r["bound"] == "hbm" and math.isclose(r["achieved"], 5000.0) and math.isclose(r["frac"], 5000.0 / 6800.0)
